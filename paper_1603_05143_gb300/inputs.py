@@ -1,0 +1,391 @@
+"""Seeded synthetic frames shaped like the PTM paper's workloads.
+
+This module only builds inputs (positions, periodic cells, species).  It holds
+none of the structure-identification arithmetic, so both the CUDA path and the
+CPU oracle may be fed from it.
+
+Every generator draws from ``numpy.random.Generator(PCG64(seed))``.  The lattices
+are the five structures of Table 1 (sc, fcc, hcp, bcc, plus icosahedral clusters)
+and the ordered alloys of Sec. 6 (L1_0, L1_2, B2).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+A_FCC_CU = 3.615      # Angstrom
+A_BCC_FE = 2.8665
+A_L12 = 3.75
+A_SC = 2.5
+A_HCP = 2.556         # nearest-neighbour distance, ideal c/a
+
+
+@dataclasses.dataclass
+class Frame:
+    """One periodic frame: positions (n x 3), cell rows = cell vectors."""
+    positions: np.ndarray
+    cell: np.ndarray                 # (3, 3) float64, rows are the cell vectors
+    pbc: tuple = (True, True, True)
+    species: np.ndarray | None = None   # int8 per atom, or None
+    name: str = ""
+    meta: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.positions.shape[0])
+
+
+def rng_for(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def random_rotation(rng: np.random.Generator) -> np.ndarray:
+    """Uniform random rotation (Shoemake's subgroup algorithm, unit quaternion)."""
+    u1, u2, u3 = rng.random(3)
+    q = np.array([math.sqrt(1 - u1) * math.sin(2 * math.pi * u2),
+                  math.sqrt(1 - u1) * math.cos(2 * math.pi * u2),
+                  math.sqrt(u1) * math.sin(2 * math.pi * u3),
+                  math.sqrt(u1) * math.cos(2 * math.pi * u3)])
+    w, x, y, z = q[3], q[0], q[1], q[2]
+    return np.array([
+        [1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+        [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+        [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+# ---------------------------------------------------------------- unit cells
+def unit_cell(kind: str, a: float):
+    """(cell rows, fractional basis, species per basis site) of a conventional cell."""
+    if kind == "sc":
+        return np.eye(3) * a, np.zeros((1, 3)), np.zeros(1, np.int8)
+    if kind in ("fcc", "l12", "l10"):
+        basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+        if kind == "l12":      # Cu3Au: Au (1) at the corner, Cu (0) on the faces
+            sp = np.array([1, 0, 0, 0], np.int8)
+        elif kind == "l10":    # CuAu: alternate (001) layers
+            sp = np.array([0, 0, 1, 1], np.int8)
+        else:
+            sp = np.zeros(4, np.int8)
+        return np.eye(3) * a, basis, sp
+    if kind in ("bcc", "b2"):
+        basis = np.array([[0, 0, 0], [0.5, 0.5, 0.5]])
+        sp = np.array([0, 1], np.int8) if kind == "b2" else np.zeros(2, np.int8)
+        return np.eye(3) * a, basis, sp
+    if kind == "hcp":          # orthohexagonal cell, 4 atoms, ideal c/a
+        c = a * math.sqrt(8.0 / 3.0)
+        cell = np.diag([a, a * math.sqrt(3.0), c])
+        basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 1.0 / 6.0, 0.5], [0, 2.0 / 3.0, 0.5]])
+        return cell, basis, np.zeros(4, np.int8)
+    raise ValueError(kind)
+
+
+def crystal(kind: str, a: float, reps, *, sigma: float = 0.0, seed: int = 0,
+            rotation: np.ndarray | None = None, deform: np.ndarray | None = None,
+            dtype=np.float64, wrap: bool = True, name: str = "") -> Frame:
+    """Periodic supercell of ``reps`` conventional cells.
+
+    ``rotation`` and ``deform`` (3x3) act on both positions and cell vectors, so
+    the crystal stays periodic (the cell becomes triclinic).  Gaussian noise of
+    standard deviation ``sigma`` is added per component.
+    """
+    rng = rng_for(seed)
+    cell0, basis, sp0 = unit_cell(kind, a)
+    reps = np.broadcast_to(np.asarray(reps, int), (3,))
+    grid = np.stack(np.meshgrid(*[np.arange(r) for r in reps], indexing="ij"), -1).reshape(-1, 3)
+    frac = (grid[:, None, :] + basis[None, :, :]).reshape(-1, 3)
+    pos = frac @ cell0
+    species = np.tile(sp0, len(grid))
+    cell = cell0 * reps[:, None]
+    lin = np.eye(3)
+    if rotation is not None:
+        lin = rotation @ lin
+    if deform is not None:
+        lin = deform @ lin
+    pos = pos @ lin.T
+    cell = cell @ lin.T
+    if sigma > 0:
+        pos = pos + rng.normal(0.0, sigma, pos.shape)
+    if wrap:
+        pos = wrap_positions(pos, cell)
+    return Frame(pos.astype(dtype), cell.astype(np.float64), (True, True, True), species,
+                 name or kind, {"kind": kind, "a": a, "reps": reps.tolist(), "sigma": sigma})
+
+
+def wrap_positions(pos: np.ndarray, cell: np.ndarray) -> np.ndarray:
+    """Map positions into the parallelepiped spanned by the cell rows."""
+    f = pos @ np.linalg.inv(cell)
+    f = f - np.floor(f)
+    f[f >= 1.0] = 0.0
+    return f @ cell
+
+
+def ico_cluster(r: float = 2.556, *, rotation=None, sigma=0.0, seed=0) -> np.ndarray:
+    """Centre plus the 12 vertices of a regular icosahedron at distance r."""
+    phi = (1 + math.sqrt(5)) / 2
+    v = []
+    for s1 in (1, -1):
+        for s2 in (1, -1):
+            v += [(0, s1, s2 * phi), (s1, s2 * phi, 0), (s2 * phi, 0, s1)]
+    v = np.array(v, float)
+    v *= r / np.linalg.norm(v[0])
+    pts = np.vstack([np.zeros(3), v])
+    if rotation is not None:
+        pts = pts @ rotation.T
+    if sigma > 0:
+        pts = pts + rng_for(seed).normal(0, sigma, pts.shape)
+    return pts
+
+
+def isolated_clusters(clusters, spacing: float = 30.0, dtype=np.float64) -> Frame:
+    """Place point clusters on a coarse grid inside one large periodic box."""
+    m = len(clusters)
+    side = int(math.ceil(m ** (1 / 3)))
+    pos = []
+    for i, c in enumerate(clusters):
+        g = np.array([i % side, (i // side) % side, i // (side * side)], float)
+        pos.append(c + (g + 0.5) * spacing)
+    cell = np.eye(3) * spacing * side
+    return Frame(np.vstack(pos).astype(dtype), cell, (True, True, True), None, "clusters")
+
+
+# ------------------------------------------------------------ workload configs
+def config_fcc_small(seed: int = 1603) -> Frame:
+    """4000-atom fcc Cu, 10^3 cells, sigma 0.10 A, float64 positions."""
+    f = crystal("fcc", A_FCC_CU, 10, sigma=0.10, seed=seed, dtype=np.float64, name="fcc4000")
+    return f
+
+
+def config_polycrystal(seed: int = 5143, n_target: int = 1 << 20, n_grains: int = 16,
+                       n_faults: int = 4, sigma: float = 0.15) -> Frame:
+    """Periodic Voronoi polycrystal of fcc Cu with stacking-fault slabs.
+
+    The box is the fcc-density cube for ``n_target`` atoms (L = 231.36 A for 2^20).
+    Each grain is filled with its own randomly rotated lattice; atoms closer than
+    1.5 A across grain boundaries are thinned; the count is trimmed or padded to
+    exactly ``n_target``.  In ``n_faults`` grains all atoms above a {111} plane
+    through the grain centre are shifted by a/6<112>, which leaves two hcp planes.
+    """
+    rng = rng_for(seed)
+    a = A_FCC_CU
+    L = (n_target / 4.0) ** (1.0 / 3.0) * a
+    cell = np.eye(3) * L
+    centres = rng.random((n_grains, 3)) * L
+    rots = [random_rotation(rng) for _ in range(n_grains)]
+    cell0, basis, _ = unit_cell("fcc", a)
+    # lattice sites within a cube of half-width r_cover around each grain centre
+    r_cover = L * 0.75
+    m = int(math.ceil(r_cover / a)) + 1
+    g = np.stack(np.meshgrid(*[np.arange(-m, m)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    local = ((g[:, None, :] + basis[None]) .reshape(-1, 3)) @ cell0
+    pieces = []
+    fault_grains = set(rng.choice(n_grains, size=min(n_faults, n_grains), replace=False).tolist())
+    for gi in range(n_grains):
+        R = rots[gi]
+        p = local.copy()
+        if gi in fault_grains:
+            nrm = np.array([1.0, 1.0, 1.0]) / math.sqrt(3)
+            shift = a / 6.0 * np.array([1.0, 1.0, -2.0])
+            h = p @ nrm
+            p[h > 0.5 * a / math.sqrt(3) * 0.5] += shift
+        p = p @ R.T + centres[gi]
+        # periodic Voronoi ownership: keep sites closest (minimum image) to this centre
+        d_own = _min_image_dist2(p, centres[gi], L)
+        keep = np.ones(len(p), bool)
+        for gj in range(n_grains):
+            if gj == gi:
+                continue
+            keep &= d_own < _min_image_dist2(p, centres[gj], L)
+        p = p[keep & (d_own < (L * 0.87) ** 2)]
+        pieces.append(np.mod(p, L))
+    pos = np.vstack(pieces)
+    pos = _thin_close_pairs(pos, L, 1.5, rng)
+    n = len(pos)
+    if n > n_target:
+        pos = pos[np.sort(rng.choice(n, n_target, replace=False))]
+    elif n < n_target:
+        extra = rng.random((n_target - n, 3)) * L
+        pos = np.vstack([pos, extra])
+    pos = pos + rng.normal(0.0, sigma, pos.shape)
+    pos = np.mod(pos, L)
+    pos[pos >= L] = 0.0
+    return Frame(pos.astype(np.float32), cell, (True, True, True), None, "polycrystal",
+                 {"L": L, "grains": n_grains, "faults": sorted(fault_grains), "raw_count": n})
+
+
+def _min_image_dist2(p, c, L):
+    d = p - c
+    d -= L * np.round(d / L)
+    return np.einsum("ij,ij->i", d, d)
+
+
+def _thin_close_pairs(pos, L, dmin, rng):
+    """Drop one atom of every pair closer than dmin (periodic cube), grid accelerated."""
+    n = len(pos)
+    nb = max(1, int(L // dmin))
+    w = L / nb
+    cidx = np.minimum((pos // w).astype(np.int64), nb - 1)
+    key = (cidx[:, 0] * nb + cidx[:, 1]) * nb + cidx[:, 2]
+    order = np.argsort(key, kind="stable")
+    skey = key[order]
+    starts = np.searchsorted(skey, np.arange(nb ** 3))
+    ends = np.searchsorted(skey, np.arange(nb ** 3), side="right")
+    removed = np.zeros(n, bool)
+    prio = rng.permutation(n)
+    for dx in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dz in (-1, 0, 1):
+                nc = (cidx + [dx, dy, dz]) % nb
+                nkey = (nc[:, 0] * nb + nc[:, 1]) * nb + nc[:, 2]
+                # pairs (i, j in neighbouring cell): vectorise over the max occupancy
+                occ = ends[nkey] - starts[nkey]
+                for t in range(int(occ.max()) if n else 0):
+                    has = occ > t
+                    ii = np.nonzero(has)[0]
+                    jj = order[starts[nkey[ii]] + t]
+                    ok = jj != ii
+                    ii, jj = ii[ok], jj[ok]
+                    d = pos[jj] - pos[ii]
+                    d -= L * np.round(d / L)
+                    close = np.einsum("ij,ij->i", d, d) < dmin * dmin
+                    ii, jj = ii[close], jj[close]
+                    lose = np.where(prio[ii] > prio[jj], ii, jj)
+                    removed[lose] = True
+    return pos[~removed]
+
+
+def config_mixed_phase(seed: int = 13, n_target: int = 1 << 22, sigma: float = 0.20,
+                       antisite: float = 0.10, ico_fraction: float = 0.01) -> Frame:
+    """Five slabs along x: bcc Fe, fcc Cu, L1_2 (species), sc, liquid with icosahedra."""
+    rng = rng_for(seed)
+    rho = {"bcc": 2 / A_BCC_FE ** 3, "fcc": 4 / A_FCC_CU ** 3, "l12": 4 / A_L12 ** 3,
+           "sc": 1 / A_SC ** 3, "liq": 4 / A_FCC_CU ** 3}
+    mean_rho = float(np.mean(list(rho.values())))
+    # cross-section Ly = Lz = Ly, slab thickness t = Lx / 5; choose Lx = 5 t = 2 Ly
+    vol = n_target / mean_rho
+    ly = (vol / 2.0) ** (1.0 / 3.0)
+    lx = 2.0 * ly
+    t = lx / 5.0
+    pieces, species = [], []
+    for si, (kind, a) in enumerate([("bcc", A_BCC_FE), ("fcc", A_FCC_CU), ("l12", A_L12),
+                                    ("sc", A_SC)]):
+        cell0, basis, sp0 = unit_cell(kind, a)
+        nx, ny = int(math.ceil(t / a)) + 1, int(math.ceil(ly / a)) + 1
+        g = np.stack(np.meshgrid(np.arange(nx), np.arange(ny), np.arange(ny), indexing="ij"),
+                     -1).reshape(-1, 3)
+        p = ((g[:, None, :] + basis[None]).reshape(-1, 3)) @ cell0
+        s = np.tile(sp0, len(g)).astype(np.int8)
+        keep = (p[:, 0] < t) & (p[:, 1] < ly) & (p[:, 2] < ly)
+        p, s = p[keep], s[keep]
+        p[:, 0] += si * t
+        if kind == "l12":
+            flip = rng.random(len(s)) < antisite
+            s = np.where(flip, 1 - s, s).astype(np.int8)
+        pieces.append(p)
+        species.append(s)
+    # liquid slab: icosahedral seeds, then random sequential addition with d_min = 2 A
+    n_liq_target = int(rho["liq"] * t * ly * ly)
+    liq = _rsa_liquid(rng, (4 * t, 5 * t), ly, n_liq_target, 2.0, ico_fraction)
+    pieces.append(liq)
+    species.append(np.zeros(len(liq), np.int8))
+    pos = np.vstack(pieces)
+    sp = np.concatenate(species)
+    pos = pos + rng.normal(0.0, sigma, pos.shape)
+    cell = np.diag([lx, ly, ly])
+    pos = wrap_positions(pos, cell)
+    n = len(pos)
+    if n > n_target:
+        idx = np.sort(rng.choice(n, n_target, replace=False))
+        pos, sp = pos[idx], sp[idx]
+    elif n < n_target:
+        extra = rng.random((n_target - n, 3)) * [lx, ly, ly]
+        pos = np.vstack([pos, extra])
+        sp = np.concatenate([sp, np.zeros(n_target - n, np.int8)])
+    return Frame(pos.astype(np.float32), cell, (True, True, True), sp, "mixed_phase",
+                 {"Lx": lx, "Ly": ly, "liquid_atoms": len(liq), "liquid_target": n_liq_target,
+                  "raw_count": n})
+
+
+def _rsa_liquid(rng, xr, ly, n_target, dmin, ico_fraction, max_attempts_factor=30):
+    """Random sequential addition in the slab x in [xr), periodic in y and z."""
+    x0, x1 = xr
+    w = dmin
+    nbx, nby = max(1, int((x1 - x0) // w)), max(1, int(ly // w))
+    wx, wy = (x1 - x0) / nbx, ly / nby
+    grid: dict = {}
+    pts = []
+
+    def ok(p):
+        cx, cy, cz = int((p[0] - x0) // wx), int(p[1] // wy), int(p[2] // wy)
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    key = (cx + dx, (cy + dy) % nby, (cz + dz) % nby)
+                    for q in grid.get(key, ()):
+                        d = p - q
+                        d[1] -= ly * round(d[1] / ly)
+                        d[2] -= ly * round(d[2] / ly)
+                        if d @ d < dmin * dmin:
+                            return False
+        return True
+
+    def add(p):
+        key = (int((p[0] - x0) // wx), int(p[1] // wy) % nby, int(p[2] // wy) % nby)
+        grid.setdefault(key, []).append(p)
+        pts.append(p)
+
+    n_ico = int(ico_fraction * n_target / 13)
+    for _ in range(n_ico):
+        c = np.array([rng.uniform(x0 + 3, x1 - 3), rng.uniform(0, ly), rng.uniform(0, ly)])
+        cl = ico_cluster(2.556, rotation=random_rotation(rng)) + c
+        cl[:, 1:] %= ly
+        if all(ok(p) for p in cl):
+            for p in cl:
+                add(p)
+    attempts = 0
+    batch = 4096
+    while len(pts) < n_target and attempts < max_attempts_factor * n_target:
+        cand = np.column_stack([rng.uniform(x0, x1, batch), rng.uniform(0, ly, batch),
+                                rng.uniform(0, ly, batch)])
+        for p in cand:
+            attempts += 1
+            if ok(p):
+                add(p)
+                if len(pts) >= n_target:
+                    break
+    return np.array(pts).reshape(-1, 3)
+
+
+def config_batch(seed: int = 256, n_frames: int = 256, n_min: float = 1e3, n_max: float = 1e6,
+                 sigma_max: float = 0.25, strain_max: float = 0.05):
+    """Uneven frames of random lattices, orientations, noise and affine strain."""
+    rng = rng_for(seed)
+    kinds = [("fcc", A_FCC_CU), ("hcp", A_HCP), ("bcc", A_BCC_FE), ("l10", A_L12),
+             ("l12", A_L12), ("sc", A_SC)]
+    frames = []
+    for fi in range(n_frames):
+        kind, a = kinds[int(rng.integers(len(kinds)))]
+        target = math.exp(rng.uniform(math.log(n_min), math.log(n_max)))
+        cell0, basis, _ = unit_cell(kind, a)
+        per = len(basis)
+        side = max(3, int(round((target / per) ** (1 / 3))))
+        reps = np.array([side, side, side])
+        if kind == "hcp":   # orthohexagonal cell is elongated in y
+            reps = np.array([side, max(3, int(round(side / math.sqrt(3)))), max(3, int(round(side * 0.61)))])
+        R = random_rotation(rng)
+        E = rng.uniform(-strain_max, strain_max, (3, 3))
+        E = 0.5 * (E + E.T)
+        sig = float(rng.uniform(0.0, sigma_max))
+        if rng.random() < 0.1:
+            sig = 0.0
+        seed_f = int(rng.integers(1 << 31))
+        f = crystal(kind, a, reps, sigma=sig, seed=seed_f, rotation=R, deform=np.eye(3) + E,
+                    dtype=np.float32, name=f"{kind}{fi}")
+        f.meta.update({"E": E.tolist(), "R": R.tolist()})
+        frames.append(f)
+    return frames
+
+
+def describe(frame: Frame) -> str:
+    return f"{frame.name}: n={frame.n} dtype={frame.positions.dtype} cell={np.round(frame.cell, 3).tolist()}"
