@@ -1,0 +1,320 @@
+"""Throughput of per-atom Polyhedral Template Matching on one GB300.
+
+Step = one ptm_classify_frame call over the 1,048,576-atom periodic fcc
+polycrystal (16 Voronoi grains, 4 stacking-fault slabs, sigma 0.15 A, float32
+positions, all five templates, species given so the alloy rules run): cell
+list, kNN, hulls, canonical codes, QCP, orientation, strain, alloy.  Inputs are
+resident in HBM; L2 (129 MB) is flushed by writing a 256 MB buffer before every
+timed step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  N > 1 runs one independent replica per GPU
+(the method needs no exchange between frames), launched with torch.distributed.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atoms classified/sec (5 templates + alloy)"
+UNIT = "atoms/s"
+SM_COUNT = 152
+FP32_LANES = 128
+SM_MAX_MHZ = 2070.0
+# Algorithmic FP32 work ("Roofline"): per scored correspondence of
+# N points, 18 (N - 1) flops for the covariance plus 232 for Horn's matrix, the
+# characteristic polynomial and 8 Newton steps; per matched atom 2000 flops for
+# the eigenvector, explicit residual, orientation and strain; per atom 126 flops
+# for the 14 neighbour vectors and their moments.
+FLOP_PER_CAND_POINT = 18.0
+FLOP_PER_CAND = 232.0 - 18.0
+FLOP_PER_MATCHED = 2000.0
+FLOP_PER_ATOM = 126.0
+# Algorithmic DRAM bytes of the per-atom kernel per atom: its cell-sorted record
+# (16 B) and cell index (4 B), the species byte, and the outputs
+# (1 + 1 + 4 + 4 + 16 + 36 + 60 B).
+BYTES_PER_ATOM = 16 + 4 + 1 + 122
+WORKLOAD = "polycrystal-1048576"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "gpu" else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def workload():
+    from paper_1603_05143_gb300 import inputs as I
+    f = I.config_polycrystal()
+    species = np.zeros(f.n, np.int8)      # pure Cu: the alloy rules run and give PURE
+    return f, species
+
+
+def config_dict(f, extra=None):
+    c = {"workload": WORKLOAD, "atoms": f.n, "box_A": round(float(f.cell[0, 0]), 3), "grains": 16,
+         "stacking_faults": 4, "sigma_A": 0.15, "positions": "float32", "templates": "SC,FCC,HCP,ICO,BCC",
+         "species": "given (all one type)", "l2": "flushed (256 MB write) before every timed step",
+         "padded_atoms": int(f.meta.get("padded", 0))}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        load = [s for s in sm if mx and s > 0.3 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------ CPU oracle arm
+def oracle_rate(f, species, seconds, threads=None, seed=7):
+    """Time the oracle (as it stands) on a seeded uniform sample of the frame's
+    atoms, sized to take about `seconds` on all host cores."""
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    F = oracle.Frame(f.positions, f.cell, f.pbc)
+    rng = np.random.default_rng(seed)
+    probe = np.sort(rng.choice(f.n, 4 * threads, replace=False))
+    t = time.perf_counter()
+    F.classify(probe, species=species, threads=threads, chunk=1)
+    per_atom = (time.perf_counter() - t) / len(probe)
+    m = int(min(f.n, max(8 * threads, seconds / max(per_atom, 1e-9))))
+    atoms = np.sort(rng.choice(f.n, m, replace=False))
+    t = time.perf_counter()
+    F.classify(atoms, species=species, threads=threads, chunk=max(1, m // (8 * threads)))
+    dt = time.perf_counter() - t
+    return m / dt, m, dt, threads
+
+
+def run_reference(args, world, rank, pg):
+    if rank != 0:
+        return
+    f, species = workload()
+    threads = os.cpu_count() or 1
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_rate(f, species, per_step / 4, threads)
+    rates, samples = [], 0
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        r, m, dt, th = oracle_rate(f, species, per_step, threads, seed=100 + s)
+        rates.append(r)
+        samples += m
+    wall = time.perf_counter() - t0
+    value = float(np.mean(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(f, {"sample": "uniform seeded atom sample per step"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{samples} atoms over {args.steps} steps, uniform seeded sample of the frame"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, world, rank, local, pg):
+    import torch
+    from paper_1603_05143_gb300 import PTM, build
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    f, species = workload()
+    ptm = PTM(local)
+    pos = torch.from_numpy(f.positions).to(dev)
+    sp = torch.from_numpy(species).to(dev)
+    from paper_1603_05143_gb300.binding import allocate_outputs
+    out = allocate_outputs(f.n, dev)
+    flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        ptm.classify(pos, f.cell, f.pbc, species=sp, out=out)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    st = ptm.stats()
+    assert st["internal"] == 0 and st["atoms"] == f.n, st
+
+    times, kernel_ms, stats = [], [], []
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(len(times))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            s = ptm.stats()
+            kernel_ms.append(s["atom_kernel_ms"])
+            stats.append(s)
+        torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    total = sum(times)
+    if pg:
+        t = torch.tensor([total], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total = float(t.item())
+    ms = total / args.steps
+    value = world * f.n / (ms * 1e-3)
+
+    # ---- end to end through the host-buffer entry point (pinned buffers)
+    e2e = None
+    if not args.no_e2e:
+        from paper_1603_05143_gb300.binding import allocate_outputs_host
+        hpos = torch.from_numpy(f.positions).pin_memory().numpy()
+        hsp = torch.from_numpy(species).pin_memory().numpy()
+        hout = allocate_outputs_host(f.n, pinned=True)
+        for _ in range(2):
+            ptm.classify_host(hpos, f.cell, f.pbc, species=hsp, out=hout)
+        if pg:
+            pg.barrier()
+        et = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ptm.classify_host(hpos, f.cell, f.pbc, species=hsp, out=hout)
+            et.append(time.perf_counter() - t0)
+        tot = sum(et)
+        if pg:
+            t = torch.tensor([tot], device=dev)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            tot = float(t.item())
+        e2e = {"value": world * f.n * args.steps / tot, "unit": UNIT,
+               "h2d_bytes_per_step": int(hpos.nbytes + hsp.nbytes),
+               "d2h_bytes_per_step": int(sum(a.nbytes for a in hout.values()))}
+    if rank != 0:
+        ptm.close()
+        return
+
+    s0 = stats[-1]
+    kms = statistics.mean(kernel_ms)
+    flops = (FLOP_PER_CAND_POINT * s0["candidate_points"] + FLOP_PER_CAND * s0["candidates"]
+             + FLOP_PER_MATCHED * s0["matched"] + FLOP_PER_ATOM * s0["atoms"])
+    achieved = flops / (kms * 1e-3) / 1e12
+    clocks = clk.summary()
+    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peaks_file = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm_peak = json.load(open(peaks_file)).get("hbm_gbs") if os.path.exists(peaks_file) else None
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_atoms", "kernel_ms": kms,
+            "peak_note": "FP32 peak derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
+            "hbm_achieved_gbs": f.n * BYTES_PER_ATOM / (kms * 1e-3) / 1e9, "hbm_peak_gbs": hbm_peak}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        r, m, dt, th = oracle_rate(f, species, args.cpu_seconds)
+        cpu = {"value": r, "unit": UNIT, "cores": th, "kind": "oracle",
+               "sample": f"{m} uniformly sampled atoms of the same frame in {dt:.1f} s"}
+    q = np.percentile(times, [50, 99])
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(f, {"parallelism": f"replicas{world}"}),
+            "latency_ms": {"p50": float(q[0]), "p99": float(q[1])},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": 6 * args.steps,
+            "fallbacks": {k: s0[k] for k in ("sos", "qcp_fp64", "tie_fp64", "knn_wide", "knn_fail", "internal")},
+            "matched": s0["matched"], "candidates_per_atom": s0["candidates"] / s0["atoms"]}
+    print(json.dumps(line), flush=True)
+    ptm.close()
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank, pg)
+    else:
+        run_gpu(args, world, rank, local, pg)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,148 @@
+/*
+ * ptm.h -- C ABI of the GB300 per-atom Polyhedral Template Matching library
+ * (libptm.so).  Method: Larsen, Schmidt & Schiotz, "Robust Structural
+ * Identification via Polyhedral Template Matching".
+ *
+ * For every atom of a periodic frame the library
+ *   - selects the 14 nearest neighbours, Euclidean order (Sec. 3, Table 1);
+ *   - builds the convex hulls of the first 6, 12 and 14 neighbours and labels
+ *     each hull graph canonically (Sec. 4);
+ *   - matches the labels against the SC, FCC, HCP, ICO and BCC templates and
+ *     evaluates the scale-invariant RMSD (Eq. 3-4) of every admissible
+ *     correspondence (Algorithm 1);
+ *   - returns structure type, RMSD, scale, orientation (Sec. 7), elastic strain
+ *     (Sec. 8, Eq. 6-7) and the binary alloy label (Sec. 6, Table 3).
+ *
+ * All compute runs in CUDA kernels on the device chosen at ptm_create.
+ * No function aborts or throws across this boundary: every failure is a
+ * ptm_status.  Functions are not thread-safe on one context; use one context
+ * per host thread.
+ */
+#ifndef PTM_H
+#define PTM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ptm_context ptm_context;   /* opaque, owned by the library */
+
+typedef enum {
+  PTM_OK = 0,
+  PTM_ERR_INVALID_ARG = 1,     /* a NULL pointer, bad size, singular cell, unknown dtype */
+  PTM_ERR_OUT_OF_MEMORY = 2,   /* device workspace could not be allocated */
+  PTM_ERR_CUDA = 3,            /* a CUDA runtime call failed; see ptm_last_cuda_error */
+  PTM_ERR_TIMEOUT = 4,         /* a bounded wait ran out (serving) */
+  PTM_ERR_DEVICE_STATUS = 5,   /* a kernel reported an internal inconsistency */
+  PTM_ERR_BUSY = 6,            /* no serving slot or memory budget free right now */
+  PTM_ERR_NOT_FOUND = 7        /* unknown serving ticket */
+} ptm_status;
+
+/* Template mask bits, in the order Algorithm 1 visits the templates. */
+enum { PTM_MASK_SC = 1, PTM_MASK_FCC = 2, PTM_MASK_HCP = 4, PTM_MASK_ICO = 8,
+       PTM_MASK_BCC = 16, PTM_MASK_ALL = 31 };
+
+/* Structure codes written to ptm_outputs.structure. */
+enum { PTM_NONE = 0, PTM_SC = 1, PTM_FCC = 2, PTM_HCP = 3, PTM_ICO = 4, PTM_BCC = 5 };
+
+/* Binary alloy labels (Sec. 6): FCC uses the coplanar groups of Table 3, BCC the
+   two neighbour shells.  "same"/"other" are relative to the central atom. */
+enum { PTM_ALLOY_NONE = 0, PTM_ALLOY_PURE = 1, PTM_ALLOY_L10 = 2, PTM_ALLOY_L12_MAJ = 3,
+       PTM_ALLOY_L12_MIN = 4, PTM_ALLOY_B2 = 5 };
+
+/* Position element types. */
+enum { PTM_F32 = 0, PTM_F64 = 1 };
+
+typedef struct {
+  int device;                /* CUDA device ordinal */
+  size_t hbm_budget_bytes;   /* serving admission budget; 0 = half the free memory at create */
+} ptm_options;
+
+/* One frame.  Problem statement of Algorithm 1: positions of every atom, the
+   periodic cell, optional species (Sec. 6), the template set and RMSD_max
+   (Sec. 5.1). */
+typedef struct {
+  int64_t n_atoms;           /* >= 1 and < 2^31 */
+  const void *positions;     /* n_atoms x 3, row-major, element type pos_dtype */
+  int pos_dtype;             /* PTM_F32 or PTM_F64 */
+  const int8_t *species;     /* n_atoms species codes, or NULL (alloy = NONE) */
+  double cell[9];            /* row-major; rows are the three cell vectors (Angstrom) */
+  uint8_t pbc[3];            /* 1 = periodic along cell vector i */
+  uint32_t template_mask;    /* PTM_MASK_* bits; 0 means PTM_MASK_ALL */
+  double rmsd_max;           /* atoms whose best RMSD exceeds it are unmatched; INFINITY = none */
+} ptm_frame;
+
+/* Per-atom outputs, indexed by atom.  Any pointer may be NULL to skip it.
+   Unmatched atoms (Algorithm 1: r* = infinity, structure disordered) get
+   structure PTM_NONE, rmsd +INF, scale 0, quat (1,0,0,0), strain 0,
+   correspondence -1, alloy PTM_ALLOY_NONE. */
+typedef struct {
+  int8_t *structure;         /* n: PTM_NONE .. PTM_BCC */
+  int8_t *alloy;             /* n: PTM_ALLOY_* */
+  float *rmsd;               /* n: scale-invariant RMSD of the best match, Eq. 3 */
+  float *scale;              /* n: the optimal s of Eq. 3 (data -> template units) */
+  float *quat;               /* n x 4: (w, x, y, z), w >= 0: rotation taking the template
+                                onto the neighbourhood, reduced to the fundamental zone */
+  float *strain;             /* n x 9: symmetric P of the left polar decomposition A = P U
+                                of the least-squares deformation gradient (Eq. 6-7) */
+  int32_t *correspondence;   /* n x 15: atom index mapped to template slot 0..k
+                                (slot 0 = the atom itself), -1 beyond k; the smallest
+                                member of its orbit under the template symmetry */
+} ptm_outputs;
+
+/* Counters of the last completed classify call (rates of the rare paths). */
+typedef struct {
+  int64_t atoms;             /* atoms processed */
+  int64_t matched;           /* atoms with a structure */
+  int64_t knn_wide;          /* atoms whose neighbour search needed more than 27 cells */
+  int64_t knn_fail;          /* atoms whose search gave up (left unmatched) */
+  int64_t sos;               /* orientation tests decided by Simulation of Simplicity */
+  int64_t qcp_fp64;          /* candidates re-solved in FP64: small eigenvalue gap */
+  int64_t tie_fp64;          /* atoms whose best candidates were re-ranked in FP64 */
+  int64_t internal;          /* internal inconsistencies (should be 0) */
+  int64_t candidates;        /* correspondences scored by QCP (symmetry-reduced, Appendix A) */
+  int64_t candidate_points;  /* sum over those correspondences of the point count N = k + 1 */
+  double pipeline_ms;        /* device time of the whole call (cell list + classification) */
+  double atom_kernel_ms;     /* device time of the per-atom classification kernel */
+} ptm_stats;
+
+/* Create a context on options->device (NULL options: device 0, default budget).
+   The context owns all device workspace and frees it in ptm_destroy. */
+ptm_status ptm_create(const ptm_options *options, ptm_context **out);
+
+/* Release the context and its workspace.  Waits for its work to finish. */
+ptm_status ptm_destroy(ptm_context *ctx);
+
+/* Classify every atom of one frame.  frame->positions, frame->species and all
+   output pointers are DEVICE pointers; the call only enqueues work on `stream`
+   (a cudaStream_t, NULL = legacy default stream) and returns.  Buffers must stay
+   alive until the stream reaches this point.  The first call for a larger frame
+   grows the context workspace (cudaMalloc), so warm up before timing or
+   capturing.  Errors in the arguments are returned before anything is
+   enqueued. */
+ptm_status ptm_classify_frame(ptm_context *ctx, const ptm_frame *frame, const ptm_outputs *out,
+                              void *stream);
+
+/* Same, but positions, species and outputs are HOST pointers (page-locked memory
+   is faster).  The library copies inputs to its own device buffers, classifies,
+   copies the outputs back and synchronises `stream` before returning. */
+ptm_status ptm_classify_frame_host(ptm_context *ctx, const ptm_frame *frame,
+                                   const ptm_outputs *out, void *stream);
+
+/* Copy the counters and device timings of the last classify call (synchronises
+   its stream).  Timings come from CUDA events recorded on that stream. */
+ptm_status ptm_get_stats(ptm_context *ctx, ptm_stats *out);
+
+/* Human-readable name of a status; never NULL. */
+const char *ptm_status_string(ptm_status status);
+
+/* Message of the last CUDA error seen by this context ("" if none). */
+const char *ptm_last_cuda_error(ptm_context *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PTM_H */

@@ -1,0 +1,201 @@
+"""ctypes binding of libptm.so: same names as include/ptm.h, marshalling only."""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import pathlib
+
+import numpy as np
+
+_LIB_PATH = pathlib.Path(__file__).resolve().parent / "_build" / "libptm.so"
+
+STRUCTURES = ("NONE", "SC", "FCC", "HCP", "ICO", "BCC")
+ALLOYS = ("NONE", "PURE", "L10", "L12_MAJ", "L12_MIN", "B2")
+MASK_SC, MASK_FCC, MASK_HCP, MASK_ICO, MASK_BCC, MASK_ALL = 1, 2, 4, 8, 16, 31
+PTM_F32, PTM_F64 = 0, 1
+STATUS = ("PTM_OK", "PTM_ERR_INVALID_ARG", "PTM_ERR_OUT_OF_MEMORY", "PTM_ERR_CUDA", "PTM_ERR_TIMEOUT",
+          "PTM_ERR_DEVICE_STATUS", "PTM_ERR_BUSY", "PTM_ERR_NOT_FOUND")
+OUTPUT_NAMES = ("structure", "alloy", "rmsd", "scale", "quat", "strain", "correspondence")
+
+
+class ptm_options(C.Structure):
+    _fields_ = [("device", C.c_int), ("hbm_budget_bytes", C.c_size_t)]
+
+
+class ptm_frame(C.Structure):
+    _fields_ = [("n_atoms", C.c_int64), ("positions", C.c_void_p), ("pos_dtype", C.c_int),
+                ("species", C.c_void_p), ("cell", C.c_double * 9), ("pbc", C.c_uint8 * 3),
+                ("template_mask", C.c_uint32), ("rmsd_max", C.c_double)]
+
+
+class ptm_outputs(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in OUTPUT_NAMES]
+
+
+class ptm_stats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("atoms", "matched", "knn_wide", "knn_fail", "sos", "qcp_fp64",
+                                         "tie_fp64", "internal", "candidates", "candidate_points")] + \
+               [("pipeline_ms", C.c_double), ("atom_kernel_ms", C.c_double)]
+
+
+class PTMError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        name = STATUS[status] if 0 <= status < len(STATUS) else f"status {status}"
+        super().__init__(f"{what}: {name}" + (f" ({detail})" if detail else ""))
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load libptm.so (built by ``build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not _LIB_PATH.exists():
+            raise RuntimeError(f"libptm.so not built ({_LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(str(_LIB_PATH))
+        P = C.c_void_p
+        L.ptm_create.argtypes = [C.POINTER(ptm_options), C.POINTER(C.c_void_p)]
+        L.ptm_destroy.argtypes = [P]
+        L.ptm_classify_frame.argtypes = [P, C.POINTER(ptm_frame), C.POINTER(ptm_outputs), P]
+        L.ptm_classify_frame_host.argtypes = [P, C.POINTER(ptm_frame), C.POINTER(ptm_outputs), P]
+        L.ptm_get_stats.argtypes = [P, C.POINTER(ptm_stats)]
+        L.ptm_status_string.argtypes = [C.c_int]
+        L.ptm_status_string.restype = C.c_char_p
+        L.ptm_last_cuda_error.argtypes = [P]
+        L.ptm_last_cuda_error.restype = C.c_char_p
+        for f in ("ptm_create", "ptm_destroy", "ptm_classify_frame", "ptm_classify_frame_host", "ptm_get_stats"):
+            getattr(L, f).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _frame(n, pos_ptr, dtype_code, species_ptr, cell, pbc, mask, rmsd_max) -> ptm_frame:
+    f = ptm_frame()
+    f.n_atoms = int(n)
+    f.positions = pos_ptr
+    f.pos_dtype = dtype_code
+    f.species = species_ptr
+    cell = np.asarray(cell, np.float64).reshape(9)
+    for i in range(9):
+        f.cell[i] = float(cell[i])
+    for i in range(3):
+        f.pbc[i] = 1 if pbc[i] else 0
+    f.template_mask = int(mask)
+    f.rmsd_max = float(rmsd_max) if rmsd_max is not None else math.inf
+    return f
+
+
+class PTM:
+    """A library context on one CUDA device (``ptm_create`` / ``ptm_destroy``)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self.lib = load()
+        opt = ptm_options(device, hbm_budget_bytes)
+        h = C.c_void_p()
+        rc = self.lib.ptm_create(C.byref(opt), C.byref(h))
+        if rc:
+            raise PTMError(rc, "ptm_create")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ptm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc:
+            raise PTMError(rc, what, self.lib.ptm_last_cuda_error(self.h).decode())
+
+    # ---------------------------------------------------------------- device
+    def classify(self, positions, cell, pbc=(True, True, True), species=None, mask=MASK_ALL,
+                 rmsd_max=math.inf, out=None, outputs=OUTPUT_NAMES, stream=None):
+        """Classify every atom of a frame held in CUDA tensors (``ptm_classify_frame``).
+
+        positions: (n, 3) float32 or float64 CUDA tensor; species: (n,) int8 or None.
+        Returns a dict of CUDA tensors (allocated unless ``out`` provides them);
+        the work is enqueued on ``stream`` (default: torch's current stream).
+        """
+        import torch
+        if not positions.is_cuda or positions.dim() != 2 or positions.shape[1] != 3:
+            raise ValueError("positions must be an (n, 3) CUDA tensor")
+        positions = positions.contiguous()
+        n = positions.shape[0]
+        dev = positions.device
+        if positions.dtype == torch.float32:
+            code = PTM_F32
+        elif positions.dtype == torch.float64:
+            code = PTM_F64
+        else:
+            raise ValueError("positions must be float32 or float64")
+        sp_ptr = None
+        if species is not None:
+            species = species.to(device=dev, dtype=torch.int8).contiguous()
+            sp_ptr = species.data_ptr()
+        if out is None:
+            out = allocate_outputs(n, dev, outputs)
+        o = ptm_outputs()
+        for name in OUTPUT_NAMES:
+            t = out.get(name)
+            setattr(o, name, t.data_ptr() if t is not None else None)
+        f = _frame(n, positions.data_ptr(), code, sp_ptr, cell, pbc, mask, rmsd_max)
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        self._keep = (positions, species)
+        self._check(self.lib.ptm_classify_frame(self.h, C.byref(f), C.byref(o), C.c_void_p(st.cuda_stream)),
+                    "ptm_classify_frame")
+        return out
+
+    # ------------------------------------------------------------------ host
+    def classify_host(self, positions, cell, pbc=(True, True, True), species=None, mask=MASK_ALL,
+                      rmsd_max=math.inf, out=None, outputs=OUTPUT_NAMES, stream=None):
+        """Same as ``classify`` for host (numpy) buffers (``ptm_classify_frame_host``):
+        the library copies to and from the device and returns when done."""
+        pos = np.ascontiguousarray(positions)
+        if pos.dtype not in (np.float32, np.float64) or pos.ndim != 2 or pos.shape[1] != 3:
+            raise ValueError("positions must be an (n, 3) float32/float64 array")
+        n = pos.shape[0]
+        sp = None if species is None else np.ascontiguousarray(species, np.int8)
+        if out is None:
+            out = allocate_outputs_host(n, outputs)
+        o = ptm_outputs()
+        for name in OUTPUT_NAMES:
+            a = out.get(name)
+            setattr(o, name, a.ctypes.data if a is not None else None)
+        f = _frame(n, pos.ctypes.data, PTM_F64 if pos.dtype == np.float64 else PTM_F32,
+                   sp.ctypes.data if sp is not None else None, cell, pbc, mask, rmsd_max)
+        st = 0 if stream is None else stream.cuda_stream
+        self._check(self.lib.ptm_classify_frame_host(self.h, C.byref(f), C.byref(o), C.c_void_p(st)),
+                    "ptm_classify_frame_host")
+        return out
+
+    def stats(self) -> dict:
+        s = ptm_stats()
+        self._check(self.lib.ptm_get_stats(self.h, C.byref(s)), "ptm_get_stats")
+        return {k: getattr(s, k) for k, _ in ptm_stats._fields_}
+
+
+def allocate_outputs(n, device, outputs=OUTPUT_NAMES):
+    import torch
+    shapes = {"structure": ((n,), torch.int8), "alloy": ((n,), torch.int8), "rmsd": ((n,), torch.float32),
+              "scale": ((n,), torch.float32), "quat": ((n, 4), torch.float32),
+              "strain": ((n, 3, 3), torch.float32), "correspondence": ((n, 15), torch.int32)}
+    return {k: torch.empty(*shapes[k][0], dtype=shapes[k][1], device=device) for k in outputs}
+
+
+def allocate_outputs_host(n, outputs=OUTPUT_NAMES, pinned=False):
+    shapes = {"structure": ((n,), np.int8), "alloy": ((n,), np.int8), "rmsd": ((n,), np.float32),
+              "scale": ((n,), np.float32), "quat": ((n, 4), np.float32), "strain": ((n, 3, 3), np.float32),
+              "correspondence": ((n, 15), np.int32)}
+    if pinned:
+        import torch
+        tt = {np.int8: torch.int8, np.float32: torch.float32, np.int32: torch.int32}
+        return {k: torch.empty(shapes[k][0], dtype=tt[shapes[k][1]], pin_memory=True).numpy() for k in outputs}
+    return {k: np.empty(shapes[k][0], shapes[k][1]) for k in outputs}

@@ -1,0 +1,355 @@
+// libptm.so host side: the C ABI of include/ptm.h (Larsen, Schmidt & Schiotz,
+// "Robust Structural Identification via Polyhedral Template Matching").
+// Validates arguments, sizes the cell list, owns the device workspace and
+// enqueues the kernels of ptm_kernels.cuh on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#define PTM_TBL_CONST __constant__ const
+#define PTM_TBL_GLOBAL __device__ const
+#include "ptm_kernels.cuh"
+
+// =================================================================== host
+using namespace ptm;
+
+struct ptm_context {
+  int device = 0;
+  size_t budget = 0;
+  std::string last_error;
+  // workspace
+  size_t cap_atoms = 0, cap_cells = 0, cap_sorted_bytes = 0;
+  void *sorted = nullptr;
+  int *sbin = nullptr, *wrapv = nullptr, *atom_cell = nullptr, *atom_rank = nullptr, *atom_wrap = nullptr;
+  int *cell_count = nullptr, *cell_start = nullptr, *block_sums = nullptr;
+  int *dstat = nullptr;
+  unsigned long long *counters = nullptr;
+  cudaStream_t last_stream = nullptr;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // call start, atom kernel start, end
+  // host-buffer entry point
+  size_t cap_host_atoms = 0;
+  void *hpos = nullptr;
+  int8_t *hspecies = nullptr;
+  int8_t *o_struct = nullptr, *o_alloy = nullptr;
+  float *o_rmsd = nullptr, *o_scale = nullptr, *o_quat = nullptr, *o_strain = nullptr;
+  int32_t *o_corr = nullptr;
+};
+
+static ptm_status cuda_fail(ptm_context *ctx, cudaError_t e, const char *what) {
+  if (ctx) ctx->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? PTM_ERR_OUT_OF_MEMORY : PTM_ERR_CUDA;
+}
+
+#define CK(call)                                                     \
+  do {                                                               \
+    cudaError_t e_ = (call);                                         \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);         \
+  } while (0)
+
+static ptm_status grow(ptm_context *ctx, size_t n, size_t ncell, int f64) {
+  size_t sb = n * (f64 ? sizeof(Atom64) : sizeof(float4));
+  if (n > ctx->cap_atoms || sb > ctx->cap_sorted_bytes) {
+    cudaFree(ctx->sorted); cudaFree(ctx->sbin); cudaFree(ctx->wrapv);
+    cudaFree(ctx->atom_cell); cudaFree(ctx->atom_rank); cudaFree(ctx->atom_wrap);
+    ctx->sorted = nullptr; ctx->sbin = ctx->wrapv = ctx->atom_cell = ctx->atom_rank = ctx->atom_wrap = nullptr;
+    ctx->cap_atoms = ctx->cap_sorted_bytes = 0;
+    size_t na = std::max(n, ctx->cap_atoms);
+    size_t nsb = std::max(sb, na * (f64 ? sizeof(Atom64) : sizeof(float4)));
+    CK(cudaMalloc(&ctx->sorted, nsb));
+    CK(cudaMalloc(&ctx->sbin, na * sizeof(int)));
+    CK(cudaMalloc(&ctx->wrapv, na * sizeof(int)));
+    CK(cudaMalloc(&ctx->atom_cell, na * sizeof(int)));
+    CK(cudaMalloc(&ctx->atom_rank, na * sizeof(int)));
+    CK(cudaMalloc(&ctx->atom_wrap, na * sizeof(int)));
+    ctx->cap_atoms = na;
+    ctx->cap_sorted_bytes = nsb;
+  }
+  if (ncell > ctx->cap_cells) {
+    cudaFree(ctx->cell_count); cudaFree(ctx->cell_start); cudaFree(ctx->block_sums);
+    ctx->cell_count = ctx->cell_start = ctx->block_sums = nullptr;
+    ctx->cap_cells = 0;
+    CK(cudaMalloc(&ctx->cell_count, (ncell + 1) * sizeof(int)));
+    CK(cudaMalloc(&ctx->cell_start, (ncell + 1) * sizeof(int)));
+    size_t nblk = (ncell + 1 + 2 * SCAN_BLOCK - 1) / (2 * SCAN_BLOCK);
+    CK(cudaMalloc(&ctx->block_sums, (nblk + 1) * sizeof(int)));
+    ctx->cap_cells = ncell;
+  }
+  return PTM_OK;
+}
+
+static bool finite_cell(const double *H) {
+  for (int i = 0; i < 9; i++) if (!std::isfinite(H[i])) return false;
+  return true;
+}
+
+// Enqueue the whole pipeline for one frame whose buffers are on the device.
+static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_outputs *o, cudaStream_t st) {
+  if (!f || !o) return PTM_ERR_INVALID_ARG;
+  if (f->n_atoms < 1 || f->n_atoms >= (1ll << 31) || !f->positions) return PTM_ERR_INVALID_ARG;
+  if (f->pos_dtype != PTM_F32 && f->pos_dtype != PTM_F64) return PTM_ERR_INVALID_ARG;
+  if (!finite_cell(f->cell)) return PTM_ERR_INVALID_ARG;
+  const double *H = f->cell;
+  double det = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+               H[2] * (H[3] * H[7] - H[4] * H[6]);
+  if (!(std::fabs(det) > 1e-12)) return PTM_ERR_INVALID_ARG;
+  const int64_t n = f->n_atoms;
+  const int f64 = f->pos_dtype == PTM_F64;
+  double Hinv[9];
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) {
+      int i1 = (j + 1) % 3, i2 = (j + 2) % 3, j1 = (i + 1) % 3, j2 = (i + 2) % 3;
+      Hinv[3 * i + j] = (H[3 * i1 + j1] * H[3 * i2 + j2] - H[3 * i1 + j2] * H[3 * i2 + j1]) / det;
+    }
+  double W[3];
+  for (int c = 0; c < 3; c++) {
+    double g = Hinv[c] * Hinv[c] + Hinv[3 + c] * Hinv[3 + c] + Hinv[6 + c] * Hinv[6 + c];
+    W[c] = 1.0 / std::sqrt(g);
+  }
+  // cells about 1.25x the expected 14-neighbour radius at the mean density
+  const double rho = (double)n / std::fabs(det);
+  const double r14 = std::cbrt(3.0 * 15.0 / (4.0 * M_PI * rho));
+  const double wt = 1.25 * r14;
+  int nb[3];
+  size_t ncell = 1;
+  for (int c = 0; c < 3; c++) {
+    nb[c] = std::max(1, (int)std::floor(W[c] / wt));
+    nb[c] = std::min(nb[c], 1024);
+    ncell *= (size_t)nb[c];
+  }
+  while (ncell > (size_t)4 * n + 64) {
+    int c = (int)(std::max_element(nb, nb + 3) - nb);
+    ncell /= nb[c];
+    nb[c] = std::max(1, nb[c] / 2);
+    ncell *= nb[c];
+  }
+  ptm_status rs = grow(ctx, (size_t)n, ncell, f64);
+  if (rs != PTM_OK) return rs;
+
+  FrameDesc desc;
+  FrameDesc *hd = &desc;
+  std::memset(hd, 0, sizeof(FrameDesc));
+  hd->sorted = ctx->sorted;
+  hd->sbin = ctx->sbin;
+  hd->cell_start = ctx->cell_start;
+  hd->wrapv = ctx->wrapv;
+  hd->species = f->species;
+  hd->positions = f->positions;
+  hd->n = n;
+  for (int c = 0; c < 3; c++) { hd->nb[c] = nb[c]; hd->pbc[c] = f->pbc[c] ? 1 : 0; }
+  hd->f64 = f64;
+  hd->mask = f->template_mask ? (f->template_mask & PTM_MASK_ALL) : PTM_MASK_ALL;
+  hd->rmsd_max = std::isnan(f->rmsd_max) ? INFINITY : (float)f->rmsd_max;
+  hd->min_cell_width = (float)std::min(W[0] / nb[0], std::min(W[1] / nb[1], W[2] / nb[2]));
+  for (int i = 0; i < 9; i++) hd->H[i] = H[i];
+  // image shifts for n in [-2, 2]^3 exactly as the contract evaluates them:
+  // (n0 H0 + n1 H1) + n2 H2 in FP64 (built with -ffp-contract=off)
+  for (int a = -2; a <= 2; a++)
+    for (int b = -2; b <= 2; b++)
+      for (int c = -2; c <= 2; c++) {
+        int i = (a + 2) * 25 + (b + 2) * 5 + (c + 2);
+        for (int k = 0; k < 3; k++) {
+          volatile double t0 = (double)a * H[k];
+          volatile double t1 = (double)b * H[3 + k];
+          volatile double t2 = (double)c * H[6 + k];
+          volatile double t01 = t0 + t1;
+          double s = t01 + t2;
+          hd->s64[i][k] = s;
+          hd->s32[i][k] = (float)s;
+          hd->slo[i][k] = (float)(s - (double)(float)s);
+        }
+      }
+  hd->structure = o->structure; hd->alloy = o->alloy; hd->rmsd = o->rmsd; hd->scale = o->scale;
+  hd->quat = o->quat; hd->strain = o->strain; hd->corr = o->correspondence;
+  hd->dstat = ctx->dstat;
+  hd->counters = ctx->counters;
+
+  BinParams bp;
+  for (int i = 0; i < 9; i++) bp.Hinv[i] = (float)Hinv[i];
+  for (int c = 0; c < 3; c++) { bp.W[c] = (float)W[c]; bp.nb[c] = nb[c]; bp.pbc[c] = hd->pbc[c]; }
+  bp.n = n;
+  bp.f64 = f64;
+
+  CK(cudaEventRecord(ctx->ev[0], st));
+  CK(cudaMemsetAsync(ctx->cell_count, 0, (ncell + 1) * sizeof(int), st));
+  CK(cudaMemsetAsync(ctx->dstat, 0, 4 * sizeof(int), st));
+  CK(cudaMemsetAsync(ctx->counters, 0, C_NCOUNTERS * sizeof(unsigned long long), st));
+  const int tb = 256;
+  const unsigned gb = (unsigned)((n + tb - 1) / tb);
+  k_bin<<<gb, tb, 0, st>>>(f->positions, bp, ctx->cell_count, ctx->atom_cell, ctx->atom_rank, ctx->atom_wrap,
+                           ctx->dstat);
+  const int nscan = (int)ncell + 1;
+  const int nblk = (nscan + 2 * SCAN_BLOCK - 1) / (2 * SCAN_BLOCK);
+  k_scan_block<<<nblk, SCAN_BLOCK, 0, st>>>(ctx->cell_count, ctx->cell_start, ctx->block_sums, nscan);
+  k_scan_sums<<<1, SCAN_BLOCK, 0, st>>>(ctx->block_sums, nblk, ctx->dstat + 2);
+  k_scan_add<<<(nscan + 255) / 256, 256, 0, st>>>(ctx->cell_start, ctx->block_sums, nscan);
+  k_scatter<<<gb, tb, 0, st>>>(f->positions, f64, n, ctx->atom_cell, ctx->atom_rank, ctx->atom_wrap,
+                               ctx->cell_start, ctx->sorted, ctx->sbin, ctx->wrapv);
+  const unsigned ga = (unsigned)((n + PTM_BLOCK - 1) / PTM_BLOCK);
+  CK(cudaEventRecord(ctx->ev[1], st));
+  if (f64) k_atoms<true><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
+  else k_atoms<false><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(ctx->ev[2], st));
+  ctx->last_stream = st;
+  return PTM_OK;
+}
+
+extern "C" {
+
+const char *ptm_status_string(ptm_status s) {
+  switch (s) {
+    case PTM_OK: return "PTM_OK";
+    case PTM_ERR_INVALID_ARG: return "PTM_ERR_INVALID_ARG";
+    case PTM_ERR_OUT_OF_MEMORY: return "PTM_ERR_OUT_OF_MEMORY";
+    case PTM_ERR_CUDA: return "PTM_ERR_CUDA";
+    case PTM_ERR_TIMEOUT: return "PTM_ERR_TIMEOUT";
+    case PTM_ERR_DEVICE_STATUS: return "PTM_ERR_DEVICE_STATUS";
+    case PTM_ERR_BUSY: return "PTM_ERR_BUSY";
+    case PTM_ERR_NOT_FOUND: return "PTM_ERR_NOT_FOUND";
+  }
+  return "PTM_ERR_UNKNOWN";
+}
+
+const char *ptm_last_cuda_error(ptm_context *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+ptm_status ptm_create(const ptm_options *opt, ptm_context **out) {
+  if (!out) return PTM_ERR_INVALID_ARG;
+  *out = nullptr;
+  ptm_context *ctx = new (std::nothrow) ptm_context();
+  if (!ctx) return PTM_ERR_OUT_OF_MEMORY;
+  ctx->device = opt ? opt->device : 0;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ctx->device < 0 || ctx->device >= ndev) {
+    delete ctx;
+    return e != cudaSuccess ? PTM_ERR_CUDA : PTM_ERR_INVALID_ARG;
+  }
+  ptm_status rs = PTM_OK;
+  do {
+    if ((e = cudaSetDevice(ctx->device)) != cudaSuccess) { rs = cuda_fail(ctx, e, "cudaSetDevice"); break; }
+    if ((e = cudaMalloc(&ctx->dstat, 8 * sizeof(int))) != cudaSuccess) { rs = cuda_fail(ctx, e, "cudaMalloc"); break; }
+    if ((e = cudaMalloc(&ctx->counters, C_NCOUNTERS * sizeof(unsigned long long))) != cudaSuccess) { rs = cuda_fail(ctx, e, "cudaMalloc"); break; }
+    for (int i = 0; i < 3 && e == cudaSuccess; i++) e = cudaEventCreate(&ctx->ev[i]);
+    if (e != cudaSuccess) { rs = cuda_fail(ctx, e, "cudaEventCreate"); break; }
+    if ((e = cudaMemset(ctx->counters, 0, C_NCOUNTERS * sizeof(unsigned long long))) != cudaSuccess) { rs = cuda_fail(ctx, e, "cudaMemset"); break; }
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    ctx->budget = (opt && opt->hbm_budget_bytes) ? opt->hbm_budget_bytes : fr / 2;
+    const size_t smem = atom_smem_bytes();
+    if ((e = cudaFuncSetAttribute(k_atoms<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_atoms<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) {
+      rs = cuda_fail(ctx, e, "cudaFuncSetAttribute");
+      break;
+    }
+  } while (0);
+  if (rs != PTM_OK) { ptm_destroy(ctx); return rs; }
+  *out = ctx;
+  return PTM_OK;
+}
+
+ptm_status ptm_destroy(ptm_context *ctx) {
+  if (!ctx) return PTM_ERR_INVALID_ARG;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  cudaFree(ctx->sorted); cudaFree(ctx->sbin); cudaFree(ctx->wrapv);
+  cudaFree(ctx->atom_cell); cudaFree(ctx->atom_rank); cudaFree(ctx->atom_wrap);
+  cudaFree(ctx->cell_count); cudaFree(ctx->cell_start); cudaFree(ctx->block_sums);
+  cudaFree(ctx->dstat); cudaFree(ctx->counters);
+  for (int i = 0; i < 3; i++) if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  cudaFree(ctx->hpos); cudaFree(ctx->hspecies);
+  cudaFree(ctx->o_struct); cudaFree(ctx->o_alloy); cudaFree(ctx->o_rmsd); cudaFree(ctx->o_scale);
+  cudaFree(ctx->o_quat); cudaFree(ctx->o_strain); cudaFree(ctx->o_corr);
+  delete ctx;
+  return PTM_OK;
+}
+
+ptm_status ptm_classify_frame(ptm_context *ctx, const ptm_frame *frame, const ptm_outputs *out, void *stream) {
+  if (!ctx) return PTM_ERR_INVALID_ARG;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  return enqueue_frame(ctx, frame, out, (cudaStream_t)stream);
+}
+
+ptm_status ptm_classify_frame_host(ptm_context *ctx, const ptm_frame *frame, const ptm_outputs *out,
+                                   void *stream) {
+  if (!ctx || !frame || !out) return PTM_ERR_INVALID_ARG;
+  if (frame->n_atoms < 1 || frame->n_atoms >= (1ll << 31) || !frame->positions) return PTM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaSetDevice(ctx->device));
+  const size_t n = (size_t)frame->n_atoms;
+  const size_t esz = frame->pos_dtype == PTM_F64 ? 8 : 4;
+  if (n > ctx->cap_host_atoms) {
+    cudaFree(ctx->hpos); cudaFree(ctx->hspecies);
+    cudaFree(ctx->o_struct); cudaFree(ctx->o_alloy); cudaFree(ctx->o_rmsd); cudaFree(ctx->o_scale);
+    cudaFree(ctx->o_quat); cudaFree(ctx->o_strain); cudaFree(ctx->o_corr);
+    ctx->hpos = nullptr; ctx->hspecies = nullptr; ctx->o_struct = ctx->o_alloy = nullptr;
+    ctx->o_rmsd = ctx->o_scale = ctx->o_quat = ctx->o_strain = nullptr; ctx->o_corr = nullptr;
+    ctx->cap_host_atoms = 0;
+    CK(cudaMalloc(&ctx->hpos, n * 3 * 8));
+    CK(cudaMalloc(&ctx->hspecies, n));
+    CK(cudaMalloc(&ctx->o_struct, n));
+    CK(cudaMalloc(&ctx->o_alloy, n));
+    CK(cudaMalloc(&ctx->o_rmsd, n * 4));
+    CK(cudaMalloc(&ctx->o_scale, n * 4));
+    CK(cudaMalloc(&ctx->o_quat, n * 16));
+    CK(cudaMalloc(&ctx->o_strain, n * 36));
+    CK(cudaMalloc(&ctx->o_corr, n * 60));
+    ctx->cap_host_atoms = n;
+  }
+  CK(cudaMemcpyAsync(ctx->hpos, frame->positions, n * 3 * esz, cudaMemcpyHostToDevice, st));
+  if (frame->species) CK(cudaMemcpyAsync(ctx->hspecies, frame->species, n, cudaMemcpyHostToDevice, st));
+  ptm_frame df = *frame;
+  df.positions = ctx->hpos;
+  df.species = frame->species ? ctx->hspecies : nullptr;
+  ptm_outputs dout;
+  dout.structure = out->structure ? ctx->o_struct : nullptr;
+  dout.alloy = out->alloy ? ctx->o_alloy : nullptr;
+  dout.rmsd = out->rmsd ? ctx->o_rmsd : nullptr;
+  dout.scale = out->scale ? ctx->o_scale : nullptr;
+  dout.quat = out->quat ? ctx->o_quat : nullptr;
+  dout.strain = out->strain ? ctx->o_strain : nullptr;
+  dout.correspondence = out->correspondence ? ctx->o_corr : nullptr;
+  ptm_status rs = enqueue_frame(ctx, &df, &dout, st);
+  if (rs != PTM_OK) return rs;
+  if (out->structure) CK(cudaMemcpyAsync(out->structure, dout.structure, n, cudaMemcpyDeviceToHost, st));
+  if (out->alloy) CK(cudaMemcpyAsync(out->alloy, dout.alloy, n, cudaMemcpyDeviceToHost, st));
+  if (out->rmsd) CK(cudaMemcpyAsync(out->rmsd, dout.rmsd, n * 4, cudaMemcpyDeviceToHost, st));
+  if (out->scale) CK(cudaMemcpyAsync(out->scale, dout.scale, n * 4, cudaMemcpyDeviceToHost, st));
+  if (out->quat) CK(cudaMemcpyAsync(out->quat, dout.quat, n * 16, cudaMemcpyDeviceToHost, st));
+  if (out->strain) CK(cudaMemcpyAsync(out->strain, dout.strain, n * 36, cudaMemcpyDeviceToHost, st));
+  if (out->correspondence) CK(cudaMemcpyAsync(out->correspondence, dout.correspondence, n * 60, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return PTM_OK;
+}
+
+ptm_status ptm_get_stats(ptm_context *ctx, ptm_stats *out) {
+  if (!ctx || !out) return PTM_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->last_stream));
+  unsigned long long c[C_NCOUNTERS];
+  CK(cudaMemcpy(c, ctx->counters, sizeof c, cudaMemcpyDeviceToHost));
+  float t_all = 0.f, t_atom = 0.f;
+  if (cudaEventElapsedTime(&t_all, ctx->ev[0], ctx->ev[2]) != cudaSuccess) t_all = -1.f;
+  if (cudaEventElapsedTime(&t_atom, ctx->ev[1], ctx->ev[2]) != cudaSuccess) t_atom = -1.f;
+  cudaGetLastError();
+  out->pipeline_ms = t_all;
+  out->atom_kernel_ms = t_atom;
+  out->candidates = (int64_t)c[C_CAND];
+  out->candidate_points = (int64_t)c[C_CANDPTS];
+  out->atoms = (int64_t)c[C_ATOMS];
+  out->matched = (int64_t)c[C_MATCHED];
+  out->knn_wide = (int64_t)c[C_KNN_WIDE];
+  out->knn_fail = (int64_t)c[C_KNN_FAIL];
+  out->sos = (int64_t)c[C_SOS];
+  out->qcp_fp64 = (int64_t)c[C_QCP64];
+  out->tie_fp64 = (int64_t)c[C_TIE64];
+  out->internal = (int64_t)c[C_INTERNAL];
+  return PTM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,524 @@
+// Per-atom Polyhedral Template Matching pipeline, one thread per atom.
+//
+// Larsen, Schmidt & Schiotz, "Robust Structural Identification via Polyhedral
+// Template Matching".  Steps per atom (Algorithm 1, Euclidean ordering):
+//   kNN (k = 14) under the distance contract  (Sec. 3)
+//   neighbour vectors, quantised copy for the exact hull predicates
+//   ONE incremental convex hull over neighbours 1..14; the hulls of the first
+//   6 and 12 neighbours are its intermediate states (Sec. 4)
+//   at k = 6, 12, 14: centre-inside test, canonical Weinberg code, template lookup
+//   QCP superposition of each admissible correspondence (Eq. 3-4)
+//   selection, then orientation (Sec. 7), strain (Sec. 8) and alloy (Sec. 6).
+//
+// Per-thread scratch lives in shared memory laid out [word][thread], so every
+// thread of a warp hits its own bank whatever index it uses.
+#pragma once
+#include <stdint.h>
+#include <math.h>
+
+#include "ptm_tables_gen.h"
+
+#define PTM_BLOCK 128
+#define PTM_KNN 14
+#define PTM_QBITS 19
+#define PTM_RMAX 6              // widest cell-search radius (in cells) before giving up
+#define PTM_BAND 1e-5f          // FP32 RMSD^2 band inside which candidates are re-ranked in FP64
+#define PTM_TIE 1e-12           // FP64 RMSD^2 tie window (earlier template, then smaller correspondence)
+#define PTM_GAP 0.02f           // minimum normalised P'(lambda_1) / B^3 for an FP32 QCP solution
+
+namespace ptm {
+
+struct Atom64 { double x, y, z; long long id; };
+
+// Device-resident description of one frame (filled by the host).
+struct FrameDesc {
+  const void *sorted;          // float4 (x, y, z, id bits) or Atom64, cell-sorted
+  const int *sbin;             // cell of each sorted slot
+  const int *cell_start;       // ncell + 1 offsets into sorted
+  const int *wrapv;            // packed lattice wrap per sorted slot
+  const int8_t *species;       // by atom id, or NULL
+  const void *positions;       // caller positions (by atom id)
+  int64_t n;
+  int nb[3];
+  int pbc[3];
+  int f64;
+  uint32_t mask;
+  float rmsd_max;
+  float min_cell_width;        // smallest perpendicular cell width (Angstrom)
+  double H[9];                 // rows = cell vectors
+  float s32[125][3];           // shift of image n in [-2,2]^3, FP64 value rounded to FP32
+  float slo[125][3];           // FP64 shift minus s32 (compensated neighbour vectors)
+  double s64[125][3];          // FP64 shift
+  // outputs (by atom id)
+  int8_t *structure;
+  int8_t *alloy;
+  float *rmsd;
+  float *scale;
+  float *quat;
+  float *strain;
+  int32_t *corr;
+  int *dstat;                  // [0] any atom wrapped, [1] overshoot (float bits, Angstrom)
+  unsigned long long *counters;  // ptm_stats order: atoms, matched, knn_wide, knn_fail, sos, qcp_fp64, tie_fp64, internal, candidates, candidate_points
+  int64_t work_offset;         // first work item of this frame in a batch
+};
+
+enum { C_ATOMS = 0, C_MATCHED, C_KNN_WIDE, C_KNN_FAIL, C_SOS, C_QCP64, C_TIE64, C_INTERNAL, C_CAND, C_CANDPTS, C_NCOUNTERS };
+
+__device__ __forceinline__ void count(const FrameDesc &d, int which, unsigned long long v = 1) {
+  atomicAdd(d.counters + which, v);
+}
+
+// ------------------------------------------------------------ shared scratch
+struct Scratch {
+  int *q;            // [42][B]  quantised neighbour vectors
+  uint16_t *fac;     // [24][B]  hull facets a | b << 4 | c << 8 (ccw from outside)
+  uint64_t *th;      // [14][B]  third vertex of directed edge u->v, nibble v of row u (0xF none)
+  uint16_t *used;    // [14][B]  directed-edge bit rows (hull horizon, Weinberg walk)
+  uint32_t *code;    // [10][B]  best Weinberg code so far (nibbles)
+  int t;             // thread index in block
+  __device__ __forceinline__ int &Q(int p, int c) const { return q[(3 * p + c) * PTM_BLOCK + t]; }
+  __device__ __forceinline__ uint16_t &F(int f) const { return fac[f * PTM_BLOCK + t]; }
+  __device__ __forceinline__ uint64_t &TH(int v) const { return th[v * PTM_BLOCK + t]; }
+  __device__ __forceinline__ uint16_t &U(int v) const { return used[v * PTM_BLOCK + t]; }
+  __device__ __forceinline__ uint32_t &CODE(int w) const { return code[w * PTM_BLOCK + t]; }
+};
+
+constexpr int SCRATCH_WORDS = 42 + 12 + 28 + 7 + 10;   // 32-bit words per thread
+
+// -------------------------------------------------------------- small helpers
+__device__ __forceinline__ int nib(uint64_t x, int i) { return (int)((x >> (4 * i)) & 15); }
+__device__ __forceinline__ uint64_t setnib(uint64_t x, int i, int v) {
+  return (x & ~(15ull << (4 * i))) | ((uint64_t)v << (4 * i));
+}
+
+__device__ __forceinline__ int img_pack(int a, int b, int c) {
+  return ((a + 128) << 16) | ((b + 128) << 8) | (c + 128);
+}
+__device__ __forceinline__ void img_unpack(int p, int &a, int &b, int &c) {
+  a = ((p >> 16) & 255) - 128; b = ((p >> 8) & 255) - 128; c = (p & 255) - 128;
+}
+
+// Shift of lattice image n, rounded from FP64 exactly as the contract states.
+__device__ __forceinline__ void shift_f32(const FrameDesc &d, int a, int b, int c, float &sx, float &sy,
+                                          float &sz, float &lx, float &ly, float &lz) {
+  if (a >= -2 && a <= 2 && b >= -2 && b <= 2 && c >= -2 && c <= 2) {
+    int i = (a + 2) * 25 + (b + 2) * 5 + (c + 2);
+    sx = d.s32[i][0]; sy = d.s32[i][1]; sz = d.s32[i][2];
+    lx = d.slo[i][0]; ly = d.slo[i][1]; lz = d.slo[i][2];
+  } else {
+    double s[3];
+    for (int k = 0; k < 3; k++)
+      s[k] = __dadd_rn(__dadd_rn(__dmul_rn((double)a, d.H[k]), __dmul_rn((double)b, d.H[3 + k])),
+                       __dmul_rn((double)c, d.H[6 + k]));
+    sx = (float)s[0]; sy = (float)s[1]; sz = (float)s[2];
+    lx = (float)(s[0] - (double)sx); ly = (float)(s[1] - (double)sy); lz = (float)(s[2] - (double)sz);
+  }
+}
+
+__device__ __forceinline__ void shift_f64(const FrameDesc &d, int a, int b, int c, double &sx, double &sy,
+                                          double &sz) {
+  if (a >= -2 && a <= 2 && b >= -2 && b <= 2 && c >= -2 && c <= 2) {
+    int i = (a + 2) * 25 + (b + 2) * 5 + (c + 2);
+    sx = d.s64[i][0]; sy = d.s64[i][1]; sz = d.s64[i][2];
+  } else {
+    double s[3];
+    for (int k = 0; k < 3; k++)
+      s[k] = __dadd_rn(__dadd_rn(__dmul_rn((double)a, d.H[k]), __dmul_rn((double)b, d.H[3 + k])),
+                       __dmul_rn((double)c, d.H[6 + k]));
+    sx = s[0]; sy = s[1]; sz = s[2];
+  }
+}
+
+// Error-free sum (Knuth): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// --------------------------------------------------- exact orientation + SoS
+// orient(a,b,c,p) = det[b-a; c-a; p-a] on the quantised integers.  |q| <= 2^19,
+// so differences fit 21 bits, cross products 42 bits and the determinant
+// |.| <= 3 * 2^61 < 2^63: exact in 64-bit integers.
+__device__ __forceinline__ long long orient_raw(int ax, int ay, int az, int bx, int by, int bz, int cx,
+                                                int cy, int cz, int px, int py, int pz) {
+  int ux = bx - ax, uy = by - ay, uz = bz - az;
+  int vx = cx - ax, vy = cy - ay, vz = cz - az;
+  int wx = px - ax, wy = py - ay, wz = pz - az;
+  long long nx = (long long)uy * vz - (long long)uz * vy;
+  long long ny = (long long)uz * vx - (long long)ux * vz;
+  long long nz = (long long)ux * vy - (long long)uy * vx;
+  return nx * wx + ny * wy + nz * wz;
+}
+
+// Entry (r, c) of the matrix [[q_r, 1]] for sorted row r of the four points.
+__device__ __forceinline__ long long sos_entry(const Scratch &sm, const int *pt, int r, int c) {
+  return c == 3 ? 1ll : (long long)sm.Q(pt[r], c);
+}
+
+// Simulation of Simplicity (Edelsbrunner & Muecke): coordinate c of the point of
+// neighbour rank r is perturbed by eps^(2^(3r + c)).  With the rows sorted by
+// rank, the expansion terms come in one fixed order (tables.py); the first term
+// with a nonzero minor decides.  Returns the sign of orient (never 0).
+__device__ __noinline__ int orient_sos_slow(const Scratch &sm, int a, int b, int c, int p) {
+  int pt[4] = {a, b, c, p};
+  int parity = 0;
+  for (int i = 0; i < 4; i++)
+    for (int j = 0; j < 3 - i; j++)
+      if (pt[j] > pt[j + 1]) { int t = pt[j]; pt[j] = pt[j + 1]; pt[j + 1] = t; parity ^= 1; }
+  for (int t = 0; t < PTM_SOS_NTERMS; t++) {
+    int code = ptm_sos_terms[t];
+    int kr = code & 15, kc = (code >> 4) & 15, neg = (code >> 8) & 1;
+    int rows[3], cols[3], m = 0, mc = 0;
+    for (int r = 0; r < 4; r++) if (kr >> r & 1) rows[m++] = r;
+    for (int cc = 0; cc < 4; cc++) if (kc >> cc & 1) cols[mc++] = cc;
+    long long v;
+    if (m == 0) {
+      v = 1;
+    } else if (m == 1) {
+      v = sos_entry(sm, pt, rows[0], cols[0]);
+    } else if (m == 2) {
+      v = sos_entry(sm, pt, rows[0], cols[0]) * sos_entry(sm, pt, rows[1], cols[1]) -
+          sos_entry(sm, pt, rows[0], cols[1]) * sos_entry(sm, pt, rows[1], cols[0]);
+    } else {
+      long long e[3][3];
+      for (int i = 0; i < 3; i++) for (int j = 0; j < 3; j++) e[i][j] = sos_entry(sm, pt, rows[i], cols[j]);
+      v = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) - e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+          e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+    }
+    if (v == 0) continue;
+    int s = (v > 0 ? 1 : -1) * (neg ? -1 : 1);      // sign of det of the perturbed sorted matrix
+    if (parity) s = -s;                              // back to argument order
+    return -s;                                       // orient = -det[[p, 1]]
+  }
+  return 1;   // unreachable: the last terms have minor 1
+}
+
+__device__ __forceinline__ int orient_sos(const Scratch &sm, int a, int b, int c, int p, const FrameDesc &d) {
+  long long o = orient_raw(sm.Q(a, 0), sm.Q(a, 1), sm.Q(a, 2), sm.Q(b, 0), sm.Q(b, 1), sm.Q(b, 2),
+                           sm.Q(c, 0), sm.Q(c, 1), sm.Q(c, 2), sm.Q(p, 0), sm.Q(p, 1), sm.Q(p, 2));
+  if (o > 0) return 1;
+  if (o < 0) return -1;
+  count(d, C_SOS);
+  return orient_sos_slow(sm, a, b, c, p);
+}
+
+// ------------------------------------------------------------ incremental hull
+__device__ __forceinline__ uint16_t fpack(int a, int b, int c) { return (uint16_t)(a | (b << 4) | (c << 8)); }
+
+// Tetrahedron on points 0..3, facets counter-clockwise seen from outside.
+__device__ __forceinline__ int hull_init(const Scratch &sm, const FrameDesc &d) {
+  int o = orient_sos(sm, 0, 1, 2, 3, d);
+  if (o < 0) {
+    sm.F(0) = fpack(0, 1, 2); sm.F(1) = fpack(0, 3, 1); sm.F(2) = fpack(1, 3, 2); sm.F(3) = fpack(0, 2, 3);
+  } else {
+    sm.F(0) = fpack(0, 2, 1); sm.F(1) = fpack(0, 3, 2); sm.F(2) = fpack(2, 3, 1); sm.F(3) = fpack(0, 1, 3);
+  }
+  return 4;
+}
+
+// Add point p; returns the new facet count, or -1 when p lies inside the hull.
+__device__ int hull_insert(const Scratch &sm, int nf, int p, const FrameDesc &d) {
+  uint32_t vis = 0;
+  for (int f = 0; f < nf; f++) {
+    int v = sm.F(f);
+    if (orient_sos(sm, v & 15, (v >> 4) & 15, (v >> 8) & 15, p, d) > 0) vis |= 1u << f;
+  }
+  if (!vis) return -1;
+  for (int v = 0; v < PTM_KNN; v++) sm.U(v) = 0;
+  for (uint32_t m = vis; m; m &= m - 1) {
+    int v = sm.F(__ffs(m) - 1);
+    int a = v & 15, b = (v >> 4) & 15, c = (v >> 8) & 15;
+    sm.U(a) |= 1 << b; sm.U(b) |= 1 << c; sm.U(c) |= 1 << a;
+  }
+  int n2 = 0;
+  for (int f = 0; f < nf; f++)
+    if (!(vis >> f & 1)) sm.F(n2++) = sm.F(f);
+  int added = 0;
+  for (int u = 0; u < PTM_KNN; u++) {
+    uint32_t row = sm.U(u);
+    while (row) {
+      int v = __ffs(row) - 1;
+      row &= row - 1;
+      if (!(sm.U(v) >> u & 1)) {               // horizon edge u -> v
+        if (n2 < 24) sm.F(n2) = fpack(u, v, p);
+        n2++;
+        added++;
+      }
+    }
+  }
+  // a triangulated disk of F visible facets with I interior vertices has
+  // F + 2 - 2I boundary edges; swallowed vertices simply leave the facet list
+  if (added < 3 || added > __popc(vis) + 2 || ((added - __popc(vis)) & 1) || n2 > 24) {
+    count(d, C_INTERNAL);
+    return -1;
+  }
+  return n2;
+}
+
+// ------------------------------------------------------- canonical Weinberg code
+// Walk from u -> v (rules in tables.py).  Compares the emitted labels with the
+// best code so far (cmp = 0 equal so far, 1 already smaller, -1 first walk)
+// and returns +1 when this walk is strictly smaller (it becomes the best and
+// its labelling is returned), 0 when equal, -1 when larger (aborted early).
+template <int K>
+__device__ int weinberg_walk(const Scratch &sm, int u, int v, bool first, uint64_t &labels, const FrameDesc &d) {
+  constexpr int LEN = 2 * (3 * K - 6) + 1;
+  uint64_t lab = 0;
+  for (int x = 0; x < K; x++) sm.U(x) = 0;
+  int state = first ? 1 : 0;        // 1: writing a new best; 0: still equal
+  int next = 1;
+  uint32_t wbuf = 0, wcur = 0;
+  // step 0: label of u
+  lab = setnib(lab, u, next++);
+  auto emit = [&](int s, int L) -> bool {
+    if (state == 0) {
+      if ((s & 7) == 0) wcur = sm.CODE(s >> 3);
+      int B = (wcur >> (4 * (s & 7))) & 15;
+      if (L > B) return false;
+      if (L < B) {                                   // smaller from here on: keep the
+        state = 1;                                   // equal prefix of this code word
+        wbuf = wcur & ((1u << (4 * (s & 7))) - 1u);
+      }
+    }
+    if (state == 1) {
+      wbuf |= (uint32_t)L << (4 * (s & 7));
+      if ((s & 7) == 7 || s == LEN - 1) { sm.CODE(s >> 3) = wbuf; wbuf = 0; }
+    }
+    return true;
+  };
+  emit(0, 1);
+  sm.U(u) |= 1 << v;
+  bool fresh = true;
+  lab = setnib(lab, v, next++);
+  if (!emit(1, 2)) return -1;
+  int s = 2;
+  for (; s < LEN; s++) {
+    int w;
+    uint64_t tv = sm.TH(v);
+    if (fresh) {
+      w = nib(tv, u);
+    } else if (!(sm.U(v) >> u & 1)) {
+      w = u;
+    } else {
+      w = -1;
+      int x = nib(tv, u);
+      int guard = 0;
+      while (x != u && guard++ < 16) {
+        if (!(sm.U(v) >> x & 1)) { w = x; break; }
+        x = nib(tv, x);
+      }
+      if (w < 0) break;
+    }
+    if (w >= K) { count(d, C_INTERNAL); return -1; }
+    sm.U(v) |= 1 << w;
+    u = v;
+    v = w;
+    int L = nib(lab, v);
+    fresh = (L == 0);
+    if (fresh) { L = next++; lab = setnib(lab, v, L); }
+    if (!emit(s, L)) return -1;
+  }
+  if (s != LEN) { count(d, C_INTERNAL); return -1; }
+  if (state == 1) { labels = lab; return 1; }
+  return 0;
+}
+
+// Canonical code of the current hull (K vertices): among starts with the
+// largest deg(u), then the largest deg(v), the smallest code.  Returns the
+// labelling of vertex t (nibble t) and the code hash; false on an internal error.
+template <int K>
+__device__ bool canonical(const Scratch &sm, int nf, uint64_t &labels, uint64_t &hash, const FrameDesc &d) {
+  uint64_t deg = 0;
+  for (int x = 0; x < K; x++) sm.TH(x) = ~0ull;
+  for (int f = 0; f < nf; f++) {
+    int v = sm.F(f);
+    int a = v & 15, b = (v >> 4) & 15, c = (v >> 8) & 15;
+    sm.TH(a) = setnib(sm.TH(a), b, c);
+    sm.TH(b) = setnib(sm.TH(b), c, a);
+    sm.TH(c) = setnib(sm.TH(c), a, b);
+    deg += (1ull << (4 * a)) + (1ull << (4 * b)) + (1ull << (4 * c));
+  }
+  int du = 0;
+  for (int x = 0; x < K; x++) du = max(du, nib(deg, x));
+  int dv = 0;
+  for (int x = 0; x < K; x++) {
+    if (nib(deg, x) != du) continue;
+    uint64_t tx = sm.TH(x);
+    for (int y = 0; y < K; y++)
+      if (nib(tx, y) != 15) dv = max(dv, nib(deg, y));
+  }
+  // every vertex of degree 5 with K = 12 is the icosahedron; every vertex of
+  // degree 4 with K = 6 is the octahedron: all starts are equivalent
+  bool transitive = (K == 12 && du == 5 && dv == 5) || (K == 6 && du == 4 && dv == 4);
+  bool first = true;
+  for (int x = 0; x < K; x++) {
+    if (nib(deg, x) != du) continue;
+    uint64_t tx = sm.TH(x);
+    for (int y = 0; y < K; y++) {
+      if (nib(tx, y) == 15 || nib(deg, y) != dv) continue;
+      uint64_t lab;
+      int r = weinberg_walk<K>(sm, x, y, first, lab, d);
+      if (first && r != 1) return false;
+      if (r == 1) labels = lab;
+      first = false;
+      if (transitive) goto done;
+    }
+  }
+done:
+  // hash of the packed code; words past its end count as zero, as the generator packs them
+  uint64_t h = PTM_HASH_INIT;
+  for (int w = 0; w < 10; w++) h = (h ^ (uint64_t)(w * 8 < 2 * (3 * K - 6) + 1 ? sm.CODE(w) : 0u)) * PTM_HASH_MUL;
+  hash = h;
+  return true;
+}
+
+// ------------------------------------------------------------------- QCP
+// Horn's 4x4 matrix from S_ab = sum_i w_ia v_ib (template w rotated onto data v),
+// characteristic polynomial P(l) = l^4 + c2 l^2 + c1 l + c0 with c2 = -2|S|^2,
+// c1 = -8 det S, c0 = det K (Theobald 2005), largest root by Newton from the
+// upper bound sqrt(Gv Gw) (Cauchy-Schwarz).
+template <typename T>
+struct Qcp {
+  T K[4][4];
+  T lam, dP;
+  int iters;
+};
+
+template <typename T>
+__device__ __forceinline__ void horn_matrix(const T S[3][3], T K[4][4]) {
+  K[0][0] = S[0][0] + S[1][1] + S[2][2];
+  K[0][1] = S[1][2] - S[2][1];
+  K[0][2] = S[2][0] - S[0][2];
+  K[0][3] = S[0][1] - S[1][0];
+  K[1][1] = S[0][0] - S[1][1] - S[2][2];
+  K[1][2] = S[0][1] + S[1][0];
+  K[1][3] = S[2][0] + S[0][2];
+  K[2][2] = -S[0][0] + S[1][1] - S[2][2];
+  K[2][3] = S[1][2] + S[2][1];
+  K[3][3] = -S[0][0] - S[1][1] + S[2][2];
+  K[1][0] = K[0][1]; K[2][0] = K[0][2]; K[3][0] = K[0][3];
+  K[2][1] = K[1][2]; K[3][1] = K[1][3]; K[3][2] = K[2][3];
+}
+
+template <typename T>
+__device__ __forceinline__ T det4(const T a[4][4]) {
+  // Laplace expansion over the 2x2 minors of rows 0-1 and rows 2-3
+  T s0 = a[0][0] * a[1][1] - a[1][0] * a[0][1];
+  T s1 = a[0][0] * a[1][2] - a[1][0] * a[0][2];
+  T s2 = a[0][0] * a[1][3] - a[1][0] * a[0][3];
+  T s3 = a[0][1] * a[1][2] - a[1][1] * a[0][2];
+  T s4 = a[0][1] * a[1][3] - a[1][1] * a[0][3];
+  T s5 = a[0][2] * a[1][3] - a[1][2] * a[0][3];
+  T c5 = a[2][2] * a[3][3] - a[3][2] * a[2][3];
+  T c4 = a[2][1] * a[3][3] - a[3][1] * a[2][3];
+  T c3 = a[2][1] * a[3][2] - a[3][1] * a[2][2];
+  T c2 = a[2][0] * a[3][3] - a[3][0] * a[2][3];
+  T c1 = a[2][0] * a[3][2] - a[3][0] * a[2][2];
+  T c0 = a[2][0] * a[3][1] - a[3][0] * a[2][1];
+  return s0 * c5 - s1 * c4 + s2 * c3 + s3 * c2 - s4 * c1 + s5 * c0;
+}
+
+template <typename T>
+__device__ __forceinline__ T det3(const T m[3][3]) {
+  return m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+         m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+}
+
+template <typename T>
+__device__ void qcp_solve(const T S[3][3], T Gv, T Gw, Qcp<T> &o) {
+  horn_matrix<T>(S, o.K);
+  T n2 = 0;
+  for (int a = 0; a < 3; a++) for (int b = 0; b < 3; b++) n2 += S[a][b] * S[a][b];
+  T c2 = T(-2) * n2;
+  T c1 = T(-8) * det3<T>(S);
+  T c0 = det4<T>(o.K);
+  T lam = sqrt(Gv * Gw);
+  const T tol = sizeof(T) == 4 ? T(1e-7) : T(1e-15);
+  T dP = 0;
+  int it = 0;
+  for (; it < 60; it++) {
+    T l2 = lam * lam;
+    T P = (l2 + c2) * l2 + c1 * lam + c0;
+    dP = (T(4) * l2 + T(2) * c2) * lam + c1;
+    if (!(dP > T(0))) break;
+    T delta = P / dP;
+    lam -= delta;
+    if (fabs(delta) <= tol * lam) { it++; break; }
+  }
+  T l2 = lam * lam;
+  o.dP = (T(4) * l2 + T(2) * c2) * lam + c1;
+  o.lam = lam;
+  o.iters = it;
+}
+
+// Unit quaternion of the largest eigenvalue: the column of adj(K - lam I) with
+// the largest norm (all nonzero columns are parallel to the eigenvector).
+template <typename T>
+__device__ void qcp_quat(const T K[4][4], T lam, T q[4]) {
+  T A[4][4];
+  for (int i = 0; i < 4; i++) for (int j = 0; j < 4; j++) A[i][j] = K[i][j] - (i == j ? lam : T(0));
+  T best = -1;
+  for (int c = 0; c < 4; c++) {
+    T col[4];
+    for (int r = 0; r < 4; r++) {
+      // cofactor (c, r): delete row c and column r
+      T m[3][3];
+      int ii = 0;
+      for (int i = 0; i < 4; i++) {
+        if (i == c) continue;
+        int jj = 0;
+        for (int j = 0; j < 4; j++) { if (j == r) continue; m[ii][jj++] = A[i][j]; }
+        ii++;
+      }
+      T v = det3<T>(m);
+      col[r] = ((c + r) & 1) ? -v : v;
+    }
+    T nn = col[0] * col[0] + col[1] * col[1] + col[2] * col[2] + col[3] * col[3];
+    if (nn > best) { best = nn; for (int r = 0; r < 4; r++) q[r] = col[r]; }
+  }
+  T inv = T(1) / sqrt(best > T(0) ? best : T(1));
+  if (!(best > T(0))) { q[0] = 1; q[1] = q[2] = q[3] = 0; inv = 1; }
+  T sgn = q[0] < T(0) ? T(-1) : T(1);
+  for (int r = 0; r < 4; r++) q[r] *= inv * sgn;
+}
+
+template <typename T>
+__device__ __forceinline__ void quat_matrix(const T q[4], T R[3][3]) {
+  T w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0][0] = 1 - 2 * (y * y + z * z); R[0][1] = 2 * (x * y - w * z); R[0][2] = 2 * (x * z + w * y);
+  R[1][0] = 2 * (x * y + w * z); R[1][1] = 1 - 2 * (x * x + z * z); R[1][2] = 2 * (y * z - w * x);
+  R[2][0] = 2 * (x * z - w * y); R[2][1] = 2 * (y * z + w * x); R[2][2] = 1 - 2 * (x * x + y * y);
+}
+
+// Cyclic Jacobi eigen-decomposition of a symmetric 3x3 matrix (FP32).
+__device__ void jacobi3(float a[3][3], float v[3][3]) {
+  for (int i = 0; i < 3; i++) for (int j = 0; j < 3; j++) v[i][j] = (i == j) ? 1.f : 0.f;
+  for (int sweep = 0; sweep < 10; sweep++) {
+    float off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+    float dg = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+    if (off <= 1e-16f * dg) break;
+#pragma unroll
+    for (int pq = 0; pq < 3; pq++) {
+      int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+      if (a[p][q] == 0.f) continue;
+      float theta = (a[q][q] - a[p][p]) / (2.f * a[p][q]);
+      float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+      float c = rsqrtf(t * t + 1.f), s = t * c;
+      for (int k = 0; k < 3; k++) {
+        float akp = a[k][p], akq = a[k][q];
+        a[k][p] = c * akp - s * akq; a[k][q] = s * akp + c * akq;
+      }
+      for (int k = 0; k < 3; k++) {
+        float apk = a[p][k], aqk = a[q][k];
+        a[p][k] = c * apk - s * aqk; a[q][k] = s * apk + c * aqk;
+      }
+      for (int k = 0; k < 3; k++) {
+        float vkp = v[k][p], vkq = v[k][q];
+        v[k][p] = c * vkp - s * vkq; v[k][q] = s * vkp + c * vkq;
+      }
+    }
+  }
+}
+
+}  // namespace ptm

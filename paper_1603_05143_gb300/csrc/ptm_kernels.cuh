@@ -1,0 +1,804 @@
+// Device code of libptm.so: the per-atom classification and the cell-list
+// kernels (Larsen, Schmidt & Schiotz, "Robust Structural Identification via
+// Polyhedral Template Matching").
+//
+// Device pipeline for one frame, all on the caller's stream:
+//   k_bin      fractional coordinates, cell of each atom (cell list)
+//   k_scan_*   exclusive scan of the cell counts
+//   k_scatter  atoms copied into cell order as float4 (x, y, z, id)
+//   k_atoms    one thread per atom: kNN .. outputs
+#pragma once
+#include "ptm_atom.cuh"
+#include "../../include/ptm.h"
+
+namespace ptm {
+
+template <bool F64> struct RT { typedef float T; };
+template <> struct RT<true> { typedef double T; };
+
+__device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+template <typename T>
+__device__ __forceinline__ bool key_less(T da, int ia, int ma, T db, int ib, int mb) {
+  return da < db || (da == db && (ia < ib || (ia == ib && ma < mb)));
+}
+
+template <bool F64>
+__device__ __forceinline__ void load_atom(const FrameDesc &d, int j, typename RT<F64>::T &x,
+                                          typename RT<F64>::T &y, typename RT<F64>::T &z, int &id) {
+  if constexpr (F64) {
+    const Atom64 *a = (const Atom64 *)d.sorted + j;
+    double2 p = __ldg((const double2 *)a);
+    double2 q = __ldg((const double2 *)a + 1);
+    x = p.x; y = p.y; z = q.x; id = (int)__double_as_longlong(q.y);
+  } else {
+    float4 p = __ldg((const float4 *)d.sorted + j);
+    x = p.x; y = p.y; z = p.z; id = __float_as_int(p.w);
+  }
+}
+
+// Contract shift of image (a, b, c) in the input precision.
+template <bool F64>
+__device__ __forceinline__ void contract_shift(const FrameDesc &d, int a, int b, int c, typename RT<F64>::T &sx,
+                                               typename RT<F64>::T &sy, typename RT<F64>::T &sz) {
+  if constexpr (F64) {
+    shift_f64(d, a, b, c, sx, sy, sz);
+  } else {
+    float lx, ly, lz;
+    shift_f32(d, a, b, c, sx, sy, sz, lx, ly, lz);
+  }
+}
+
+// The distance contract (Sec. 3 ordering, reading R4): in the input precision,
+// one rounded operation at a time, no fused multiply-add:
+//   dr = (x_j - x_i) + shift,  d2 = (dr_x^2 + dr_y^2) + dr_z^2
+__device__ __forceinline__ float contract_dr(float xj, float xi, float s) { return __fadd_rn(__fsub_rn(xj, xi), s); }
+__device__ __forceinline__ double contract_dr(double xj, double xi, double s) { return __dadd_rn(__dsub_rn(xj, xi), s); }
+__device__ __forceinline__ float contract_d2(float a, float b, float c) {
+  return __fadd_rn(__fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b)), __fmul_rn(c, c));
+}
+__device__ __forceinline__ double contract_d2(double a, double b, double c) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(c, c));
+}
+
+// ----------------------------------------------------------------- kNN
+// The 14 nearest images of atom s by (d2, atom id, image), scanning the
+// (2R+1)^3 cells around it; R grows until the 14th distance lies inside the
+// radius the scanned cells are guaranteed to cover.  Returns the neighbour
+// count (14, fewer only for a small fully non-periodic system) or -1.
+template <bool F64>
+__device__ int knn(const FrameDesc &d, int s, typename RT<F64>::T xi, typename RT<F64>::T yi,
+                   typename RT<F64>::T zi, int bx, int by, int bz, int wix, int wiy, int wiz, bool wrapped,
+                   typename RT<F64>::T (&Ld2)[PTM_KNN], int (&Lid)[PTM_KNN], int (&Ljs)[PTM_KNN],
+                   int (&Limg)[PTM_KNN]) {
+  typedef typename RT<F64>::T T;
+  const int nbx = d.nb[0], nby = d.nb[1], nbz = d.nb[2];
+  const float over = __int_as_float(d.dstat[1]);
+  const T INF = (T)INFINITY;
+  for (int R = 1; R <= PTM_RMAX; R++) {
+#pragma unroll
+    for (int t = 0; t < PTM_KNN; t++) { Ld2[t] = INF; Lid[t] = 0x7fffffff; Ljs[t] = -1; Limg[t] = 0x7fffffff; }
+    for (int dx = -R; dx <= R; dx++) {
+      int cx = bx + dx, mx = 0;
+      if (d.pbc[0]) { mx = floordiv(cx, nbx); cx -= mx * nbx; } else if (cx < 0 || cx >= nbx) continue;
+      for (int dy = -R; dy <= R; dy++) {
+        int cy = by + dy, my = 0;
+        if (d.pbc[1]) { my = floordiv(cy, nby); cy -= my * nby; } else if (cy < 0 || cy >= nby) continue;
+        for (int dz = -R; dz <= R; dz++) {
+          int cz = bz + dz, mz = 0;
+          if (d.pbc[2]) { mz = floordiv(cz, nbz); cz -= mz * nbz; } else if (cz < 0 || cz >= nbz) continue;
+          int c = (cx * nby + cy) * nbz + cz;
+          int j0 = __ldg(d.cell_start + c), j1 = __ldg(d.cell_start + c + 1);
+          if (j0 == j1) continue;
+          const int n0 = mx + wix, n1 = my + wiy, n2 = mz + wiz;
+          T sx, sy, sz;
+          contract_shift<F64>(d, n0, n1, n2, sx, sy, sz);
+          for (int j = j0; j < j1; j++) {
+            T xj, yj, zj;
+            int idj;
+            load_atom<F64>(d, j, xj, yj, zj, idj);
+            int a0 = n0, a1 = n1, a2 = n2;
+            if (wrapped) {
+              int wj = __ldg(d.wrapv + j);
+              int w0, w1, w2;
+              img_unpack(wj, w0, w1, w2);
+              a0 -= w0; a1 -= w1; a2 -= w2;
+              contract_shift<F64>(d, a0, a1, a2, sx, sy, sz);
+            }
+            if (j == s && a0 == 0 && a1 == 0 && a2 == 0) continue;
+            T ex = contract_dr(xj, xi, sx), ey = contract_dr(yj, yi, sy), ez = contract_dr(zj, zi, sz);
+            T d2 = contract_d2(ex, ey, ez);
+            if (!(d2 <= Ld2[PTM_KNN - 1])) continue;
+            int img = img_pack(a0, a1, a2);
+            if (!key_less(d2, idj, img, Ld2[PTM_KNN - 1], Lid[PTM_KNN - 1], Limg[PTM_KNN - 1])) continue;
+            // insertion into the sorted list (all indices static: stays in registers)
+            bool above = true;
+#pragma unroll
+            for (int t = PTM_KNN - 1; t >= 1; t--) {
+              bool lt = key_less(d2, idj, img, Ld2[t - 1], Lid[t - 1], Limg[t - 1]);
+              if (lt) { Ld2[t] = Ld2[t - 1]; Lid[t] = Lid[t - 1]; Ljs[t] = Ljs[t - 1]; Limg[t] = Limg[t - 1]; }
+              else if (above) { Ld2[t] = d2; Lid[t] = idj; Ljs[t] = j; Limg[t] = img; }
+              above = lt;
+            }
+            if (above) { Ld2[0] = d2; Lid[0] = idj; Ljs[0] = j; Limg[0] = img; }
+          }
+        }
+      }
+    }
+    float rg = (float)R * d.min_cell_width - over;
+    if (rg > 0.f && (float)Ld2[PTM_KNN - 1] < rg * rg * (1.f - 1e-3f)) {
+      if (R > 1) count(d, C_KNN_WIDE);
+      return PTM_KNN;
+    }
+    if (!d.pbc[0] && !d.pbc[1] && !d.pbc[2] && R >= max(nbx, max(nby, nbz))) {
+      int cnt = 0;
+#pragma unroll
+      for (int t = 0; t < PTM_KNN; t++) cnt += Ljs[t] >= 0;
+      return cnt;
+    }
+  }
+  count(d, C_KNN_FAIL);
+  return -1;
+}
+
+// ---------------------------------------------------------- per-atom state
+struct Best {
+  float b1, b2;       // best and second-best FP32 RMSD^2
+  int K, cand;        // winning snapshot (6, 12, 14) and candidate index
+  int fp64;           // winner's eigenvalue needed the FP64 solve
+  uint64_t lam[3];    // canonical labelling per snapshot (k = 6, 12, 14)
+  int ent[3];         // table entry per snapshot, -1 = none
+};
+
+__device__ __forceinline__ int snap_index(int K) { return K == 6 ? 0 : (K == 12 ? 1 : 2); }
+
+template <int K>
+__device__ __forceinline__ int lookup(const Scratch &sm, uint64_t h) {
+  constexpr int LEN = 2 * (3 * K - 6) + 1;
+  constexpr int NW = (LEN + 7) / 8;
+  int pos = (int)(h & (PTM_TBL_NSLOTS - 1));
+  for (int probe = 0; probe < PTM_TBL_NSLOTS; probe++) {
+    const ptm_tbl_entry *e = &ptm_tbl[pos];
+    uint64_t eh = __ldg((const unsigned long long *)&e->hash);
+    int cntv = __ldg(&e->count);
+    if (eh == 0 && cntv == 0) return -1;
+    if (eh == h && __ldg(&e->nv) == K) {
+      bool eq = true;
+#pragma unroll
+      for (int w = 0; w < NW; w++) eq &= (__ldg(&e->code[w]) == sm.CODE(w));
+      if (eq) return pos;
+    }
+    pos = (pos + 1) & (PTM_TBL_NSLOTS - 1);
+  }
+  return -1;
+}
+
+// S_ab = sum_j w_{slot(j), a} dr_{j, b} for the correspondence "neighbour rank j ->
+// template slot" given by the canonical labelling and the table candidate.
+// Because the template barycentre is the origin and slot 0 (the centre) sits at
+// it, the data barycentre drops out of S.
+template <int K>
+__device__ __forceinline__ void cov_matrix(const float4 *tplw, int S, uint64_t lab, uint64_t cand,
+                                           const float (&dx)[PTM_KNN], const float (&dy)[PTM_KNN],
+                                           const float (&dz)[PTM_KNN], float (&Sm)[3][3]) {
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = 0; b < 3; b++) Sm[a][b] = 0.f;
+#pragma unroll
+  for (int j = 0; j < K; j++) {
+    int L = nib(lab, j);
+    int slot = nib(cand, L - 1);
+    float4 w = tplw[S * 15 + slot];
+    Sm[0][0] = fmaf(w.x, dx[j], Sm[0][0]); Sm[0][1] = fmaf(w.x, dy[j], Sm[0][1]); Sm[0][2] = fmaf(w.x, dz[j], Sm[0][2]);
+    Sm[1][0] = fmaf(w.y, dx[j], Sm[1][0]); Sm[1][1] = fmaf(w.y, dy[j], Sm[1][1]); Sm[1][2] = fmaf(w.y, dz[j], Sm[1][2]);
+    Sm[2][0] = fmaf(w.z, dx[j], Sm[2][0]); Sm[2][1] = fmaf(w.z, dy[j], Sm[2][1]); Sm[2][2] = fmaf(w.z, dz[j], Sm[2][2]);
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void data_moments(const float (&dx)[PTM_KNN], const float (&dy)[PTM_KNN],
+                                             const float (&dz)[PTM_KNN], float &mx, float &my, float &mz,
+                                             float &Gv) {
+  float sx = 0, sy = 0, sz = 0, g = 0;
+#pragma unroll
+  for (int j = 0; j < K; j++) {
+    sx += dx[j]; sy += dy[j]; sz += dz[j];
+    g = fmaf(dx[j], dx[j], fmaf(dy[j], dy[j], fmaf(dz[j], dz[j], g)));
+  }
+  const float inv = 1.f / (float)(K + 1);
+  mx = sx * inv; my = sy * inv; mz = sz * inv;
+  Gv = g - (float)(K + 1) * (mx * mx + my * my + mz * mz);
+}
+
+// RMSD^2 of one candidate from its covariance (closed form after Eq. 3); the
+// FP32 Newton solution is replaced by an FP64 one when the top eigenvalue is
+// not well separated (normalised P'(lambda_1) below PTM_GAP).
+__device__ __noinline__ float r2_fp64(const float (&Sm)[3][3], float Gv, float Gw, int N) {
+  double S[3][3];
+  for (int a = 0; a < 3; a++) for (int b = 0; b < 3; b++) S[a][b] = Sm[a][b];
+  Qcp<double> o;
+  qcp_solve<double>(S, (double)Gv, (double)Gw, o);
+  return (float)(((double)Gw - o.lam * o.lam / (double)Gv) / N);
+}
+
+__device__ __forceinline__ float cand_r2(const float (&Sm)[3][3], float Gv, float Gw, int N, int &fp64,
+                                         const FrameDesc &d) {
+  Qcp<float> o;
+  qcp_solve<float>(Sm, Gv, Gw, o);
+  float B = sqrtf(Gv * Gw);
+  float gamma = o.dP / (B * B * B);
+  if (!(gamma >= PTM_GAP) || o.iters >= 60) {
+    fp64 = 1;
+    count(d, C_QCP64);
+    return fmaxf(r2_fp64(Sm, Gv, Gw, N), 0.f);
+  }
+  fp64 = 0;
+  return fmaxf((Gw - o.lam * o.lam / Gv) / (float)N, 0.f);
+}
+
+// Hull of the first K neighbours is complete: centre test, canonical code,
+// lookup and QCP of every admissible correspondence (Algorithm 1, inner loops).
+template <int K>
+__device__ void snapshot(const Scratch &sm, const FrameDesc &d, const float4 *tplw, int nf,
+                         const float (&dx)[PTM_KNN], const float (&dy)[PTM_KNN], const float (&dz)[PTM_KNN],
+                         Best &bst) {
+  if (nf != 2 * K - 4) return;                    // a neighbour is not a hull vertex
+  for (int f = 0; f < nf; f++) {                  // centre strictly inside (exact, no SoS)
+    int v = sm.F(f);
+    int a = v & 15, b = (v >> 4) & 15, c = (v >> 8) & 15;
+    long long o = orient_raw(sm.Q(a, 0), sm.Q(a, 1), sm.Q(a, 2), sm.Q(b, 0), sm.Q(b, 1), sm.Q(b, 2),
+                             sm.Q(c, 0), sm.Q(c, 1), sm.Q(c, 2), 0, 0, 0);
+    if (o >= 0) return;
+  }
+  uint64_t lab = 0, h = 0;
+  if (!canonical<K>(sm, nf, lab, h, d)) return;
+  int e = lookup<K>(sm, h);
+  if (e < 0) return;
+  const int si = snap_index(K);
+  bst.lam[si] = lab;
+  bst.ent[si] = e;
+  float mx, my, mz, Gv;
+  data_moments<K>(dx, dy, dz, mx, my, mz, Gv);
+  const int first = __ldg(&ptm_tbl[e].first), cnt = __ldg(&ptm_tbl[e].count);
+  int scored = 0;
+  for (int c = first; c < first + cnt; c++) {
+    uint64_t cand = __ldg((const unsigned long long *)&ptm_cand[c]);
+    int S = (int)(cand >> 60) & 7;
+    if (!(d.mask >> S & 1)) continue;
+    scored++;
+    float Sm[3][3];
+    cov_matrix<K>(tplw, S, lab, cand, dx, dy, dz, Sm);
+    float Gw = tplw[S * 15].w;
+    int fp64;
+    float r2 = cand_r2(Sm, Gv, Gw, K + 1, fp64, d);
+    if (r2 < bst.b1) { bst.b2 = bst.b1; bst.b1 = r2; bst.K = K; bst.cand = c; bst.fp64 = fp64; }
+    else if (r2 < bst.b2) bst.b2 = r2;
+  }
+  if (scored) { count(d, C_CAND, scored); count(d, C_CANDPTS, (unsigned long long)scored * (K + 1)); }
+}
+
+// Canonical correspondence (reading R12): nibble 15 - s holds the neighbour rank
+// of template slot s; the orbit minimum under the template rotation group, read
+// slot 1 first, is the numerically smallest packing.
+__device__ uint64_t canonical_corr(int S, int K, uint64_t corr) {
+  uint64_t best = ~0ull;
+  const int g0 = ptm_group_off[S], g1 = ptm_group_off[S + 1];
+  for (int g = g0; g < g1; g++) {
+    uint64_t cur = 0;
+    for (int s = 1; s <= K; s++) cur |= (uint64_t)nib(corr, 15 - ptm_group_perm[g][s]) << (4 * (15 - s));
+    best = cur < best ? cur : best;
+  }
+  return best;
+}
+
+template <int K>
+__device__ __forceinline__ uint64_t corr_of(uint64_t lab, uint64_t cand) {
+  uint64_t corr = 0;
+#pragma unroll
+  for (int j = 0; j < K; j++) {
+    int slot = nib(cand, nib(lab, j) - 1);
+    corr |= (uint64_t)(j + 1) << (4 * (15 - slot));
+  }
+  return corr;
+}
+
+__device__ __forceinline__ uint64_t corr_of_k(int K, uint64_t lab, uint64_t cand) {
+  return K == 6 ? corr_of<6>(lab, cand) : (K == 12 ? corr_of<12>(lab, cand) : corr_of<14>(lab, cand));
+}
+
+// Rare path: the best FP32 candidates lie within PTM_BAND.  Every candidate is
+// re-scored in FP64 from neighbour vectors recomputed in FP64 from the input
+// positions; ties within PTM_TIE go to the earlier template, then to the smaller
+// canonical correspondence (reading R13).
+template <bool F64>
+__device__ __noinline__ void rerank_fp64(const FrameDesc &d, int s, Best &bst, int bx, int by, int bz, int wix,
+                                         int wiy, int wiz, bool wrapped) {
+  typedef typename RT<F64>::T T;
+  T xi, yi, zi;
+  int idi;
+  load_atom<F64>(d, s, xi, yi, zi, idi);
+  T Ld2[PTM_KNN];
+  int Lid[PTM_KNN], Ljs[PTM_KNN], Limg[PTM_KNN];
+  int cnt = knn<F64>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, Ld2, Lid, Ljs, Limg);
+  if (cnt < 0) return;
+  double ex[PTM_KNN], ey[PTM_KNN], ez[PTM_KNN];
+  for (int t = 0; t < cnt; t++) {
+    T xj, yj, zj;
+    int idj;
+    load_atom<F64>(d, Ljs[t], xj, yj, zj, idj);
+    int a, b, c;
+    img_unpack(Limg[t], a, b, c);
+    double sx, sy, sz;
+    shift_f64(d, a, b, c, sx, sy, sz);
+    ex[t] = ((double)xj - (double)xi) + sx;
+    ey[t] = ((double)yj - (double)yi) + sy;
+    ez[t] = ((double)zj - (double)zi) + sz;
+  }
+  double best_r2 = INFINITY;
+  int bK = -1, bc = -1, bS = 99;
+  uint64_t bcp = ~0ull;
+  double r2s[3 * 64];
+  int nr = 0;
+  (void)nr;
+  // pass 1: FP64 score of every candidate
+  for (int pass = 0; pass < 2; pass++) {
+    for (int si = 0; si < 3; si++) {
+      const int K = si == 0 ? 6 : (si == 1 ? 12 : 14);
+      int e = bst.ent[si];
+      if (e < 0) continue;
+      uint64_t lab = bst.lam[si];
+      double m[3] = {0, 0, 0}, g = 0;
+      for (int j = 0; j < K; j++) { m[0] += ex[j]; m[1] += ey[j]; m[2] += ez[j]; g += ex[j] * ex[j] + ey[j] * ey[j] + ez[j] * ez[j]; }
+      for (int c = 0; c < 3; c++) m[c] /= (K + 1);
+      double Gv = g - (K + 1) * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+      const int first = ptm_tbl[e].first, ncand = ptm_tbl[e].count;
+      for (int ci = first; ci < first + ncand; ci++) {
+        uint64_t cand = ptm_cand[ci];
+        int S = (int)(cand >> 60) & 7;
+        if (!(d.mask >> S & 1)) continue;
+        double Sm[3][3] = {{0}}, Gw = 0;
+        for (int j = 0; j < K; j++) {
+          int slot = nib(cand, nib(lab, j) - 1);
+          const double *w = ptm_tpl64[S][slot];
+          Sm[0][0] += w[0] * ex[j]; Sm[0][1] += w[0] * ey[j]; Sm[0][2] += w[0] * ez[j];
+          Sm[1][0] += w[1] * ex[j]; Sm[1][1] += w[1] * ey[j]; Sm[1][2] += w[1] * ez[j];
+          Sm[2][0] += w[2] * ex[j]; Sm[2][1] += w[2] * ey[j]; Sm[2][2] += w[2] * ez[j];
+        }
+        for (int slot = 0; slot <= K; slot++)
+          Gw += ptm_tpl64[S][slot][0] * ptm_tpl64[S][slot][0] + ptm_tpl64[S][slot][1] * ptm_tpl64[S][slot][1] +
+                ptm_tpl64[S][slot][2] * ptm_tpl64[S][slot][2];
+        Qcp<double> o;
+        qcp_solve<double>(Sm, Gv, Gw, o);
+        double r2 = fmax((Gw - o.lam * o.lam / Gv) / (K + 1), 0.0);
+        if (pass == 0) {
+          best_r2 = fmin(best_r2, r2);
+        } else if (r2 <= best_r2 + PTM_TIE) {
+          uint64_t cp = canonical_corr(S, K, corr_of_k(K, lab, cand));
+          if (S < bS || (S == bS && cp < bcp)) { bS = S; bcp = cp; bK = K; bc = ci; }
+        }
+      }
+    }
+  }
+  (void)r2s;
+  if (bK > 0) { bst.K = bK; bst.cand = bc; }
+}
+
+// ------------------------------------------------------------ finalisation
+template <int K>
+__device__ void finalize(const FrameDesc &d, const Scratch &sm, const float4 *tplw, const Best &bst, int idi,
+                         const float (&dx)[PTM_KNN], const float (&dy)[PTM_KNN], const float (&dz)[PTM_KNN],
+                         const int (&nid)[PTM_KNN]) {
+  const int si = snap_index(K);
+  const uint64_t lab = bst.lam[si];
+  const uint64_t cand = __ldg((const unsigned long long *)&ptm_cand[bst.cand]);
+  const int S = (int)(cand >> 60) & 7;
+  float Sm[3][3];
+  cov_matrix<K>(tplw, S, lab, cand, dx, dy, dz, Sm);
+  float mx, my, mz, Gv;
+  data_moments<K>(dx, dy, dz, mx, my, mz, Gv);
+  const float Gw = tplw[S * 15].w;
+  float lam, q[4];
+  {
+    Qcp<float> o;
+    qcp_solve<float>(Sm, Gv, Gw, o);
+    float B = sqrtf(Gv * Gw);
+    if (bst.fp64 || !(o.dP / (B * B * B) >= PTM_GAP)) {
+      double S64[3][3];
+      for (int a = 0; a < 3; a++) for (int b = 0; b < 3; b++) S64[a][b] = Sm[a][b];
+      Qcp<double> o64;
+      qcp_solve<double>(S64, (double)Gv, (double)Gw, o64);
+      double q64[4];
+      qcp_quat<double>(o64.K, o64.lam, q64);
+      lam = (float)o64.lam;
+      for (int i = 0; i < 4; i++) q[i] = (float)q64[i];
+    } else {
+      qcp_quat<float>(o.K, o.lam, q);
+      lam = o.lam;
+    }
+  }
+  const float s = lam / Gv;
+  float R[3][3];
+  quat_matrix<float>(q, R);
+  // explicit residual of Eq. 3 at the optimum (avoids the cancellation of the
+  // closed form near RMSD 0); the centre pairs with template slot 0 (origin)
+  float r2 = 0.f;
+  {
+    float ux = -s * mx, uy = -s * my, uz = -s * mz;
+    r2 = ux * ux + uy * uy + uz * uz;
+  }
+  float lsum = sqrtf(mx * mx + my * my + mz * mz);
+  uint64_t corr = 0;
+#pragma unroll
+  for (int j = 0; j < K; j++) {
+    int slot = nib(cand, nib(lab, j) - 1);
+    float4 w = tplw[S * 15 + slot];
+    float vx = dx[j] - mx, vy = dy[j] - my, vz = dz[j] - mz;
+    float rx = R[0][0] * w.x + R[0][1] * w.y + R[0][2] * w.z;
+    float ry = R[1][0] * w.x + R[1][1] * w.y + R[1][2] * w.z;
+    float rz = R[2][0] * w.x + R[2][1] * w.y + R[2][2] * w.z;
+    float ex = s * vx - rx, ey = s * vy - ry, ez = s * vz - rz;
+    r2 += ex * ex + ey * ey + ez * ez;
+    lsum += sqrtf(vx * vx + vy * vy + vz * vz);
+    corr |= (uint64_t)(j + 1) << (4 * (15 - slot));
+  }
+  const float rmsd = sqrtf(r2 / (float)(K + 1));
+  const int64_t a = idi;
+  if (!(rmsd <= d.rmsd_max)) {
+    // unmatched after the RMSD_max cut (Sec. 5.1)
+    if (d.structure) d.structure[a] = PTM_NONE;
+    if (d.alloy) d.alloy[a] = PTM_ALLOY_NONE;
+    if (d.rmsd) d.rmsd[a] = INFINITY;
+    if (d.scale) d.scale[a] = 0.f;
+    if (d.quat) { d.quat[4 * a] = 1.f; d.quat[4 * a + 1] = 0.f; d.quat[4 * a + 2] = 0.f; d.quat[4 * a + 3] = 0.f; }
+    if (d.strain) for (int i = 0; i < 9; i++) d.strain[9 * a + i] = 0.f;
+    if (d.corr) for (int i = 0; i < 15; i++) d.corr[15 * a + i] = -1;
+    return;
+  }
+  count(d, C_MATCHED);
+  // correspondence: smallest member of its orbit (R12), atom ids per slot
+  const uint64_t cp = canonical_corr(S, K, corr);
+  for (int j = 0; j < K; j++) sm.Q(j, 0) = nid[j];
+  if (d.structure) d.structure[a] = (int8_t)(S + 1);
+  if (d.rmsd) d.rmsd[a] = rmsd;
+  if (d.scale) d.scale[a] = s;
+  if (d.corr) {
+    d.corr[15 * a] = idi;
+    for (int sl = 1; sl < 15; sl++) d.corr[15 * a + sl] = sl <= K ? sm.Q(nib(cp, 15 - sl) - 1, 0) : -1;
+  }
+  // orientation in the fundamental zone: the equivalent rotation Q g with the
+  // largest |w| (smallest angle); ties keep the earlier group element (Sec. 7)
+  if (d.quat) {
+    float bw = -1.f, bq[4] = {1.f, 0.f, 0.f, 0.f};
+    for (int g = ptm_group_off[S]; g < ptm_group_off[S + 1]; g++) {
+      const float *gq = ptm_group_quat[g];
+      float o0 = q[0] * gq[0] - q[1] * gq[1] - q[2] * gq[2] - q[3] * gq[3];
+      if (fabsf(o0) > bw) {
+        bw = fabsf(o0);
+        bq[0] = o0;
+        bq[1] = q[0] * gq[1] + q[1] * gq[0] + q[2] * gq[3] - q[3] * gq[2];
+        bq[2] = q[0] * gq[2] - q[1] * gq[3] + q[2] * gq[0] + q[3] * gq[1];
+        bq[3] = q[0] * gq[3] + q[1] * gq[2] - q[2] * gq[1] + q[3] * gq[0];
+      }
+    }
+    float sg = bq[0] < 0.f ? -1.f : 1.f;
+    for (int i = 0; i < 4; i++) d.quat[4 * a + i] = sg * bq[i];
+  }
+  // strain (Sec. 8, Eq. 6-7): both sets barycentred and scaled to mean distance
+  // 1; the isotropic templates give pinv(V) = V^T / (G_w / 3), so
+  // A = 3 S^T / (G_w l_data); then P = (A A^T)^(1/2), U proper.
+  if (d.strain) {
+    const float ldat = lsum / (float)(K + 1);
+    const float f = 3.f / (Gw * ldat);
+    float A[3][3], AA[3][3], X[3][3];
+    for (int i = 0; i < 3; i++) for (int j = 0; j < 3; j++) A[i][j] = f * Sm[j][i];
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++) AA[i][j] = A[i][0] * A[j][0] + A[i][1] * A[j][1] + A[i][2] * A[j][2];
+    jacobi3(AA, X);
+    float sig[3];
+    int imin = 0;
+    for (int i = 0; i < 3; i++) { sig[i] = sqrtf(fmaxf(AA[i][i], 0.f)); if (sig[i] < sig[imin]) imin = i; }
+    if (det3<float>(A) < 0.f) sig[imin] = -sig[imin];
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++)
+        d.strain[9 * a + 3 * i + j] = X[i][0] * sig[0] * X[j][0] + X[i][1] * sig[1] * X[j][1] + X[i][2] * sig[2] * X[j][2];
+  }
+  // binary alloy label (Sec. 6, Table 3)
+  if (d.alloy) {
+    int8_t lab8 = PTM_ALLOY_NONE;
+    if (d.species && (S == 1 || S == 4)) {
+      const int8_t c = __ldg(d.species + a);
+      auto same = [&](int sl) { return __ldg(d.species + sm.Q(nib(cp, 15 - sl) - 1, 0)) == c; };
+      if (S == 1) {          // FCC: slots 1-4 in z = 0, 5-8 in y = 0, 9-12 in x = 0
+        int sp = 0, op = 0;
+        for (int p = 0; p < 3; p++) {
+          int n = 0;
+          for (int sl = 1 + 4 * p; sl <= 4 + 4 * p; sl++) n += same(sl);
+          sp += n == 4;
+          op += n == 0;
+        }
+        if (sp == 3) lab8 = PTM_ALLOY_PURE;
+        else if (sp == 1 && op == 2) lab8 = PTM_ALLOY_L10;
+        else if (sp == 2 && op == 1) lab8 = PTM_ALLOY_L12_MAJ;
+        else if (op == 3) lab8 = PTM_ALLOY_L12_MIN;
+      } else {               // BCC: slots 1-8 first shell, 9-14 second shell
+        int in = 0, out = 0;
+        for (int sl = 1; sl <= 8; sl++) in += same(sl);
+        for (int sl = 9; sl <= 14; sl++) out += same(sl);
+        if (in == 8 && out == 6) lab8 = PTM_ALLOY_PURE;
+        else if (in == 0 && out == 6) lab8 = PTM_ALLOY_B2;
+      }
+    }
+    d.alloy[a] = lab8;
+  }
+}
+
+__device__ void write_unmatched(const FrameDesc &d, int64_t a) {
+  if (d.structure) d.structure[a] = PTM_NONE;
+  if (d.alloy) d.alloy[a] = PTM_ALLOY_NONE;
+  if (d.rmsd) d.rmsd[a] = INFINITY;
+  if (d.scale) d.scale[a] = 0.f;
+  if (d.quat) { d.quat[4 * a] = 1.f; d.quat[4 * a + 1] = 0.f; d.quat[4 * a + 2] = 0.f; d.quat[4 * a + 3] = 0.f; }
+  if (d.strain) for (int i = 0; i < 9; i++) d.strain[9 * a + i] = 0.f;
+  if (d.corr) for (int i = 0; i < 15; i++) d.corr[15 * a + i] = -1;
+}
+
+// ------------------------------------------------------------ one atom
+template <bool F64>
+__device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, const float4 *tplw) {
+  typedef typename RT<F64>::T T;
+  T xi, yi, zi;
+  int idi;
+  load_atom<F64>(d, s, xi, yi, zi, idi);
+  const int b = __ldg(d.sbin + s);
+  const int bz = b % d.nb[2], byx = b / d.nb[2];
+  const int by = byx % d.nb[1], bx = byx / d.nb[1];
+  const bool wrapped = d.dstat[0] != 0;
+  int wix = 0, wiy = 0, wiz = 0;
+  if (wrapped) img_unpack(__ldg(d.wrapv + s), wix, wiy, wiz);
+  count(d, C_ATOMS);
+
+  // ---- neighbours (Sec. 3)
+  float dx[PTM_KNN], dy[PTM_KNN], dz[PTM_KNN];
+  int nid[PTM_KNN];
+  int cnt;
+  {
+    T Ld2[PTM_KNN];
+    int Lid[PTM_KNN], Ljs[PTM_KNN], Limg[PTM_KNN];
+    cnt = knn<F64>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, Ld2, Lid, Ljs, Limg);
+    if (cnt < 4) { write_unmatched(d, idi); return; }
+    T emax = 0;
+#pragma unroll
+    for (int t = 0; t < PTM_KNN; t++) {
+      nid[t] = Lid[t];
+      dx[t] = dy[t] = dz[t] = 0.f;
+      if (t >= cnt) continue;
+      T xj, yj, zj;
+      int idj;
+      load_atom<F64>(d, Ljs[t], xj, yj, zj, idj);
+      int a0, a1, a2;
+      img_unpack(Limg[t], a0, a1, a2);
+      T sx, sy, sz;
+      contract_shift<F64>(d, a0, a1, a2, sx, sy, sz);
+      T cx = contract_dr(xj, xi, sx), cy = contract_dr(yj, yi, sy), cz = contract_dr(zj, zi, sz);
+      emax = fmax(emax, fmax(fabs(cx), fmax(fabs(cy), fabs(cz))));
+      // neighbour vectors for the metric steps: the contract values, or for a
+      // shifted image an error-free FP32 sum of difference and shift
+      if constexpr (F64) {
+        dx[t] = (float)cx; dy[t] = (float)cy; dz[t] = (float)cz;
+      } else {
+        if (a0 == 0 && a1 == 0 && a2 == 0) {
+          dx[t] = cx; dy[t] = cy; dz[t] = cz;
+        } else {
+          float hx, hy, hz, lx, ly, lz;
+          shift_f32(d, a0, a1, a2, hx, hy, hz, lx, ly, lz);
+          float p, e1, q2, e2;
+          two_sum(xj, -xi, p, e1); two_sum(p, hx, q2, e2); dx[t] = q2 + (e1 + (e2 + lx));
+          two_sum(yj, -yi, p, e1); two_sum(p, hy, q2, e2); dy[t] = q2 + (e1 + (e2 + ly));
+          two_sum(zj, -zi, p, e1); two_sum(p, hz, q2, e2); dz[t] = q2 + (e1 + (e2 + lz));
+        }
+      }
+    }
+    // quantised copy for the exact hull predicates (reading R7): grid 2^(e - 19)
+    // with 2^e above the largest neighbour-vector component
+    int e;
+    if constexpr (F64) frexp(emax, &e); else frexpf(emax, &e);
+    const T sc = F64 ? (T)ldexp(1.0, PTM_QBITS - e) : (T)ldexpf(1.f, PTM_QBITS - e);
+#pragma unroll
+    for (int t = 0; t < PTM_KNN; t++) {
+      if (t >= cnt) continue;
+      T xj, yj, zj;
+      int idj;
+      load_atom<F64>(d, Ljs[t], xj, yj, zj, idj);
+      int a0, a1, a2;
+      img_unpack(Limg[t], a0, a1, a2);
+      T sx, sy, sz;
+      contract_shift<F64>(d, a0, a1, a2, sx, sy, sz);
+      T cx = contract_dr(xj, xi, sx), cy = contract_dr(yj, yi, sy), cz = contract_dr(zj, zi, sz);
+      if constexpr (F64) {
+        sm.Q(t, 0) = __double2int_rn(cx * sc); sm.Q(t, 1) = __double2int_rn(cy * sc); sm.Q(t, 2) = __double2int_rn(cz * sc);
+      } else {
+        sm.Q(t, 0) = __float2int_rn(cx * sc); sm.Q(t, 1) = __float2int_rn(cy * sc); sm.Q(t, 2) = __float2int_rn(cz * sc);
+      }
+    }
+  }
+
+  // ---- hulls of the first 6, 12, 14 neighbours, built incrementally (Sec. 4)
+  Best bst;
+  bst.b1 = bst.b2 = INFINITY;
+  bst.K = -1; bst.cand = -1; bst.fp64 = 0;
+  bst.ent[0] = bst.ent[1] = bst.ent[2] = -1;
+  bst.lam[0] = bst.lam[1] = bst.lam[2] = 0;
+  const uint32_t mask = d.mask;
+  int kmax = (mask & 16) ? 14 : ((mask & 14) ? 12 : 6);
+  kmax = min(kmax, cnt);
+  if (kmax >= 6) {
+    int nf = hull_init(sm, d);
+    for (int p = 4; p <= kmax; p++) {
+      if (p == 6 && (mask & 1)) snapshot<6>(sm, d, tplw, nf, dx, dy, dz, bst);
+      if (p == 12 && (mask & 14)) snapshot<12>(sm, d, tplw, nf, dx, dy, dz, bst);
+      if (p == 14 && (mask & 16)) snapshot<14>(sm, d, tplw, nf, dx, dy, dz, bst);
+      if (p == kmax) break;
+      nf = hull_insert(sm, nf, p, d);
+      if (nf < 0) break;
+    }
+  }
+  if (bst.K < 0) { write_unmatched(d, idi); return; }
+  if (bst.b2 <= bst.b1 + PTM_BAND) {
+    count(d, C_TIE64);
+    rerank_fp64<F64>(d, s, bst, bx, by, bz, wix, wiy, wiz, wrapped);
+  }
+  if (bst.K == 6) finalize<6>(d, sm, tplw, bst, idi, dx, dy, dz, nid);
+  else if (bst.K == 12) finalize<12>(d, sm, tplw, bst, idi, dx, dy, dz, nid);
+  else finalize<14>(d, sm, tplw, bst, idi, dx, dy, dz, nid);
+}
+
+// ------------------------------------------------------------------ kernels
+struct BinParams {
+  float Hinv[9];     // fractional = x . Hinv
+  float W[3];        // perpendicular cell widths
+  int nb[3];
+  int pbc[3];
+  int64_t n;
+  int f64;
+};
+
+#define PTM_WRAP_TOL 1e-4f
+
+__global__ void k_bin(const void *pos, BinParams p, int *cell_count, int *atom_cell, int *atom_rank,
+                      int *atom_wrap, int *dstat) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p.n) return;
+  float x, y, z;
+  if (p.f64) {
+    const double *q = (const double *)pos + 3 * i;
+    x = (float)q[0]; y = (float)q[1]; z = (float)q[2];
+  } else {
+    const float *q = (const float *)pos + 3 * i;
+    x = q[0]; y = q[1]; z = q[2];
+  }
+  int bc[3], w[3];
+  float over = 0.f;
+  for (int c = 0; c < 3; c++) {
+    float f = x * p.Hinv[c] + y * p.Hinv[3 + c] + z * p.Hinv[6 + c];
+    w[c] = 0;
+    if (p.pbc[c] && (f < -PTM_WRAP_TOL || f >= 1.f + PTM_WRAP_TOL)) {
+      w[c] = (int)floorf(f);
+      f -= (float)w[c];
+    }
+    over = fmaxf(over, fmaxf(-f, f - 1.f) * p.W[c]);
+    int b = (int)floorf(f * (float)p.nb[c]);
+    bc[c] = min(max(b, 0), p.nb[c] - 1);
+  }
+  if (w[0] | w[1] | w[2]) dstat[0] = 1;
+  // rounding of the fractional coordinates is covered by a small extra slack
+  over = fmaxf(over, 0.f) + 1e-5f * fmaxf(p.W[0], fmaxf(p.W[1], p.W[2]));
+  atomicMax(dstat + 1, __float_as_int(over));
+  int cell = (bc[0] * p.nb[1] + bc[1]) * p.nb[2] + bc[2];
+  atom_cell[i] = cell;
+  atom_rank[i] = atomicAdd(cell_count + cell, 1);
+  atom_wrap[i] = img_pack(w[0], w[1], w[2]);
+}
+
+#define SCAN_BLOCK 1024
+// exclusive scan, level 1: per-block scan of 2 elements per thread
+__global__ void k_scan_block(const int *in, int *out, int *block_sums, int n) {
+  __shared__ int sh[SCAN_BLOCK * 2];
+  int base = blockIdx.x * SCAN_BLOCK * 2;
+  int t = threadIdx.x;
+  int a = base + 2 * t, b = a + 1;
+  int va = a < n ? in[a] : 0, vb = b < n ? in[b] : 0;
+  sh[2 * t] = va;
+  sh[2 * t + 1] = va + vb;
+  __syncthreads();
+  // Hillis-Steele over the pair sums
+  int v = sh[2 * t + 1];
+  for (int off = 1; off < SCAN_BLOCK; off <<= 1) {
+    int add = t >= off ? sh[2 * (t - off) + 1] : 0;
+    __syncthreads();
+    v += add;
+    sh[2 * t + 1] = v;
+    __syncthreads();
+  }
+  int excl = v - (va + vb);
+  if (a < n) out[a] = excl;
+  if (b < n) out[b] = excl + va;
+  if (t == SCAN_BLOCK - 1) block_sums[blockIdx.x] = v;
+}
+
+// level 2: one block scans the block sums serially in chunks
+__global__ void k_scan_sums(int *block_sums, int nblocks, int *total_out) {
+  __shared__ int sh[SCAN_BLOCK];
+  int carry = 0;
+  for (int base = 0; base < nblocks; base += SCAN_BLOCK) {
+    int t = threadIdx.x, i = base + t;
+    int v = i < nblocks ? block_sums[i] : 0;
+    sh[t] = v;
+    __syncthreads();
+    for (int off = 1; off < SCAN_BLOCK; off <<= 1) {
+      int add = t >= off ? sh[t - off] : 0;
+      __syncthreads();
+      sh[t] += add;
+      __syncthreads();
+    }
+    if (i < nblocks) block_sums[i] = carry + sh[t] - v;
+    int tot = sh[SCAN_BLOCK - 1];
+    __syncthreads();
+    carry += tot;
+  }
+  if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void k_scan_add(int *out, const int *block_sums, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] += block_sums[i / (SCAN_BLOCK * 2)];
+}
+
+__global__ void k_scatter(const void *pos, int f64, int64_t n, const int *atom_cell, const int *atom_rank,
+                          const int *atom_wrap, const int *cell_start, void *sorted, int *sbin, int *wrapv) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c = atom_cell[i];
+  int slot = cell_start[c] + atom_rank[i];
+  if (f64) {
+    const double *q = (const double *)pos + 3 * i;
+    Atom64 a;
+    a.x = q[0]; a.y = q[1]; a.z = q[2]; a.id = i;
+    ((Atom64 *)sorted)[slot] = a;
+  } else {
+    const float *q = (const float *)pos + 3 * i;
+    ((float4 *)sorted)[slot] = make_float4(q[0], q[1], q[2], __int_as_float((int)i));
+  }
+  sbin[slot] = c;
+  wrapv[slot] = atom_wrap[i];
+}
+
+constexpr size_t atom_smem_bytes() {
+  return (size_t)PTM_BLOCK * SCRATCH_WORDS * 4 + 5 * 15 * sizeof(float4);
+}
+
+// The frame descriptor travels by value in the kernel parameters, so back-to-back
+// asynchronous calls never share a staging buffer.
+template <bool F64>
+__global__ void __launch_bounds__(PTM_BLOCK, 4) k_atoms(const __grid_constant__ FrameDesc d) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t *th = (uint64_t *)smem;
+  int *q = (int *)(th + 14 * PTM_BLOCK);
+  uint32_t *code = (uint32_t *)(q + 42 * PTM_BLOCK);
+  uint16_t *fac = (uint16_t *)(code + 10 * PTM_BLOCK);
+  uint16_t *used = fac + 24 * PTM_BLOCK;
+  float4 *tplw = (float4 *)(used + 14 * PTM_BLOCK);
+  for (int i = threadIdx.x; i < 75; i += blockDim.x) {
+    const float *w = ptm_tpl[i / 15][i % 15];
+    tplw[i] = make_float4(w[0], w[1], w[2], w[3]);
+  }
+  __syncthreads();
+  Scratch sm;
+  sm.q = q; sm.fac = fac; sm.th = th; sm.used = used; sm.code = code; sm.t = threadIdx.x;
+  int64_t s = (int64_t)blockIdx.x * PTM_BLOCK + threadIdx.x;
+  if (s >= d.n) return;
+  classify_atom<F64>(d, (int)s, sm, tplw);
+}
+
+}  // namespace ptm
+

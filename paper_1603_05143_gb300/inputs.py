@@ -162,10 +162,12 @@ def config_polycrystal(seed: int = 5143, n_target: int = 1 << 20, n_grains: int 
     """Periodic Voronoi polycrystal of fcc Cu with stacking-fault slabs.
 
     The box is the fcc-density cube for ``n_target`` atoms (L = 231.36 A for 2^20).
-    Each grain is filled with its own randomly rotated lattice; atoms closer than
-    1.5 A across grain boundaries are thinned; the count is trimmed or padded to
-    exactly ``n_target``.  In ``n_faults`` grains all atoms above a {111} plane
-    through the grain centre are shifted by a/6<112>, which leaves two hcp planes.
+    Each grain fills the part of the box closest (minimum image) to its centre
+    with its own randomly rotated lattice; atoms closer than 1.5 A across grain
+    boundaries are thinned; the count is trimmed (or, rarely, padded with random
+    points) to exactly ``n_target``.  In ``n_faults`` grains all atoms above a
+    {111} plane through the grain centre are shifted by a/6<112>, which leaves
+    two hcp planes at the fault.
     """
     rng = rng_for(seed)
     a = A_FCC_CU
@@ -173,32 +175,33 @@ def config_polycrystal(seed: int = 5143, n_target: int = 1 << 20, n_grains: int 
     cell = np.eye(3) * L
     centres = rng.random((n_grains, 3)) * L
     rots = [random_rotation(rng) for _ in range(n_grains)]
-    cell0, basis, _ = unit_cell("fcc", a)
-    # lattice sites within a cube of half-width r_cover around each grain centre
-    r_cover = L * 0.75
-    m = int(math.ceil(r_cover / a)) + 1
-    g = np.stack(np.meshgrid(*[np.arange(-m, m)] * 3, indexing="ij"), -1).reshape(-1, 3)
-    local = ((g[:, None, :] + basis[None]) .reshape(-1, 3)) @ cell0
-    pieces = []
     fault_grains = set(rng.choice(n_grains, size=min(n_faults, n_grains), replace=False).tolist())
+    # radius of each grain's cell from a coarse ownership grid
+    g = (np.arange(40) + 0.5) / 40 * L
+    grid = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    dg = np.stack([_min_image_dist2(grid, c, L) for c in centres], 1)
+    own = dg.argmin(1)
+    rg = np.array([math.sqrt(dg[own == i, i].max()) if np.any(own == i) else 0.0
+                   for i in range(n_grains)]) + 2 * L / 40 + 2 * a
+    cell0, basis, _ = unit_cell("fcc", a)
+    pieces = []
     for gi in range(n_grains):
-        R = rots[gi]
-        p = local.copy()
+        m = int(math.ceil(rg[gi] / a)) + 1
+        ijk = np.stack(np.meshgrid(*[np.arange(-m, m + 1)] * 3, indexing="ij"), -1).reshape(-1, 3)
+        p = ((ijk[:, None, :] + basis[None]).reshape(-1, 3)) @ cell0
+        p = p[np.einsum("ij,ij->i", p, p) <= rg[gi] ** 2]
         if gi in fault_grains:
             nrm = np.array([1.0, 1.0, 1.0]) / math.sqrt(3)
-            shift = a / 6.0 * np.array([1.0, 1.0, -2.0])
-            h = p @ nrm
-            p[h > 0.5 * a / math.sqrt(3) * 0.5] += shift
-        p = p @ R.T + centres[gi]
-        # periodic Voronoi ownership: keep sites closest (minimum image) to this centre
-        d_own = _min_image_dist2(p, centres[gi], L)
-        keep = np.ones(len(p), bool)
+            p[p @ nrm > a / (4 * math.sqrt(3))] += a / 6.0 * np.array([1.0, 1.0, -2.0])
+        off = p @ rots[gi].T
+        off = off[np.all(np.abs(off) < L / 2, axis=1)]          # minimal image only
+        q = off + centres[gi]
+        d_own = np.einsum("ij,ij->i", off, off)
+        keep = np.ones(len(q), bool)
         for gj in range(n_grains):
-            if gj == gi:
-                continue
-            keep &= d_own < _min_image_dist2(p, centres[gj], L)
-        p = p[keep & (d_own < (L * 0.87) ** 2)]
-        pieces.append(np.mod(p, L))
+            if gj != gi:
+                keep &= d_own < _min_image_dist2(q, centres[gj], L)
+        pieces.append(np.mod(q[keep], L))
     pos = np.vstack(pieces)
     pos = _thin_close_pairs(pos, L, 1.5, rng)
     n = len(pos)
@@ -211,7 +214,8 @@ def config_polycrystal(seed: int = 5143, n_target: int = 1 << 20, n_grains: int 
     pos = np.mod(pos, L)
     pos[pos >= L] = 0.0
     return Frame(pos.astype(np.float32), cell, (True, True, True), None, "polycrystal",
-                 {"L": L, "grains": n_grains, "faults": sorted(fault_grains), "raw_count": n})
+                 {"L": L, "grains": n_grains, "faults": sorted(fault_grains), "raw_count": n,
+                  "padded": max(0, n_target - n)})
 
 
 def _min_image_dist2(p, c, L):
