@@ -18,7 +18,7 @@
 
 #include "ptm_tables_gen.h"
 
-#define PTM_BLOCK 128
+#define PTM_BLOCK 64
 #define PTM_KNN 14
 #define PTM_QBITS 19
 #define PTM_RMAX 6              // widest cell-search radius (in cells) before giving up
@@ -70,6 +70,8 @@ __device__ __forceinline__ void count(const FrameDesc &d, int which, unsigned lo
 
 // ------------------------------------------------------------ shared scratch
 struct Scratch {
+  float *nv;         // [42][B]  neighbour vectors for the metric steps (x[14], y[14], z[14])
+  int *nid;          // [14][B]  neighbour atom ids
   int *q;            // [42][B]  quantised neighbour vectors
   uint16_t *fac;     // [24][B]  hull facets a | b << 4 | c << 8 (ccw from outside)
   uint64_t *th;      // [14][B]  third vertex of directed edge u->v, nibble v of row u (0xF none)
@@ -77,13 +79,17 @@ struct Scratch {
   uint32_t *code;    // [10][B]  best Weinberg code so far (nibbles)
   int t;             // thread index in block
   __device__ __forceinline__ int &Q(int p, int c) const { return q[(3 * p + c) * PTM_BLOCK + t]; }
+  __device__ __forceinline__ float &DX(int j) const { return nv[j * PTM_BLOCK + t]; }
+  __device__ __forceinline__ float &DY(int j) const { return nv[(PTM_KNN + j) * PTM_BLOCK + t]; }
+  __device__ __forceinline__ float &DZ(int j) const { return nv[(2 * PTM_KNN + j) * PTM_BLOCK + t]; }
+  __device__ __forceinline__ int &NID(int j) const { return nid[j * PTM_BLOCK + t]; }
   __device__ __forceinline__ uint16_t &F(int f) const { return fac[f * PTM_BLOCK + t]; }
   __device__ __forceinline__ uint64_t &TH(int v) const { return th[v * PTM_BLOCK + t]; }
   __device__ __forceinline__ uint16_t &U(int v) const { return used[v * PTM_BLOCK + t]; }
   __device__ __forceinline__ uint32_t &CODE(int w) const { return code[w * PTM_BLOCK + t]; }
 };
 
-constexpr int SCRATCH_WORDS = 42 + 12 + 28 + 7 + 10;   // 32-bit words per thread
+constexpr int SCRATCH_WORDS = 28 + 42 + 42 + 14 + 10 + 12 + 7;   // 32-bit words per thread
 
 // -------------------------------------------------------------- small helpers
 __device__ __forceinline__ int nib(uint64_t x, int i) { return (int)((x >> (4 * i)) & 15); }
@@ -257,20 +263,19 @@ __device__ int hull_insert(const Scratch &sm, int nf, int p, const FrameDesc &d)
 }
 
 // ------------------------------------------------------- canonical Weinberg code
-// Walk from u -> v (rules in tables.py).  Compares the emitted labels with the
-// best code so far (cmp = 0 equal so far, 1 already smaller, -1 first walk)
-// and returns +1 when this walk is strictly smaller (it becomes the best and
-// its labelling is returned), 0 when equal, -1 when larger (aborted early).
-template <int K>
-__device__ int weinberg_walk(const Scratch &sm, int u, int v, bool first, uint64_t &labels, const FrameDesc &d) {
-  constexpr int LEN = 2 * (3 * K - 6) + 1;
+// Walk from u -> v over the K-vertex hull (rules in tables.py).  The emitted
+// labels are compared with the best code so far; returns +1 when this walk is
+// strictly smaller (it becomes the best and its labelling is returned), 0 when
+// equal, -1 when larger (aborted at the first larger label).
+__device__ int weinberg_walk(const Scratch &sm, int K, int u, int v, bool first, uint64_t &labels,
+                             const FrameDesc &d) {
+  const int LEN = 2 * (3 * K - 6) + 1;
   uint64_t lab = 0;
-  for (int x = 0; x < K; x++) sm.U(x) = 0;
+#pragma unroll
+  for (int x = 0; x < PTM_KNN; x++) sm.U(x) = 0;
   int state = first ? 1 : 0;        // 1: writing a new best; 0: still equal
   int next = 1;
   uint32_t wbuf = 0, wcur = 0;
-  // step 0: label of u
-  lab = setnib(lab, u, next++);
   auto emit = [&](int s, int L) -> bool {
     if (state == 0) {
       if ((s & 7) == 0) wcur = sm.CODE(s >> 3);
@@ -287,6 +292,7 @@ __device__ int weinberg_walk(const Scratch &sm, int u, int v, bool first, uint64
     }
     return true;
   };
+  lab = setnib(lab, u, next++);
   emit(0, 1);
   sm.U(u) |= 1 << v;
   bool fresh = true;
@@ -294,24 +300,20 @@ __device__ int weinberg_walk(const Scratch &sm, int u, int v, bool first, uint64
   if (!emit(1, 2)) return -1;
   int s = 2;
   for (; s < LEN; s++) {
-    int w;
-    uint64_t tv = sm.TH(v);
-    if (fresh) {
-      w = nib(tv, u);
-    } else if (!(sm.U(v) >> u & 1)) {
-      w = u;
-    } else {
-      w = -1;
-      int x = nib(tv, u);
-      int guard = 0;
-      while (x != u && guard++ < 16) {
-        if (!(sm.U(v) >> x & 1)) { w = x; break; }
-        x = nib(tv, x);
+    const uint64_t tv = sm.TH(v);
+    const uint32_t uv = sm.U(v);
+    int w = nib(tv, u);                              // next edge counter-clockwise
+    if (!fresh) {
+      if (!(uv >> u & 1)) {
+        w = u;                                       // old vertex, new edge: walk back
+      } else {
+        int guard = 0;                               // first unused edge after arrival
+        while (w != u && (uv >> w & 1) && guard++ < 16) w = nib(tv, w);
+        if (w == u || guard > 16) break;
       }
-      if (w < 0) break;
     }
     if (w >= K) { count(d, C_INTERNAL); return -1; }
-    sm.U(v) |= 1 << w;
+    sm.U(v) = (uint16_t)(uv | (1u << w));
     u = v;
     v = w;
     int L = nib(lab, v);
@@ -324,13 +326,16 @@ __device__ int weinberg_walk(const Scratch &sm, int u, int v, bool first, uint64
   return 0;
 }
 
-// Canonical code of the current hull (K vertices): among starts with the
-// largest deg(u), then the largest deg(v), the smallest code.  Returns the
-// labelling of vertex t (nibble t) and the code hash; false on an internal error.
-template <int K>
-__device__ bool canonical(const Scratch &sm, int nf, uint64_t &labels, uint64_t &hash, const FrameDesc &d) {
+// Canonical code of the current K-vertex hull: among starts with the largest
+// deg(u), then the largest deg(v), the smallest code.  Returns the labelling
+// (nibble t = label of neighbour t) and the code hash; false on an internal
+// error.  The candidate starts are visited by one flat loop, so the threads of
+// a warp run their walks together.
+__device__ bool canonical(const Scratch &sm, int K, int nf, uint64_t &labels, uint64_t &hash,
+                          const FrameDesc &d) {
   uint64_t deg = 0;
-  for (int x = 0; x < K; x++) sm.TH(x) = ~0ull;
+#pragma unroll
+  for (int x = 0; x < PTM_KNN; x++) sm.TH(x) = ~0ull;
   for (int f = 0; f < nf; f++) {
     int v = sm.F(f);
     int a = v & 15, b = (v >> 4) & 15, c = (v >> 8) & 15;
@@ -340,35 +345,48 @@ __device__ bool canonical(const Scratch &sm, int nf, uint64_t &labels, uint64_t 
     deg += (1ull << (4 * a)) + (1ull << (4 * b)) + (1ull << (4 * c));
   }
   int du = 0;
-  for (int x = 0; x < K; x++) du = max(du, nib(deg, x));
+#pragma unroll
+  for (int x = 0; x < PTM_KNN; x++) if (x < K) du = max(du, nib(deg, x));
+  uint32_t umask = 0;
+#pragma unroll
+  for (int x = 0; x < PTM_KNN; x++) if (x < K && nib(deg, x) == du) umask |= 1u << x;
   int dv = 0;
-  for (int x = 0; x < K; x++) {
-    if (nib(deg, x) != du) continue;
-    uint64_t tx = sm.TH(x);
-    for (int y = 0; y < K; y++)
-      if (nib(tx, y) != 15) dv = max(dv, nib(deg, y));
+  for (uint32_t m = umask; m; m &= m - 1) {
+    const uint64_t tx = sm.TH(__ffs(m) - 1);
+#pragma unroll
+    for (int y = 0; y < PTM_KNN; y++)
+      if (y < K && nib(tx, y) != 15) dv = max(dv, nib(deg, y));
   }
-  // every vertex of degree 5 with K = 12 is the icosahedron; every vertex of
-  // degree 4 with K = 6 is the octahedron: all starts are equivalent
-  bool transitive = (K == 12 && du == 5 && dv == 5) || (K == 6 && du == 4 && dv == 4);
+  // K = 12 with every degree 5 is the icosahedron, K = 6 with every degree 4 the
+  // octahedron: every directed edge is equivalent, one walk suffices
+  const bool transitive = (K == 12 && du == 5 && dv == 5) || (K == 6 && du == 4 && dv == 4);
   bool first = true;
-  for (int x = 0; x < K; x++) {
-    if (nib(deg, x) != du) continue;
-    uint64_t tx = sm.TH(x);
-    for (int y = 0; y < K; y++) {
-      if (nib(tx, y) == 15 || nib(deg, y) != dv) continue;
-      uint64_t lab;
-      int r = weinberg_walk<K>(sm, x, y, first, lab, d);
-      if (first && r != 1) return false;
-      if (r == 1) labels = lab;
-      first = false;
-      if (transitive) goto done;
+  uint32_t vmask = 0;
+  int u = 0;
+  for (;;) {
+    while (vmask == 0 && umask) {
+      u = __ffs(umask) - 1;
+      umask &= umask - 1;
+      const uint64_t tu = sm.TH(u);
+#pragma unroll
+      for (int y = 0; y < PTM_KNN; y++)
+        if (y < K && nib(tu, y) != 15 && nib(deg, y) == dv) vmask |= 1u << y;
     }
+    if (!vmask) break;
+    const int v = __ffs(vmask) - 1;
+    vmask &= vmask - 1;
+    uint64_t lab = 0;
+    const int r = weinberg_walk(sm, K, u, v, first, lab, d);
+    if (first && r != 1) return false;
+    if (r == 1) labels = lab;
+    first = false;
+    if (transitive) break;
   }
-done:
   // hash of the packed code; words past its end count as zero, as the generator packs them
+  const int LEN = 2 * (3 * K - 6) + 1;
   uint64_t h = PTM_HASH_INIT;
-  for (int w = 0; w < 10; w++) h = (h ^ (uint64_t)(w * 8 < 2 * (3 * K - 6) + 1 ? sm.CODE(w) : 0u)) * PTM_HASH_MUL;
+#pragma unroll
+  for (int w = 0; w < 10; w++) h = (h ^ (uint64_t)(w * 8 < LEN ? sm.CODE(w) : 0u)) * PTM_HASH_MUL;
   hash = h;
   return true;
 }
@@ -454,33 +472,37 @@ __device__ void qcp_solve(const T S[3][3], T Gv, T Gw, Qcp<T> &o) {
 
 // Unit quaternion of the largest eigenvalue: the column of adj(K - lam I) with
 // the largest norm (all nonzero columns are parallel to the eigenvector).
+// Cofactor (c, r) deletes row c and column r; every index is static once the
+// loops are unrolled, so nothing lands in local memory.
 template <typename T>
 __device__ void qcp_quat(const T K[4][4], T lam, T q[4]) {
   T A[4][4];
-  for (int i = 0; i < 4; i++) for (int j = 0; j < 4; j++) A[i][j] = K[i][j] - (i == j ? lam : T(0));
-  T best = -1;
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) A[i][j] = K[i][j] - (i == j ? lam : T(0));
+  T best = T(-1);
+  T b0 = 1, b1 = 0, b2 = 0, b3 = 0;
+#pragma unroll
   for (int c = 0; c < 4; c++) {
     T col[4];
+#pragma unroll
     for (int r = 0; r < 4; r++) {
-      // cofactor (c, r): delete row c and column r
       T m[3][3];
-      int ii = 0;
-      for (int i = 0; i < 4; i++) {
-        if (i == c) continue;
-        int jj = 0;
-        for (int j = 0; j < 4; j++) { if (j == r) continue; m[ii][jj++] = A[i][j]; }
-        ii++;
-      }
-      T v = det3<T>(m);
+#pragma unroll
+      for (int ii = 0; ii < 3; ii++)
+#pragma unroll
+        for (int jj = 0; jj < 3; jj++) m[ii][jj] = A[ii + (ii >= c)][jj + (jj >= r)];
+      const T v = det3<T>(m);
       col[r] = ((c + r) & 1) ? -v : v;
     }
-    T nn = col[0] * col[0] + col[1] * col[1] + col[2] * col[2] + col[3] * col[3];
-    if (nn > best) { best = nn; for (int r = 0; r < 4; r++) q[r] = col[r]; }
+    const T nn = col[0] * col[0] + col[1] * col[1] + col[2] * col[2] + col[3] * col[3];
+    if (nn > best) { best = nn; b0 = col[0]; b1 = col[1]; b2 = col[2]; b3 = col[3]; }
   }
-  T inv = T(1) / sqrt(best > T(0) ? best : T(1));
-  if (!(best > T(0))) { q[0] = 1; q[1] = q[2] = q[3] = 0; inv = 1; }
-  T sgn = q[0] < T(0) ? T(-1) : T(1);
-  for (int r = 0; r < 4; r++) q[r] *= inv * sgn;
+  if (!(best > T(0))) { q[0] = 1; q[1] = q[2] = q[3] = 0; return; }
+  T inv = T(1) / sqrt(best);
+  if (b0 < T(0)) inv = -inv;
+  q[0] = b0 * inv; q[1] = b1 * inv; q[2] = b2 * inv; q[3] = b3 * inv;
 }
 
 template <typename T>

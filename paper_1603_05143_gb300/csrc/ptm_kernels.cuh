@@ -142,20 +142,23 @@ __device__ int knn(const FrameDesc &d, int s, typename RT<F64>::T xi, typename R
 }
 
 // ---------------------------------------------------------- per-atom state
+// Per-atom selection state.  Plain scalars (no arrays) so that it stays in
+// registers; snapshot k = 6, 12, 14 keeps its canonical labelling and table entry.
 struct Best {
-  float b1, b2;       // best and second-best FP32 RMSD^2
-  int K, cand;        // winning snapshot (6, 12, 14) and candidate index
-  int fp64;           // winner's eigenvalue needed the FP64 solve
-  uint64_t lam[3];    // canonical labelling per snapshot (k = 6, 12, 14)
-  int ent[3];         // table entry per snapshot, -1 = none
+  float b1, b2;                 // best and second-best FP32 RMSD^2
+  int K, cand;                  // winning snapshot (6, 12, 14) and candidate index
+  int fp64;                     // the winner's eigenvalue needed the FP64 solve
+  uint64_t lam6, lam12, lam14;  // canonical labelling per snapshot
+  int ent6, ent12, ent14;       // table entry per snapshot, -1 = none
+  __device__ __forceinline__ uint64_t lam(int K) const { return K == 6 ? lam6 : (K == 12 ? lam12 : lam14); }
+  __device__ __forceinline__ int ent(int K) const { return K == 6 ? ent6 : (K == 12 ? ent12 : ent14); }
 };
 
 __device__ __forceinline__ int snap_index(int K) { return K == 6 ? 0 : (K == 12 ? 1 : 2); }
 
-template <int K>
-__device__ __forceinline__ int lookup(const Scratch &sm, uint64_t h) {
-  constexpr int LEN = 2 * (3 * K - 6) + 1;
-  constexpr int NW = (LEN + 7) / 8;
+__device__ __forceinline__ int lookup(const Scratch &sm, int K, uint64_t h) {
+  const int LEN = 2 * (3 * K - 6) + 1;
+  const int NW = (LEN + 7) / 8;
   int pos = (int)(h & (PTM_TBL_NSLOTS - 1));
   for (int probe = 0; probe < PTM_TBL_NSLOTS; probe++) {
     const ptm_tbl_entry *e = &ptm_tbl[pos];
@@ -165,7 +168,7 @@ __device__ __forceinline__ int lookup(const Scratch &sm, uint64_t h) {
     if (eh == h && __ldg(&e->nv) == K) {
       bool eq = true;
 #pragma unroll
-      for (int w = 0; w < NW; w++) eq &= (__ldg(&e->code[w]) == sm.CODE(w));
+      for (int w = 0; w < 10; w++) if (w < NW) eq &= (__ldg(&e->code[w]) == sm.CODE(w));
       if (eq) return pos;
     }
     pos = (pos + 1) & (PTM_TBL_NSLOTS - 1);
@@ -177,34 +180,31 @@ __device__ __forceinline__ int lookup(const Scratch &sm, uint64_t h) {
 // template slot" given by the canonical labelling and the table candidate.
 // Because the template barycentre is the origin and slot 0 (the centre) sits at
 // it, the data barycentre drops out of S.
-template <int K>
-__device__ __forceinline__ void cov_matrix(const float4 *tplw, int S, uint64_t lab, uint64_t cand,
-                                           const float (&dx)[PTM_KNN], const float (&dy)[PTM_KNN],
-                                           const float (&dz)[PTM_KNN], float (&Sm)[3][3]) {
+__device__ __forceinline__ void cov_matrix(int K, const Scratch &sm, const float4 *tplw, int S, uint64_t lab,
+                                           uint64_t cand, float (&Sm)[3][3]) {
 #pragma unroll
   for (int a = 0; a < 3; a++)
 #pragma unroll
     for (int b = 0; b < 3; b++) Sm[a][b] = 0.f;
-#pragma unroll
+#pragma unroll 2
   for (int j = 0; j < K; j++) {
-    int L = nib(lab, j);
-    int slot = nib(cand, L - 1);
-    float4 w = tplw[S * 15 + slot];
-    Sm[0][0] = fmaf(w.x, dx[j], Sm[0][0]); Sm[0][1] = fmaf(w.x, dy[j], Sm[0][1]); Sm[0][2] = fmaf(w.x, dz[j], Sm[0][2]);
-    Sm[1][0] = fmaf(w.y, dx[j], Sm[1][0]); Sm[1][1] = fmaf(w.y, dy[j], Sm[1][1]); Sm[1][2] = fmaf(w.y, dz[j], Sm[1][2]);
-    Sm[2][0] = fmaf(w.z, dx[j], Sm[2][0]); Sm[2][1] = fmaf(w.z, dy[j], Sm[2][1]); Sm[2][2] = fmaf(w.z, dz[j], Sm[2][2]);
+    const int slot = nib(cand, nib(lab, j) - 1);
+    const float4 w = tplw[S * 15 + slot];
+    const float x = sm.DX(j), y = sm.DY(j), z = sm.DZ(j);
+    Sm[0][0] = fmaf(w.x, x, Sm[0][0]); Sm[0][1] = fmaf(w.x, y, Sm[0][1]); Sm[0][2] = fmaf(w.x, z, Sm[0][2]);
+    Sm[1][0] = fmaf(w.y, x, Sm[1][0]); Sm[1][1] = fmaf(w.y, y, Sm[1][1]); Sm[1][2] = fmaf(w.y, z, Sm[1][2]);
+    Sm[2][0] = fmaf(w.z, x, Sm[2][0]); Sm[2][1] = fmaf(w.z, y, Sm[2][1]); Sm[2][2] = fmaf(w.z, z, Sm[2][2]);
   }
 }
 
-template <int K>
-__device__ __forceinline__ void data_moments(const float (&dx)[PTM_KNN], const float (&dy)[PTM_KNN],
-                                             const float (&dz)[PTM_KNN], float &mx, float &my, float &mz,
-                                             float &Gv) {
+// Barycentre of the centre and its first K neighbours, and G_v = sum |v - mean|^2.
+__device__ __forceinline__ void data_moments(int K, const Scratch &sm, float &mx, float &my, float &mz, float &Gv) {
   float sx = 0, sy = 0, sz = 0, g = 0;
-#pragma unroll
+#pragma unroll 2
   for (int j = 0; j < K; j++) {
-    sx += dx[j]; sy += dy[j]; sz += dz[j];
-    g = fmaf(dx[j], dx[j], fmaf(dy[j], dy[j], fmaf(dz[j], dz[j], g)));
+    const float x = sm.DX(j), y = sm.DY(j), z = sm.DZ(j);
+    sx += x; sy += y; sz += z;
+    g = fmaf(x, x, fmaf(y, y, fmaf(z, z, g)));
   }
   const float inv = 1.f / (float)(K + 1);
   mx = sx * inv; my = sy * inv; mz = sz * inv;
@@ -214,9 +214,9 @@ __device__ __forceinline__ void data_moments(const float (&dx)[PTM_KNN], const f
 // RMSD^2 of one candidate from its covariance (closed form after Eq. 3); the
 // FP32 Newton solution is replaced by an FP64 one when the top eigenvalue is
 // not well separated (normalised P'(lambda_1) below PTM_GAP).
-__device__ __noinline__ float r2_fp64(const float (&Sm)[3][3], float Gv, float Gw, int N) {
-  double S[3][3];
-  for (int a = 0; a < 3; a++) for (int b = 0; b < 3; b++) S[a][b] = Sm[a][b];
+__device__ __noinline__ float r2_fp64(float s00, float s01, float s02, float s10, float s11, float s12, float s20,
+                                      float s21, float s22, float Gv, float Gw, int N) {
+  double S[3][3] = {{s00, s01, s02}, {s10, s11, s12}, {s20, s21, s22}};
   Qcp<double> o;
   qcp_solve<double>(S, (double)Gv, (double)Gw, o);
   return (float)(((double)Gw - o.lam * o.lam / (double)Gv) / N);
@@ -231,7 +231,8 @@ __device__ __forceinline__ float cand_r2(const float (&Sm)[3][3], float Gv, floa
   if (!(gamma >= PTM_GAP) || o.iters >= 60) {
     fp64 = 1;
     count(d, C_QCP64);
-    return fmaxf(r2_fp64(Sm, Gv, Gw, N), 0.f);
+    return fmaxf(r2_fp64(Sm[0][0], Sm[0][1], Sm[0][2], Sm[1][0], Sm[1][1], Sm[1][2], Sm[2][0], Sm[2][1], Sm[2][2],
+                         Gv, Gw, N), 0.f);
   }
   fp64 = 0;
   return fmaxf((Gw - o.lam * o.lam / Gv) / (float)N, 0.f);
@@ -239,10 +240,7 @@ __device__ __forceinline__ float cand_r2(const float (&Sm)[3][3], float Gv, floa
 
 // Hull of the first K neighbours is complete: centre test, canonical code,
 // lookup and QCP of every admissible correspondence (Algorithm 1, inner loops).
-template <int K>
-__device__ void snapshot(const Scratch &sm, const FrameDesc &d, const float4 *tplw, int nf,
-                         const float (&dx)[PTM_KNN], const float (&dy)[PTM_KNN], const float (&dz)[PTM_KNN],
-                         Best &bst) {
+__device__ void snapshot(int K, const Scratch &sm, const FrameDesc &d, const float4 *tplw, int nf, Best &bst) {
   if (nf != 2 * K - 4) return;                    // a neighbour is not a hull vertex
   for (int f = 0; f < nf; f++) {                  // centre strictly inside (exact, no SoS)
     int v = sm.F(f);
@@ -252,14 +250,15 @@ __device__ void snapshot(const Scratch &sm, const FrameDesc &d, const float4 *tp
     if (o >= 0) return;
   }
   uint64_t lab = 0, h = 0;
-  if (!canonical<K>(sm, nf, lab, h, d)) return;
-  int e = lookup<K>(sm, h);
+  if (!canonical(sm, K, nf, lab, h, d)) return;
+  int e = lookup(sm, K, h);
   if (e < 0) return;
   const int si = snap_index(K);
-  bst.lam[si] = lab;
-  bst.ent[si] = e;
+  if (K == 6) { bst.lam6 = lab; bst.ent6 = e; }
+  else if (K == 12) { bst.lam12 = lab; bst.ent12 = e; }
+  else { bst.lam14 = lab; bst.ent14 = e; }
   float mx, my, mz, Gv;
-  data_moments<K>(dx, dy, dz, mx, my, mz, Gv);
+  data_moments(K, sm, mx, my, mz, Gv);
   const int first = __ldg(&ptm_tbl[e].first), cnt = __ldg(&ptm_tbl[e].count);
   int scored = 0;
   for (int c = first; c < first + cnt; c++) {
@@ -268,7 +267,7 @@ __device__ void snapshot(const Scratch &sm, const FrameDesc &d, const float4 *tp
     if (!(d.mask >> S & 1)) continue;
     scored++;
     float Sm[3][3];
-    cov_matrix<K>(tplw, S, lab, cand, dx, dy, dz, Sm);
+    cov_matrix(K, sm, tplw, S, lab, cand, Sm);
     float Gw = tplw[S * 15].w;
     int fp64;
     float r2 = cand_r2(Sm, Gv, Gw, K + 1, fp64, d);
@@ -292,28 +291,25 @@ __device__ uint64_t canonical_corr(int S, int K, uint64_t corr) {
   return best;
 }
 
-template <int K>
-__device__ __forceinline__ uint64_t corr_of(uint64_t lab, uint64_t cand) {
+__device__ __forceinline__ uint64_t corr_of(int K, uint64_t lab, uint64_t cand) {
   uint64_t corr = 0;
 #pragma unroll
-  for (int j = 0; j < K; j++) {
+  for (int j = 0; j < PTM_KNN; j++) {
+    if (j >= K) break;
     int slot = nib(cand, nib(lab, j) - 1);
     corr |= (uint64_t)(j + 1) << (4 * (15 - slot));
   }
   return corr;
 }
 
-__device__ __forceinline__ uint64_t corr_of_k(int K, uint64_t lab, uint64_t cand) {
-  return K == 6 ? corr_of<6>(lab, cand) : (K == 12 ? corr_of<12>(lab, cand) : corr_of<14>(lab, cand));
-}
 
 // Rare path: the best FP32 candidates lie within PTM_BAND.  Every candidate is
 // re-scored in FP64 from neighbour vectors recomputed in FP64 from the input
 // positions; ties within PTM_TIE go to the earlier template, then to the smaller
 // canonical correspondence (reading R13).
 template <bool F64>
-__device__ __noinline__ void rerank_fp64(const FrameDesc &d, int s, Best &bst, int bx, int by, int bz, int wix,
-                                         int wiy, int wiz, bool wrapped) {
+__device__ __noinline__ int rerank_fp64(const FrameDesc &d, int s, const Best bst, int bx, int by, int bz,
+                                        int wix, int wiy, int wiz, bool wrapped) {
   typedef typename RT<F64>::T T;
   T xi, yi, zi;
   int idi;
@@ -321,7 +317,7 @@ __device__ __noinline__ void rerank_fp64(const FrameDesc &d, int s, Best &bst, i
   T Ld2[PTM_KNN];
   int Lid[PTM_KNN], Ljs[PTM_KNN], Limg[PTM_KNN];
   int cnt = knn<F64>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, Ld2, Lid, Ljs, Limg);
-  if (cnt < 0) return;
+  if (cnt < 0) return -1;
   double ex[PTM_KNN], ey[PTM_KNN], ez[PTM_KNN];
   for (int t = 0; t < cnt; t++) {
     T xj, yj, zj;
@@ -345,9 +341,9 @@ __device__ __noinline__ void rerank_fp64(const FrameDesc &d, int s, Best &bst, i
   for (int pass = 0; pass < 2; pass++) {
     for (int si = 0; si < 3; si++) {
       const int K = si == 0 ? 6 : (si == 1 ? 12 : 14);
-      int e = bst.ent[si];
+      int e = bst.ent(K);
       if (e < 0) continue;
-      uint64_t lab = bst.lam[si];
+      uint64_t lab = bst.lam(K);
       double m[3] = {0, 0, 0}, g = 0;
       for (int j = 0; j < K; j++) { m[0] += ex[j]; m[1] += ey[j]; m[2] += ez[j]; g += ex[j] * ex[j] + ey[j] * ey[j] + ez[j] * ez[j]; }
       for (int c = 0; c < 3; c++) m[c] /= (K + 1);
@@ -374,29 +370,26 @@ __device__ __noinline__ void rerank_fp64(const FrameDesc &d, int s, Best &bst, i
         if (pass == 0) {
           best_r2 = fmin(best_r2, r2);
         } else if (r2 <= best_r2 + PTM_TIE) {
-          uint64_t cp = canonical_corr(S, K, corr_of_k(K, lab, cand));
+          uint64_t cp = canonical_corr(S, K, corr_of(K, lab, cand));
           if (S < bS || (S == bS && cp < bcp)) { bS = S; bcp = cp; bK = K; bc = ci; }
         }
       }
     }
   }
   (void)r2s;
-  if (bK > 0) { bst.K = bK; bst.cand = bc; }
+  return bK > 0 ? (bK << 16) | bc : -1;
 }
 
 // ------------------------------------------------------------ finalisation
-template <int K>
-__device__ void finalize(const FrameDesc &d, const Scratch &sm, const float4 *tplw, const Best &bst, int idi,
-                         const float (&dx)[PTM_KNN], const float (&dy)[PTM_KNN], const float (&dz)[PTM_KNN],
-                         const int (&nid)[PTM_KNN]) {
-  const int si = snap_index(K);
-  const uint64_t lab = bst.lam[si];
+__device__ void finalize(const FrameDesc &d, const Scratch &sm, const float4 *tplw, const Best &bst, int idi) {
+  const int K = bst.K;
+  const uint64_t lab = bst.lam(K);
   const uint64_t cand = __ldg((const unsigned long long *)&ptm_cand[bst.cand]);
   const int S = (int)(cand >> 60) & 7;
   float Sm[3][3];
-  cov_matrix<K>(tplw, S, lab, cand, dx, dy, dz, Sm);
+  cov_matrix(K, sm, tplw, S, lab, cand, Sm);
   float mx, my, mz, Gv;
-  data_moments<K>(dx, dy, dz, mx, my, mz, Gv);
+  data_moments(K, sm, mx, my, mz, Gv);
   const float Gw = tplw[S * 15].w;
   float lam, q[4];
   {
@@ -429,11 +422,11 @@ __device__ void finalize(const FrameDesc &d, const Scratch &sm, const float4 *tp
   }
   float lsum = sqrtf(mx * mx + my * my + mz * mz);
   uint64_t corr = 0;
-#pragma unroll
+#pragma unroll 2
   for (int j = 0; j < K; j++) {
     int slot = nib(cand, nib(lab, j) - 1);
     float4 w = tplw[S * 15 + slot];
-    float vx = dx[j] - mx, vy = dy[j] - my, vz = dz[j] - mz;
+    float vx = sm.DX(j) - mx, vy = sm.DY(j) - my, vz = sm.DZ(j) - mz;
     float rx = R[0][0] * w.x + R[0][1] * w.y + R[0][2] * w.z;
     float ry = R[1][0] * w.x + R[1][1] * w.y + R[1][2] * w.z;
     float rz = R[2][0] * w.x + R[2][1] * w.y + R[2][2] * w.z;
@@ -458,13 +451,12 @@ __device__ void finalize(const FrameDesc &d, const Scratch &sm, const float4 *tp
   count(d, C_MATCHED);
   // correspondence: smallest member of its orbit (R12), atom ids per slot
   const uint64_t cp = canonical_corr(S, K, corr);
-  for (int j = 0; j < K; j++) sm.Q(j, 0) = nid[j];
   if (d.structure) d.structure[a] = (int8_t)(S + 1);
   if (d.rmsd) d.rmsd[a] = rmsd;
   if (d.scale) d.scale[a] = s;
   if (d.corr) {
     d.corr[15 * a] = idi;
-    for (int sl = 1; sl < 15; sl++) d.corr[15 * a + sl] = sl <= K ? sm.Q(nib(cp, 15 - sl) - 1, 0) : -1;
+    for (int sl = 1; sl < 15; sl++) d.corr[15 * a + sl] = sl <= K ? sm.NID(nib(cp, 15 - sl) - 1) : -1;
   }
   // orientation in the fundamental zone: the equivalent rotation Q g with the
   // largest |w| (smallest angle); ties keep the earlier group element (Sec. 7)
@@ -495,10 +487,13 @@ __device__ void finalize(const FrameDesc &d, const Scratch &sm, const float4 *tp
     for (int i = 0; i < 3; i++)
       for (int j = 0; j < 3; j++) AA[i][j] = A[i][0] * A[j][0] + A[i][1] * A[j][1] + A[i][2] * A[j][2];
     jacobi3(AA, X);
-    float sig[3];
-    int imin = 0;
-    for (int i = 0; i < 3; i++) { sig[i] = sqrtf(fmaxf(AA[i][i], 0.f)); if (sig[i] < sig[imin]) imin = i; }
-    if (det3<float>(A) < 0.f) sig[imin] = -sig[imin];
+    float s0 = sqrtf(fmaxf(AA[0][0], 0.f)), s1 = sqrtf(fmaxf(AA[1][1], 0.f)), s2 = sqrtf(fmaxf(AA[2][2], 0.f));
+    if (det3<float>(A) < 0.f) {         // U must stay proper: flip the smallest singular value
+      if (s0 <= s1 && s0 <= s2) s0 = -s0;
+      else if (s1 <= s2) s1 = -s1;
+      else s2 = -s2;
+    }
+    const float sig[3] = {s0, s1, s2};
     for (int i = 0; i < 3; i++)
       for (int j = 0; j < 3; j++)
         d.strain[9 * a + 3 * i + j] = X[i][0] * sig[0] * X[j][0] + X[i][1] * sig[1] * X[j][1] + X[i][2] * sig[2] * X[j][2];
@@ -508,7 +503,7 @@ __device__ void finalize(const FrameDesc &d, const Scratch &sm, const float4 *tp
     int8_t lab8 = PTM_ALLOY_NONE;
     if (d.species && (S == 1 || S == 4)) {
       const int8_t c = __ldg(d.species + a);
-      auto same = [&](int sl) { return __ldg(d.species + sm.Q(nib(cp, 15 - sl) - 1, 0)) == c; };
+      auto same = [&](int sl) { return __ldg(d.species + sm.NID(nib(cp, 15 - sl) - 1)) == c; };
       if (S == 1) {          // FCC: slots 1-4 in z = 0, 5-8 in y = 0, 9-12 in x = 0
         int sp = 0, op = 0;
         for (int p = 0; p < 3; p++) {
@@ -559,8 +554,6 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
   count(d, C_ATOMS);
 
   // ---- neighbours (Sec. 3)
-  float dx[PTM_KNN], dy[PTM_KNN], dz[PTM_KNN];
-  int nid[PTM_KNN];
   int cnt;
   {
     T Ld2[PTM_KNN];
@@ -570,8 +563,8 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
     T emax = 0;
 #pragma unroll
     for (int t = 0; t < PTM_KNN; t++) {
-      nid[t] = Lid[t];
-      dx[t] = dy[t] = dz[t] = 0.f;
+      sm.NID(t) = Lid[t];
+      sm.DX(t) = sm.DY(t) = sm.DZ(t) = 0.f;
       if (t >= cnt) continue;
       T xj, yj, zj;
       int idj;
@@ -585,17 +578,17 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
       // neighbour vectors for the metric steps: the contract values, or for a
       // shifted image an error-free FP32 sum of difference and shift
       if constexpr (F64) {
-        dx[t] = (float)cx; dy[t] = (float)cy; dz[t] = (float)cz;
+        sm.DX(t) = (float)cx; sm.DY(t) = (float)cy; sm.DZ(t) = (float)cz;
       } else {
         if (a0 == 0 && a1 == 0 && a2 == 0) {
-          dx[t] = cx; dy[t] = cy; dz[t] = cz;
+          sm.DX(t) = cx; sm.DY(t) = cy; sm.DZ(t) = cz;
         } else {
           float hx, hy, hz, lx, ly, lz;
           shift_f32(d, a0, a1, a2, hx, hy, hz, lx, ly, lz);
           float p, e1, q2, e2;
-          two_sum(xj, -xi, p, e1); two_sum(p, hx, q2, e2); dx[t] = q2 + (e1 + (e2 + lx));
-          two_sum(yj, -yi, p, e1); two_sum(p, hy, q2, e2); dy[t] = q2 + (e1 + (e2 + ly));
-          two_sum(zj, -zi, p, e1); two_sum(p, hz, q2, e2); dz[t] = q2 + (e1 + (e2 + lz));
+          two_sum(xj, -xi, p, e1); two_sum(p, hx, q2, e2); sm.DX(t) = q2 + (e1 + (e2 + lx));
+          two_sum(yj, -yi, p, e1); two_sum(p, hy, q2, e2); sm.DY(t) = q2 + (e1 + (e2 + ly));
+          two_sum(zj, -zi, p, e1); two_sum(p, hz, q2, e2); sm.DZ(t) = q2 + (e1 + (e2 + lz));
         }
       }
     }
@@ -627,17 +620,17 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
   Best bst;
   bst.b1 = bst.b2 = INFINITY;
   bst.K = -1; bst.cand = -1; bst.fp64 = 0;
-  bst.ent[0] = bst.ent[1] = bst.ent[2] = -1;
-  bst.lam[0] = bst.lam[1] = bst.lam[2] = 0;
+  bst.ent6 = bst.ent12 = bst.ent14 = -1;
+  bst.lam6 = bst.lam12 = bst.lam14 = 0;
   const uint32_t mask = d.mask;
   int kmax = (mask & 16) ? 14 : ((mask & 14) ? 12 : 6);
   kmax = min(kmax, cnt);
   if (kmax >= 6) {
     int nf = hull_init(sm, d);
     for (int p = 4; p <= kmax; p++) {
-      if (p == 6 && (mask & 1)) snapshot<6>(sm, d, tplw, nf, dx, dy, dz, bst);
-      if (p == 12 && (mask & 14)) snapshot<12>(sm, d, tplw, nf, dx, dy, dz, bst);
-      if (p == 14 && (mask & 16)) snapshot<14>(sm, d, tplw, nf, dx, dy, dz, bst);
+      // the hull now holds neighbours 0..p-1: complete for K = 6, 12, 14
+      const bool want = (p == 6 && (mask & 1)) || (p == 12 && (mask & 14)) || (p == 14 && (mask & 16));
+      if (want) snapshot(p, sm, d, tplw, nf, bst);
       if (p == kmax) break;
       nf = hull_insert(sm, nf, p, d);
       if (nf < 0) break;
@@ -646,11 +639,10 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
   if (bst.K < 0) { write_unmatched(d, idi); return; }
   if (bst.b2 <= bst.b1 + PTM_BAND) {
     count(d, C_TIE64);
-    rerank_fp64<F64>(d, s, bst, bx, by, bz, wix, wiy, wiz, wrapped);
+    const int w = rerank_fp64<F64>(d, s, bst, bx, by, bz, wix, wiy, wiz, wrapped);
+    if (w >= 0) { bst.K = w >> 16; bst.cand = w & 0xffff; }
   }
-  if (bst.K == 6) finalize<6>(d, sm, tplw, bst, idi, dx, dy, dz, nid);
-  else if (bst.K == 12) finalize<12>(d, sm, tplw, bst, idi, dx, dy, dz, nid);
-  else finalize<14>(d, sm, tplw, bst, idi, dx, dy, dz, nid);
+  finalize(d, sm, tplw, bst, idi);
 }
 
 // ------------------------------------------------------------------ kernels
@@ -780,11 +772,13 @@ constexpr size_t atom_smem_bytes() {
 // The frame descriptor travels by value in the kernel parameters, so back-to-back
 // asynchronous calls never share a staging buffer.
 template <bool F64>
-__global__ void __launch_bounds__(PTM_BLOCK, 4) k_atoms(const __grid_constant__ FrameDesc d) {
+__global__ void __launch_bounds__(PTM_BLOCK, 5) k_atoms(const __grid_constant__ FrameDesc d) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t *th = (uint64_t *)smem;
   int *q = (int *)(th + 14 * PTM_BLOCK);
-  uint32_t *code = (uint32_t *)(q + 42 * PTM_BLOCK);
+  float *nv = (float *)(q + 42 * PTM_BLOCK);
+  int *nid = (int *)(nv + 42 * PTM_BLOCK);
+  uint32_t *code = (uint32_t *)(nid + 14 * PTM_BLOCK);
   uint16_t *fac = (uint16_t *)(code + 10 * PTM_BLOCK);
   uint16_t *used = fac + 24 * PTM_BLOCK;
   float4 *tplw = (float4 *)(used + 14 * PTM_BLOCK);
@@ -794,7 +788,8 @@ __global__ void __launch_bounds__(PTM_BLOCK, 4) k_atoms(const __grid_constant__ 
   }
   __syncthreads();
   Scratch sm;
-  sm.q = q; sm.fac = fac; sm.th = th; sm.used = used; sm.code = code; sm.t = threadIdx.x;
+  sm.q = q; sm.nv = nv; sm.nid = nid; sm.fac = fac; sm.th = th; sm.used = used; sm.code = code;
+  sm.t = threadIdx.x;
   int64_t s = (int64_t)blockIdx.x * PTM_BLOCK + threadIdx.x;
   if (s >= d.n) return;
   classify_atom<F64>(d, (int)s, sm, tplw);
