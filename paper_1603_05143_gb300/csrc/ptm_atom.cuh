@@ -72,13 +72,14 @@ __device__ __forceinline__ void count(const FrameDesc &d, int which, unsigned lo
 struct Scratch {
   float *nv;         // [42][B]  neighbour vectors for the metric steps (x[14], y[14], z[14])
   int *nid;          // [14][B]  neighbour atom ids
-  int *q;            // [42][B]  quantised neighbour vectors
+  float *q;          // [42][B]  quantised neighbour vectors (integers |q| <= 2^19, exact in FP32)
   uint16_t *fac;     // [24][B]  hull facets a | b << 4 | c << 8 (ccw from outside)
   uint64_t *th;      // [14][B]  third vertex of directed edge u->v, nibble v of row u (0xF none)
   uint16_t *used;    // [14][B]  directed-edge bit rows (hull horizon, Weinberg walk)
   uint32_t *code;    // [10][B]  best Weinberg code so far (nibbles)
   int t;             // thread index in block
-  __device__ __forceinline__ int &Q(int p, int c) const { return q[(3 * p + c) * PTM_BLOCK + t]; }
+  __device__ __forceinline__ float &Q(int p, int c) const { return q[(3 * p + c) * PTM_BLOCK + t]; }
+  __device__ __forceinline__ int QI(int p, int c) const { return (int)q[(3 * p + c) * PTM_BLOCK + t]; }
   __device__ __forceinline__ float &DX(int j) const { return nv[j * PTM_BLOCK + t]; }
   __device__ __forceinline__ float &DY(int j) const { return nv[(PTM_KNN + j) * PTM_BLOCK + t]; }
   __device__ __forceinline__ float &DZ(int j) const { return nv[(2 * PTM_KNN + j) * PTM_BLOCK + t]; }
@@ -159,7 +160,7 @@ __device__ __forceinline__ long long orient_raw(int ax, int ay, int az, int bx, 
 
 // Entry (r, c) of the matrix [[q_r, 1]] for sorted row r of the four points.
 __device__ __forceinline__ long long sos_entry(const Scratch &sm, const int *pt, int r, int c) {
-  return c == 3 ? 1ll : (long long)sm.Q(pt[r], c);
+  return c == 3 ? 1ll : (long long)sm.QI(pt[r], c);
 }
 
 // Simulation of Simplicity (Edelsbrunner & Muecke): coordinate c of the point of
@@ -200,13 +201,49 @@ __device__ __noinline__ int orient_sos_slow(const Scratch &sm, int a, int b, int
   return 1;   // unreachable: the last terms have minor 1
 }
 
-__device__ __forceinline__ int orient_sos(const Scratch &sm, int a, int b, int c, int p, const FrameDesc &d) {
-  long long o = orient_raw(sm.Q(a, 0), sm.Q(a, 1), sm.Q(a, 2), sm.Q(b, 0), sm.Q(b, 1), sm.Q(b, 2),
-                           sm.Q(c, 0), sm.Q(c, 1), sm.Q(c, 2), sm.Q(p, 0), sm.Q(p, 1), sm.Q(p, 2));
+// FP32 filter for orient on the quantised integers.  The coordinates are exact
+// floats (|q| <= 2^19), so are the differences (<= 2^20).  Each product of the
+// cross product rounds by <= 2^16 and the fused difference by <= 2^17, so each
+// normal component is within 2^18 of exact; the fused dot product then adds at
+// most 2^37 + 3 * 2^38 (propagated) + 2^38 + 2^39 (roundings) = 13 * 2^37 < 2^41.
+// |det| > 2^42 therefore fixes the sign; otherwise 0 ("decide exactly").
+__device__ __forceinline__ int orient_filter(float ax, float ay, float az, float bx, float by, float bz, float cx,
+                                             float cy, float cz, float px, float py, float pz) {
+  const float ux = bx - ax, uy = by - ay, uz = bz - az;
+  const float vx = cx - ax, vy = cy - ay, vz = cz - az;
+  const float wx = px - ax, wy = py - ay, wz = pz - az;
+  const float nx = fmaf(uy, vz, -(uz * vy));
+  const float ny = fmaf(uz, vx, -(ux * vz));
+  const float nz = fmaf(ux, vy, -(uy * vx));
+  const float det = fmaf(nx, wx, fmaf(ny, wy, nz * wz));
+  return det > 0x1p42f ? 1 : (det < -0x1p42f ? -1 : 0);
+}
+
+__device__ __noinline__ int orient_exact_sos(const Scratch &sm, int a, int b, int c, int p, const FrameDesc &d) {
+  long long o = orient_raw(sm.QI(a, 0), sm.QI(a, 1), sm.QI(a, 2), sm.QI(b, 0), sm.QI(b, 1), sm.QI(b, 2),
+                           sm.QI(c, 0), sm.QI(c, 1), sm.QI(c, 2), sm.QI(p, 0), sm.QI(p, 1), sm.QI(p, 2));
   if (o > 0) return 1;
   if (o < 0) return -1;
   count(d, C_SOS);
   return orient_sos_slow(sm, a, b, c, p);
+}
+
+// Orientation of neighbours a, b, c, p with the SoS tie rule; never 0.
+__device__ __forceinline__ int orient_sos(const Scratch &sm, int a, int b, int c, int p, float px, float py,
+                                          float pz, const FrameDesc &d) {
+  const int s = orient_filter(sm.Q(a, 0), sm.Q(a, 1), sm.Q(a, 2), sm.Q(b, 0), sm.Q(b, 1), sm.Q(b, 2), sm.Q(c, 0),
+                              sm.Q(c, 1), sm.Q(c, 2), px, py, pz);
+  return s ? s : orient_exact_sos(sm, a, b, c, p, d);
+}
+
+// Sign of orient(a, b, c, origin) without SoS (the centre test of Algorithm 1).
+__device__ __forceinline__ int orient_centre(const Scratch &sm, int a, int b, int c) {
+  const int s = orient_filter(sm.Q(a, 0), sm.Q(a, 1), sm.Q(a, 2), sm.Q(b, 0), sm.Q(b, 1), sm.Q(b, 2), sm.Q(c, 0),
+                              sm.Q(c, 1), sm.Q(c, 2), 0.f, 0.f, 0.f);
+  if (s) return s;
+  const long long o = orient_raw(sm.QI(a, 0), sm.QI(a, 1), sm.QI(a, 2), sm.QI(b, 0), sm.QI(b, 1), sm.QI(b, 2),
+                                 sm.QI(c, 0), sm.QI(c, 1), sm.QI(c, 2), 0, 0, 0);
+  return (o > 0) - (o < 0);
 }
 
 // ------------------------------------------------------------ incremental hull
@@ -214,7 +251,7 @@ __device__ __forceinline__ uint16_t fpack(int a, int b, int c) { return (uint16_
 
 // Tetrahedron on points 0..3, facets counter-clockwise seen from outside.
 __device__ __forceinline__ int hull_init(const Scratch &sm, const FrameDesc &d) {
-  int o = orient_sos(sm, 0, 1, 2, 3, d);
+  int o = orient_sos(sm, 0, 1, 2, 3, sm.Q(3, 0), sm.Q(3, 1), sm.Q(3, 2), d);
   if (o < 0) {
     sm.F(0) = fpack(0, 1, 2); sm.F(1) = fpack(0, 3, 1); sm.F(2) = fpack(1, 3, 2); sm.F(3) = fpack(0, 2, 3);
   } else {
@@ -226,9 +263,10 @@ __device__ __forceinline__ int hull_init(const Scratch &sm, const FrameDesc &d) 
 // Add point p; returns the new facet count, or -1 when p lies inside the hull.
 __device__ int hull_insert(const Scratch &sm, int nf, int p, const FrameDesc &d) {
   uint32_t vis = 0;
+  const float px = sm.Q(p, 0), py = sm.Q(p, 1), pz = sm.Q(p, 2);
   for (int f = 0; f < nf; f++) {
     int v = sm.F(f);
-    if (orient_sos(sm, v & 15, (v >> 4) & 15, (v >> 8) & 15, p, d) > 0) vis |= 1u << f;
+    if (orient_sos(sm, v & 15, (v >> 4) & 15, (v >> 8) & 15, p, px, py, pz, d) > 0) vis |= 1u << f;
   }
   if (!vis) return -1;
   for (int v = 0; v < PTM_KNN; v++) sm.U(v) = 0;
@@ -326,11 +364,13 @@ __device__ int weinberg_walk(const Scratch &sm, int K, int u, int v, bool first,
   return 0;
 }
 
-// Canonical code of the current K-vertex hull: among starts with the largest
-// deg(u), then the largest deg(v), the smallest code.  Returns the labelling
-// (nibble t = label of neighbour t) and the code hash; false on an internal
-// error.  The candidate starts are visited by one flat loop, so the threads of
-// a warp run their walks together.
+// Canonical code of the current K-vertex hull.  Every directed edge u->v gets
+// the key (deg u, deg v, deg w1, deg w2) with (u, v, w1) and (v, u, w2) the two
+// facets on the edge; among the edges with the largest key the smallest
+// Weinberg code wins (definition in tables.py).  Returns the labelling (nibble
+// t = label of neighbour t) and the code hash; false on an internal error.
+// Start edges are kept as a bit mask over (facet, corner) and visited by one
+// flat loop, so the threads of a warp run their walks together.
 __device__ bool canonical(const Scratch &sm, int K, int nf, uint64_t &labels, uint64_t &hash,
                           const FrameDesc &d) {
   uint64_t deg = 0;
@@ -344,44 +384,48 @@ __device__ bool canonical(const Scratch &sm, int K, int nf, uint64_t &labels, ui
     sm.TH(c) = setnib(sm.TH(c), a, b);
     deg += (1ull << (4 * a)) + (1ull << (4 * b)) + (1ull << (4 * c));
   }
-  int du = 0;
+  // keys of the directed edges (a->b, b->c, c->a of every facet); keep the maximum
+  uint32_t top = 0;
+  uint64_t m0 = 0;          // edge ids 0..63 (id = 3 f + corner)
+  uint32_t m1 = 0;          // edge ids 64..71
+  for (int f = 0; f < nf; f++) {
+    const int v = sm.F(f);
+    const int p0 = v & 15, p1 = (v >> 4) & 15, p2 = (v >> 8) & 15;
+    const int dg0 = nib(deg, p0), dg1 = nib(deg, p1), dg2 = nib(deg, p2);
 #pragma unroll
-  for (int x = 0; x < PTM_KNN; x++) if (x < K) du = max(du, nib(deg, x));
-  uint32_t umask = 0;
-#pragma unroll
-  for (int x = 0; x < PTM_KNN; x++) if (x < K && nib(deg, x) == du) umask |= 1u << x;
-  int dv = 0;
-  for (uint32_t m = umask; m; m &= m - 1) {
-    const uint64_t tx = sm.TH(__ffs(m) - 1);
-#pragma unroll
-    for (int y = 0; y < PTM_KNN; y++)
-      if (y < K && nib(tx, y) != 15) dv = max(dv, nib(deg, y));
+    for (int e = 0; e < 3; e++) {
+      const int x = e == 0 ? p0 : (e == 1 ? p1 : p2);      // edge x -> y, third vertex z
+      const int y = e == 0 ? p1 : (e == 1 ? p2 : p0);
+      const int dx = e == 0 ? dg0 : (e == 1 ? dg1 : dg2);
+      const int dy = e == 0 ? dg1 : (e == 1 ? dg2 : dg0);
+      const int dz = e == 0 ? dg2 : (e == 1 ? dg0 : dg1);
+      const int w2 = nib(sm.TH(y), x);
+      const uint32_t key = (uint32_t)((dx << 12) | (dy << 8) | (dz << 4) | nib(deg, w2));
+      const int id = 3 * f + e;
+      if (key > top) { top = key; m0 = 0; m1 = 0; }
+      if (key == top) { if (id < 64) m0 |= 1ull << id; else m1 |= 1u << (id - 64); }
+    }
   }
   // K = 12 with every degree 5 is the icosahedron, K = 6 with every degree 4 the
   // octahedron: every directed edge is equivalent, one walk suffices
-  const bool transitive = (K == 12 && du == 5 && dv == 5) || (K == 6 && du == 4 && dv == 4);
+  const bool transitive = (K == 12 && top == 0x5555u) || (K == 6 && top == 0x4444u);
   bool first = true;
-  uint32_t vmask = 0;
-  int u = 0;
-  for (;;) {
-    while (vmask == 0 && umask) {
-      u = __ffs(umask) - 1;
-      umask &= umask - 1;
-      const uint64_t tu = sm.TH(u);
-#pragma unroll
-      for (int y = 0; y < PTM_KNN; y++)
-        if (y < K && nib(tu, y) != 15 && nib(deg, y) == dv) vmask |= 1u << y;
-    }
-    if (!vmask) break;
-    const int v = __ffs(vmask) - 1;
-    vmask &= vmask - 1;
+  while (m0 | m1) {
+    int id;
+    if (m0) { id = __ffsll((long long)m0) - 1; m0 &= m0 - 1; }
+    else { id = 64 + __ffs(m1) - 1; m1 &= m1 - 1; }
+    const int v = sm.F(id / 3), e = id % 3;
+    const int p0 = v & 15, p1 = (v >> 4) & 15, p2 = (v >> 8) & 15;
+    const int su = e == 0 ? p0 : (e == 1 ? p1 : p2);
+    const int sv = e == 0 ? p1 : (e == 1 ? p2 : p0);
     uint64_t lab = 0;
-    const int r = weinberg_walk(sm, K, u, v, first, lab, d);
+    const int r = weinberg_walk(sm, K, su, sv, first, lab, d);
     if (first && r != 1) return false;
     if (r == 1) labels = lab;
     first = false;
     if (transitive) break;
   }
+  if (first) return false;
   // hash of the packed code; words past its end count as zero, as the generator packs them
   const int LEN = 2 * (3 * K - 6) + 1;
   uint64_t h = PTM_HASH_INIT;

@@ -62,75 +62,89 @@ __device__ __forceinline__ double contract_d2(double a, double b, double c) {
 }
 
 // ----------------------------------------------------------------- kNN
-// The 14 nearest images of atom s by (d2, atom id, image), scanning the
-// (2R+1)^3 cells around it; R grows until the 14th distance lies inside the
-// radius the scanned cells are guaranteed to cover.  Returns the neighbour
-// count (14, fewer only for a small fully non-periodic system) or -1.
-template <bool F64>
-__device__ int knn(const FrameDesc &d, int s, typename RT<F64>::T xi, typename RT<F64>::T yi,
-                   typename RT<F64>::T zi, int bx, int by, int bz, int wix, int wiy, int wiz, bool wrapped,
-                   typename RT<F64>::T (&Ld2)[PTM_KNN], int (&Lid)[PTM_KNN], int (&Ljs)[PTM_KNN],
-                   int (&Limg)[PTM_KNN]) {
+// Visit every (atom, image) in the (2R+1)^3 cells around cell (bx, by, bz):
+// visit(j, d2, idj, image) with d2 by the distance contract.
+template <bool F64, typename V>
+__device__ __forceinline__ void scan_cells(const FrameDesc &d, int s, typename RT<F64>::T xi,
+                                           typename RT<F64>::T yi, typename RT<F64>::T zi, int bx, int by, int bz,
+                                           int wix, int wiy, int wiz, bool wrapped, int R, V &&visit) {
   typedef typename RT<F64>::T T;
   const int nbx = d.nb[0], nby = d.nb[1], nbz = d.nb[2];
-  const float over = __int_as_float(d.dstat[1]);
+  for (int dx = -R; dx <= R; dx++) {
+    int cx = bx + dx, mx = 0;
+    if (d.pbc[0]) { mx = floordiv(cx, nbx); cx -= mx * nbx; } else if (cx < 0 || cx >= nbx) continue;
+    for (int dy = -R; dy <= R; dy++) {
+      int cy = by + dy, my = 0;
+      if (d.pbc[1]) { my = floordiv(cy, nby); cy -= my * nby; } else if (cy < 0 || cy >= nby) continue;
+      for (int dz = -R; dz <= R; dz++) {
+        int cz = bz + dz, mz = 0;
+        if (d.pbc[2]) { mz = floordiv(cz, nbz); cz -= mz * nbz; } else if (cz < 0 || cz >= nbz) continue;
+        const int c = (cx * nby + cy) * nbz + cz;
+        const int j0 = __ldg(d.cell_start + c), j1 = __ldg(d.cell_start + c + 1);
+        if (j0 == j1) continue;
+        const int n0 = mx + wix, n1 = my + wiy, n2 = mz + wiz;
+        T sx, sy, sz;
+        contract_shift<F64>(d, n0, n1, n2, sx, sy, sz);
+        for (int j = j0; j < j1; j++) {
+          T xj, yj, zj;
+          int idj;
+          load_atom<F64>(d, j, xj, yj, zj, idj);
+          int a0 = n0, a1 = n1, a2 = n2;
+          if (wrapped) {
+            int w0, w1, w2;
+            img_unpack(__ldg(d.wrapv + j), w0, w1, w2);
+            a0 -= w0; a1 -= w1; a2 -= w2;
+            contract_shift<F64>(d, a0, a1, a2, sx, sy, sz);
+          }
+          if (j == s && a0 == 0 && a1 == 0 && a2 == 0) continue;
+          const T ex = contract_dr(xj, xi, sx), ey = contract_dr(yj, yi, sy), ez = contract_dr(zj, zi, sz);
+          visit(j, contract_d2(ex, ey, ez), idj, a0, a1, a2);
+        }
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ bool search_complete(const FrameDesc &d, int R, float d2_last) {
+  const float rg = (float)R * d.min_cell_width - __int_as_float(d.dstat[1]);
+  return rg > 0.f && d2_last < rg * rg * (1.f - 1e-3f);
+}
+
+// General kNN: the 14 nearest images of atom s by the full key (d2, atom id,
+// image), R growing until the 14th distance lies inside the radius the scanned
+// cells are guaranteed to cover.  Returns the neighbour count (14, fewer only
+// for a small fully non-periodic system) or -1.
+template <bool F64>
+__device__ __noinline__ int knn(const FrameDesc &d, int s, typename RT<F64>::T xi, typename RT<F64>::T yi,
+                                typename RT<F64>::T zi, int bx, int by, int bz, int wix, int wiy, int wiz,
+                                bool wrapped, typename RT<F64>::T (&Ld2)[PTM_KNN], int (&Lid)[PTM_KNN],
+                                int (&Ljs)[PTM_KNN], int (&Limg)[PTM_KNN]) {
+  typedef typename RT<F64>::T T;
   const T INF = (T)INFINITY;
   for (int R = 1; R <= PTM_RMAX; R++) {
 #pragma unroll
     for (int t = 0; t < PTM_KNN; t++) { Ld2[t] = INF; Lid[t] = 0x7fffffff; Ljs[t] = -1; Limg[t] = 0x7fffffff; }
-    for (int dx = -R; dx <= R; dx++) {
-      int cx = bx + dx, mx = 0;
-      if (d.pbc[0]) { mx = floordiv(cx, nbx); cx -= mx * nbx; } else if (cx < 0 || cx >= nbx) continue;
-      for (int dy = -R; dy <= R; dy++) {
-        int cy = by + dy, my = 0;
-        if (d.pbc[1]) { my = floordiv(cy, nby); cy -= my * nby; } else if (cy < 0 || cy >= nby) continue;
-        for (int dz = -R; dz <= R; dz++) {
-          int cz = bz + dz, mz = 0;
-          if (d.pbc[2]) { mz = floordiv(cz, nbz); cz -= mz * nbz; } else if (cz < 0 || cz >= nbz) continue;
-          int c = (cx * nby + cy) * nbz + cz;
-          int j0 = __ldg(d.cell_start + c), j1 = __ldg(d.cell_start + c + 1);
-          if (j0 == j1) continue;
-          const int n0 = mx + wix, n1 = my + wiy, n2 = mz + wiz;
-          T sx, sy, sz;
-          contract_shift<F64>(d, n0, n1, n2, sx, sy, sz);
-          for (int j = j0; j < j1; j++) {
-            T xj, yj, zj;
-            int idj;
-            load_atom<F64>(d, j, xj, yj, zj, idj);
-            int a0 = n0, a1 = n1, a2 = n2;
-            if (wrapped) {
-              int wj = __ldg(d.wrapv + j);
-              int w0, w1, w2;
-              img_unpack(wj, w0, w1, w2);
-              a0 -= w0; a1 -= w1; a2 -= w2;
-              contract_shift<F64>(d, a0, a1, a2, sx, sy, sz);
-            }
-            if (j == s && a0 == 0 && a1 == 0 && a2 == 0) continue;
-            T ex = contract_dr(xj, xi, sx), ey = contract_dr(yj, yi, sy), ez = contract_dr(zj, zi, sz);
-            T d2 = contract_d2(ex, ey, ez);
-            if (!(d2 <= Ld2[PTM_KNN - 1])) continue;
-            int img = img_pack(a0, a1, a2);
-            if (!key_less(d2, idj, img, Ld2[PTM_KNN - 1], Lid[PTM_KNN - 1], Limg[PTM_KNN - 1])) continue;
-            // insertion into the sorted list (all indices static: stays in registers)
-            bool above = true;
+    scan_cells<F64>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, R,
+                    [&](int j, T d2, int idj, int a0, int a1, int a2) {
+      if (!(d2 <= Ld2[PTM_KNN - 1])) return;
+      const int img = img_pack(a0, a1, a2);
+      if (!key_less(d2, idj, img, Ld2[PTM_KNN - 1], Lid[PTM_KNN - 1], Limg[PTM_KNN - 1])) return;
+      // insertion into the sorted list (all indices static: stays in registers)
+      bool above = true;
 #pragma unroll
-            for (int t = PTM_KNN - 1; t >= 1; t--) {
-              bool lt = key_less(d2, idj, img, Ld2[t - 1], Lid[t - 1], Limg[t - 1]);
-              if (lt) { Ld2[t] = Ld2[t - 1]; Lid[t] = Lid[t - 1]; Ljs[t] = Ljs[t - 1]; Limg[t] = Limg[t - 1]; }
-              else if (above) { Ld2[t] = d2; Lid[t] = idj; Ljs[t] = j; Limg[t] = img; }
-              above = lt;
-            }
-            if (above) { Ld2[0] = d2; Lid[0] = idj; Ljs[0] = j; Limg[0] = img; }
-          }
-        }
+      for (int t = PTM_KNN - 1; t >= 1; t--) {
+        bool lt = key_less(d2, idj, img, Ld2[t - 1], Lid[t - 1], Limg[t - 1]);
+        if (lt) { Ld2[t] = Ld2[t - 1]; Lid[t] = Lid[t - 1]; Ljs[t] = Ljs[t - 1]; Limg[t] = Limg[t - 1]; }
+        else if (above) { Ld2[t] = d2; Lid[t] = idj; Ljs[t] = j; Limg[t] = img; }
+        above = lt;
       }
-    }
-    float rg = (float)R * d.min_cell_width - over;
-    if (rg > 0.f && (float)Ld2[PTM_KNN - 1] < rg * rg * (1.f - 1e-3f)) {
+      if (above) { Ld2[0] = d2; Lid[0] = idj; Ljs[0] = j; Limg[0] = img; }
+    });
+    if (search_complete(d, R, (float)Ld2[PTM_KNN - 1])) {
       if (R > 1) count(d, C_KNN_WIDE);
       return PTM_KNN;
     }
-    if (!d.pbc[0] && !d.pbc[1] && !d.pbc[2] && R >= max(nbx, max(nby, nbz))) {
+    if (!d.pbc[0] && !d.pbc[1] && !d.pbc[2] && R >= max(d.nb[0], max(d.nb[1], d.nb[2]))) {
       int cnt = 0;
 #pragma unroll
       for (int t = 0; t < PTM_KNN; t++) cnt += Ljs[t] >= 0;
@@ -139,6 +153,54 @@ __device__ int knn(const FrameDesc &d, int s, typename RT<F64>::T xi, typename R
   }
   count(d, C_KNN_FAIL);
   return -1;
+}
+
+// General kNN writing its result like knn_fast: sorted index of neighbour t in
+// scratch row NID(t), its packed image in row DX(t).
+template <bool F64>
+__device__ __noinline__ int knn_to_scratch(const FrameDesc &d, const Scratch &sm, int s, typename RT<F64>::T xi,
+                                           typename RT<F64>::T yi, typename RT<F64>::T zi, int bx, int by, int bz,
+                                           int wix, int wiy, int wiz, bool wrapped) {
+  typename RT<F64>::T Ld2[PTM_KNN];
+  int Lid[PTM_KNN], Ljs[PTM_KNN], Limg[PTM_KNN];
+  const int cnt = knn<F64>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, Ld2, Lid, Ljs, Limg);
+  for (int t = 0; t < PTM_KNN; t++) { sm.NID(t) = Ljs[t]; sm.DX(t) = __int_as_float(Limg[t]); }
+  return cnt;
+}
+
+// Fast kNN for the common case (27 cells suffice, no equal distances among the
+// 15 nearest): pass 1 keeps the 15 smallest distances with a min/max network;
+// pass 2 rescans and drops each of the 14 nearest into its rank slot (the
+// scratch rows NID / DX hold sorted index and image until the caller reads
+// them).  With no equal distances the distance order is the full key order.
+// Returns false when the general kNN must decide.
+template <bool F64>
+__device__ __forceinline__ bool knn_fast(const FrameDesc &d, const Scratch &sm, int s, typename RT<F64>::T xi,
+                                         typename RT<F64>::T yi, typename RT<F64>::T zi, int bx, int by, int bz) {
+  typedef typename RT<F64>::T T;
+  T L[PTM_KNN + 1];
+#pragma unroll
+  for (int t = 0; t <= PTM_KNN; t++) L[t] = (T)INFINITY;
+  scan_cells<F64>(d, s, xi, yi, zi, bx, by, bz, 0, 0, 0, false, 1, [&](int j, T d2, int, int, int, int) {
+    if (!(d2 < L[PTM_KNN])) return;
+    T x = d2;
+#pragma unroll
+    for (int t = 0; t <= PTM_KNN; t++) { const T lo = fmin(L[t], x); x = fmax(L[t], x); L[t] = lo; }
+  });
+  bool distinct = L[PTM_KNN] < (T)INFINITY;
+#pragma unroll
+  for (int t = 0; t < PTM_KNN; t++) distinct &= L[t] < L[t + 1];
+  if (!distinct || !search_complete(d, 1, (float)L[PTM_KNN - 1])) return false;
+  const T last = L[PTM_KNN - 1];
+  scan_cells<F64>(d, s, xi, yi, zi, bx, by, bz, 0, 0, 0, false, 1, [&](int j, T d2, int, int a0, int a1, int a2) {
+    if (!(d2 <= last)) return;
+    int rank = 0;
+#pragma unroll
+    for (int t = 0; t < PTM_KNN - 1; t++) rank += L[t] < d2;
+    sm.NID(rank) = j;
+    sm.DX(rank) = __int_as_float(img_pack(a0, a1, a2));
+  });
+  return true;
 }
 
 // ---------------------------------------------------------- per-atom state
@@ -244,10 +306,7 @@ __device__ void snapshot(int K, const Scratch &sm, const FrameDesc &d, const flo
   if (nf != 2 * K - 4) return;                    // a neighbour is not a hull vertex
   for (int f = 0; f < nf; f++) {                  // centre strictly inside (exact, no SoS)
     int v = sm.F(f);
-    int a = v & 15, b = (v >> 4) & 15, c = (v >> 8) & 15;
-    long long o = orient_raw(sm.Q(a, 0), sm.Q(a, 1), sm.Q(a, 2), sm.Q(b, 0), sm.Q(b, 1), sm.Q(b, 2),
-                             sm.Q(c, 0), sm.Q(c, 1), sm.Q(c, 2), 0, 0, 0);
-    if (o >= 0) return;
+    if (orient_centre(sm, v & 15, (v >> 4) & 15, (v >> 8) & 15) >= 0) return;
   }
   uint64_t lab = 0, h = 0;
   if (!canonical(sm, K, nf, lab, h, d)) return;
@@ -556,21 +615,27 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
   // ---- neighbours (Sec. 3)
   int cnt;
   {
-    T Ld2[PTM_KNN];
-    int Lid[PTM_KNN], Ljs[PTM_KNN], Limg[PTM_KNN];
-    cnt = knn<F64>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, Ld2, Lid, Ljs, Limg);
+    if (!wrapped && knn_fast<F64>(d, sm, s, xi, yi, zi, bx, by, bz)) cnt = PTM_KNN;
+    else cnt = knn_to_scratch<F64>(d, sm, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped);
     if (cnt < 4) { write_unmatched(d, idi); return; }
-    T emax = 0;
+    // rows NID / DX hold (sorted index, image) of each neighbour; move them to
+    // rows Q(t, 0) / Q(t, 1) (free until quantisation) and keep NID / DX for
+    // ids and vectors
 #pragma unroll
+    for (int t = 0; t < PTM_KNN; t++) { sm.Q(t, 0) = __int_as_float(sm.NID(t)); sm.Q(t, 1) = sm.DX(t); }
+    T emax = 0;
+#pragma unroll 2
     for (int t = 0; t < PTM_KNN; t++) {
-      sm.NID(t) = Lid[t];
+      const int jt = __float_as_int(sm.Q(t, 0)), it = __float_as_int(sm.Q(t, 1));
+      sm.NID(t) = -1;
       sm.DX(t) = sm.DY(t) = sm.DZ(t) = 0.f;
       if (t >= cnt) continue;
       T xj, yj, zj;
       int idj;
-      load_atom<F64>(d, Ljs[t], xj, yj, zj, idj);
+      load_atom<F64>(d, jt, xj, yj, zj, idj);
+      sm.NID(t) = idj;
       int a0, a1, a2;
-      img_unpack(Limg[t], a0, a1, a2);
+      img_unpack(it, a0, a1, a2);
       T sx, sy, sz;
       contract_shift<F64>(d, a0, a1, a2, sx, sy, sz);
       T cx = contract_dr(xj, xi, sx), cy = contract_dr(yj, yi, sy), cz = contract_dr(zj, zi, sz);
@@ -597,21 +662,23 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
     int e;
     if constexpr (F64) frexp(emax, &e); else frexpf(emax, &e);
     const T sc = F64 ? (T)ldexp(1.0, PTM_QBITS - e) : (T)ldexpf(1.f, PTM_QBITS - e);
-#pragma unroll
+#pragma unroll 2
     for (int t = 0; t < PTM_KNN; t++) {
       if (t >= cnt) continue;
+      const int jt = __float_as_int(sm.Q(t, 0)), it = __float_as_int(sm.Q(t, 1));
       T xj, yj, zj;
       int idj;
-      load_atom<F64>(d, Ljs[t], xj, yj, zj, idj);
+      load_atom<F64>(d, jt, xj, yj, zj, idj);
       int a0, a1, a2;
-      img_unpack(Limg[t], a0, a1, a2);
+      img_unpack(it, a0, a1, a2);
       T sx, sy, sz;
       contract_shift<F64>(d, a0, a1, a2, sx, sy, sz);
       T cx = contract_dr(xj, xi, sx), cy = contract_dr(yj, yi, sy), cz = contract_dr(zj, zi, sz);
       if constexpr (F64) {
-        sm.Q(t, 0) = __double2int_rn(cx * sc); sm.Q(t, 1) = __double2int_rn(cy * sc); sm.Q(t, 2) = __double2int_rn(cz * sc);
+        sm.Q(t, 0) = (float)__double2int_rn(cx * sc); sm.Q(t, 1) = (float)__double2int_rn(cy * sc);
+        sm.Q(t, 2) = (float)__double2int_rn(cz * sc);
       } else {
-        sm.Q(t, 0) = __float2int_rn(cx * sc); sm.Q(t, 1) = __float2int_rn(cy * sc); sm.Q(t, 2) = __float2int_rn(cz * sc);
+        sm.Q(t, 0) = rintf(cx * sc); sm.Q(t, 1) = rintf(cy * sc); sm.Q(t, 2) = rintf(cz * sc);
       }
     }
   }
@@ -775,8 +842,8 @@ template <bool F64>
 __global__ void __launch_bounds__(PTM_BLOCK, 5) k_atoms(const __grid_constant__ FrameDesc d) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t *th = (uint64_t *)smem;
-  int *q = (int *)(th + 14 * PTM_BLOCK);
-  float *nv = (float *)(q + 42 * PTM_BLOCK);
+  float *q = (float *)(th + 14 * PTM_BLOCK);
+  float *nv = q + 42 * PTM_BLOCK;
   int *nid = (int *)(nv + 42 * PTM_BLOCK);
   uint32_t *code = (uint32_t *)(nid + 14 * PTM_BLOCK);
   uint16_t *fac = (uint16_t *)(code + 10 * PTM_BLOCK);

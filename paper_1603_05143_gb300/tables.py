@@ -12,12 +12,13 @@ For each reference template of Table 1 this module builds, from geometry alone:
   code, the symmetry-inequivalent correspondences "canonical label -> template
   slot" (Appendix A: equivalent correspondences give equal RMSD).
 
-Canonical form (one embedding, orientation-preserving; Sec. 4): among all
-directed edges u->v of the triangulation, start from those with the largest
-deg(u), then the largest deg(v), and take the lexicographically smallest
-Weinberg code; its first-visit labelling is the canonical labelling.  Degrees
-are isomorphism invariants, so this is a canonical form: two embedded graphs
-get the same code exactly when an orientation-preserving isomorphism exists.
+Canonical form (one embedding, orientation-preserving; Sec. 4): every directed
+edge u->v gets the key (deg u, deg v, deg w1, deg w2), where (u, v, w1) and
+(v, u, w2) are the two facets on the edge; among the edges with the largest
+key (compared in that order) the lexicographically smallest Weinberg code is
+the canonical code and its first-visit labelling the canonical labelling.  The
+key is invariant under orientation-preserving isomorphisms, so two embedded
+graphs get the same code exactly when such an isomorphism exists.
 
 Weinberg walk (counter-clockwise rotation seen from outside): at a new vertex
 leave by the edge after the arrival edge; at an old vertex reached along an edge
@@ -209,18 +210,21 @@ def weinberg(facets, u, v):
     return tuple(code), lab
 
 
+def edge_key(deg, th, a, b):
+    return (deg[a], deg[b], deg[th[(a, b)]], deg[th[(b, a)]])
+
+
 def canonical_form(facets):
-    """(code, labelling, list of canonical start edges) under the degree-keyed
-    definition of the module docstring."""
+    """(code, list of canonical labellings) under the edge-keyed definition of the
+    module docstring."""
     deg: dict = {}
     for f in facets:
         for x in f:
             deg[x] = deg.get(x, 0) + 1
+    th = _third(facets)
     starts = [(a, b) for f in facets for a, b in ((f[0], f[1]), (f[1], f[2]), (f[2], f[0]))]
-    du = max(deg[a] for a, _ in starts)
-    starts = [(a, b) for a, b in starts if deg[a] == du]
-    dv = max(deg[b] for _, b in starts)
-    starts = [(a, b) for a, b in starts if deg[b] == dv]
+    top = max(edge_key(deg, th, a, b) for a, b in starts)
+    starts = [(a, b) for a, b in starts if edge_key(deg, th, a, b) == top]
     best, labs = None, []
     for a, b in starts:
         code, lab = weinberg(facets, a, b)
