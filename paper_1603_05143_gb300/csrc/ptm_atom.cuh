@@ -236,16 +236,6 @@ __device__ __forceinline__ int orient_sos(const Scratch &sm, int a, int b, int c
   return s ? s : orient_exact_sos(sm, a, b, c, p, d);
 }
 
-// Sign of orient(a, b, c, origin) without SoS (the centre test of Algorithm 1).
-__device__ __forceinline__ int orient_centre(const Scratch &sm, int a, int b, int c) {
-  const int s = orient_filter(sm.Q(a, 0), sm.Q(a, 1), sm.Q(a, 2), sm.Q(b, 0), sm.Q(b, 1), sm.Q(b, 2), sm.Q(c, 0),
-                              sm.Q(c, 1), sm.Q(c, 2), 0.f, 0.f, 0.f);
-  if (s) return s;
-  const long long o = orient_raw(sm.QI(a, 0), sm.QI(a, 1), sm.QI(a, 2), sm.QI(b, 0), sm.QI(b, 1), sm.QI(b, 2),
-                                 sm.QI(c, 0), sm.QI(c, 1), sm.QI(c, 2), 0, 0, 0);
-  return (o > 0) - (o < 0);
-}
-
 // ------------------------------------------------------------ incremental hull
 __device__ __forceinline__ uint16_t fpack(int a, int b, int c) { return (uint16_t)(a | (b << 4) | (c << 8)); }
 
@@ -260,15 +250,75 @@ __device__ __forceinline__ int hull_init(const Scratch &sm, const FrameDesc &d) 
   return 4;
 }
 
-// Add point p; returns the new facet count, or -1 when p lies inside the hull.
-__device__ int hull_insert(const Scratch &sm, int nf, int p, const FrameDesc &d) {
+// Signs of orient(a, b, c, p) and orient(a, b, c, origin) with the FP32 filter
+// of orient_filter; both share the facet normal n = (b - a) x (c - a), and
+// orient(a, b, c, origin) = -n . a (|a| <= 2^19, inside the same error bound).
+// A sign of 0 means "decide exactly".
+__device__ __forceinline__ void orient_pair_filter(float ax, float ay, float az, float bx, float by, float bz,
+                                                   float cx, float cy, float cz, float px, float py, float pz,
+                                                   int &sp, int &sc) {
+  const float ux = bx - ax, uy = by - ay, uz = bz - az;
+  const float vx = cx - ax, vy = cy - ay, vz = cz - az;
+  const float nx = fmaf(uy, vz, -(uz * vy));
+  const float ny = fmaf(uz, vx, -(ux * vz));
+  const float nz = fmaf(ux, vy, -(uy * vx));
+  const float dp = fmaf(nx, px - ax, fmaf(ny, py - ay, nz * (pz - az)));
+  const float dc = -fmaf(nx, ax, fmaf(ny, ay, nz * az));
+  sp = dp > 0x1p42f ? 1 : (dp < -0x1p42f ? -1 : 0);
+  sc = dc > 0x1p42f ? 1 : (dc < -0x1p42f ? -1 : 0);
+}
+
+__device__ __noinline__ int orient_centre_exact(const Scratch &sm, int a, int b, int c) {
+  const long long o = orient_raw(sm.QI(a, 0), sm.QI(a, 1), sm.QI(a, 2), sm.QI(b, 0), sm.QI(b, 1), sm.QI(b, 2),
+                                 sm.QI(c, 0), sm.QI(c, 1), sm.QI(c, 2), 0, 0, 0);
+  return (o > 0) - (o < 0);
+}
+
+// Facets of the current hull visible from point p (bit f set), and whether the
+// centre lies strictly inside the current hull (exact, no SoS: zero rejects),
+// computed only when `centre` is asked for.  Both use one normal per facet.
+__device__ uint32_t hull_visibility(const Scratch &sm, int nf, int p, bool centre, bool &centre_in,
+                                    const FrameDesc &d) {
   uint32_t vis = 0;
+  bool inside = true;
   const float px = sm.Q(p, 0), py = sm.Q(p, 1), pz = sm.Q(p, 2);
+#pragma unroll 2
   for (int f = 0; f < nf; f++) {
-    int v = sm.F(f);
-    if (orient_sos(sm, v & 15, (v >> 4) & 15, (v >> 8) & 15, p, px, py, pz, d) > 0) vis |= 1u << f;
+    const int v = sm.F(f);
+    const int a = v & 15, b = (v >> 4) & 15, c = (v >> 8) & 15;
+    int sp, sc;
+    orient_pair_filter(sm.Q(a, 0), sm.Q(a, 1), sm.Q(a, 2), sm.Q(b, 0), sm.Q(b, 1), sm.Q(b, 2), sm.Q(c, 0),
+                       sm.Q(c, 1), sm.Q(c, 2), px, py, pz, sp, sc);
+    if (!sp) sp = orient_exact_sos(sm, a, b, c, p, d);
+    if (centre && !sc) sc = orient_centre_exact(sm, a, b, c);
+    if (sp > 0) vis |= 1u << f;
+    inside &= sc < 0;
   }
-  if (!vis) return -1;
+  centre_in = centre && inside;
+  return vis;
+}
+
+// Centre strictly inside the current hull (for the last snapshot, where no
+// further point is inserted).
+__device__ bool hull_centre_inside(const Scratch &sm, int nf) {
+  bool inside = true;
+#pragma unroll 2
+  for (int f = 0; f < nf; f++) {
+    const int v = sm.F(f);
+    const int a = v & 15, b = (v >> 4) & 15, c = (v >> 8) & 15;
+    int sp, sc;
+    orient_pair_filter(sm.Q(a, 0), sm.Q(a, 1), sm.Q(a, 2), sm.Q(b, 0), sm.Q(b, 1), sm.Q(b, 2), sm.Q(c, 0),
+                       sm.Q(c, 1), sm.Q(c, 2), 0.f, 0.f, 0.f, sp, sc);
+    if (!sc) sc = orient_centre_exact(sm, a, b, c);
+    inside &= sc < 0;
+  }
+  return inside;
+}
+
+// Insert point p given its visible facets (vis != 0): remove them and fan the
+// horizon to p.  Returns the new facet count, or -1 on an internal error.
+__device__ int hull_apply(const Scratch &sm, int nf, uint32_t vis, int p, const FrameDesc &d) {
+#pragma unroll
   for (int v = 0; v < PTM_KNN; v++) sm.U(v) = 0;
   for (uint32_t m = vis; m; m &= m - 1) {
     int v = sm.F(__ffs(m) - 1);

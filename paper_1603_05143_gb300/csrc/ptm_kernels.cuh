@@ -85,6 +85,7 @@ __device__ __forceinline__ void scan_cells(const FrameDesc &d, int s, typename R
         const int n0 = mx + wix, n1 = my + wiy, n2 = mz + wiz;
         T sx, sy, sz;
         contract_shift<F64>(d, n0, n1, n2, sx, sy, sz);
+#pragma unroll 2
         for (int j = j0; j < j1; j++) {
           T xj, yj, zj;
           int idj;
@@ -300,14 +301,11 @@ __device__ __forceinline__ float cand_r2(const float (&Sm)[3][3], float Gv, floa
   return fmaxf((Gw - o.lam * o.lam / Gv) / (float)N, 0.f);
 }
 
-// Hull of the first K neighbours is complete: centre test, canonical code,
-// lookup and QCP of every admissible correspondence (Algorithm 1, inner loops).
+// Hull of the first K neighbours is complete and contains the centre: canonical
+// code, lookup and QCP of every admissible correspondence (Algorithm 1, inner
+// loops).
 __device__ void snapshot(int K, const Scratch &sm, const FrameDesc &d, const float4 *tplw, int nf, Best &bst) {
   if (nf != 2 * K - 4) return;                    // a neighbour is not a hull vertex
-  for (int f = 0; f < nf; f++) {                  // centre strictly inside (exact, no SoS)
-    int v = sm.F(f);
-    if (orient_centre(sm, v & 15, (v >> 4) & 15, (v >> 8) & 15) >= 0) return;
-  }
   uint64_t lab = 0, h = 0;
   if (!canonical(sm, K, nf, lab, h, d)) return;
   int e = lookup(sm, K, h);
@@ -695,11 +693,16 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
   if (kmax >= 6) {
     int nf = hull_init(sm, d);
     for (int p = 4; p <= kmax; p++) {
-      // the hull now holds neighbours 0..p-1: complete for K = 6, 12, 14
+      // the hull now holds neighbours 0..p-1: complete for K = 6, 12, 14.  The
+      // centre test of a snapshot rides on the visibility test of point p.
       const bool want = (p == 6 && (mask & 1)) || (p == 12 && (mask & 14)) || (p == 14 && (mask & 16));
-      if (want) snapshot(p, sm, d, tplw, nf, bst);
-      if (p == kmax) break;
-      nf = hull_insert(sm, nf, p, d);
+      bool centre_in = false;
+      uint32_t vis = 0;
+      if (p < kmax) vis = hull_visibility(sm, nf, p, want, centre_in, d);
+      else if (want) centre_in = hull_centre_inside(sm, nf);
+      if (want && centre_in) snapshot(p, sm, d, tplw, nf, bst);
+      if (p == kmax || !vis) break;              // done, or p lies inside the hull
+      nf = hull_apply(sm, nf, vis, p, d);
       if (nf < 0) break;
     }
   }
