@@ -49,6 +49,21 @@ BYTES_PER_ATOM = 16 + 4 + 1 + 122
 WORKLOAD = "polycrystal-1048576"
 
 
+def measured_traffic():
+    """DRAM bytes per k_atoms launch from the committed ncu capture, or None when
+    the kernel sources changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_atoms_traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    csrc = os.path.join(ROOT, "paper_1603_05143_gb300", "csrc")
+    src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("ptm.cu", "ptm_kernels.cuh", "ptm_atom.cuh"))
+    if hashlib.sha256(src).hexdigest() != rec.get("source_sha256"):
+        return None
+    return rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -283,7 +298,7 @@ def run_gpu(args, world, rank, local, pg):
     peaks_file = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm_peak = json.load(open(peaks_file)).get("hbm_gbs") if os.path.exists(peaks_file) else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "k_atoms", "kernel_ms": kms,
+            "traffic": measured_traffic(), "kernel": "k_atoms", "kernel_ms": kms,
             "peak_note": "FP32 peak derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
             "hbm_achieved_gbs": f.n * BYTES_PER_ATOM / (kms * 1e-3) / 1e9, "hbm_peak_gbs": hbm_peak}
     cpu = None

@@ -136,6 +136,27 @@ ptm_status ptm_classify_frame_host(ptm_context *ctx, const ptm_frame *frame,
    its stream).  Timings come from CUDA events recorded on that stream. */
 ptm_status ptm_get_stats(ptm_context *ctx, ptm_stats *out);
 
+/* Largest frame accepted by ptm_classify_frame_noalloc. */
+#define PTM_NOALLOC_MAX_ATOMS 32768
+
+/* Classify one frame of at most PTM_NOALLOC_MAX_ATOMS atoms without allocating
+   any memory (the paper has no counterpart: this is a service to callers).
+   It is for callers that cannot let a library call cudaMalloc: host
+   applications that own all device memory through their own pool, and in-situ
+   analysis inside a running simulation, where cudaMalloc and cudaFree may
+   synchronise the device and stall the caller's pipeline.  No context is
+   needed: the call runs on the current device, on `stream`, with the same
+   kernels and results as ptm_classify_frame; positions, species and outputs are
+   DEVICE pointers owned by the caller.  Its workspace is one static device
+   array of about 2.6 MiB that every GPU loading this library holds until the
+   process exits.  The first call on a device looks up that array's device
+   address; make that first call before any stream capture.  All calls share
+   the array and keep its last contents (the call clears what must start at
+   zero), so calls whose work overlaps on the GPU race: order them on one
+   stream.  Returns PTM_ERR_INVALID_ARG for frames above the limit (or bad
+   arguments) before enqueueing anything, PTM_ERR_CUDA if a launch fails. */
+ptm_status ptm_classify_frame_noalloc(const ptm_frame *frame, const ptm_outputs *out, void *stream);
+
 /* Human-readable name of a status; never NULL. */
 const char *ptm_status_string(ptm_status status);
 

@@ -61,6 +61,8 @@ def load():
         L.ptm_classify_frame.argtypes = [P, C.POINTER(ptm_frame), C.POINTER(ptm_outputs), P]
         L.ptm_classify_frame_host.argtypes = [P, C.POINTER(ptm_frame), C.POINTER(ptm_outputs), P]
         L.ptm_get_stats.argtypes = [P, C.POINTER(ptm_stats)]
+        L.ptm_classify_frame_noalloc.argtypes = [C.POINTER(ptm_frame), C.POINTER(ptm_outputs), P]
+        L.ptm_classify_frame_noalloc.restype = C.c_int
         L.ptm_status_string.argtypes = [C.c_int]
         L.ptm_status_string.restype = C.c_char_p
         L.ptm_last_cuda_error.argtypes = [P]

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -353,3 +354,158 @@ ptm_status ptm_get_stats(ptm_context *ctx, ptm_stats *out) {
 }
 
 }  // extern "C"
+
+// ============================================================ no-allocation entry
+// ptm_classify_frame_noalloc: the same kernels with their workspace in one
+// file-scope device array, for callers that cannot allocate device memory.  The
+// array is sized for frames of up to PTM_NOALLOC_MAX_ATOMS atoms and stays
+// resident on every device that loads the library until the process exits.
+namespace {
+
+constexpr int kNoallocAtoms = PTM_NOALLOC_MAX_ATOMS;
+constexpr int kNoallocCells = 4 * kNoallocAtoms + 64;                 // the cell-count cap of the frame setup
+constexpr int kNoallocScanBlocks = (kNoallocCells + 1 + 2 * SCAN_BLOCK - 1) / (2 * SCAN_BLOCK) + 1;
+
+struct NoallocLayout {                  // byte offsets inside the static array
+  static constexpr size_t sorted = 0;                                            // Atom64 records (float4 fits too)
+  static constexpr size_t sbin = sorted + sizeof(Atom64) * kNoallocAtoms;
+  static constexpr size_t wrapv = sbin + sizeof(int) * kNoallocAtoms;
+  static constexpr size_t atom_cell = wrapv + sizeof(int) * kNoallocAtoms;
+  static constexpr size_t atom_rank = atom_cell + sizeof(int) * kNoallocAtoms;
+  static constexpr size_t atom_wrap = atom_rank + sizeof(int) * kNoallocAtoms;
+  static constexpr size_t cell_count = atom_wrap + sizeof(int) * kNoallocAtoms;
+  static constexpr size_t cell_start = cell_count + sizeof(int) * (kNoallocCells + 1);
+  static constexpr size_t block_sums = cell_start + sizeof(int) * (kNoallocCells + 1);
+  static constexpr size_t dstat = block_sums + sizeof(int) * kNoallocScanBlocks;
+  static constexpr size_t counters = ((dstat + sizeof(int) * 8) + 7) / 8 * 8;
+  static constexpr size_t total = counters + sizeof(unsigned long long) * C_NCOUNTERS;
+};
+
+static __device__ __align__(256) unsigned char ptm_noalloc_scratch[NoallocLayout::total];
+
+// Device address of the array on each device, resolved once with that device current.
+constexpr int kMaxDevices = 64;
+unsigned char *g_noalloc_ptr[kMaxDevices] = {nullptr};
+std::mutex g_noalloc_mutex;
+
+ptm_status noalloc_setup(int dev, unsigned char **out) {
+  if (dev < 0 || dev >= kMaxDevices) return PTM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, ptm_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return PTM_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = (unsigned char *)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return PTM_OK;
+}
+
+}  // namespace
+
+extern "C" ptm_status ptm_classify_frame_noalloc(const ptm_frame *f, const ptm_outputs *o, void *stream) {
+  if (!f || !o) return PTM_ERR_INVALID_ARG;
+  if (f->n_atoms < 1 || f->n_atoms > kNoallocAtoms || !f->positions) return PTM_ERR_INVALID_ARG;
+  if (f->pos_dtype != PTM_F32 && f->pos_dtype != PTM_F64) return PTM_ERR_INVALID_ARG;
+  if (!finite_cell(f->cell)) return PTM_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return PTM_ERR_CUDA; }
+  unsigned char *base = nullptr;
+  ptm_status rs = noalloc_setup(dev, &base);
+  if (rs != PTM_OK) return rs;
+  cudaStream_t st = (cudaStream_t)stream;
+  const double *H = f->cell;
+  const double det = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+                     H[2] * (H[3] * H[7] - H[4] * H[6]);
+  if (!(std::fabs(det) > 1e-12)) return PTM_ERR_INVALID_ARG;
+  const int64_t n = f->n_atoms;
+  const int f64 = f->pos_dtype == PTM_F64;
+  double Hinv[9];
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) {
+      int i1 = (j + 1) % 3, i2 = (j + 2) % 3, j1 = (i + 1) % 3, j2 = (i + 2) % 3;
+      Hinv[3 * i + j] = (H[3 * i1 + j1] * H[3 * i2 + j2] - H[3 * i1 + j2] * H[3 * i2 + j1]) / det;
+    }
+  double W[3];
+  for (int c = 0; c < 3; c++) W[c] = 1.0 / std::sqrt(Hinv[c] * Hinv[c] + Hinv[3 + c] * Hinv[3 + c] + Hinv[6 + c] * Hinv[6 + c]);
+  const double rho = (double)n / std::fabs(det);
+  const double wt = 1.25 * std::cbrt(3.0 * 15.0 / (4.0 * M_PI * rho));
+  int nb[3];
+  size_t ncell = 1;
+  for (int c = 0; c < 3; c++) {
+    nb[c] = std::min(std::max(1, (int)std::floor(W[c] / wt)), 1024);
+    ncell *= (size_t)nb[c];
+  }
+  while (ncell > (size_t)4 * n + 64) {
+    int c = (int)(std::max_element(nb, nb + 3) - nb);
+    ncell /= nb[c];
+    nb[c] = std::max(1, nb[c] / 2);
+    ncell *= nb[c];
+  }
+  if (ncell > (size_t)kNoallocCells) return PTM_ERR_INVALID_ARG;
+  void *sorted = base + NoallocLayout::sorted;
+  int *sbin = (int *)(base + NoallocLayout::sbin), *wrapv = (int *)(base + NoallocLayout::wrapv);
+  int *atom_cell = (int *)(base + NoallocLayout::atom_cell), *atom_rank = (int *)(base + NoallocLayout::atom_rank);
+  int *atom_wrap = (int *)(base + NoallocLayout::atom_wrap);
+  int *cell_count = (int *)(base + NoallocLayout::cell_count), *cell_start = (int *)(base + NoallocLayout::cell_start);
+  int *block_sums = (int *)(base + NoallocLayout::block_sums), *dstat = (int *)(base + NoallocLayout::dstat);
+  unsigned long long *counters = (unsigned long long *)(base + NoallocLayout::counters);
+
+  FrameDesc desc;
+  std::memset(&desc, 0, sizeof desc);
+  desc.sorted = sorted; desc.sbin = sbin; desc.cell_start = cell_start; desc.wrapv = wrapv;
+  desc.species = f->species; desc.positions = f->positions; desc.n = n;
+  for (int c = 0; c < 3; c++) { desc.nb[c] = nb[c]; desc.pbc[c] = f->pbc[c] ? 1 : 0; }
+  desc.f64 = f64;
+  desc.mask = f->template_mask ? (f->template_mask & PTM_MASK_ALL) : PTM_MASK_ALL;
+  desc.rmsd_max = std::isnan(f->rmsd_max) ? INFINITY : (float)f->rmsd_max;
+  desc.min_cell_width = (float)std::min(W[0] / nb[0], std::min(W[1] / nb[1], W[2] / nb[2]));
+  for (int i = 0; i < 9; i++) desc.H[i] = H[i];
+  for (int a = -2; a <= 2; a++)
+    for (int b = -2; b <= 2; b++)
+      for (int c = -2; c <= 2; c++) {
+        const int i = (a + 2) * 25 + (b + 2) * 5 + (c + 2);
+        for (int k = 0; k < 3; k++) {
+          volatile double t0 = (double)a * H[k];
+          volatile double t1 = (double)b * H[3 + k];
+          volatile double t2 = (double)c * H[6 + k];
+          volatile double t01 = t0 + t1;
+          const double s = t01 + t2;
+          desc.s64[i][k] = s;
+          desc.s32[i][k] = (float)s;
+          desc.slo[i][k] = (float)(s - (double)(float)s);
+        }
+      }
+  desc.structure = o->structure; desc.alloy = o->alloy; desc.rmsd = o->rmsd; desc.scale = o->scale;
+  desc.quat = o->quat; desc.strain = o->strain; desc.corr = o->correspondence;
+  desc.dstat = dstat;
+  desc.counters = counters;
+  BinParams bp;
+  for (int i = 0; i < 9; i++) bp.Hinv[i] = (float)Hinv[i];
+  for (int c = 0; c < 3; c++) { bp.W[c] = (float)W[c]; bp.nb[c] = nb[c]; bp.pbc[c] = desc.pbc[c]; }
+  bp.n = n;
+  bp.f64 = f64;
+  // the array keeps the previous call's contents: clear what must start at zero
+  if (cudaMemsetAsync(cell_count, 0, (ncell + 1) * sizeof(int), st) != cudaSuccess ||
+      cudaMemsetAsync(dstat, 0, 8 * sizeof(int), st) != cudaSuccess ||
+      cudaMemsetAsync(counters, 0, C_NCOUNTERS * sizeof(unsigned long long), st) != cudaSuccess) {
+    cudaGetLastError();
+    return PTM_ERR_CUDA;
+  }
+  const int tb = 256;
+  const unsigned gb = (unsigned)((n + tb - 1) / tb);
+  k_bin<<<gb, tb, 0, st>>>(f->positions, bp, cell_count, atom_cell, atom_rank, atom_wrap, dstat);
+  const int nscan = (int)ncell + 1;
+  const int nblk = (nscan + 2 * SCAN_BLOCK - 1) / (2 * SCAN_BLOCK);
+  k_scan_block<<<nblk, SCAN_BLOCK, 0, st>>>(cell_count, cell_start, block_sums, nscan);
+  k_scan_sums<<<1, SCAN_BLOCK, 0, st>>>(block_sums, nblk, dstat + 2);
+  k_scan_add<<<(nscan + 255) / 256, 256, 0, st>>>(cell_start, block_sums, nscan);
+  k_scatter<<<gb, tb, 0, st>>>(f->positions, f64, n, atom_cell, atom_rank, atom_wrap, cell_start, sorted, sbin, wrapv);
+  const unsigned ga = (unsigned)((n + PTM_BLOCK - 1) / PTM_BLOCK);
+  if (f64) k_atoms<true><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
+  else k_atoms<false><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
+  if (cudaGetLastError() != cudaSuccess) return PTM_ERR_CUDA;
+  return PTM_OK;
+}
