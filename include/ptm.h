@@ -136,6 +136,56 @@ ptm_status ptm_classify_frame_host(ptm_context *ctx, const ptm_frame *frame,
    its stream).  Timings come from CUDA events recorded on that stream. */
 ptm_status ptm_get_stats(ptm_context *ctx, ptm_stats *out);
 
+/* ---------------------------------------------------------------- batches
+   Many frames of uneven size classified by one persistent launch: every frame
+   gets its own cell list, one scan covers all cells, and the per-atom kernel
+   pulls tiles of atoms from one global queue until the batch is exhausted, so
+   small and large frames balance across the GPU.  A batch remembers the
+   caller's device buffers; running it again re-reads them (update positions in
+   place for the next MD frame of the same size and cell shape). */
+typedef struct ptm_batch ptm_batch;
+
+/* Tunables of a batch; a field <= 0 keeps its default.
+   cell_factor: cell width / expected 14-neighbour radius (default 1.25);
+   tile_atoms: atoms taken from the queue per grab (default 256);
+   blocks_per_sm: resident 64-thread blocks per SM for the persistent grid
+   (default 5, the shared-memory limit).  Atoms per warp are fixed at 32 (one
+   atom per lane). */
+typedef struct {
+  double cell_factor;
+  int tile_atoms;
+  int blocks_per_sm;
+} ptm_tuning;
+
+/* Build a batch of n_frames frames (all PTM_F32 or all PTM_F64; device
+   buffers; outs[i] belongs to frames[i]).  Allocates the batch workspace
+   (about 40 B per atom plus 8 B per cell) and copies the frame descriptors to
+   the device.  tuning may be NULL. */
+ptm_status ptm_batch_create(ptm_context *ctx, int n_frames, const ptm_frame *frames,
+                            const ptm_outputs *outs, const ptm_tuning *tuning, ptm_batch **out);
+
+/* Enqueue the whole batch on `stream`; if the batch was captured, replay its
+   CUDA graph instead.  Asynchronous. */
+ptm_status ptm_batch_run(ptm_batch *batch, void *stream);
+
+/* Capture one run of the batch into a CUDA graph owned by the batch (stream
+   must be a non-NULL capturable stream); later ptm_batch_run calls launch the
+   graph. */
+ptm_status ptm_batch_capture(ptm_batch *batch, void *stream);
+
+/* Counters and device timings of the batch's last run (waits for it). */
+ptm_status ptm_batch_stats(ptm_batch *batch, ptm_stats *out);
+
+/* Free the batch and its workspace (waits for its last run). */
+ptm_status ptm_batch_destroy(ptm_batch *batch);
+
+/* Time every candidate tuning on this batch (cell_factor in {1.0, 1.125, 1.25,
+   1.4, 1.6}, tile_atoms in {64, 256, 1024}, blocks_per_sm in {4, 5}) and
+   return the fastest in *best.  Runs the batch about 150 times; outputs are
+   written with the same results each time. */
+ptm_status ptm_autotune_batch(ptm_context *ctx, int n_frames, const ptm_frame *frames,
+                              const ptm_outputs *outs, void *stream, ptm_tuning *best);
+
 /* Largest frame accepted by ptm_classify_frame_noalloc. */
 #define PTM_NOALLOC_MAX_ATOMS 32768
 

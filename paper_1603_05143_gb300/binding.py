@@ -38,6 +38,10 @@ class ptm_stats(C.Structure):
                [("pipeline_ms", C.c_double), ("atom_kernel_ms", C.c_double)]
 
 
+class ptm_tuning(C.Structure):
+    _fields_ = [("cell_factor", C.c_double), ("tile_atoms", C.c_int), ("blocks_per_sm", C.c_int)]
+
+
 class PTMError(RuntimeError):
     def __init__(self, status: int, what: str, detail: str = ""):
         name = STATUS[status] if 0 <= status < len(STATUS) else f"status {status}"
@@ -63,6 +67,17 @@ def load():
         L.ptm_get_stats.argtypes = [P, C.POINTER(ptm_stats)]
         L.ptm_classify_frame_noalloc.argtypes = [C.POINTER(ptm_frame), C.POINTER(ptm_outputs), P]
         L.ptm_classify_frame_noalloc.restype = C.c_int
+        L.ptm_batch_create.argtypes = [P, C.c_int, C.POINTER(ptm_frame), C.POINTER(ptm_outputs),
+                                       C.POINTER(ptm_tuning), C.POINTER(C.c_void_p)]
+        L.ptm_batch_run.argtypes = [P, P]
+        L.ptm_batch_capture.argtypes = [P, P]
+        L.ptm_batch_stats.argtypes = [P, C.POINTER(ptm_stats)]
+        L.ptm_batch_destroy.argtypes = [P]
+        L.ptm_autotune_batch.argtypes = [P, C.c_int, C.POINTER(ptm_frame), C.POINTER(ptm_outputs), P,
+                                         C.POINTER(ptm_tuning)]
+        for f in ("ptm_batch_create", "ptm_batch_run", "ptm_batch_capture", "ptm_batch_stats",
+                  "ptm_batch_destroy", "ptm_autotune_batch"):
+            getattr(L, f).restype = C.c_int
         L.ptm_status_string.argtypes = [C.c_int]
         L.ptm_status_string.restype = C.c_char_p
         L.ptm_last_cuda_error.argtypes = [P]
@@ -182,6 +197,107 @@ class PTM:
         s = ptm_stats()
         self._check(self.lib.ptm_get_stats(self.h, C.byref(s)), "ptm_get_stats")
         return {k: getattr(s, k) for k, _ in ptm_stats._fields_}
+
+    # --------------------------------------------------------------- batches
+    def batch(self, frames, mask=MASK_ALL, rmsd_max=math.inf, tuning=None, outputs=OUTPUT_NAMES):
+        """A ``Batch`` over frames given as dicts with CUDA tensors
+        ``positions`` (n, 3), optional ``species`` (n,), and ``cell``, ``pbc``."""
+        return Batch(self, frames, mask, rmsd_max, tuning, outputs)
+
+    def autotune(self, frames, mask=MASK_ALL, rmsd_max=math.inf, stream=None, cache=None):
+        """Fastest ptm_tuning for these frames (``ptm_autotune_batch``), cached in a
+        JSON file keyed by device name and workload signature."""
+        import json
+        import os
+        import torch
+        key = None
+        if cache:
+            name = torch.cuda.get_device_name(self.device)
+            n = [int(f["positions"].shape[0]) for f in frames]
+            key = f"{name}|{len(n)}|{sum(n)}|{min(n)}|{max(n)}|{frames[0]['positions'].dtype}"
+            if os.path.exists(cache):
+                data = json.load(open(cache))
+                if key in data:
+                    return data[key]
+        fr, outs, keep, _ = _batch_structs(frames, mask, rmsd_max, OUTPUT_NAMES)
+        best = ptm_tuning()
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._check(self.lib.ptm_autotune_batch(self.h, len(frames), fr, outs, C.c_void_p(st.cuda_stream),
+                                                C.byref(best)), "ptm_autotune_batch")
+        res = {"cell_factor": best.cell_factor, "tile_atoms": best.tile_atoms, "blocks_per_sm": best.blocks_per_sm}
+        if cache:
+            data = json.load(open(cache)) if os.path.exists(cache) else {}
+            data[key] = res
+            os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+            json.dump(data, open(cache, "w"), indent=1)
+        return res
+
+
+def _batch_structs(frames, mask, rmsd_max, outputs):
+    import torch
+    n = len(frames)
+    fr = (ptm_frame * n)()
+    outs = (ptm_outputs * n)()
+    keep, out_tensors = [], []
+    for i, f in enumerate(frames):
+        pos = f["positions"].contiguous()
+        sp = f.get("species")
+        if sp is not None:
+            sp = sp.to(device=pos.device, dtype=torch.int8).contiguous()
+        code = PTM_F64 if pos.dtype == torch.float64 else PTM_F32
+        fr[i] = _frame(pos.shape[0], pos.data_ptr(), code, None if sp is None else sp.data_ptr(), f["cell"],
+                       f.get("pbc", (True, True, True)), mask, rmsd_max)
+        o = allocate_outputs(pos.shape[0], pos.device, outputs)
+        for name in OUTPUT_NAMES:
+            t = o.get(name)
+            setattr(outs[i], name, t.data_ptr() if t is not None else None)
+        keep.append((pos, sp))
+        out_tensors.append(o)
+    return fr, outs, keep, out_tensors
+
+
+class Batch:
+    """Frames classified together by one persistent launch (``ptm_batch_*``)."""
+
+    def __init__(self, ptm, frames, mask=MASK_ALL, rmsd_max=math.inf, tuning=None, outputs=OUTPUT_NAMES):
+        self.ptm = ptm
+        self.lib = ptm.lib
+        fr, outs, self._keep, self.outputs = _batch_structs(frames, mask, rmsd_max, outputs)
+        t = None
+        if tuning:
+            t = ptm_tuning(float(tuning.get("cell_factor", 0)), int(tuning.get("tile_atoms", 0)),
+                           int(tuning.get("blocks_per_sm", 0)))
+        h = C.c_void_p()
+        ptm._check(self.lib.ptm_batch_create(ptm.h, len(frames), fr, outs, C.byref(t) if t else None, C.byref(h)),
+                   "ptm_batch_create")
+        self.h = h
+        self._structs = (fr, outs)
+
+    def _stream(self, stream):
+        import torch
+        return stream if stream is not None else torch.cuda.current_stream(self.ptm.device)
+
+    def run(self, stream=None):
+        self.ptm._check(self.lib.ptm_batch_run(self.h, C.c_void_p(self._stream(stream).cuda_stream)), "ptm_batch_run")
+
+    def capture(self, stream):
+        self.ptm._check(self.lib.ptm_batch_capture(self.h, C.c_void_p(stream.cuda_stream)), "ptm_batch_capture")
+
+    def stats(self) -> dict:
+        s = ptm_stats()
+        self.ptm._check(self.lib.ptm_batch_stats(self.h, C.byref(s)), "ptm_batch_stats")
+        return {k: getattr(s, k) for k, _ in ptm_stats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ptm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def allocate_outputs(n, device, outputs=OUTPUT_NAMES):

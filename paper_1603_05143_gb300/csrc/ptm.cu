@@ -11,6 +11,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #define PTM_TBL_CONST __constant__ const
 #define PTM_TBL_GLOBAL __device__ const
@@ -175,6 +176,7 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
   bp.n = n;
   bp.f64 = f64;
 
+  cudaGetLastError();   // launch errors are read below; drop any left by earlier calls
   CK(cudaEventRecord(ctx->ev[0], st));
   CK(cudaMemsetAsync(ctx->cell_count, 0, (ncell + 1) * sizeof(int), st));
   CK(cudaMemsetAsync(ctx->dstat, 0, 4 * sizeof(int), st));
@@ -355,6 +357,312 @@ ptm_status ptm_get_stats(ptm_context *ctx, ptm_stats *out) {
 
 }  // extern "C"
 
+// ================================================================== batches
+// Host description of one frame of a batch: its descriptor (device pointers are
+// filled in when the batch workspace exists) and its binning parameters.
+static ptm_status setup_frame(const ptm_frame *f, double cell_factor, FrameDesc *desc, BinParams *bp,
+                              size_t *ncell_out) {
+  if (!f || f->n_atoms < 1 || f->n_atoms >= (1ll << 31) || !f->positions) return PTM_ERR_INVALID_ARG;
+  if (f->pos_dtype != PTM_F32 && f->pos_dtype != PTM_F64) return PTM_ERR_INVALID_ARG;
+  if (!finite_cell(f->cell)) return PTM_ERR_INVALID_ARG;
+  const double *H = f->cell;
+  const double det = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+                     H[2] * (H[3] * H[7] - H[4] * H[6]);
+  if (!(std::fabs(det) > 1e-12)) return PTM_ERR_INVALID_ARG;
+  const int64_t n = f->n_atoms;
+  double Hinv[9], W[3];
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) {
+      int i1 = (j + 1) % 3, i2 = (j + 2) % 3, j1 = (i + 1) % 3, j2 = (i + 2) % 3;
+      Hinv[3 * i + j] = (H[3 * i1 + j1] * H[3 * i2 + j2] - H[3 * i1 + j2] * H[3 * i2 + j1]) / det;
+    }
+  for (int c = 0; c < 3; c++) W[c] = 1.0 / std::sqrt(Hinv[c] * Hinv[c] + Hinv[3 + c] * Hinv[3 + c] + Hinv[6 + c] * Hinv[6 + c]);
+  const double rho = (double)n / std::fabs(det);
+  const double wt = cell_factor * std::cbrt(3.0 * 15.0 / (4.0 * M_PI * rho));
+  int nb[3];
+  size_t ncell = 1;
+  for (int c = 0; c < 3; c++) {
+    nb[c] = std::min(std::max(1, (int)std::floor(W[c] / wt)), 1024);
+    ncell *= (size_t)nb[c];
+  }
+  while (ncell > (size_t)4 * n + 64) {
+    int c = (int)(std::max_element(nb, nb + 3) - nb);
+    ncell /= nb[c];
+    nb[c] = std::max(1, nb[c] / 2);
+    ncell *= nb[c];
+  }
+  std::memset(desc, 0, sizeof(FrameDesc));
+  desc->species = f->species;
+  desc->positions = f->positions;
+  desc->n = n;
+  for (int c = 0; c < 3; c++) { desc->nb[c] = nb[c]; desc->pbc[c] = f->pbc[c] ? 1 : 0; }
+  desc->f64 = f->pos_dtype == PTM_F64;
+  desc->mask = f->template_mask ? (f->template_mask & PTM_MASK_ALL) : PTM_MASK_ALL;
+  desc->rmsd_max = std::isnan(f->rmsd_max) ? INFINITY : (float)f->rmsd_max;
+  desc->min_cell_width = (float)std::min(W[0] / nb[0], std::min(W[1] / nb[1], W[2] / nb[2]));
+  for (int i = 0; i < 9; i++) desc->H[i] = H[i];
+  for (int a = -2; a <= 2; a++)
+    for (int b = -2; b <= 2; b++)
+      for (int c = -2; c <= 2; c++) {
+        const int i = (a + 2) * 25 + (b + 2) * 5 + (c + 2);
+        for (int k = 0; k < 3; k++) {
+          volatile double t0 = (double)a * H[k];
+          volatile double t1 = (double)b * H[3 + k];
+          volatile double t2 = (double)c * H[6 + k];
+          volatile double t01 = t0 + t1;
+          const double sh = t01 + t2;
+          desc->s64[i][k] = sh;
+          desc->s32[i][k] = (float)sh;
+          desc->slo[i][k] = (float)(sh - (double)(float)sh);
+        }
+      }
+  std::memset(bp, 0, sizeof(BinParams));
+  for (int i = 0; i < 9; i++) bp->Hinv[i] = (float)Hinv[i];
+  for (int c = 0; c < 3; c++) { bp->W[c] = (float)W[c]; bp->nb[c] = nb[c]; bp->pbc[c] = desc->pbc[c]; }
+  bp->n = n;
+  bp->f64 = desc->f64;
+  bp->pos = f->positions;
+  *ncell_out = ncell;
+  return PTM_OK;
+}
+
+struct ptm_batch {
+  ptm_context *ctx = nullptr;
+  int nframes = 0, f64 = 0;
+  int64_t ntotal = 0;
+  size_t ncell = 0;
+  int tile_atoms = 256, blocks_per_sm = 5;
+  double cell_factor = 1.25;
+  FrameDesc *d_descs = nullptr;
+  BinParams *d_bp = nullptr;
+  int64_t *d_atom_off = nullptr;
+  int *d_dstat = nullptr;
+  void *sorted = nullptr;
+  int *sbin = nullptr, *wrapv = nullptr, *atom_cell = nullptr, *atom_rank = nullptr, *atom_wrap = nullptr;
+  int *cell_count = nullptr, *cell_start = nullptr, *block_sums = nullptr, *scan_total = nullptr;
+  unsigned long long *queue = nullptr, *counters = nullptr;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int nsm = 152;
+};
+
+static void batch_free(ptm_batch *b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  cudaFree(b->d_descs); cudaFree(b->d_bp); cudaFree(b->d_atom_off); cudaFree(b->d_dstat);
+  cudaFree(b->sorted); cudaFree(b->sbin); cudaFree(b->wrapv); cudaFree(b->atom_cell); cudaFree(b->atom_rank);
+  cudaFree(b->atom_wrap); cudaFree(b->cell_count); cudaFree(b->cell_start); cudaFree(b->block_sums);
+  cudaFree(b->scan_total); cudaFree(b->queue); cudaFree(b->counters);
+  for (int i = 0; i < 3; i++) if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+  delete b;
+}
+
+// Enqueue one pass over the whole batch: binning of every frame, one scan over
+// all cells, scatter, then the persistent classification launch.
+static ptm_status batch_enqueue(ptm_batch *b, cudaStream_t st) {
+  ptm_context *ctx = b->ctx;
+  cudaGetLastError();   // launch errors are read below; drop any left by earlier calls
+  CK(cudaEventRecord(b->ev[0], st));
+  CK(cudaMemsetAsync(b->cell_count, 0, (b->ncell + 1) * sizeof(int), st));
+  CK(cudaMemsetAsync(b->d_dstat, 0, (size_t)4 * b->nframes * sizeof(int), st));
+  CK(cudaMemsetAsync(b->counters, 0, C_NCOUNTERS * sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(b->queue, 0, sizeof(unsigned long long), st));
+  const int tb = 256;
+  const unsigned gb = (unsigned)((b->ntotal + tb - 1) / tb);
+  k_bin_batch<<<gb, tb, 0, st>>>(b->d_bp, b->d_atom_off, b->nframes, b->ntotal, b->cell_count, b->atom_cell,
+                                 b->atom_rank, b->atom_wrap);
+  const int nscan = (int)b->ncell + 1;
+  const int nblk = (nscan + 2 * SCAN_BLOCK - 1) / (2 * SCAN_BLOCK);
+  k_scan_block<<<nblk, SCAN_BLOCK, 0, st>>>(b->cell_count, b->cell_start, b->block_sums, nscan);
+  k_scan_sums<<<1, SCAN_BLOCK, 0, st>>>(b->block_sums, nblk, b->scan_total);
+  k_scan_add<<<(nscan + 255) / 256, 256, 0, st>>>(b->cell_start, b->block_sums, nscan);
+  k_scatter_batch<<<gb, tb, 0, st>>>(b->d_bp, b->d_atom_off, b->nframes, b->ntotal, b->atom_cell, b->atom_rank,
+                                     b->atom_wrap, b->cell_start, b->sorted, b->sbin, b->wrapv);
+  CK(cudaEventRecord(b->ev[1], st));
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->nsm * b->blocks_per_sm,
+                                                                       (b->ntotal + b->tile_atoms - 1) / b->tile_atoms));
+  if (b->f64)
+    k_atoms_batch<true><<<grid, PTM_BLOCK, atom_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes,
+                                                                    b->ntotal, b->tile_atoms, b->queue);
+  else
+    k_atoms_batch<false><<<grid, PTM_BLOCK, atom_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes,
+                                                                     b->ntotal, b->tile_atoms, b->queue);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(b->ev[2], st));
+  return PTM_OK;
+}
+
+extern "C" ptm_status ptm_batch_create(ptm_context *ctx, int nframes, const ptm_frame *frames, const ptm_outputs *outs,
+                                       const ptm_tuning *tuning, ptm_batch **out) {
+  if (!ctx || !frames || !outs || !out || nframes < 1) return PTM_ERR_INVALID_ARG;
+  *out = nullptr;
+  CK(cudaSetDevice(ctx->device));
+  ptm_batch *b = new (std::nothrow) ptm_batch();
+  if (!b) return PTM_ERR_OUT_OF_MEMORY;
+  b->ctx = ctx;
+  b->nframes = nframes;
+  if (tuning) {
+    if (tuning->cell_factor > 0) b->cell_factor = tuning->cell_factor;
+    if (tuning->tile_atoms > 0) b->tile_atoms = (tuning->tile_atoms + PTM_BLOCK - 1) / PTM_BLOCK * PTM_BLOCK;
+    if (tuning->blocks_per_sm > 0) b->blocks_per_sm = tuning->blocks_per_sm;
+  }
+  if (!(b->cell_factor >= 0.5 && b->cell_factor <= 4.0)) { delete b; return PTM_ERR_INVALID_ARG; }
+  cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+  std::vector<FrameDesc> hd(nframes);
+  std::vector<BinParams> hb(nframes);
+  std::vector<int64_t> off(nframes);
+  b->f64 = frames[0].pos_dtype == PTM_F64;
+  for (int f = 0; f < nframes; f++) {
+    size_t nc = 0;
+    ptm_status rs = setup_frame(&frames[f], b->cell_factor, &hd[f], &hb[f], &nc);
+    if (rs == PTM_OK && (frames[f].pos_dtype == PTM_F64) != (b->f64 != 0)) rs = PTM_ERR_INVALID_ARG;
+    if (rs != PTM_OK) { delete b; return rs; }
+    off[f] = b->ntotal;
+    hb[f].atom_off = b->ntotal;
+    hb[f].cell_off = (int)b->ncell;
+    hd[f].atom_offset = b->ntotal;
+    b->ntotal += frames[f].n_atoms;
+    b->ncell += nc;
+    if (b->ntotal >= (1ll << 31) || b->ncell >= (1ull << 31)) { delete b; return PTM_ERR_INVALID_ARG; }
+  }
+  const size_t n = (size_t)b->ntotal, nc = b->ncell;
+  const size_t rec = b->f64 ? sizeof(Atom64) : sizeof(float4);
+  const size_t nblk = (nc + 1 + 2 * SCAN_BLOCK - 1) / (2 * SCAN_BLOCK) + 1;
+  cudaError_t e = cudaSuccess;
+  auto M = [&](void **p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
+  M((void **)&b->d_descs, sizeof(FrameDesc) * nframes);
+  M((void **)&b->d_bp, sizeof(BinParams) * nframes);
+  M((void **)&b->d_atom_off, sizeof(int64_t) * nframes);
+  M((void **)&b->d_dstat, sizeof(int) * 4 * nframes);
+  M(&b->sorted, rec * n);
+  M((void **)&b->sbin, 4 * n); M((void **)&b->wrapv, 4 * n); M((void **)&b->atom_cell, 4 * n);
+  M((void **)&b->atom_rank, 4 * n); M((void **)&b->atom_wrap, 4 * n);
+  M((void **)&b->cell_count, 4 * (nc + 1)); M((void **)&b->cell_start, 4 * (nc + 1));
+  M((void **)&b->block_sums, 4 * nblk); M((void **)&b->scan_total, 4);
+  M((void **)&b->queue, 8); M((void **)&b->counters, 8 * C_NCOUNTERS);
+  for (int i = 0; i < 3 && e == cudaSuccess; i++) e = cudaEventCreate(&b->ev[i]);
+  if (e != cudaSuccess) { ptm_status rs = cuda_fail(ctx, e, "ptm_batch_create"); batch_free(b); return rs; }
+  for (int f = 0; f < nframes; f++) {
+    hd[f].sorted = b->sorted;
+    hd[f].sbin = b->sbin;
+    hd[f].cell_start = b->cell_start + hb[f].cell_off;
+    hd[f].wrapv = b->wrapv;
+    hd[f].structure = outs[f].structure; hd[f].alloy = outs[f].alloy; hd[f].rmsd = outs[f].rmsd;
+    hd[f].scale = outs[f].scale; hd[f].quat = outs[f].quat; hd[f].strain = outs[f].strain;
+    hd[f].corr = outs[f].correspondence;
+    hd[f].dstat = b->d_dstat + 4 * f;
+    hd[f].counters = b->counters;
+    hb[f].dstat = b->d_dstat + 4 * f;
+  }
+  if ((e = cudaMemcpy(b->d_descs, hd.data(), sizeof(FrameDesc) * nframes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(b->d_bp, hb.data(), sizeof(BinParams) * nframes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(b->d_atom_off, off.data(), sizeof(int64_t) * nframes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(b->counters, 0, 8 * C_NCOUNTERS)) != cudaSuccess) {
+    ptm_status rs = cuda_fail(ctx, e, "ptm_batch_create");
+    batch_free(b);
+    return rs;
+  }
+  *out = b;
+  return PTM_OK;
+}
+
+extern "C" ptm_status ptm_batch_run(ptm_batch *b, void *stream) {
+  if (!b) return PTM_ERR_INVALID_ARG;
+  ptm_context *ctx = b->ctx;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (b->exec) {
+    CK(cudaGraphLaunch(b->exec, st));
+    return PTM_OK;
+  }
+  return batch_enqueue(b, st);
+}
+
+extern "C" ptm_status ptm_batch_capture(ptm_batch *b, void *stream) {
+  if (!b || !stream) return PTM_ERR_INVALID_ARG;
+  ptm_context *ctx = b->ctx;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  ptm_status rs = batch_enqueue(b, st);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (rs != PTM_OK) { if (g) cudaGraphDestroy(g); return rs; }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+  b->graph = g;
+  CK(cudaGraphInstantiate(&b->exec, g, 0));
+  return PTM_OK;
+}
+
+extern "C" ptm_status ptm_batch_stats(ptm_batch *b, ptm_stats *out) {
+  if (!b || !out) return PTM_ERR_INVALID_ARG;
+  ptm_context *ctx = b->ctx;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaEventSynchronize(b->ev[2]));
+  unsigned long long c[C_NCOUNTERS];
+  CK(cudaMemcpy(c, b->counters, sizeof c, cudaMemcpyDeviceToHost));
+  float t_all = -1.f, t_atom = -1.f;
+  if (cudaEventElapsedTime(&t_all, b->ev[0], b->ev[2]) != cudaSuccess) t_all = -1.f;
+  if (cudaEventElapsedTime(&t_atom, b->ev[1], b->ev[2]) != cudaSuccess) t_atom = -1.f;
+  cudaGetLastError();
+  out->atoms = (int64_t)c[C_ATOMS]; out->matched = (int64_t)c[C_MATCHED]; out->knn_wide = (int64_t)c[C_KNN_WIDE];
+  out->knn_fail = (int64_t)c[C_KNN_FAIL]; out->sos = (int64_t)c[C_SOS]; out->qcp_fp64 = (int64_t)c[C_QCP64];
+  out->tie_fp64 = (int64_t)c[C_TIE64]; out->internal = (int64_t)c[C_INTERNAL];
+  out->candidates = (int64_t)c[C_CAND]; out->candidate_points = (int64_t)c[C_CANDPTS];
+  out->pipeline_ms = t_all;
+  out->atom_kernel_ms = t_atom;
+  return PTM_OK;
+}
+
+extern "C" ptm_status ptm_batch_destroy(ptm_batch *b) {
+  if (!b) return PTM_ERR_INVALID_ARG;
+  cudaSetDevice(b->ctx->device);
+  for (int i = 0; i < 3; i++) if (b->ev[i]) cudaEventSynchronize(b->ev[i]);
+  batch_free(b);
+  cudaGetLastError();
+  return PTM_OK;
+}
+
+// Autotuner: time every (cell size factor, queue tile, blocks per SM) candidate
+// on the caller's batch (two warm runs, then the best of three timed runs) and
+// return the fastest.  Outputs are overwritten with identical results.
+extern "C" ptm_status ptm_autotune_batch(ptm_context *ctx, int nframes, const ptm_frame *frames,
+                                         const ptm_outputs *outs, void *stream, ptm_tuning *best) {
+  if (!ctx || !best) return PTM_ERR_INVALID_ARG;
+  static const double factors[] = {1.0, 1.125, 1.25, 1.4, 1.6};
+  static const int tiles[] = {64, 256, 1024};
+  static const int bpsm[] = {4, 5};
+  cudaStream_t st = (cudaStream_t)stream;
+  float best_ms = INFINITY;
+  for (double fc : factors)
+    for (int tl : tiles)
+      for (int bs : bpsm) {
+        ptm_tuning t = {fc, tl, bs};
+        ptm_batch *b = nullptr;
+        ptm_status rs = ptm_batch_create(ctx, nframes, frames, outs, &t, &b);
+        if (rs != PTM_OK) return rs;
+        float ms = INFINITY;
+        for (int r = 0; r < 5 && rs == PTM_OK; r++) {
+          rs = batch_enqueue(b, st);
+          if (rs != PTM_OK) break;
+          if (r >= 2) {
+            float m = 0.f;
+            if (cudaEventSynchronize(b->ev[2]) != cudaSuccess ||
+                cudaEventElapsedTime(&m, b->ev[0], b->ev[2]) != cudaSuccess) { rs = PTM_ERR_CUDA; break; }
+            ms = std::min(ms, m);
+          }
+        }
+        batch_free(b);
+        if (rs != PTM_OK) return rs;
+        if (ms < best_ms) { best_ms = ms; *best = t; }
+      }
+  return PTM_OK;
+}
+
 // ============================================================ no-allocation entry
 // ptm_classify_frame_noalloc: the same kernels with their workspace in one
 // file-scope device array, for callers that cannot allocate device memory.  The
@@ -487,6 +795,7 @@ extern "C" ptm_status ptm_classify_frame_noalloc(const ptm_frame *f, const ptm_o
   for (int c = 0; c < 3; c++) { bp.W[c] = (float)W[c]; bp.nb[c] = nb[c]; bp.pbc[c] = desc.pbc[c]; }
   bp.n = n;
   bp.f64 = f64;
+  cudaGetLastError();   // launch errors are read below; drop any left by earlier calls
   // the array keeps the previous call's contents: clear what must start at zero
   if (cudaMemsetAsync(cell_count, 0, (ncell + 1) * sizeof(int), st) != cudaSuccess ||
       cudaMemsetAsync(dstat, 0, 8 * sizeof(int), st) != cudaSuccess ||

@@ -32,9 +32,9 @@ struct Atom64 { double x, y, z; long long id; };
 
 // Device-resident description of one frame (filled by the host).
 struct FrameDesc {
-  const void *sorted;          // float4 (x, y, z, id bits) or Atom64, cell-sorted
-  const int *sbin;             // cell of each sorted slot
-  const int *cell_start;       // ncell + 1 offsets into sorted
+  const void *sorted;          // float4 (x, y, z, id bits) or Atom64, cell-sorted (ids are frame-local)
+  const int *sbin;             // frame-local cell of each sorted slot
+  const int *cell_start;       // this frame's ncell + 1 offsets into sorted (global sorted indices)
   const int *wrapv;            // packed lattice wrap per sorted slot
   const int8_t *species;       // by atom id, or NULL
   const void *positions;       // caller positions (by atom id)
@@ -59,7 +59,7 @@ struct FrameDesc {
   int32_t *corr;
   int *dstat;                  // [0] any atom wrapped, [1] overshoot (float bits, Angstrom)
   unsigned long long *counters;  // ptm_stats order: atoms, matched, knn_wide, knn_fail, sos, qcp_fp64, tie_fp64, internal, candidates, candidate_points
-  int64_t work_offset;         // first work item of this frame in a batch
+  int64_t atom_offset;         // first sorted slot of this frame (0 for a single frame)
 };
 
 enum { C_ATOMS = 0, C_MATCHED, C_KNN_WIDE, C_KNN_FAIL, C_SOS, C_QCP64, C_TIE64, C_INTERNAL, C_CAND, C_CANDPTS, C_NCOUNTERS };

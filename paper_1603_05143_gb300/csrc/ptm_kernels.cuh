@@ -723,6 +723,11 @@ struct BinParams {
   int pbc[3];
   int64_t n;
   int f64;
+  // batches only: where this frame lives
+  const void *pos;   // the frame's positions
+  int *dstat;        // the frame's status words
+  int64_t atom_off;  // first atom of the frame in the batch order
+  int cell_off;      // first cell of the frame in the batch's cell array
 };
 
 #define PTM_WRAP_TOL 1e-4f
@@ -835,6 +840,84 @@ __global__ void k_scatter(const void *pos, int f64, int64_t n, const int *atom_c
   wrapv[slot] = atom_wrap[i];
 }
 
+// ------------------------------------------------------------ batched frames
+// Frame of batch atom i: the last frame whose first atom is <= i.
+__device__ __forceinline__ int frame_of(const int64_t *atom_off, int nframes, int64_t i) {
+  int lo = 0, hi = nframes - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg((const unsigned long long *)atom_off + mid) <= (unsigned long long)i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Cell of one atom of frame p (shared by the single-frame and batched binning).
+__device__ __forceinline__ int bin_atom(const BinParams &p, const void *pos, int64_t li, int &wrap, float &over) {
+  float x, y, z;
+  if (p.f64) {
+    const double *q = (const double *)pos + 3 * li;
+    x = (float)q[0]; y = (float)q[1]; z = (float)q[2];
+  } else {
+    const float *q = (const float *)pos + 3 * li;
+    x = q[0]; y = q[1]; z = q[2];
+  }
+  int bc[3], w[3];
+  over = 0.f;
+  for (int c = 0; c < 3; c++) {
+    float f = x * p.Hinv[c] + y * p.Hinv[3 + c] + z * p.Hinv[6 + c];
+    w[c] = 0;
+    if (p.pbc[c] && (f < -PTM_WRAP_TOL || f >= 1.f + PTM_WRAP_TOL)) {
+      w[c] = (int)floorf(f);
+      f -= (float)w[c];
+    }
+    over = fmaxf(over, fmaxf(-f, f - 1.f) * p.W[c]);
+    int b = (int)floorf(f * (float)p.nb[c]);
+    bc[c] = min(max(b, 0), p.nb[c] - 1);
+  }
+  over = fmaxf(over, 0.f) + 1e-5f * fmaxf(p.W[0], fmaxf(p.W[1], p.W[2]));
+  wrap = img_pack(w[0], w[1], w[2]);
+  return (bc[0] * p.nb[1] + bc[1]) * p.nb[2] + bc[2];
+}
+
+__global__ void k_bin_batch(const BinParams *__restrict__ bp, const int64_t *__restrict__ atom_off, int nframes,
+                            int64_t ntotal, int *cell_count, int *atom_cell, int *atom_rank, int *atom_wrap) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntotal) return;
+  const int f = frame_of(atom_off, nframes, i);
+  const BinParams &p = bp[f];
+  int wrap;
+  float over;
+  const int cell = p.cell_off + bin_atom(p, p.pos, i - p.atom_off, wrap, over);
+  if (wrap != img_pack(0, 0, 0)) p.dstat[0] = 1;
+  atomicMax(p.dstat + 1, __float_as_int(over));
+  atom_cell[i] = cell;
+  atom_rank[i] = atomicAdd(cell_count + cell, 1);
+  atom_wrap[i] = wrap;
+}
+
+__global__ void k_scatter_batch(const BinParams *__restrict__ bp, const int64_t *__restrict__ atom_off, int nframes,
+                                int64_t ntotal, const int *atom_cell, const int *atom_rank, const int *atom_wrap,
+                                const int *cell_start, void *sorted, int *sbin, int *wrapv) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntotal) return;
+  const int f = frame_of(atom_off, nframes, i);
+  const BinParams &p = bp[f];
+  const int64_t li = i - p.atom_off;
+  const int c = atom_cell[i];
+  const int slot = cell_start[c] + atom_rank[i];
+  if (p.f64) {
+    const double *q = (const double *)p.pos + 3 * li;
+    Atom64 a;
+    a.x = q[0]; a.y = q[1]; a.z = q[2]; a.id = li;
+    ((Atom64 *)sorted)[slot] = a;
+  } else {
+    const float *q = (const float *)p.pos + 3 * li;
+    ((float4 *)sorted)[slot] = make_float4(q[0], q[1], q[2], __int_as_float((int)li));
+  }
+  sbin[slot] = c - p.cell_off;
+  wrapv[slot] = atom_wrap[i];
+}
+
 constexpr size_t atom_smem_bytes() {
   return (size_t)PTM_BLOCK * SCRATCH_WORDS * 4 + 5 * 15 * sizeof(float4);
 }
@@ -863,6 +946,47 @@ __global__ void __launch_bounds__(PTM_BLOCK, 5) k_atoms(const __grid_constant__ 
   int64_t s = (int64_t)blockIdx.x * PTM_BLOCK + threadIdx.x;
   if (s >= d.n) return;
   classify_atom<F64>(d, (int)s, sm, tplw);
+}
+
+// Persistent classification of a batch: every block pulls tiles of PTM_BLOCK
+// consecutive sorted slots from one global queue until the batch is exhausted,
+// so uneven frames balance across the GPU.  Each slot finds its frame by a
+// binary search over the frames' first slots.
+template <bool F64>
+__global__ void __launch_bounds__(PTM_BLOCK, 5)
+    k_atoms_batch(const FrameDesc *__restrict__ descs, const int64_t *__restrict__ atom_off, int nframes,
+                  int64_t ntotal, int tile_atoms, unsigned long long *queue) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t *th = (uint64_t *)smem;
+  float *q = (float *)(th + 14 * PTM_BLOCK);
+  float *nv = q + 42 * PTM_BLOCK;
+  int *nid = (int *)(nv + 42 * PTM_BLOCK);
+  uint32_t *code = (uint32_t *)(nid + 14 * PTM_BLOCK);
+  uint16_t *fac = (uint16_t *)(code + 10 * PTM_BLOCK);
+  uint16_t *used = fac + 24 * PTM_BLOCK;
+  float4 *tplw = (float4 *)(used + 14 * PTM_BLOCK);
+  __shared__ long long tile0;
+  for (int i = threadIdx.x; i < 75; i += blockDim.x) {
+    const float *w = ptm_tpl[i / 15][i % 15];
+    tplw[i] = make_float4(w[0], w[1], w[2], w[3]);
+  }
+  Scratch sm;
+  sm.q = q; sm.nv = nv; sm.nid = nid; sm.fac = fac; sm.th = th; sm.used = used; sm.code = code;
+  sm.t = threadIdx.x;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) tile0 = (long long)atomicAdd(queue, (unsigned long long)tile_atoms);
+    __syncthreads();
+    const long long base = tile0;
+    if (base >= ntotal) break;
+    for (int k = 0; k < tile_atoms; k += PTM_BLOCK) {
+      const long long s = base + k + threadIdx.x;
+      if (s < ntotal) {
+        const int f = frame_of(atom_off, nframes, s);
+        classify_atom<F64>(descs[f], (int)s, sm, tplw);
+      }
+    }
+  }
 }
 
 }  // namespace ptm
