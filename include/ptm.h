@@ -180,9 +180,9 @@ ptm_status ptm_batch_stats(ptm_batch *batch, ptm_stats *out);
 ptm_status ptm_batch_destroy(ptm_batch *batch);
 
 /* Time every candidate tuning on this batch (cell_factor in {1.0, 1.125, 1.25,
-   1.4, 1.6}, tile_atoms in {64, 256, 1024}, blocks_per_sm in {4, 5}) and
-   return the fastest in *best.  Runs the batch about 150 times; outputs are
-   written with the same results each time. */
+   1.4}, tile_atoms in {64, 256, 1024}, blocks_per_sm in {4, 5}) and return the
+   fastest in *best.  Runs the batch 72 times; outputs are written with the same
+   results each time. */
 ptm_status ptm_autotune_batch(ptm_context *ctx, int n_frames, const ptm_frame *frames,
                               const ptm_outputs *outs, void *stream, ptm_tuning *best);
 

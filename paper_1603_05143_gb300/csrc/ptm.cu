@@ -628,12 +628,12 @@ extern "C" ptm_status ptm_batch_destroy(ptm_batch *b) {
 }
 
 // Autotuner: time every (cell size factor, queue tile, blocks per SM) candidate
-// on the caller's batch (two warm runs, then the best of three timed runs) and
+// on the caller's batch (one warm run, then the best of two timed runs) and
 // return the fastest.  Outputs are overwritten with identical results.
 extern "C" ptm_status ptm_autotune_batch(ptm_context *ctx, int nframes, const ptm_frame *frames,
                                          const ptm_outputs *outs, void *stream, ptm_tuning *best) {
   if (!ctx || !best) return PTM_ERR_INVALID_ARG;
-  static const double factors[] = {1.0, 1.125, 1.25, 1.4, 1.6};
+  static const double factors[] = {1.0, 1.125, 1.25, 1.4};
   static const int tiles[] = {64, 256, 1024};
   static const int bpsm[] = {4, 5};
   cudaStream_t st = (cudaStream_t)stream;
@@ -646,10 +646,10 @@ extern "C" ptm_status ptm_autotune_batch(ptm_context *ctx, int nframes, const pt
         ptm_status rs = ptm_batch_create(ctx, nframes, frames, outs, &t, &b);
         if (rs != PTM_OK) return rs;
         float ms = INFINITY;
-        for (int r = 0; r < 5 && rs == PTM_OK; r++) {
+        for (int r = 0; r < 3 && rs == PTM_OK; r++) {
           rs = batch_enqueue(b, st);
           if (rs != PTM_OK) break;
-          if (r >= 2) {
+          if (r >= 1) {
             float m = 0.f;
             if (cudaEventSynchronize(b->ev[2]) != cudaSuccess ||
                 cudaEventElapsedTime(&m, b->ev[0], b->ev[2]) != cudaSuccess) { rs = PTM_ERR_CUDA; break; }
