@@ -181,10 +181,58 @@ ptm_status ptm_batch_destroy(ptm_batch *batch);
 
 /* Time every candidate tuning on this batch (cell_factor in {1.0, 1.125, 1.25,
    1.4}, tile_atoms in {64, 256, 1024}, blocks_per_sm in {4, 5}) and return the
-   fastest in *best.  Runs the batch 72 times; outputs are written with the same
-   results each time. */
+   fastest in *best.  Runs the batch (every m-th frame of it when it holds more
+   than about 4 M atoms) 72 times; outputs are written with the same results
+   each time. */
 ptm_status ptm_autotune_batch(ptm_context *ctx, int n_frames, const ptm_frame *frames,
                               const ptm_outputs *outs, void *stream, ptm_tuning *best);
+
+/* ---------------------------------------------------------------- serving
+   In-situ analysis of MD frames that arrive at any time.  A server owns one
+   scheduler thread and a few non-blocking streams.  Submitted frames (HOST
+   buffers, ideally page-locked) wait in a FIFO and are admitted when their
+   device bytes (inputs, outputs and workspace, about 300 B per atom) fit the
+   HBM budget next to the frames already on the device.  Whenever a stream is
+   free, every admitted frame not yet launched (up to max_batch_frames) forms
+   one batch: copy in, one persistent launch, copy out.  Frames arriving while
+   batches run join the next batch as memory and streams free up, and batches
+   on different streams overlap on the device (continuous batching).  Device
+   memory is pooled and reused; nothing is freed while the server runs.  Each
+   frame's results equal those of ptm_classify_frame. */
+typedef struct ptm_server ptm_server;
+
+typedef struct {
+  size_t hbm_budget_bytes;   /* 0 = the context's budget (half the free memory at create) */
+  int max_batch_frames;      /* frames per launch; 0 = 64 */
+  int streams;               /* batches in flight; 0 = 2, at most 8 */
+  ptm_tuning tuning;         /* zeros = defaults */
+} ptm_server_options;
+
+ptm_status ptm_server_create(ptm_context *ctx, const ptm_server_options *options, ptm_server **out);
+
+/* Queue one frame (HOST pointers; they must stay valid until the ticket
+   completes).  Never blocks on the GPU. */
+ptm_status ptm_submit(ptm_server *server, const ptm_frame *frame, const ptm_outputs *out,
+                      uint64_t *ticket);
+
+/* *done = 1 once the ticket finished (its outputs are on the host); returns the
+   frame's status when done (PTM_ERR_OUT_OF_MEMORY if it can never fit the
+   budget), PTM_ERR_NOT_FOUND for an unknown ticket. */
+ptm_status ptm_poll(ptm_server *server, uint64_t ticket, int *done);
+
+/* Wait at most timeout_ms (< 0: no limit) for a ticket; PTM_ERR_TIMEOUT if it
+   is still running, else the frame's status. */
+ptm_status ptm_wait(ptm_server *server, uint64_t ticket, int timeout_ms);
+
+/* times[0..2] = submit, launch and completion times (seconds, steady clock);
+   *batch = index of the batch that carried the frame (-1 before launch). */
+ptm_status ptm_ticket_info(ptm_server *server, uint64_t ticket, double *times, int64_t *batch);
+
+/* Forget a finished ticket (PTM_ERR_BUSY while it runs). */
+ptm_status ptm_release(ptm_server *server, uint64_t ticket);
+
+/* Finish all queued and running frames, then free the server. */
+ptm_status ptm_server_destroy(ptm_server *server);
 
 /* Largest frame accepted by ptm_classify_frame_noalloc. */
 #define PTM_NOALLOC_MAX_ATOMS 32768

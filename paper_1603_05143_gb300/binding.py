@@ -42,6 +42,11 @@ class ptm_tuning(C.Structure):
     _fields_ = [("cell_factor", C.c_double), ("tile_atoms", C.c_int), ("blocks_per_sm", C.c_int)]
 
 
+class ptm_server_options(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_batch_frames", C.c_int), ("streams", C.c_int),
+                ("tuning", ptm_tuning)]
+
+
 class PTMError(RuntimeError):
     def __init__(self, status: int, what: str, detail: str = ""):
         name = STATUS[status] if 0 <= status < len(STATUS) else f"status {status}"
@@ -77,6 +82,16 @@ def load():
                                          C.POINTER(ptm_tuning)]
         for f in ("ptm_batch_create", "ptm_batch_run", "ptm_batch_capture", "ptm_batch_stats",
                   "ptm_batch_destroy", "ptm_autotune_batch"):
+            getattr(L, f).restype = C.c_int
+        L.ptm_server_create.argtypes = [P, C.POINTER(ptm_server_options), C.POINTER(C.c_void_p)]
+        L.ptm_submit.argtypes = [P, C.POINTER(ptm_frame), C.POINTER(ptm_outputs), C.POINTER(C.c_uint64)]
+        L.ptm_poll.argtypes = [P, C.c_uint64, C.POINTER(C.c_int)]
+        L.ptm_wait.argtypes = [P, C.c_uint64, C.c_int]
+        L.ptm_ticket_info.argtypes = [P, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+        L.ptm_release.argtypes = [P, C.c_uint64]
+        L.ptm_server_destroy.argtypes = [P]
+        for f in ("ptm_server_create", "ptm_submit", "ptm_poll", "ptm_wait", "ptm_ticket_info", "ptm_release",
+                  "ptm_server_destroy"):
             getattr(L, f).restype = C.c_int
         L.ptm_status_string.argtypes = [C.c_int]
         L.ptm_status_string.restype = C.c_char_p
@@ -317,3 +332,79 @@ def allocate_outputs_host(n, outputs=OUTPUT_NAMES, pinned=False):
         tt = {np.int8: torch.int8, np.float32: torch.float32, np.int32: torch.int32}
         return {k: torch.empty(shapes[k][0], dtype=tt[shapes[k][1]], pin_memory=True).numpy() for k in outputs}
     return {k: np.empty(shapes[k][0], shapes[k][1]) for k in outputs}
+
+
+class Server:
+    """Continuous-batching server (``ptm_server_*``) for frames held in host memory.
+
+    ``submit`` returns a ticket immediately; the frame's outputs (numpy arrays,
+    page-locked when ``pinned``) are filled when the ticket completes."""
+
+    def __init__(self, ptm, hbm_budget_bytes=0, max_batch_frames=0, streams=0, tuning=None):
+        self.ptm = ptm
+        self.lib = ptm.lib
+        t = tuning or {}
+        opt = ptm_server_options(int(hbm_budget_bytes), int(max_batch_frames), int(streams),
+                                 ptm_tuning(float(t.get("cell_factor", 0)), int(t.get("tile_atoms", 0)),
+                                            int(t.get("blocks_per_sm", 0))))
+        h = C.c_void_p()
+        ptm._check(self.lib.ptm_server_create(ptm.h, C.byref(opt), C.byref(h)), "ptm_server_create")
+        self.h = h
+        self._live = {}
+
+    def submit(self, positions, cell, pbc=(True, True, True), species=None, mask=MASK_ALL, rmsd_max=math.inf,
+               out=None, pinned=False):
+        pos = np.ascontiguousarray(positions)
+        n = pos.shape[0]
+        sp = None if species is None else np.ascontiguousarray(species, np.int8)
+        if out is None:
+            out = allocate_outputs_host(n, pinned=pinned)
+        o = ptm_outputs()
+        for name in OUTPUT_NAMES:
+            a = out.get(name)
+            setattr(o, name, a.ctypes.data if a is not None else None)
+        f = _frame(n, pos.ctypes.data, PTM_F64 if pos.dtype == np.float64 else PTM_F32,
+                   sp.ctypes.data if sp is not None else None, cell, pbc, mask, rmsd_max)
+        t = C.c_uint64()
+        rc = self.lib.ptm_submit(self.h, C.byref(f), C.byref(o), C.byref(t))
+        if rc:
+            raise PTMError(rc, "ptm_submit")
+        self._live[t.value] = (pos, sp, out)          # keep the host buffers alive
+        return t.value
+
+    def poll(self, ticket) -> bool:
+        d = C.c_int()
+        rc = self.lib.ptm_poll(self.h, ticket, C.byref(d))
+        if rc:
+            raise PTMError(rc, "ptm_poll")
+        return bool(d.value)
+
+    def wait(self, ticket, timeout_ms=-1):
+        """Outputs of the ticket; raises PTMError (PTM_ERR_TIMEOUT, ...) otherwise."""
+        rc = self.lib.ptm_wait(self.h, ticket, int(timeout_ms))
+        if rc:
+            raise PTMError(rc, "ptm_wait")
+        return self._live[ticket][2]
+
+    def info(self, ticket):
+        times = (C.c_double * 3)()
+        b = C.c_int64()
+        rc = self.lib.ptm_ticket_info(self.h, ticket, times, C.byref(b))
+        if rc:
+            raise PTMError(rc, "ptm_ticket_info")
+        return {"submit": times[0], "start": times[1], "done": times[2], "batch": b.value}
+
+    def release(self, ticket):
+        self.lib.ptm_release(self.h, ticket)
+        self._live.pop(ticket, None)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ptm_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

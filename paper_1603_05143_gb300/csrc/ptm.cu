@@ -445,16 +445,15 @@ struct ptm_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int nsm = 152;
+  void *block = nullptr;          // the workspace (one allocation, or a pool block when served)
+  bool owns_block = true;
 };
 
 static void batch_free(ptm_batch *b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  cudaFree(b->d_descs); cudaFree(b->d_bp); cudaFree(b->d_atom_off); cudaFree(b->d_dstat);
-  cudaFree(b->sorted); cudaFree(b->sbin); cudaFree(b->wrapv); cudaFree(b->atom_cell); cudaFree(b->atom_rank);
-  cudaFree(b->atom_wrap); cudaFree(b->cell_count); cudaFree(b->cell_start); cudaFree(b->block_sums);
-  cudaFree(b->scan_total); cudaFree(b->queue); cudaFree(b->counters);
+  if (b->owns_block) cudaFree(b->block);
   for (int i = 0; i < 3; i++) if (b->ev[i]) cudaEventDestroy(b->ev[i]);
   delete b;
 }
@@ -464,7 +463,10 @@ static void batch_free(ptm_batch *b) {
 static ptm_status batch_enqueue(ptm_batch *b, cudaStream_t st) {
   ptm_context *ctx = b->ctx;
   cudaGetLastError();   // launch errors are read below; drop any left by earlier calls
-  CK(cudaEventRecord(b->ev[0], st));
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(st, &cap));
+  const unsigned rec = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+  CK(cudaEventRecordWithFlags(b->ev[0], st, rec));
   CK(cudaMemsetAsync(b->cell_count, 0, (b->ncell + 1) * sizeof(int), st));
   CK(cudaMemsetAsync(b->d_dstat, 0, (size_t)4 * b->nframes * sizeof(int), st));
   CK(cudaMemsetAsync(b->counters, 0, C_NCOUNTERS * sizeof(unsigned long long), st));
@@ -480,7 +482,7 @@ static ptm_status batch_enqueue(ptm_batch *b, cudaStream_t st) {
   k_scan_add<<<(nscan + 255) / 256, 256, 0, st>>>(b->cell_start, b->block_sums, nscan);
   k_scatter_batch<<<gb, tb, 0, st>>>(b->d_bp, b->d_atom_off, b->nframes, b->ntotal, b->atom_cell, b->atom_rank,
                                      b->atom_wrap, b->cell_start, b->sorted, b->sbin, b->wrapv);
-  CK(cudaEventRecord(b->ev[1], st));
+  CK(cudaEventRecordWithFlags(b->ev[1], st, rec));
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->nsm * b->blocks_per_sm,
                                                                        (b->ntotal + b->tile_atoms - 1) / b->tile_atoms));
   if (b->f64)
@@ -490,8 +492,80 @@ static ptm_status batch_enqueue(ptm_batch *b, cudaStream_t st) {
     k_atoms_batch<false><<<grid, PTM_BLOCK, atom_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes,
                                                                      b->ntotal, b->tile_atoms, b->queue);
   CK(cudaGetLastError());
-  CK(cudaEventRecord(b->ev[2], st));
+  CK(cudaEventRecordWithFlags(b->ev[2], st, rec));
   return PTM_OK;
+}
+
+// Host-side preparation of a batch: descriptors, binning parameters and
+// offsets of every frame, total atoms and cells.
+struct BatchPlan {
+  std::vector<FrameDesc> hd;
+  std::vector<BinParams> hb;
+  std::vector<int64_t> off;
+  int64_t ntotal = 0;
+  size_t ncell = 0;
+  int f64 = 0;
+};
+
+static ptm_status batch_plan(int nframes, const ptm_frame *frames, double cell_factor, BatchPlan &P) {
+  P.hd.resize(nframes);
+  P.hb.resize(nframes);
+  P.off.resize(nframes);
+  P.f64 = frames[0].pos_dtype == PTM_F64;
+  for (int f = 0; f < nframes; f++) {
+    size_t nc = 0;
+    ptm_status rs = setup_frame(&frames[f], cell_factor, &P.hd[f], &P.hb[f], &nc);
+    if (rs == PTM_OK && (frames[f].pos_dtype == PTM_F64) != (P.f64 != 0)) rs = PTM_ERR_INVALID_ARG;
+    if (rs != PTM_OK) return rs;
+    P.off[f] = P.ntotal;
+    P.hb[f].atom_off = P.ntotal;
+    P.hb[f].cell_off = (int)P.ncell;
+    P.hd[f].atom_offset = P.ntotal;
+    P.ntotal += frames[f].n_atoms;
+    P.ncell += nc;
+    if (P.ntotal >= (1ll << 31) || P.ncell >= (1ull << 31)) return PTM_ERR_INVALID_ARG;
+  }
+  return PTM_OK;
+}
+
+// Device bytes of a batch's workspace (descriptors, sorted atoms, cell lists).
+static size_t batch_workspace_bytes(int nframes, int64_t ntotal, size_t ncell, int f64) {
+  const size_t n = (size_t)ntotal, rec = f64 ? sizeof(Atom64) : sizeof(float4);
+  const size_t nblk = (ncell + 1 + 2 * SCAN_BLOCK - 1) / (2 * SCAN_BLOCK) + 1;
+  return (sizeof(FrameDesc) + sizeof(BinParams) + sizeof(int64_t) + 16) * nframes + rec * n + 20 * n +
+         8 * (ncell + 1) + 4 * nblk + 4 + 8 + 8 * C_NCOUNTERS + 16 * 256;
+}
+
+// Carve the batch workspace out of one device block (256-byte aligned pieces)
+// and point the descriptors at it.
+static void batch_layout(ptm_batch *b, unsigned char *base, BatchPlan &P, const ptm_outputs *outs) {
+  size_t o = 0;
+  auto take = [&](size_t bytes) { void *p = base + o; o += (bytes + 255) / 256 * 256; return p; };
+  const size_t n = (size_t)P.ntotal, nc = P.ncell;
+  const size_t nblk = (nc + 1 + 2 * SCAN_BLOCK - 1) / (2 * SCAN_BLOCK) + 1;
+  const int nf = b->nframes;
+  b->d_descs = (FrameDesc *)take(sizeof(FrameDesc) * nf);
+  b->d_bp = (BinParams *)take(sizeof(BinParams) * nf);
+  b->d_atom_off = (int64_t *)take(sizeof(int64_t) * nf);
+  b->d_dstat = (int *)take(sizeof(int) * 4 * nf);
+  b->sorted = take((P.f64 ? sizeof(Atom64) : sizeof(float4)) * n);
+  b->sbin = (int *)take(4 * n); b->wrapv = (int *)take(4 * n); b->atom_cell = (int *)take(4 * n);
+  b->atom_rank = (int *)take(4 * n); b->atom_wrap = (int *)take(4 * n);
+  b->cell_count = (int *)take(4 * (nc + 1)); b->cell_start = (int *)take(4 * (nc + 1));
+  b->block_sums = (int *)take(4 * nblk); b->scan_total = (int *)take(4);
+  b->queue = (unsigned long long *)take(8); b->counters = (unsigned long long *)take(8 * C_NCOUNTERS);
+  for (int f = 0; f < nf; f++) {
+    P.hd[f].sorted = b->sorted;
+    P.hd[f].sbin = b->sbin;
+    P.hd[f].cell_start = b->cell_start + P.hb[f].cell_off;
+    P.hd[f].wrapv = b->wrapv;
+    P.hd[f].structure = outs[f].structure; P.hd[f].alloy = outs[f].alloy; P.hd[f].rmsd = outs[f].rmsd;
+    P.hd[f].scale = outs[f].scale; P.hd[f].quat = outs[f].quat; P.hd[f].strain = outs[f].strain;
+    P.hd[f].corr = outs[f].correspondence;
+    P.hd[f].dstat = b->d_dstat + 4 * f;
+    P.hd[f].counters = b->counters;
+    P.hb[f].dstat = b->d_dstat + 4 * f;
+  }
 }
 
 extern "C" ptm_status ptm_batch_create(ptm_context *ctx, int nframes, const ptm_frame *frames, const ptm_outputs *outs,
@@ -510,57 +584,21 @@ extern "C" ptm_status ptm_batch_create(ptm_context *ctx, int nframes, const ptm_
   }
   if (!(b->cell_factor >= 0.5 && b->cell_factor <= 4.0)) { delete b; return PTM_ERR_INVALID_ARG; }
   cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
-  std::vector<FrameDesc> hd(nframes);
-  std::vector<BinParams> hb(nframes);
-  std::vector<int64_t> off(nframes);
-  b->f64 = frames[0].pos_dtype == PTM_F64;
-  for (int f = 0; f < nframes; f++) {
-    size_t nc = 0;
-    ptm_status rs = setup_frame(&frames[f], b->cell_factor, &hd[f], &hb[f], &nc);
-    if (rs == PTM_OK && (frames[f].pos_dtype == PTM_F64) != (b->f64 != 0)) rs = PTM_ERR_INVALID_ARG;
-    if (rs != PTM_OK) { delete b; return rs; }
-    off[f] = b->ntotal;
-    hb[f].atom_off = b->ntotal;
-    hb[f].cell_off = (int)b->ncell;
-    hd[f].atom_offset = b->ntotal;
-    b->ntotal += frames[f].n_atoms;
-    b->ncell += nc;
-    if (b->ntotal >= (1ll << 31) || b->ncell >= (1ull << 31)) { delete b; return PTM_ERR_INVALID_ARG; }
-  }
-  const size_t n = (size_t)b->ntotal, nc = b->ncell;
-  const size_t rec = b->f64 ? sizeof(Atom64) : sizeof(float4);
-  const size_t nblk = (nc + 1 + 2 * SCAN_BLOCK - 1) / (2 * SCAN_BLOCK) + 1;
-  cudaError_t e = cudaSuccess;
-  auto M = [&](void **p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
-  M((void **)&b->d_descs, sizeof(FrameDesc) * nframes);
-  M((void **)&b->d_bp, sizeof(BinParams) * nframes);
-  M((void **)&b->d_atom_off, sizeof(int64_t) * nframes);
-  M((void **)&b->d_dstat, sizeof(int) * 4 * nframes);
-  M(&b->sorted, rec * n);
-  M((void **)&b->sbin, 4 * n); M((void **)&b->wrapv, 4 * n); M((void **)&b->atom_cell, 4 * n);
-  M((void **)&b->atom_rank, 4 * n); M((void **)&b->atom_wrap, 4 * n);
-  M((void **)&b->cell_count, 4 * (nc + 1)); M((void **)&b->cell_start, 4 * (nc + 1));
-  M((void **)&b->block_sums, 4 * nblk); M((void **)&b->scan_total, 4);
-  M((void **)&b->queue, 8); M((void **)&b->counters, 8 * C_NCOUNTERS);
+  BatchPlan P;
+  ptm_status rs = batch_plan(nframes, frames, b->cell_factor, P);
+  if (rs != PTM_OK) { delete b; return rs; }
+  b->f64 = P.f64;
+  b->ntotal = P.ntotal;
+  b->ncell = P.ncell;
+  cudaError_t e = cudaMalloc(&b->block, batch_workspace_bytes(nframes, P.ntotal, P.ncell, P.f64));
   for (int i = 0; i < 3 && e == cudaSuccess; i++) e = cudaEventCreate(&b->ev[i]);
-  if (e != cudaSuccess) { ptm_status rs = cuda_fail(ctx, e, "ptm_batch_create"); batch_free(b); return rs; }
-  for (int f = 0; f < nframes; f++) {
-    hd[f].sorted = b->sorted;
-    hd[f].sbin = b->sbin;
-    hd[f].cell_start = b->cell_start + hb[f].cell_off;
-    hd[f].wrapv = b->wrapv;
-    hd[f].structure = outs[f].structure; hd[f].alloy = outs[f].alloy; hd[f].rmsd = outs[f].rmsd;
-    hd[f].scale = outs[f].scale; hd[f].quat = outs[f].quat; hd[f].strain = outs[f].strain;
-    hd[f].corr = outs[f].correspondence;
-    hd[f].dstat = b->d_dstat + 4 * f;
-    hd[f].counters = b->counters;
-    hb[f].dstat = b->d_dstat + 4 * f;
-  }
-  if ((e = cudaMemcpy(b->d_descs, hd.data(), sizeof(FrameDesc) * nframes, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(b->d_bp, hb.data(), sizeof(BinParams) * nframes, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(b->d_atom_off, off.data(), sizeof(int64_t) * nframes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+  if (e != cudaSuccess) { rs = cuda_fail(ctx, e, "ptm_batch_create"); batch_free(b); return rs; }
+  batch_layout(b, (unsigned char *)b->block, P, outs);
+  if ((e = cudaMemcpy(b->d_descs, P.hd.data(), sizeof(FrameDesc) * nframes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(b->d_bp, P.hb.data(), sizeof(BinParams) * nframes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(b->d_atom_off, P.off.data(), sizeof(int64_t) * nframes, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemset(b->counters, 0, 8 * C_NCOUNTERS)) != cudaSuccess) {
-    ptm_status rs = cuda_fail(ctx, e, "ptm_batch_create");
+    rs = cuda_fail(ctx, e, "ptm_batch_create");
     batch_free(b);
     return rs;
   }
@@ -628,8 +666,9 @@ extern "C" ptm_status ptm_batch_destroy(ptm_batch *b) {
 }
 
 // Autotuner: time every (cell size factor, queue tile, blocks per SM) candidate
-// on the caller's batch (one warm run, then the best of two timed runs) and
-// return the fastest.  Outputs are overwritten with identical results.
+// on the caller's batch, or on every m-th frame of it when it holds more than
+// about 4 M atoms (one warm run, then the best of two timed runs), and return the
+// fastest.  Outputs are overwritten with identical results.
 extern "C" ptm_status ptm_autotune_batch(ptm_context *ctx, int nframes, const ptm_frame *frames,
                                          const ptm_outputs *outs, void *stream, ptm_tuning *best) {
   if (!ctx || !best) return PTM_ERR_INVALID_ARG;
@@ -637,6 +676,16 @@ extern "C" ptm_status ptm_autotune_batch(ptm_context *ctx, int nframes, const pt
   static const int tiles[] = {64, 256, 1024};
   static const int bpsm[] = {4, 5};
   cudaStream_t st = (cudaStream_t)stream;
+  // tune on every m-th frame so that at most about 4 M atoms are timed per candidate
+  int64_t total = 0;
+  for (int f = 0; f < nframes; f++) total += frames[f].n_atoms;
+  const int stride = (int)std::max<int64_t>(1, (total + 4000000 - 1) / 4000000);
+  std::vector<ptm_frame> fs;
+  std::vector<ptm_outputs> os;
+  for (int f = 0; f < nframes; f += stride) { fs.push_back(frames[f]); os.push_back(outs[f]); }
+  nframes = (int)fs.size();
+  frames = fs.data();
+  outs = os.data();
   float best_ms = INFINITY;
   for (double fc : factors)
     for (int tl : tiles)
@@ -818,3 +867,5 @@ extern "C" ptm_status ptm_classify_frame_noalloc(const ptm_frame *f, const ptm_o
   if (cudaGetLastError() != cudaSuccess) return PTM_ERR_CUDA;
   return PTM_OK;
 }
+
+#include "ptm_serve.cuh"

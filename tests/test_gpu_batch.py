@@ -67,6 +67,8 @@ def test_batch_graph_replay_follows_positions(ptm):
         b.capture(s)
         b.run(s)
         s.synchronize()
+    st = b.stats()                       # events recorded by the graph replay
+    assert st["atoms"] == sum(f.n for f in frames) and st["atom_kernel_ms"] > 0
     for a, o in zip(first, b.outputs):
         for k in a:
             assert np.array_equal(a[k], o[k].cpu().numpy()), k
