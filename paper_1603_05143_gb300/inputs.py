@@ -259,106 +259,104 @@ def _thin_close_pairs(pos, L, dmin, rng):
     return pos[~removed]
 
 
+LIQUID_DENSITY = 0.058   # A^-3: ~70 % of fcc Cu, reachable by bounded random sequential addition
+
+
 def config_mixed_phase(seed: int = 13, n_target: int = 1 << 22, sigma: float = 0.20,
                        antisite: float = 0.10, ico_fraction: float = 0.01) -> Frame:
-    """Five slabs along x: bcc Fe, fcc Cu, L1_2 (species), sc, liquid with icosahedra."""
+    """Five equal slabs along x: bcc Fe, fcc Cu, L1_2 Cu3Au (int8 species, 10 %
+    antisites), sc, and a liquid: random sequential addition with a 2.0 A
+    minimum distance, seeded with 13-atom Mackay icosahedra (1 % of the liquid
+    atoms).  fcc density is ~93 % of the RSA jamming limit for 2.0 A, which
+    uniform proposals approach only slowly, so the box is sized for a liquid
+    near LIQUID_DENSITY.  Each crystal's lattice constant is rescaled (by well
+    under 1 % at 2^22 atoms) to a whole number of cells across Ly, so the
+    periodic y and z boundaries leave no seam; the liquid takes exactly the
+    atoms that remain to n_target."""
     rng = rng_for(seed)
-    rho = {"bcc": 2 / A_BCC_FE ** 3, "fcc": 4 / A_FCC_CU ** 3, "l12": 4 / A_L12 ** 3,
-           "sc": 1 / A_SC ** 3, "liq": 4 / A_FCC_CU ** 3}
-    mean_rho = float(np.mean(list(rho.values())))
-    # cross-section Ly = Lz = Ly, slab thickness t = Lx / 5; choose Lx = 5 t = 2 Ly
-    vol = n_target / mean_rho
-    ly = (vol / 2.0) ** (1.0 / 3.0)
+    phases = [("bcc", A_BCC_FE), ("fcc", A_FCC_CU), ("l12", A_L12), ("sc", A_SC)]
+    rho = [len(unit_cell(k, a)[1]) / a ** 3 for k, a in phases] + [LIQUID_DENSITY]
+    ly = (n_target / (sum(rho) * 0.4)) ** (1.0 / 3.0)
     lx = 2.0 * ly
     t = lx / 5.0
     pieces, species = [], []
-    for si, (kind, a) in enumerate([("bcc", A_BCC_FE), ("fcc", A_FCC_CU), ("l12", A_L12),
-                                    ("sc", A_SC)]):
+    for si, (kind, a0) in enumerate(phases):
+        ncell = max(1, int(round(ly / a0)))
+        a = ly / ncell
         cell0, basis, sp0 = unit_cell(kind, a)
-        nx, ny = int(math.ceil(t / a)) + 1, int(math.ceil(ly / a)) + 1
-        g = np.stack(np.meshgrid(np.arange(nx), np.arange(ny), np.arange(ny), indexing="ij"),
-                     -1).reshape(-1, 3)
+        nx = int(math.ceil(t / a))
+        g = np.stack(np.meshgrid(np.arange(nx), np.arange(ncell), np.arange(ncell), indexing="ij"), -1).reshape(-1, 3)
         p = ((g[:, None, :] + basis[None]).reshape(-1, 3)) @ cell0
-        s = np.tile(sp0, len(g)).astype(np.int8)
-        keep = (p[:, 0] < t) & (p[:, 1] < ly) & (p[:, 2] < ly)
-        p, s = p[keep], s[keep]
+        sp = np.tile(sp0, len(g)).astype(np.int8)
+        keep = p[:, 0] < t
+        p, sp = p[keep], sp[keep]
         p[:, 0] += si * t
         if kind == "l12":
-            flip = rng.random(len(s)) < antisite
-            s = np.where(flip, 1 - s, s).astype(np.int8)
+            flip = rng.random(len(sp)) < antisite
+            sp = np.where(flip, 1 - sp, sp).astype(np.int8)
         pieces.append(p)
-        species.append(s)
-    # liquid slab: icosahedral seeds, then random sequential addition with d_min = 2 A
-    n_liq_target = int(rho["liq"] * t * ly * ly)
-    liq = _rsa_liquid(rng, (4 * t, 5 * t), ly, n_liq_target, 2.0, ico_fraction)
+        species.append(sp)
+    n_liq = n_target - sum(len(p) for p in pieces)
+    liq = _rsa_liquid(rng, (4 * t, 5 * t), ly, n_liq, 2.0, ico_fraction)
+    if len(liq) < n_liq:
+        raise RuntimeError(f"liquid short of atoms: {len(liq)} < {n_liq}")
     pieces.append(liq)
     species.append(np.zeros(len(liq), np.int8))
     pos = np.vstack(pieces)
-    sp = np.concatenate(species)
     pos = pos + rng.normal(0.0, sigma, pos.shape)
     cell = np.diag([lx, ly, ly])
     pos = wrap_positions(pos, cell)
-    n = len(pos)
-    if n > n_target:
-        idx = np.sort(rng.choice(n, n_target, replace=False))
-        pos, sp = pos[idx], sp[idx]
-    elif n < n_target:
-        extra = rng.random((n_target - n, 3)) * [lx, ly, ly]
-        pos = np.vstack([pos, extra])
-        sp = np.concatenate([sp, np.zeros(n_target - n, np.int8)])
-    return Frame(pos.astype(np.float32), cell, (True, True, True), sp, "mixed_phase",
-                 {"Lx": lx, "Ly": ly, "liquid_atoms": len(liq), "liquid_target": n_liq_target,
-                  "raw_count": n})
+    return Frame(pos.astype(np.float32), cell, (True, True, True), np.concatenate(species), "mixed_phase",
+                 {"Lx": lx, "Ly": ly, "liquid_atoms": len(liq),
+                  "liquid_density": len(liq) / (t * ly * ly)})
 
 
-def _rsa_liquid(rng, xr, ly, n_target, dmin, ico_fraction, max_attempts_factor=30):
-    """Random sequential addition in the slab x in [xr), periodic in y and z."""
+def _rsa_liquid(rng, xr, ly, n_target, dmin, ico_fraction, max_rounds=60, batch=None):
+    """Random sequential addition of points at least dmin apart in the slab
+    x in [xr), periodic in y and z, seeded with 13-atom Mackay icosahedra
+    (centre + 12 at 2.556 A).  Proposals come in vectorised rounds: each round
+    rejects points too close to the accepted set (KD tree) and resolves clashes
+    inside the round in proposal order.  Close to the RSA jamming density the
+    acceptance rate falls, so the rounds are capped and the count reached is
+    returned."""
+    from scipy.spatial import cKDTree
     x0, x1 = xr
-    w = dmin
-    nbx, nby = max(1, int((x1 - x0) // w)), max(1, int(ly // w))
-    wx, wy = (x1 - x0) / nbx, ly / nby
-    grid: dict = {}
-    pts = []
-
-    def ok(p):
-        cx, cy, cz = int((p[0] - x0) // wx), int(p[1] // wy), int(p[2] // wy)
-        for dx in (-1, 0, 1):
-            for dy in (-1, 0, 1):
-                for dz in (-1, 0, 1):
-                    key = (cx + dx, (cy + dy) % nby, (cz + dz) % nby)
-                    for q in grid.get(key, ()):
-                        d = p - q
-                        d[1] -= ly * round(d[1] / ly)
-                        d[2] -= ly * round(d[2] / ly)
-                        if d @ d < dmin * dmin:
-                            return False
-        return True
-
-    def add(p):
-        key = (int((p[0] - x0) // wx), int(p[1] // wy) % nby, int(p[2] // wy) % nby)
-        grid.setdefault(key, []).append(p)
-        pts.append(p)
-
+    box = np.array([x1 - x0, ly, ly])
+    pts = np.zeros((0, 3))
     n_ico = int(ico_fraction * n_target / 13)
-    for _ in range(n_ico):
-        c = np.array([rng.uniform(x0 + 3, x1 - 3), rng.uniform(0, ly), rng.uniform(0, ly)])
-        cl = ico_cluster(2.556, rotation=random_rotation(rng)) + c
+    if n_ico:
+        cs = np.column_stack([rng.uniform(3, box[0] - 3, n_ico), rng.uniform(0, ly, n_ico), rng.uniform(0, ly, n_ico)])
+        cl = np.vstack([ico_cluster(2.556, rotation=random_rotation(rng)) + c for c in cs])
         cl[:, 1:] %= ly
-        if all(ok(p) for p in cl):
-            for p in cl:
-                add(p)
-    attempts = 0
-    batch = 4096
-    while len(pts) < n_target and attempts < max_attempts_factor * n_target:
-        cand = np.column_stack([rng.uniform(x0, x1, batch), rng.uniform(0, ly, batch),
-                                rng.uniform(0, ly, batch)])
-        for p in cand:
-            attempts += 1
-            if ok(p):
-                add(p)
-                if len(pts) >= n_target:
-                    break
-    return np.array(pts).reshape(-1, 3)
+        keep = np.ones(n_ico, bool)
+        tree = cKDTree(cs, boxsize=[1e9, ly, ly])
+        for i, j in sorted(tree.query_pairs(2.556 * 2 + dmin)):
+            if keep[i]:
+                keep[j] = False
+        pts = cl.reshape(n_ico, 13, 3)[keep].reshape(-1, 3)
+    batch = batch or max(4096, n_target // 8)
+    rate = 1.0    # acceptance rate of the previous round sizes the next one
+    for _ in range(max_rounds):
+        need = n_target - len(pts)
+        if need <= 0:
+            break
+        m = int(min(max(batch, 2.0 * need / max(rate, 1e-3)), 8 * n_target + 4096))
+        cand = rng.random((m, 3)) * box
+        if len(pts):
+            tree = cKDTree(pts, boxsize=[1e9, ly, ly])
+            dist, _ = tree.query(cand, k=1, distance_upper_bound=dmin)
+            cand = cand[~np.isfinite(dist)]
+        if len(cand) > 1:
+            ok = np.ones(len(cand), bool)
+            for i, j in sorted(cKDTree(cand, boxsize=[1e9, ly, ly]).query_pairs(dmin)):
+                if ok[i] and ok[j]:
+                    ok[j] = False
+            cand = cand[ok]
+        rate = max(len(cand), 1) / m
+        pts = np.vstack([pts, cand[:need]])
+    out = pts.copy()
+    out[:, 0] += x0
+    return out
 
 
 def config_batch(seed: int = 256, n_frames: int = 256, n_min: float = 1e3, n_max: float = 1e6,

@@ -141,6 +141,25 @@ def test_polycrystal_full_size_sampled(ptm):
     assert st["matched"] > 0.9 * len(atoms)
 
 
+def test_mixed_phase_small_full(ptm):
+    """65536-atom mixed-phase frame (bcc / fcc / L1_2 with antisites / sc /
+    liquid with icosahedral seeds), int8 species, sigma 0.20 A: every atom."""
+    f = I.config_mixed_phase(n_target=1 << 16)
+    st, g, ref = check(ptm, f)
+    counts = np.bincount(g["structure"], minlength=6)
+    assert counts[5] > 0.1 * f.n and counts[2] > 0.2 * f.n and counts[1] > 0.1 * f.n
+    assert np.any(g["alloy"] >= 3)      # L1_2 sites found
+
+
+def test_mixed_phase_full_size_sampled(ptm):
+    """The 4,194,304-atom mixed-phase frame; a seeded sample of atoms (liquid
+    included) is checked against the oracle one by one."""
+    f = I.config_mixed_phase()
+    atoms = np.sort(I.rng_for(78).choice(f.n, 3000, replace=False))
+    st, g, ref = check(ptm, f, atoms=atoms)
+    assert st["matched"] > 0.5 * len(atoms)
+
+
 def test_host_entry_point_matches_device(ptm):
     f = I.crystal("l12", I.A_L12, 5, sigma=0.1, seed=9, dtype=np.float32)
     d = run_gpu(ptm, f)
