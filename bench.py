@@ -73,9 +73,13 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", default="frame", choices=["frame", "batch"],
+    ap.add_argument("--mode", default="frame", choices=["frame", "batch", "serve"],
                     help="frame: the 2^20-atom polycrystal (default line); batch: 256 uneven frames in one "
-                         "persistent, graph-replayed launch")
+                         "persistent, graph-replayed launch; serve: a Poisson stream of mixed-phase frames "
+                         "through the continuous-batching server")
+    ap.add_argument("--serve-requests", type=int, default=512, help="frames per offered load (serve mode)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=WORKLOADS, help="frame mode: which frame")
+    ap.add_argument("--no-fp64-form", action="store_true", help="frame mode: skip timing the FP64 form")
     return ap.parse_args()
 
 
@@ -95,18 +99,36 @@ def dist_setup(args):
     return world, rank, local, pg
 
 
-def workload():
+WORKLOADS = ("polycrystal-1048576", "mixed-phase-4194304", "fcc-4000")
+
+
+def workload(name=WORKLOAD):
+    """(frame, species, config) of a named single-frame workload."""
     from paper_1603_05143_gb300 import inputs as I
-    f = I.config_polycrystal()
-    species = np.zeros(f.n, np.int8)      # pure Cu: the alloy rules run and give PURE
-    return f, species
+    if name == "polycrystal-1048576":
+        f = I.config_polycrystal()
+        species = np.zeros(f.n, np.int8)      # pure Cu: the alloy rules run and give PURE
+        c = {"workload": name, "atoms": f.n, "box_A": round(float(f.cell[0, 0]), 3), "grains": 16,
+             "stacking_faults": 4, "sigma_A": 0.15, "positions": "float32", "species": "given (all one type)",
+             "padded_atoms": int(f.meta.get("padded", 0))}
+    elif name == "mixed-phase-4194304":
+        f = I.config_mixed_phase()
+        species = f.species
+        c = {"workload": name, "atoms": f.n, "box_A": [round(float(x), 3) for x in np.diag(f.cell)],
+             "slabs": "bcc / fcc / L1_2 (10 % antisites) / sc / liquid", "sigma_A": 0.20, "positions": "float32",
+             "species": "int8 (Cu / Au)", "liquid_density": round(f.meta["liquid_density"], 4)}
+    elif name == "fcc-4000":
+        f = I.config_fcc_small()
+        species = np.zeros(f.n, np.int8)
+        c = {"workload": name, "atoms": f.n, "sigma_A": 0.10, "positions": "float64", "species": "given (all one type)"}
+    else:
+        raise ValueError(name)
+    c.update({"templates": "SC,FCC,HCP,ICO,BCC", "l2": "flushed (256 MB write) before every timed step"})
+    return f, species, c
 
 
-def config_dict(f, extra=None):
-    c = {"workload": WORKLOAD, "atoms": f.n, "box_A": round(float(f.cell[0, 0]), 3), "grains": 16,
-         "stacking_faults": 4, "sigma_A": 0.15, "positions": "float32", "templates": "SC,FCC,HCP,ICO,BCC",
-         "species": "given (all one type)", "l2": "flushed (256 MB write) before every timed step",
-         "padded_atoms": int(f.meta.get("padded", 0))}
+def config_dict(c, extra=None):
+    c = dict(c)
     if extra:
         c.update(extra)
     return c
@@ -163,9 +185,10 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU oracle arm
-def oracle_rate(f, species, seconds, threads=None, seed=7):
+def oracle_rate(f, species, seconds, threads=None, seed=7, outputs=False):
     """Time the oracle (as it stands) on a seeded uniform sample of the frame's
-    atoms, sized to take about `seconds` on all host cores."""
+    atoms, sized to take about `seconds` on `threads` host cores (all by
+    default).  With outputs=True also returns (atoms, oracle outputs)."""
     import oracle
     threads = threads or os.cpu_count() or 1
     F = oracle.Frame(f.positions, f.cell, f.pbc)
@@ -177,15 +200,57 @@ def oracle_rate(f, species, seconds, threads=None, seed=7):
     m = int(min(f.n, max(8 * threads, seconds / max(per_atom, 1e-9))))
     atoms = np.sort(rng.choice(f.n, m, replace=False))
     t = time.perf_counter()
-    F.classify(atoms, species=species, threads=threads, chunk=max(1, m // (8 * threads)))
+    ref = F.classify(atoms, species=species, threads=threads, chunk=max(1, m // (8 * threads)))
     dt = time.perf_counter() - t
+    if outputs:
+        return m / dt, m, dt, threads, atoms, ref
     return m / dt, m, dt, threads
+
+
+def errors_vs_oracle(gpu, atoms, ref):
+    """Per-output difference of the FP32 path from the FP64 oracle on the
+    sampled atoms: mismatch counts of the combinatorial outputs, maximum errors
+    of the floating-point ones (RMSD and strain absolute, scale relative,
+    orientation as the misorientation angle modulo the template group)."""
+    import oracle
+    gs = gpu["structure"][atoms]
+    out = {"atoms": int(len(atoms)),
+           "structure_mismatch": int(np.sum(gs != ref["structure"])),
+           "correspondence_mismatch": int(np.sum(np.any(gpu["correspondence"][atoms] != ref["corr"], axis=1))),
+           "alloy_mismatch": int(np.sum(gpu["alloy"][atoms] != ref["alloy"]))}
+    m = (ref["structure"] > 0) & (gs == ref["structure"])
+    if not m.any():
+        return out
+    out["rmsd_abs"] = float(np.abs(gpu["rmsd"][atoms][m] - ref["rmsd"][m]).max())
+    out["scale_rel"] = float(np.abs(gpu["scale"][atoms][m] / ref["scale"][m] - 1).max())
+    out["strain_abs"] = float(np.abs(gpu["strain"][atoms][m].astype(np.float64) - ref["strain"][m]).max())
+    groups = {}
+    ang = 0.0
+    for i in np.nonzero(m)[0]:
+        S = int(ref["structure"][i])
+        if S not in groups:
+            groups[S] = oracle.group(S - 1)[1]
+        qa = gpu["quat"][atoms[i]].astype(np.float64)
+        for g in groups[S]:      # q_ref * g over the group: the closest equivalent orientation
+            w, x, y, z = ref["quat"][i]
+            e = np.array([w * g[0] - x * g[1] - y * g[2] - z * g[3], w * g[1] + x * g[0] + y * g[3] - z * g[2],
+                          w * g[2] - x * g[3] + y * g[0] + z * g[1], w * g[3] + x * g[2] - y * g[1] + z * g[0]])
+            c = min(1.0, abs(float(np.dot(qa, e))) / np.linalg.norm(qa))
+            if c > 1 - 1e-3:
+                d = np.linalg.norm(qa / np.linalg.norm(qa) - np.sign(np.dot(qa, e)) * e)
+                ang_i = 4 * math.asin(min(1.0, d / 2))
+                break
+        else:
+            ang_i = math.pi
+        ang = max(ang, ang_i)
+    out["misorientation_rad"] = ang
+    return out
 
 
 def run_reference(args, world, rank, pg):
     if rank != 0:
         return
-    f, species = workload()
+    f, species, cfg = workload(args.workload)
     threads = os.cpu_count() or 1
     per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
@@ -201,7 +266,7 @@ def run_reference(args, world, rank, pg):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_dict(f, {"sample": "uniform seeded atom sample per step"}),
+            "data": "synthetic", "config": config_dict(cfg, {"sample": "uniform seeded atom sample per step"}),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{samples} atoms over {args.steps} steps, uniform seeded sample of the frame"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -215,7 +280,7 @@ def run_gpu(args, world, rank, local, pg):
     build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    f, species = workload()
+    f, species, cfg = workload(args.workload)
     ptm = PTM(local)
     pos = torch.from_numpy(f.positions).to(dev)
     sp = torch.from_numpy(species).to(dev)
@@ -287,6 +352,30 @@ def run_gpu(args, world, rank, local, pg):
         e2e = {"value": world * f.n * args.steps / tot, "unit": UNIT,
                "h2d_bytes_per_step": int(hpos.nbytes + hsp.nbytes),
                "d2h_bytes_per_step": int(sum(a.nbytes for a in hout.values()))}
+    # ---- the one-frame-per-launch FP64 form on the same frame (comparison)
+    fp64_form = None
+    if not args.no_fp64_form and rank == 0:
+        p64 = PTM(local, precision="fp64")
+        out64 = allocate_outputs(f.n, dev)
+        p64.classify(pos, f.cell, f.pbc, species=sp, out=out64)
+        torch.cuda.synchronize()
+        t64 = []
+        for _ in range(max(1, min(3, args.steps))):
+            flush.fill_(2)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p64.classify(pos, f.cell, f.pbc, species=sp, out=out64)
+            e1.record(stream)
+            e1.synchronize()
+            t64.append(e0.elapsed_time(e1))
+        s64 = p64.stats()
+        same = all(bool(torch.equal(out[k], out64[k])) for k in ("structure", "alloy", "correspondence"))
+        fp64_form = {"value": f.n / (statistics.median(t64) * 1e-3), "unit": UNIT, "ms_median": statistics.median(t64),
+                     "steps": len(t64), "form": "every candidate and the winner's outputs in FP64, one frame per launch",
+                     "structure_alloy_correspondence_equal_to_fp32_path": same,
+                     "rmsd_max_abs_diff_vs_fp32_path": float((out["rmsd"] - out64["rmsd"]).abs().nan_to_num(0.0).max())}
+        p64.close()
     if rank != 0:
         ptm.close()
         return
@@ -300,22 +389,30 @@ def run_gpu(args, world, rank, local, pg):
     peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     peaks_file = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm_peak = json.load(open(peaks_file)).get("hbm_gbs") if os.path.exists(peaks_file) else None
+    from paper_1603_05143_gb300 import measure_fma_peak
+    fma = {"fp32_tflops": measure_fma_peak("fp32", local) / 1e12, "fp64_tflops": measure_fma_peak("fp64", local) / 1e12}
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": measured_traffic(), "kernel": "k_atoms", "kernel_ms": kms,
-            "peak_note": "FP32 peak derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
+            "traffic": measured_traffic() if args.workload == WORKLOAD else None, "kernel": "k_atoms",
+            "kernel_ms": kms, "peak_note": "FP32 peak derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
+            "fma_measured": fma, "frac_of_measured_fma": achieved / fma["fp32_tflops"],
             "hbm_achieved_gbs": f.n * BYTES_PER_ATOM / (kms * 1e-3) / 1e9, "hbm_peak_gbs": hbm_peak}
-    cpu = None
+    cpu, errors = None, None
     if not args.no_cpu_baseline and world == 1:
-        r, m, dt, th = oracle_rate(f, species, args.cpu_seconds)
+        r, m, dt, th, atoms, ref = oracle_rate(f, species, args.cpu_seconds, outputs=True)
+        r1, m1, dt1, _ = oracle_rate(f, species, min(5.0, args.cpu_seconds / 3), threads=1, seed=8)
         cpu = {"value": r, "unit": UNIT, "cores": th, "kind": "oracle",
-               "sample": f"{m} uniformly sampled atoms of the same frame in {dt:.1f} s"}
+               "sample": f"{m} uniformly sampled atoms of the same frame in {dt:.1f} s",
+               "single_thread": {"value": r1, "sample": f"{m1} atoms in {dt1:.1f} s"}}
+        gout = {k: v.cpu().numpy() for k, v in out.items()}
+        errors = errors_vs_oracle(gout, atoms, ref)
     q = np.percentile(times, [50, 99])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_dict(f, {"parallelism": f"replicas{world}"}),
-            "latency_ms": {"p50": float(q[0]), "p99": float(q[1])},
+            "config": config_dict(cfg, {"parallelism": f"replicas{world}"}),
+            "latency_ms": {"p50": float(q[0]), "p99": float(q[1]), "best": float(min(times))},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "errors_vs_oracle": errors, "fp64_form": fp64_form,
             "gpu_launches": 6 * args.steps,
             "fallbacks": {k: s0[k] for k in ("sos", "qcp_fp64", "tie_fp64", "knn_wide", "knn_fail", "internal")},
             "matched": s0["matched"], "candidates_per_atom": s0["candidates"] / s0["atoms"]}
@@ -386,6 +483,130 @@ def run_batch(args, world, rank, local, pg):
     ptm.close()
 
 
+def _drive(srv, pool, hpos, hsp, outs, times, idx, timeout_s=600.0):
+    """Submit request i at times[i] (seconds from start) and collect the
+    server's own submit / launch / completion stamps for every frame."""
+    import queue
+    import threading
+    q = queue.Queue()
+    rec = [None] * len(times)
+    err = []
+
+    def reaper():
+        for _ in range(len(times)):
+            i, t = q.get()
+            try:
+                srv.wait(t, timeout_ms=int(timeout_s * 1e3))
+                rec[i] = srv.info(t)
+                srv.release(t)
+            except Exception as e:          # recorded, raised after the stream
+                err.append(repr(e))
+
+    th = threading.Thread(target=reaper, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    for i, (ti, k) in enumerate(zip(times, idx)):
+        dt = t0 + ti - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        f = pool[k]
+        q.put((i, srv.submit(hpos[k], f.cell, f.pbc, species=hsp[k], out=outs[k])))
+    th.join(timeout_s)
+    if err or any(r is None for r in rec):
+        raise RuntimeError(f"serving stream failed: {err[:3]}")
+    atoms = sum(pool[k].n for k in idx)
+    span = max(r["done"] for r in rec) - min(r["submit"] for r in rec)
+    lat = np.array([r["done"] - r["submit"] for r in rec]) * 1e3
+    return {"frames": len(times), "atoms": int(atoms), "achieved_atoms_per_s": atoms / span,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "batches": len({r["batch"] for r in rec})}
+
+
+def run_serve(args, world, rank, local, pg):
+    """A Poisson stream of mixed-phase frames (log-uniform sizes 1e4..1.6e7
+    atoms, strain up to 5 %) held in pinned host memory, classified through
+    the continuous-batching server under an HBM budget of half the free device
+    memory.  Capacity is the closed-loop rate (all requests queued at once);
+    the stream is then offered at 0.5, 0.8 and 0.95 of it.  The comparison is
+    FP64 form, one frame per ptm_classify_frame_host call, fed the
+    0.8-load arrivals in order (its latency counts from each arrival)."""
+    import torch
+    from paper_1603_05143_gb300 import PTM, Server, build, inputs as I
+    from paper_1603_05143_gb300.binding import allocate_outputs_host
+    build.build()
+    torch.cuda.set_device(local)
+    t_gen = time.perf_counter()
+    pool = I.config_serve_pool()
+    gen_s = time.perf_counter() - t_gen
+
+    def pin(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    hpos = [pin(f.positions) for f in pool]
+    hsp = [pin(f.species) for f in pool]
+    outs = [allocate_outputs_host(f.n, pinned=True) for f in pool]
+    ptm = PTM(local)
+    tuning = None                 # library defaults: the stream's batches change from launch to launch
+    srv = Server(ptm, tuning=tuning)
+    rng = I.rng_for(2024)
+    mean_atoms = float(np.mean([f.n for f in pool]))
+    n_req = args.serve_requests
+    with ClockSampler(local) as clk:
+        # warm-up: every pool frame once, queued together
+        _drive(srv, pool, hpos, hsp, outs, np.zeros(len(pool)), np.arange(len(pool)))
+        cap_idx = rng.integers(len(pool), size=max(64, n_req // 4))
+        cap = _drive(srv, pool, hpos, hsp, outs, np.zeros(len(cap_idx)), cap_idx)
+        capacity = cap["achieved_atoms_per_s"]
+        loads = []
+        for load in (0.5, 0.8, 0.95):
+            rate_hz = load * capacity / mean_atoms
+            times, idx = I.poisson_arrivals(rng, n_req, rate_hz, len(pool))
+            r = _drive(srv, pool, hpos, hsp, outs, times, idx)
+            r.update(offered_load=load, offered_atoms_per_s=load * capacity)
+            loads.append(r)
+            if load == 0.8:
+                base_req = (times[: max(32, n_req // 4)], idx[: max(32, n_req // 4)])
+    srv.close()
+    # the one-frame-per-launch FP64 form, fed the same arrivals (0.8 load) in order
+    p64 = PTM(local, precision="fp64")
+    for k in range(len(pool)):
+        p64.classify_host(hpos[k], pool[k].cell, pool[k].pbc, species=hsp[k], out=outs[k])
+    lat, t0 = [], time.perf_counter()
+    b_atoms = 0
+    for ti, k in zip(*base_req):
+        dt = t0 + ti - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        f = pool[k]
+        p64.classify_host(hpos[k], f.cell, f.pbc, species=hsp[k], out=outs[k])
+        lat.append((time.perf_counter() - t0 - ti) * 1e3)
+        b_atoms += f.n
+    b_span = time.perf_counter() - t0
+    p64.close()
+    lat = np.array(lat)
+    base = {"frames": len(lat), "atoms": int(b_atoms), "achieved_atoms_per_s": b_atoms / b_span,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "offered_load": 0.8, "form": "FP64 form (PTM_PREC_FP64), one ptm_classify_frame_host call per frame"}
+    st = ptm.stats()
+    ptm.close()
+    if rank == 0:
+        sizes = [f.n for f in pool]
+        line = {"metric": METRIC, "value": world * capacity, "unit": UNIT, "n_gpus": world,
+                "steps": n_req, "warmup": len(pool), "ms_per_step": loads[-1]["mean_ms"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": "serve-mixed-phase-1e4-1.6e7", "pool_frames": len(pool),
+                           "min_frame": min(sizes), "max_frame": max(sizes), "mean_frame": mean_atoms,
+                           "strain_max": 0.05, "sigma_A": 0.20, "hbm_budget": "half the free device memory",
+                           "io": "host pinned positions/species in, all outputs out, per frame",
+                           "l2": "inputs larger than L2", "pool_gen_s": round(gen_s, 1), "tuning": tuning},
+                "serving": {"capacity": cap, "loads": loads, "one_frame_per_launch": base},
+                "e2e": {"value": world * capacity, "unit": UNIT, "h2d_bytes_per_step": int(mean_atoms * 13),
+                        "d2h_bytes_per_step": int(mean_atoms * 122)},
+                "clocks": clk.summary(),
+                "fallbacks": {k: st[k] for k in ("sos", "qcp_fp64", "tie_fp64", "knn_wide", "knn_fail", "internal")}}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local, pg = dist_setup(args)
@@ -393,6 +614,8 @@ def main():
         run_reference(args, world, rank, pg)
     elif args.mode == "batch":
         run_batch(args, world, rank, local, pg)
+    elif args.mode == "serve":
+        run_serve(args, world, rank, local, pg)
     else:
         run_gpu(args, world, rank, local, pg)
     if pg:

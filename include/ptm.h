@@ -56,9 +56,20 @@ enum { PTM_ALLOY_NONE = 0, PTM_ALLOY_PURE = 1, PTM_ALLOY_L10 = 2, PTM_ALLOY_L12_
 /* Position element types. */
 enum { PTM_F32 = 0, PTM_F64 = 1 };
 
+/* Arithmetic of the metric steps (QCP, selection, outputs).  The exact hull
+   predicates, canonical codes and lookup are the same in both. */
+enum {
+  PTM_PREC_FP32 = 0,         /* FP32, with FP64 where stability needs it (the product path) */
+  PTM_PREC_FP64 = 1          /* every candidate and the winner's outputs in FP64: the
+                                one-frame-per-launch comparison form; ptm_classify_frame
+                                and ptm_classify_frame_host only (batches and servers
+                                always use PTM_PREC_FP32) */
+};
+
 typedef struct {
   int device;                /* CUDA device ordinal */
   size_t hbm_budget_bytes;   /* serving admission budget; 0 = half the free memory at create */
+  int precision;             /* PTM_PREC_FP32 (0) or PTM_PREC_FP64 */
 } ptm_options;
 
 /* One frame.  Problem statement of Algorithm 1: positions of every atom, the
@@ -193,8 +204,8 @@ ptm_status ptm_autotune_batch(ptm_context *ctx, int n_frames, const ptm_frame *f
    buffers, ideally page-locked) wait in a FIFO and are admitted when their
    device bytes (inputs, outputs and workspace, about 300 B per atom) fit the
    HBM budget next to the frames already on the device.  Whenever a stream is
-   free, every admitted frame not yet launched (up to max_batch_frames) forms
-   one batch: copy in, one persistent launch, copy out.  Frames arriving while
+   free, the admitted frames not yet launched (up to max_batch_frames and
+   max_batch_atoms, in arrival order) form one batch: copy in, one persistent launch, copy out.  Frames arriving while
    batches run join the next batch as memory and streams free up, and batches
    on different streams overlap on the device (continuous batching).  Device
    memory is pooled and reused; nothing is freed while the server runs.  Each
@@ -206,6 +217,8 @@ typedef struct {
   int max_batch_frames;      /* frames per launch; 0 = 64 */
   int streams;               /* batches in flight; 0 = 2, at most 8 */
   ptm_tuning tuning;         /* zeros = defaults */
+  int64_t max_batch_atoms;   /* atoms per launch (a larger single frame runs alone);
+                                0 = 4,194,304 */
 } ptm_server_options;
 
 ptm_status ptm_server_create(ptm_context *ctx, const ptm_server_options *options, ptm_server **out);
@@ -254,6 +267,16 @@ ptm_status ptm_server_destroy(ptm_server *server);
    stream.  Returns PTM_ERR_INVALID_ARG for frames above the limit (or bad
    arguments) before enqueueing anything, PTM_ERR_CUDA if a launch fails. */
 ptm_status ptm_classify_frame_noalloc(const ptm_frame *frame, const ptm_outputs *out, void *stream);
+
+/* Measured FMA throughput of the current device, for the ALU roofline of the
+   per-atom kernel (the paper has no counterpart).  kind 0 = FP32, 1 = FP64.
+   Launches a kernel of independent FMA chains that fills every SM, on
+   `stream` (NULL = legacy default stream), times about 50 ms of it with CUDA
+   events (best of three) and stores flop/s (two per FMA) in *flops_per_s.
+   Allocates and frees a small device buffer; synchronises `stream`.
+   PTM_ERR_INVALID_ARG for another kind or a NULL result pointer,
+   PTM_ERR_CUDA if no device is usable. */
+ptm_status ptm_measure_fma_peak(int kind, void *stream, double *flops_per_s);
 
 /* Human-readable name of a status; never NULL. */
 const char *ptm_status_string(ptm_status status);

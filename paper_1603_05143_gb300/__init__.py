@@ -12,8 +12,8 @@ arguments.  PyTorch provides device memory and streams.
 There is no CPU fallback: if the library is missing or no GPU is present the
 calls raise.
 """
-from .binding import (PTM, PTMError, Batch, Server, load, STRUCTURES, ALLOYS, MASK_ALL, MASK_SC, MASK_FCC, MASK_HCP,
+from .binding import (PTM, PTMError, Batch, Server, load, measure_fma_peak, STRUCTURES, ALLOYS, MASK_ALL, MASK_SC, MASK_FCC, MASK_HCP,
                       MASK_ICO, MASK_BCC)
 
-__all__ = ["PTM", "PTMError", "Batch", "Server", "load", "STRUCTURES", "ALLOYS", "MASK_ALL", "MASK_SC", "MASK_FCC",
+__all__ = ["PTM", "PTMError", "Batch", "Server", "load", "measure_fma_peak", "STRUCTURES", "ALLOYS", "MASK_ALL", "MASK_SC", "MASK_FCC",
            "MASK_HCP", "MASK_ICO", "MASK_BCC"]

@@ -19,7 +19,7 @@ OUTPUT_NAMES = ("structure", "alloy", "rmsd", "scale", "quat", "strain", "corres
 
 
 class ptm_options(C.Structure):
-    _fields_ = [("device", C.c_int), ("hbm_budget_bytes", C.c_size_t)]
+    _fields_ = [("device", C.c_int), ("hbm_budget_bytes", C.c_size_t), ("precision", C.c_int)]
 
 
 class ptm_frame(C.Structure):
@@ -44,7 +44,7 @@ class ptm_tuning(C.Structure):
 
 class ptm_server_options(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_batch_frames", C.c_int), ("streams", C.c_int),
-                ("tuning", ptm_tuning)]
+                ("tuning", ptm_tuning), ("max_batch_atoms", C.c_int64)]
 
 
 class PTMError(RuntimeError):
@@ -93,6 +93,8 @@ def load():
         for f in ("ptm_server_create", "ptm_submit", "ptm_poll", "ptm_wait", "ptm_ticket_info", "ptm_release",
                   "ptm_server_destroy"):
             getattr(L, f).restype = C.c_int
+        L.ptm_measure_fma_peak.argtypes = [C.c_int, P, C.POINTER(C.c_double)]
+        L.ptm_measure_fma_peak.restype = C.c_int
         L.ptm_status_string.argtypes = [C.c_int]
         L.ptm_status_string.restype = C.c_char_p
         L.ptm_last_cuda_error.argtypes = [P]
@@ -101,6 +103,20 @@ def load():
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
+
+
+def measure_fma_peak(kind="fp32", device=0, stream=None) -> float:
+    """Measured FMA throughput (flop/s) of a device (``ptm_measure_fma_peak``):
+    kind "fp32" or "fp64"."""
+    import torch
+    k = {"fp32": 0, "fp64": 1}[kind]
+    with torch.cuda.device(device):
+        st = stream if stream is not None else torch.cuda.current_stream(device)
+        v = C.c_double()
+        rc = load().ptm_measure_fma_peak(k, C.c_void_p(st.cuda_stream), C.byref(v))
+    if rc:
+        raise PTMError(rc, "ptm_measure_fma_peak")
+    return v.value
 
 
 def _frame(n, pos_ptr, dtype_code, species_ptr, cell, pbc, mask, rmsd_max) -> ptm_frame:
@@ -122,9 +138,11 @@ def _frame(n, pos_ptr, dtype_code, species_ptr, cell, pbc, mask, rmsd_max) -> pt
 class PTM:
     """A library context on one CUDA device (``ptm_create`` / ``ptm_destroy``)."""
 
-    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, precision: str = "fp32"):
+        """precision "fp32" (the product path) or "fp64" (every candidate and the
+        winner's outputs in FP64: the one-frame-per-launch comparison form)."""
         self.lib = load()
-        opt = ptm_options(device, hbm_budget_bytes)
+        opt = ptm_options(device, hbm_budget_bytes, {"fp32": 0, "fp64": 1}[precision])
         h = C.c_void_p()
         rc = self.lib.ptm_create(C.byref(opt), C.byref(h))
         if rc:
@@ -340,13 +358,13 @@ class Server:
     ``submit`` returns a ticket immediately; the frame's outputs (numpy arrays,
     page-locked when ``pinned``) are filled when the ticket completes."""
 
-    def __init__(self, ptm, hbm_budget_bytes=0, max_batch_frames=0, streams=0, tuning=None):
+    def __init__(self, ptm, hbm_budget_bytes=0, max_batch_frames=0, streams=0, tuning=None, max_batch_atoms=0):
         self.ptm = ptm
         self.lib = ptm.lib
         t = tuning or {}
         opt = ptm_server_options(int(hbm_budget_bytes), int(max_batch_frames), int(streams),
                                  ptm_tuning(float(t.get("cell_factor", 0)), int(t.get("tile_atoms", 0)),
-                                            int(t.get("blocks_per_sm", 0))))
+                                            int(t.get("blocks_per_sm", 0))), int(max_batch_atoms))
         h = C.c_void_p()
         ptm._check(self.lib.ptm_server_create(ptm.h, C.byref(opt), C.byref(h)), "ptm_server_create")
         self.h = h

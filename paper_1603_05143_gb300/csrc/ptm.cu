@@ -22,6 +22,7 @@ using namespace ptm;
 
 struct ptm_context {
   int device = 0;
+  int precision = PTM_PREC_FP32;
   size_t budget = 0;
   std::string last_error;
   // workspace
@@ -194,8 +195,13 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
                                ctx->cell_start, ctx->sorted, ctx->sbin, ctx->wrapv);
   const unsigned ga = (unsigned)((n + PTM_BLOCK - 1) / PTM_BLOCK);
   CK(cudaEventRecord(ctx->ev[1], st));
-  if (f64) k_atoms<true><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
-  else k_atoms<false><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
+  if (ctx->precision == PTM_PREC_FP64) {
+    if (f64) k_atoms<true, true><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
+    else k_atoms<false, true><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
+  } else {
+    if (f64) k_atoms<true><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
+    else k_atoms<false><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
+  }
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev[2], st));
   ctx->last_stream = st;
@@ -226,6 +232,8 @@ ptm_status ptm_create(const ptm_options *opt, ptm_context **out) {
   ptm_context *ctx = new (std::nothrow) ptm_context();
   if (!ctx) return PTM_ERR_OUT_OF_MEMORY;
   ctx->device = opt ? opt->device : 0;
+  ctx->precision = opt ? opt->precision : PTM_PREC_FP32;
+  if (ctx->precision != PTM_PREC_FP32 && ctx->precision != PTM_PREC_FP64) { delete ctx; return PTM_ERR_INVALID_ARG; }
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || ctx->device < 0 || ctx->device >= ndev) {
@@ -245,7 +253,9 @@ ptm_status ptm_create(const ptm_options *opt, ptm_context **out) {
     ctx->budget = (opt && opt->hbm_budget_bytes) ? opt->hbm_budget_bytes : fr / 2;
     const size_t smem = atom_smem_bytes();
     if ((e = cudaFuncSetAttribute(k_atoms<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_atoms<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) {
+        (e = cudaFuncSetAttribute(k_atoms<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_atoms<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_atoms<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) {
       rs = cuda_fail(ctx, e, "cudaFuncSetAttribute");
       break;
     }
@@ -869,3 +879,4 @@ extern "C" ptm_status ptm_classify_frame_noalloc(const ptm_frame *f, const ptm_o
 }
 
 #include "ptm_serve.cuh"
+#include "ptm_peak.cuh"

@@ -607,30 +607,35 @@ __device__ __forceinline__ void quat_matrix(const T q[4], T R[3][3]) {
   R[2][0] = 2 * (x * z - w * y); R[2][1] = 2 * (y * z + w * x); R[2][2] = 1 - 2 * (x * x + y * y);
 }
 
-// Cyclic Jacobi eigen-decomposition of a symmetric 3x3 matrix (FP32).
-__device__ void jacobi3(float a[3][3], float v[3][3]) {
-  for (int i = 0; i < 3; i++) for (int j = 0; j < 3; j++) v[i][j] = (i == j) ? 1.f : 0.f;
-  for (int sweep = 0; sweep < 10; sweep++) {
-    float off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
-    float dg = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
-    if (off <= 1e-16f * dg) break;
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
+
+// Cyclic Jacobi eigen-decomposition of a symmetric 3x3 matrix.
+template <typename T>
+__device__ void jacobi3(T a[3][3], T v[3][3]) {
+  const T tol = sizeof(T) == 4 ? (T)1e-16 : (T)1e-30;
+  for (int i = 0; i < 3; i++) for (int j = 0; j < 3; j++) v[i][j] = (i == j) ? (T)1 : (T)0;
+  for (int sweep = 0; sweep < (sizeof(T) == 4 ? 10 : 20); sweep++) {
+    T off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+    T dg = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+    if (off <= tol * dg) break;
 #pragma unroll
     for (int pq = 0; pq < 3; pq++) {
       int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
-      if (a[p][q] == 0.f) continue;
-      float theta = (a[q][q] - a[p][p]) / (2.f * a[p][q]);
-      float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
-      float c = rsqrtf(t * t + 1.f), s = t * c;
+      if (a[p][q] == (T)0) continue;
+      T theta = (a[q][q] - a[p][p]) / ((T)2 * a[p][q]);
+      T t = (theta >= (T)0 ? (T)1 : (T)-1) / (fabs(theta) + sqrt(theta * theta + (T)1));
+      T c = rsq(t * t + (T)1), s = t * c;
       for (int k = 0; k < 3; k++) {
-        float akp = a[k][p], akq = a[k][q];
+        T akp = a[k][p], akq = a[k][q];
         a[k][p] = c * akp - s * akq; a[k][q] = s * akp + c * akq;
       }
       for (int k = 0; k < 3; k++) {
-        float apk = a[p][k], aqk = a[q][k];
+        T apk = a[p][k], aqk = a[q][k];
         a[p][k] = c * apk - s * aqk; a[q][k] = s * apk + c * aqk;
       }
       for (int k = 0; k < 3; k++) {
-        float vkp = v[k][p], vkq = v[k][q];
+        T vkp = v[k][p], vkq = v[k][q];
         v[k][p] = c * vkp - s * vkq; v[k][q] = s * vkp + c * vkq;
       }
     }

@@ -304,16 +304,19 @@ __device__ __forceinline__ float cand_r2(const float (&Sm)[3][3], float Gv, floa
 // Hull of the first K neighbours is complete and contains the centre: canonical
 // code, lookup and QCP of every admissible correspondence (Algorithm 1, inner
 // loops).
+// In the FP64 form (P64) only the labelling and table entry are kept; the
+// candidates are scored later, all in FP64.
+template <bool P64>
 __device__ void snapshot(int K, const Scratch &sm, const FrameDesc &d, const float4 *tplw, int nf, Best &bst) {
   if (nf != 2 * K - 4) return;                    // a neighbour is not a hull vertex
   uint64_t lab = 0, h = 0;
   if (!canonical(sm, K, nf, lab, h, d)) return;
   int e = lookup(sm, K, h);
   if (e < 0) return;
-  const int si = snap_index(K);
   if (K == 6) { bst.lam6 = lab; bst.ent6 = e; }
   else if (K == 12) { bst.lam12 = lab; bst.ent12 = e; }
   else { bst.lam14 = lab; bst.ent14 = e; }
+  if constexpr (P64) { bst.K = K; return; }
   float mx, my, mz, Gv;
   data_moments(K, sm, mx, my, mz, Gv);
   const int first = __ldg(&ptm_tbl[e].first), cnt = __ldg(&ptm_tbl[e].count);
@@ -360,41 +363,16 @@ __device__ __forceinline__ uint64_t corr_of(int K, uint64_t lab, uint64_t cand) 
 }
 
 
-// Rare path: the best FP32 candidates lie within PTM_BAND.  Every candidate is
-// re-scored in FP64 from neighbour vectors recomputed in FP64 from the input
-// positions; ties within PTM_TIE go to the earlier template, then to the smaller
-// canonical correspondence (reading R13).
-template <bool F64>
-__device__ __noinline__ int rerank_fp64(const FrameDesc &d, int s, const Best bst, int bx, int by, int bz,
-                                        int wix, int wiy, int wiz, bool wrapped) {
-  typedef typename RT<F64>::T T;
-  T xi, yi, zi;
-  int idi;
-  load_atom<F64>(d, s, xi, yi, zi, idi);
-  T Ld2[PTM_KNN];
-  int Lid[PTM_KNN], Ljs[PTM_KNN], Limg[PTM_KNN];
-  int cnt = knn<F64>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, Ld2, Lid, Ljs, Limg);
-  if (cnt < 0) return -1;
-  double ex[PTM_KNN], ey[PTM_KNN], ez[PTM_KNN];
-  for (int t = 0; t < cnt; t++) {
-    T xj, yj, zj;
-    int idj;
-    load_atom<F64>(d, Ljs[t], xj, yj, zj, idj);
-    int a, b, c;
-    img_unpack(Limg[t], a, b, c);
-    double sx, sy, sz;
-    shift_f64(d, a, b, c, sx, sy, sz);
-    ex[t] = ((double)xj - (double)xi) + sx;
-    ey[t] = ((double)yj - (double)yi) + sy;
-    ez[t] = ((double)zj - (double)zi) + sz;
-  }
+// FP64 selection over every candidate of the matched snapshots (Algorithm 1,
+// inner loops), from FP64 neighbour vectors: ties within PTM_TIE go to the
+// earlier template, then to the smaller canonical correspondence (reading R13).
+// Returns (K << 16) | candidate index, or -1; *scored counts the candidates.
+__device__ __noinline__ int select_fp64(const FrameDesc &d, const Best &bst, const double (&ex)[PTM_KNN],
+                                        const double (&ey)[PTM_KNN], const double (&ez)[PTM_KNN], int *scored) {
   double best_r2 = INFINITY;
-  int bK = -1, bc = -1, bS = 99;
+  int bK = -1, bc = -1, bS = 99, ns = 0;
   uint64_t bcp = ~0ull;
-  double r2s[3 * 64];
-  int nr = 0;
-  (void)nr;
-  // pass 1: FP64 score of every candidate
+  // pass 0 finds the minimum, pass 1 picks among the candidates tied with it
   for (int pass = 0; pass < 2; pass++) {
     for (int si = 0; si < 3; si++) {
       const int K = si == 0 ? 6 : (si == 1 ? 12 : 14);
@@ -410,6 +388,7 @@ __device__ __noinline__ int rerank_fp64(const FrameDesc &d, int s, const Best bs
         uint64_t cand = ptm_cand[ci];
         int S = (int)(cand >> 60) & 7;
         if (!(d.mask >> S & 1)) continue;
+        if (pass == 0) ns++;
         double Sm[3][3] = {{0}}, Gw = 0;
         for (int j = 0; j < K; j++) {
           int slot = nib(cand, nib(lab, j) - 1);
@@ -433,11 +412,78 @@ __device__ __noinline__ int rerank_fp64(const FrameDesc &d, int s, const Best bs
       }
     }
   }
-  (void)r2s;
+  if (scored) *scored = ns;
   return bK > 0 ? (bK << 16) | bc : -1;
 }
 
+// FP64 neighbour vector of neighbour (sorted slot js, image img) of an atom at
+// (xi, yi, zi): (x_j - x_i) + n.H with the shift exactly as the contract rounds it.
+template <bool F64>
+__device__ __forceinline__ void vec_fp64(const FrameDesc &d, typename RT<F64>::T xi, typename RT<F64>::T yi,
+                                         typename RT<F64>::T zi, int js, int img, double &x, double &y, double &z) {
+  typedef typename RT<F64>::T T;
+  T xj, yj, zj;
+  int idj;
+  load_atom<F64>(d, js, xj, yj, zj, idj);
+  int a, b, c;
+  img_unpack(img, a, b, c);
+  double sx, sy, sz;
+  shift_f64(d, a, b, c, sx, sy, sz);
+  x = ((double)xj - (double)xi) + sx;
+  y = ((double)yj - (double)yi) + sy;
+  z = ((double)zj - (double)zi) + sz;
+}
+
+// Rare path: the best FP32 candidates lie within PTM_BAND.  Every candidate is
+// re-scored in FP64 from neighbour vectors recomputed in FP64 from the input
+// positions.
+template <bool F64>
+__device__ __noinline__ int rerank_fp64(const FrameDesc &d, int s, const Best bst, int bx, int by, int bz,
+                                        int wix, int wiy, int wiz, bool wrapped) {
+  typedef typename RT<F64>::T T;
+  T xi, yi, zi;
+  int idi;
+  load_atom<F64>(d, s, xi, yi, zi, idi);
+  T Ld2[PTM_KNN];
+  int Lid[PTM_KNN], Ljs[PTM_KNN], Limg[PTM_KNN];
+  int cnt = knn<F64>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, Ld2, Lid, Ljs, Limg);
+  if (cnt < 0) return -1;
+  double ex[PTM_KNN], ey[PTM_KNN], ez[PTM_KNN];
+  for (int t = 0; t < cnt; t++) vec_fp64<F64>(d, xi, yi, zi, Ljs[t], Limg[t], ex[t], ey[t], ez[t]);
+  return select_fp64(d, bst, ex, ey, ez, nullptr);
+}
+
 // ------------------------------------------------------------ finalisation
+// Binary alloy label (Sec. 6, Table 3) of atom a matched to template S with
+// canonical correspondence cp (nibble 15 - slot = neighbour rank + 1).
+__device__ __forceinline__ int8_t alloy_label(const FrameDesc &d, const Scratch &sm, int S, uint64_t cp, int64_t a) {
+  int8_t lab8 = PTM_ALLOY_NONE;
+  if (d.species && (S == 1 || S == 4)) {
+    const int8_t c = __ldg(d.species + a);
+    auto same = [&](int sl) { return __ldg(d.species + sm.NID(nib(cp, 15 - sl) - 1)) == c; };
+    if (S == 1) {          // FCC: slots 1-4 in z = 0, 5-8 in y = 0, 9-12 in x = 0
+      int sp = 0, op = 0;
+      for (int p = 0; p < 3; p++) {
+        int n = 0;
+        for (int sl = 1 + 4 * p; sl <= 4 + 4 * p; sl++) n += same(sl);
+        sp += n == 4;
+        op += n == 0;
+      }
+      if (sp == 3) lab8 = PTM_ALLOY_PURE;
+      else if (sp == 1 && op == 2) lab8 = PTM_ALLOY_L10;
+      else if (sp == 2 && op == 1) lab8 = PTM_ALLOY_L12_MAJ;
+      else if (op == 3) lab8 = PTM_ALLOY_L12_MIN;
+    } else {               // BCC: slots 1-8 first shell, 9-14 second shell
+      int in = 0, out = 0;
+      for (int sl = 1; sl <= 8; sl++) in += same(sl);
+      for (int sl = 9; sl <= 14; sl++) out += same(sl);
+      if (in == 8 && out == 6) lab8 = PTM_ALLOY_PURE;
+      else if (in == 0 && out == 6) lab8 = PTM_ALLOY_B2;
+    }
+  }
+  return lab8;
+}
+
 __device__ void finalize(const FrameDesc &d, const Scratch &sm, const float4 *tplw, const Best &bst, int idi) {
   const int K = bst.K;
   const uint64_t lab = bst.lam(K);
@@ -555,34 +601,7 @@ __device__ void finalize(const FrameDesc &d, const Scratch &sm, const float4 *tp
       for (int j = 0; j < 3; j++)
         d.strain[9 * a + 3 * i + j] = X[i][0] * sig[0] * X[j][0] + X[i][1] * sig[1] * X[j][1] + X[i][2] * sig[2] * X[j][2];
   }
-  // binary alloy label (Sec. 6, Table 3)
-  if (d.alloy) {
-    int8_t lab8 = PTM_ALLOY_NONE;
-    if (d.species && (S == 1 || S == 4)) {
-      const int8_t c = __ldg(d.species + a);
-      auto same = [&](int sl) { return __ldg(d.species + sm.NID(nib(cp, 15 - sl) - 1)) == c; };
-      if (S == 1) {          // FCC: slots 1-4 in z = 0, 5-8 in y = 0, 9-12 in x = 0
-        int sp = 0, op = 0;
-        for (int p = 0; p < 3; p++) {
-          int n = 0;
-          for (int sl = 1 + 4 * p; sl <= 4 + 4 * p; sl++) n += same(sl);
-          sp += n == 4;
-          op += n == 0;
-        }
-        if (sp == 3) lab8 = PTM_ALLOY_PURE;
-        else if (sp == 1 && op == 2) lab8 = PTM_ALLOY_L10;
-        else if (sp == 2 && op == 1) lab8 = PTM_ALLOY_L12_MAJ;
-        else if (op == 3) lab8 = PTM_ALLOY_L12_MIN;
-      } else {               // BCC: slots 1-8 first shell, 9-14 second shell
-        int in = 0, out = 0;
-        for (int sl = 1; sl <= 8; sl++) in += same(sl);
-        for (int sl = 9; sl <= 14; sl++) out += same(sl);
-        if (in == 8 && out == 6) lab8 = PTM_ALLOY_PURE;
-        else if (in == 0 && out == 6) lab8 = PTM_ALLOY_B2;
-      }
-    }
-    d.alloy[a] = lab8;
-  }
+  if (d.alloy) d.alloy[a] = alloy_label(d, sm, S, cp, a);
 }
 
 __device__ void write_unmatched(const FrameDesc &d, int64_t a) {
@@ -595,10 +614,105 @@ __device__ void write_unmatched(const FrameDesc &d, int64_t a) {
   if (d.corr) for (int i = 0; i < 15; i++) d.corr[15 * a + i] = -1;
 }
 
+// Outputs of the winner in the FP64 form: the same steps as finalize, every
+// metric quantity in FP64 from the FP64 neighbour vectors (results rounded to
+// FP32 only when stored).
+__device__ __noinline__ void finalize_fp64(const FrameDesc &d, const Scratch &sm, int K, uint64_t lab, int ci,
+                                           const double (&ex)[PTM_KNN], const double (&ey)[PTM_KNN],
+                                           const double (&ez)[PTM_KNN], int idi) {
+  const uint64_t cand = ptm_cand[ci];
+  const int S = (int)(cand >> 60) & 7;
+  double m[3] = {0, 0, 0}, g = 0;
+  for (int j = 0; j < K; j++) { m[0] += ex[j]; m[1] += ey[j]; m[2] += ez[j]; g += ex[j] * ex[j] + ey[j] * ey[j] + ez[j] * ez[j]; }
+  for (int c = 0; c < 3; c++) m[c] /= (K + 1);
+  const double Gv = g - (K + 1) * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+  double Sm[3][3] = {{0}}, Gw = 0;
+  for (int j = 0; j < K; j++) {
+    const double *w = ptm_tpl64[S][nib(cand, nib(lab, j) - 1)];
+    Sm[0][0] += w[0] * ex[j]; Sm[0][1] += w[0] * ey[j]; Sm[0][2] += w[0] * ez[j];
+    Sm[1][0] += w[1] * ex[j]; Sm[1][1] += w[1] * ey[j]; Sm[1][2] += w[1] * ez[j];
+    Sm[2][0] += w[2] * ex[j]; Sm[2][1] += w[2] * ey[j]; Sm[2][2] += w[2] * ez[j];
+  }
+  for (int slot = 0; slot <= K; slot++)
+    Gw += ptm_tpl64[S][slot][0] * ptm_tpl64[S][slot][0] + ptm_tpl64[S][slot][1] * ptm_tpl64[S][slot][1] +
+          ptm_tpl64[S][slot][2] * ptm_tpl64[S][slot][2];
+  Qcp<double> o;
+  qcp_solve<double>(Sm, Gv, Gw, o);
+  double q[4], R[3][3];
+  qcp_quat<double>(o.K, o.lam, q);
+  const double s = o.lam / Gv;
+  quat_matrix<double>(q, R);
+  // explicit residual of Eq. 3; the centre pairs with template slot 0 (origin)
+  double r2 = s * s * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+  double lsum = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+  uint64_t corr = 0;
+  for (int j = 0; j < K; j++) {
+    const int slot = nib(cand, nib(lab, j) - 1);
+    const double *w = ptm_tpl64[S][slot];
+    const double vx = ex[j] - m[0], vy = ey[j] - m[1], vz = ez[j] - m[2];
+    const double rx = R[0][0] * w[0] + R[0][1] * w[1] + R[0][2] * w[2];
+    const double ry = R[1][0] * w[0] + R[1][1] * w[1] + R[1][2] * w[2];
+    const double rz = R[2][0] * w[0] + R[2][1] * w[1] + R[2][2] * w[2];
+    const double dx = s * vx - rx, dy = s * vy - ry, dz = s * vz - rz;
+    r2 += dx * dx + dy * dy + dz * dz;
+    lsum += sqrt(vx * vx + vy * vy + vz * vz);
+    corr |= (uint64_t)(j + 1) << (4 * (15 - slot));
+  }
+  const double rmsd = sqrt(r2 / (K + 1));
+  const int64_t a = idi;
+  if (!(rmsd <= d.rmsd_max)) { write_unmatched(d, a); return; }
+  count(d, C_MATCHED);
+  const uint64_t cp = canonical_corr(S, K, corr);
+  if (d.structure) d.structure[a] = (int8_t)(S + 1);
+  if (d.rmsd) d.rmsd[a] = (float)rmsd;
+  if (d.scale) d.scale[a] = (float)s;
+  if (d.corr) {
+    d.corr[15 * a] = idi;
+    for (int sl = 1; sl < 15; sl++) d.corr[15 * a + sl] = sl <= K ? sm.NID(nib(cp, 15 - sl) - 1) : -1;
+  }
+  if (d.quat) {
+    double bw = -1.0, bq[4] = {1.0, 0.0, 0.0, 0.0};
+    for (int gi = ptm_group_off[S]; gi < ptm_group_off[S + 1]; gi++) {
+      const float *gq = ptm_group_quat[gi];
+      const double o0 = q[0] * gq[0] - q[1] * gq[1] - q[2] * gq[2] - q[3] * gq[3];
+      if (fabs(o0) > bw) {
+        bw = fabs(o0);
+        bq[0] = o0;
+        bq[1] = q[0] * gq[1] + q[1] * gq[0] + q[2] * gq[3] - q[3] * gq[2];
+        bq[2] = q[0] * gq[2] - q[1] * gq[3] + q[2] * gq[0] + q[3] * gq[1];
+        bq[3] = q[0] * gq[3] + q[1] * gq[2] - q[2] * gq[1] + q[3] * gq[0];
+      }
+    }
+    const double sg = bq[0] < 0.0 ? -1.0 : 1.0;
+    for (int i = 0; i < 4; i++) d.quat[4 * a + i] = (float)(sg * bq[i]);
+  }
+  if (d.strain) {
+    const double f = 3.0 / (Gw * (lsum / (K + 1)));
+    double A[3][3], AA[3][3], X[3][3];
+    for (int i = 0; i < 3; i++) for (int j = 0; j < 3; j++) A[i][j] = f * Sm[j][i];
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++) AA[i][j] = A[i][0] * A[j][0] + A[i][1] * A[j][1] + A[i][2] * A[j][2];
+    jacobi3(AA, X);
+    double sg[3] = {sqrt(fmax(AA[0][0], 0.0)), sqrt(fmax(AA[1][1], 0.0)), sqrt(fmax(AA[2][2], 0.0))};
+    if (det3<double>(A) < 0.0) {
+      const int k = (sg[0] <= sg[1] && sg[0] <= sg[2]) ? 0 : (sg[1] <= sg[2] ? 1 : 2);
+      sg[k] = -sg[k];
+    }
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++)
+        d.strain[9 * a + 3 * i + j] = (float)(X[i][0] * sg[0] * X[j][0] + X[i][1] * sg[1] * X[j][1] + X[i][2] * sg[2] * X[j][2]);
+  }
+  if (d.alloy) d.alloy[a] = alloy_label(d, sm, S, cp, a);
+}
+
 // ------------------------------------------------------------ one atom
-template <bool F64>
+// P64 selects the FP64 form: the same exact predicates, canonical codes and
+// lookup, then every candidate scored and the winner's outputs computed in FP64
+// (the one-frame-per-launch comparison form).
+template <bool F64, bool P64 = false>
 __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, const float4 *tplw) {
   typedef typename RT<F64>::T T;
+  double ex[P64 ? PTM_KNN : 1], ey[P64 ? PTM_KNN : 1], ez[P64 ? PTM_KNN : 1];
   T xi, yi, zi;
   int idi;
   load_atom<F64>(d, s, xi, yi, zi, idi);
@@ -638,6 +752,13 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
       contract_shift<F64>(d, a0, a1, a2, sx, sy, sz);
       T cx = contract_dr(xj, xi, sx), cy = contract_dr(yj, yi, sy), cz = contract_dr(zj, zi, sz);
       emax = fmax(emax, fmax(fabs(cx), fmax(fabs(cy), fabs(cz))));
+      if constexpr (P64) {
+        double hx, hy, hz;
+        shift_f64(d, a0, a1, a2, hx, hy, hz);
+        ex[t] = ((double)xj - (double)xi) + hx;
+        ey[t] = ((double)yj - (double)yi) + hy;
+        ez[t] = ((double)zj - (double)zi) + hz;
+      }
       // neighbour vectors for the metric steps: the contract values, or for a
       // shifted image an error-free FP32 sum of difference and shift
       if constexpr (F64) {
@@ -700,13 +821,22 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
       uint32_t vis = 0;
       if (p < kmax) vis = hull_visibility(sm, nf, p, want, centre_in, d);
       else if (want) centre_in = hull_centre_inside(sm, nf);
-      if (want && centre_in) snapshot(p, sm, d, tplw, nf, bst);
+      if (want && centre_in) snapshot<P64>(p, sm, d, tplw, nf, bst);
       if (p == kmax || !vis) break;              // done, or p lies inside the hull
       nf = hull_apply(sm, nf, vis, p, d);
       if (nf < 0) break;
     }
   }
   if (bst.K < 0) { write_unmatched(d, idi); return; }
+  if constexpr (P64) {
+    int ns = 0;
+    const int w = select_fp64(d, bst, ex, ey, ez, &ns);
+    if (ns) { count(d, C_CAND, ns); }
+    if (w < 0) { write_unmatched(d, idi); return; }
+    const int K = w >> 16;
+    finalize_fp64(d, sm, K, bst.lam(K), w & 0xffff, ex, ey, ez, idi);
+    return;
+  }
   if (bst.b2 <= bst.b1 + PTM_BAND) {
     count(d, C_TIE64);
     const int w = rerank_fp64<F64>(d, s, bst, bx, by, bz, wix, wiy, wiz, wrapped);
@@ -924,7 +1054,7 @@ constexpr size_t atom_smem_bytes() {
 
 // The frame descriptor travels by value in the kernel parameters, so back-to-back
 // asynchronous calls never share a staging buffer.
-template <bool F64>
+template <bool F64, bool P64 = false>
 __global__ void __launch_bounds__(PTM_BLOCK, 5) k_atoms(const __grid_constant__ FrameDesc d) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t *th = (uint64_t *)smem;
@@ -945,7 +1075,7 @@ __global__ void __launch_bounds__(PTM_BLOCK, 5) k_atoms(const __grid_constant__ 
   sm.t = threadIdx.x;
   int64_t s = (int64_t)blockIdx.x * PTM_BLOCK + threadIdx.x;
   if (s >= d.n) return;
-  classify_atom<F64>(d, (int)s, sm, tplw);
+  classify_atom<F64, P64>(d, (int)s, sm, tplw);
 }
 
 // Persistent classification of a batch: every block pulls tiles of PTM_BLOCK

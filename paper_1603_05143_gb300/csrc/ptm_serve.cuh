@@ -4,7 +4,8 @@
 // One scheduler thread per server owns every CUDA call of the server.  Frames
 // wait in a FIFO; a frame is admitted when its device bytes fit the HBM budget
 // beside the frames already on the device.  Whenever a stream slot is free, all
-// admitted frames not yet launched (up to max_batch_frames) become one batch:
+// admitted frames not yet launched (up to max_batch_frames, and up to
+// max_batch_atoms atoms unless a single frame is larger) become one batch:
 // inputs are copied in, one persistent launch classifies them, outputs are
 // copied back, and an event marks completion.  Frames that arrive while batches
 // run join the next batch as soon as memory and a slot free up, and the slots'
@@ -84,6 +85,7 @@ struct ptm_server {
   ptm_context *ctx = nullptr;
   size_t budget = 0, in_use = 0;
   int max_batch = 64, nslots = 2;
+  int64_t max_batch_atoms = 4 << 20;
   ptm_tuning tuning{};
   std::vector<cudaStream_t> streams;
   std::vector<bool> slot_busy;
@@ -240,6 +242,7 @@ void serve_loop(ptm_server *S) {
     int slot = -1;
     for (int i = 0; i < S->nslots; i++) if (!S->slot_busy[i]) { slot = i; break; }
     std::vector<Request *> take;
+    int64_t batch_atoms = 0;
     if (slot >= 0) {
       while (!S->queue.empty() && (int)take.size() < S->max_batch) {
         Request *r = S->queue.front();
@@ -253,6 +256,8 @@ void serve_loop(ptm_server *S) {
         }
         if (S->in_use + r->bytes > S->budget) break;
         if (!take.empty() && r->frame.pos_dtype != take[0]->frame.pos_dtype) break;
+        if (!take.empty() && batch_atoms + r->frame.n_atoms > S->max_batch_atoms) break;
+        batch_atoms += r->frame.n_atoms;
         S->queue.pop_front();
         S->in_use += r->bytes;
         take.push_back(r);
@@ -305,6 +310,7 @@ extern "C" ptm_status ptm_server_create(ptm_context *ctx, const ptm_server_optio
   S->budget = (opt && opt->hbm_budget_bytes) ? opt->hbm_budget_bytes : ctx->budget;
   if (opt && opt->max_batch_frames > 0) S->max_batch = opt->max_batch_frames;
   if (opt && opt->streams > 0) S->nslots = std::min(opt->streams, 8);
+  if (opt && opt->max_batch_atoms > 0) S->max_batch_atoms = opt->max_batch_atoms;
   if (opt) S->tuning = opt->tuning;
   S->staging_bytes = (sizeof(FrameDesc) + sizeof(BinParams) + sizeof(int64_t)) * (size_t)S->max_batch;
   cudaError_t e = cudaSuccess;

@@ -359,34 +359,94 @@ def _rsa_liquid(rng, xr, ly, n_target, dmin, ico_fraction, max_rounds=60, batch=
     return out
 
 
+_BATCH_KINDS = [("fcc", A_FCC_CU), ("hcp", A_HCP), ("bcc", A_BCC_FE), ("l10", A_L12),
+                ("l12", A_L12), ("sc", A_SC)]
+
+
+def _lattice_frame(rng, kind, a, target, fi, sigma_max, strain_max):
+    """A random rotation, symmetric affine strain (|E_ij| <= strain_max) and
+    noise (uniform in [0, sigma_max], zero for one frame in ten) applied to a
+    lattice of about `target` atoms."""
+    cell0, basis, _ = unit_cell(kind, a)
+    per = len(basis)
+    side = max(3, int(round((target / per) ** (1 / 3))))
+    reps = np.array([side, side, side])
+    if kind == "hcp":   # orthohexagonal cell is elongated in y
+        reps = np.array([side, max(3, int(round(side / math.sqrt(3)))), max(3, int(round(side * 0.61)))])
+    R = random_rotation(rng)
+    E = rng.uniform(-strain_max, strain_max, (3, 3))
+    E = 0.5 * (E + E.T)
+    sig = float(rng.uniform(0.0, sigma_max))
+    if rng.random() < 0.1:
+        sig = 0.0
+    seed_f = int(rng.integers(1 << 31))
+    f = crystal(kind, a, reps, sigma=sig, seed=seed_f, rotation=R, deform=np.eye(3) + E,
+                dtype=np.float32, name=f"{kind}{fi}")
+    f.meta.update({"E": E.tolist(), "R": R.tolist()})
+    return f
+
+
 def config_batch(seed: int = 256, n_frames: int = 256, n_min: float = 1e3, n_max: float = 1e6,
                  sigma_max: float = 0.25, strain_max: float = 0.05):
-    """Uneven frames of random lattices, orientations, noise and affine strain."""
+    """Uneven frames of random lattices, orientations, noise and affine strain;
+    sizes log-uniform in [n_min, n_max]."""
     rng = rng_for(seed)
-    kinds = [("fcc", A_FCC_CU), ("hcp", A_HCP), ("bcc", A_BCC_FE), ("l10", A_L12),
-             ("l12", A_L12), ("sc", A_SC)]
     frames = []
     for fi in range(n_frames):
-        kind, a = kinds[int(rng.integers(len(kinds)))]
+        kind, a = _BATCH_KINDS[int(rng.integers(len(_BATCH_KINDS)))]
         target = math.exp(rng.uniform(math.log(n_min), math.log(n_max)))
-        cell0, basis, _ = unit_cell(kind, a)
-        per = len(basis)
-        side = max(3, int(round((target / per) ** (1 / 3))))
-        reps = np.array([side, side, side])
-        if kind == "hcp":   # orthohexagonal cell is elongated in y
-            reps = np.array([side, max(3, int(round(side / math.sqrt(3)))), max(3, int(round(side * 0.61)))])
+        frames.append(_lattice_frame(rng, kind, a, target, fi, sigma_max, strain_max))
+    return frames
+
+
+def tile_frame(f: Frame, reps) -> Frame:
+    """Periodic repeat of a frame reps[0] x reps[1] x reps[2] times."""
+    reps = np.asarray(reps, int)
+    g = np.stack(np.meshgrid(*[np.arange(r) for r in reps], indexing="ij"), -1).reshape(-1, 3)
+    shift = g @ f.cell
+    pos = (f.positions[None, :, :].astype(np.float64) + shift[:, None, :]).reshape(-1, 3)
+    sp = None if f.species is None else np.tile(f.species, len(g))
+    return Frame(pos.astype(f.positions.dtype), f.cell * reps[:, None], f.pbc, sp, f.name, dict(f.meta, reps=reps.tolist()))
+
+
+_SERVE_TILES = [(1, 1, 1), (2, 1, 1), (2, 2, 1), (3, 2, 1), (2, 2, 2), (3, 2, 2), (5, 3, 1)]
+
+
+def config_serve_pool(seed: int = 4096, n_sizes: int = 16, n_min: float = 1e4, n_max: float = 1.6e7,
+                      strain_max: float = 0.05, tile_atoms: int = 1 << 20):
+    """Frames for a serving workload: mixed-phase frames (bcc / fcc / L1_2 /
+    sc / liquid slabs, sigma 0.20 A) whose sizes are log-spaced over
+    [n_min, n_max], so a frame drawn uniformly from the pool has a log-uniform
+    size.  Frames up to tile_atoms are generated at their size; larger ones
+    are periodic tilings of one tile_atoms frame.  Each then gets a random
+    rotation and a symmetric affine strain with |E_ij| <= strain_max (cell and
+    positions alike, so the frame stays periodic and becomes triclinic)."""
+    rng = rng_for(seed)
+    base = None
+    frames = []
+    for fi, target in enumerate(np.geomspace(n_min, n_max, n_sizes)):
+        if target <= 1.25 * tile_atoms:
+            f = config_mixed_phase(seed=seed + 1 + fi, n_target=int(round(target)))
+        else:
+            if base is None:
+                base = config_mixed_phase(seed=seed, n_target=tile_atoms)
+            reps = min(_SERVE_TILES, key=lambda r: abs(math.log(np.prod(r) * tile_atoms / target)))
+            f = tile_frame(base, reps)
         R = random_rotation(rng)
         E = rng.uniform(-strain_max, strain_max, (3, 3))
         E = 0.5 * (E + E.T)
-        sig = float(rng.uniform(0.0, sigma_max))
-        if rng.random() < 0.1:
-            sig = 0.0
-        seed_f = int(rng.integers(1 << 31))
-        f = crystal(kind, a, reps, sigma=sig, seed=seed_f, rotation=R, deform=np.eye(3) + E,
-                    dtype=np.float32, name=f"{kind}{fi}")
-        f.meta.update({"E": E.tolist(), "R": R.tolist()})
-        frames.append(f)
+        lin = (np.eye(3) + E) @ R
+        pos = wrap_positions(f.positions.astype(np.float64) @ lin.T, f.cell @ lin.T)
+        frames.append(Frame(pos.astype(np.float32), f.cell @ lin.T, f.pbc, f.species, f"mixed{fi}",
+                            dict(f.meta, E=E.tolist(), R=R.tolist())))
     return frames
+
+
+def poisson_arrivals(rng, n: int, rate_hz: float, pool_size: int):
+    """n request times (seconds from 0) of a Poisson process of rate rate_hz,
+    each with a pool index drawn uniformly."""
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, n))
+    return t - t[0], rng.integers(pool_size, size=n)
 
 
 def describe(frame: Frame) -> str:

@@ -46,6 +46,7 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.ptm_destroy(None) == 1
     assert lib.ptm_classify_frame(None, ctypes.byref(ptm_frame()), ctypes.byref(ptm_outputs()), None) == 1
     assert lib.ptm_get_stats(None, None) == 1
+    assert lib.ptm_measure_fma_peak(2, None, None) == 1
 
 
 def test_create_without_device_fails_cleanly(lib):

@@ -181,3 +181,47 @@ def test_repeatable_and_stream_ordered(ptm):
     for o in outs:
         for k in a:
             assert np.array_equal(a[k], o[k].cpu().numpy()), k
+
+
+# --------------------------------------------------------------- FP64 form
+@pytest.fixture(scope="module")
+def ptm64():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1603_05143_gb300 import PTM
+    p = PTM(0, precision="fp64")
+    yield p
+    p.close()
+
+
+@pytest.mark.parametrize("case", ["fcc4000", "l12", "bcc_b2_strained", "hcp", "ico", "polycrystal"])
+def test_fp64_form_matches_oracle(ptm64, case):
+    """The one-frame-per-launch FP64 form meets the same parity bar."""
+    rng = I.rng_for(31)
+    if case == "fcc4000":
+        f = I.config_fcc_small()
+    elif case == "l12":
+        f = I.crystal("l12", I.A_L12, 5, sigma=0.08, seed=4, rotation=I.random_rotation(rng), dtype=np.float32)
+    elif case == "bcc_b2_strained":
+        E = np.eye(3) + np.array([[0.03, 0.01, 0], [0.01, -0.02, 0.02], [0, 0.02, 0.01]])
+        f = I.crystal("b2", I.A_BCC_FE, 6, sigma=0.0, rotation=I.random_rotation(rng), deform=E, dtype=np.float32)
+    elif case == "hcp":
+        f = I.crystal("hcp", I.A_HCP, (6, 4, 4), sigma=0.1, seed=5, dtype=np.float32)
+    elif case == "ico":
+        cl = [I.ico_cluster(2.556, rotation=I.random_rotation(rng), sigma=0.05, seed=i) for i in range(20)]
+        f = I.isolated_clusters(cl, dtype=np.float32)
+    else:
+        f = I.config_polycrystal(n_target=1 << 14)
+    st, g, ref = check(ptm64, f)
+    assert st["matched"] > 0
+
+
+def test_fp64_form_agrees_with_fp32_form(ptm, ptm64):
+    f = I.config_mixed_phase(n_target=1 << 15)
+    a = run_gpu(ptm, f)
+    b = run_gpu(ptm64, f)
+    for k in ("structure", "alloy", "correspondence"):
+        assert np.array_equal(a[k], b[k]), k
+    m = a["structure"] > 0
+    assert np.abs(a["rmsd"][m] - b["rmsd"][m]).max() < 1e-5
