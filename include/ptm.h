@@ -158,7 +158,8 @@ typedef struct ptm_batch ptm_batch;
 
 /* Tunables of a batch; a field <= 0 keeps its default.
    cell_factor: cell width / expected 14-neighbour radius (default 1.25);
-   tile_atoms: atoms taken from the queue per grab (default 256);
+   tile_atoms: atoms taken from the queue per grab (default 64, one per
+   thread of a block: larger grabs measured 2-2.5x slower);
    blocks_per_sm: resident 64-thread blocks per SM for the persistent grid
    (default 5, the shared-memory limit).  Atoms per warp are fixed at 32 (one
    atom per lane). */
@@ -190,10 +191,10 @@ ptm_status ptm_batch_stats(ptm_batch *batch, ptm_stats *out);
 /* Free the batch and its workspace (waits for its last run). */
 ptm_status ptm_batch_destroy(ptm_batch *batch);
 
-/* Time every candidate tuning on this batch (cell_factor in {1.0, 1.125, 1.25,
-   1.4}, tile_atoms in {64, 256, 1024}, blocks_per_sm in {4, 5}) and return the
+/* Time every candidate tuning on this batch (cell_factor in {1.125, 1.25,
+   1.4}, tile_atoms in {64, 128}, blocks_per_sm in {4, 5}) and return the
    fastest in *best.  Runs the batch (every m-th frame of it when it holds more
-   than about 4 M atoms) 72 times; outputs are written with the same results
+   than about 4 M atoms) 36 times; outputs are written with the same results
    each time. */
 ptm_status ptm_autotune_batch(ptm_context *ctx, int n_frames, const ptm_frame *frames,
                               const ptm_outputs *outs, void *stream, ptm_tuning *best);

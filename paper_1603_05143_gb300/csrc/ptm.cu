@@ -441,7 +441,7 @@ struct ptm_batch {
   int nframes = 0, f64 = 0;
   int64_t ntotal = 0;
   size_t ncell = 0;
-  int tile_atoms = 256, blocks_per_sm = 5;
+  int tile_atoms = 64, blocks_per_sm = 5;
   double cell_factor = 1.25;
   FrameDesc *d_descs = nullptr;
   BinParams *d_bp = nullptr;
@@ -682,8 +682,8 @@ extern "C" ptm_status ptm_batch_destroy(ptm_batch *b) {
 extern "C" ptm_status ptm_autotune_batch(ptm_context *ctx, int nframes, const ptm_frame *frames,
                                          const ptm_outputs *outs, void *stream, ptm_tuning *best) {
   if (!ctx || !best) return PTM_ERR_INVALID_ARG;
-  static const double factors[] = {1.0, 1.125, 1.25, 1.4};
-  static const int tiles[] = {64, 256, 1024};
+  static const double factors[] = {1.125, 1.25, 1.4};
+  static const int tiles[] = {64, 128};
   static const int bpsm[] = {4, 5};
   cudaStream_t st = (cudaStream_t)stream;
   // tune on every m-th frame so that at most about 4 M atoms are timed per candidate
