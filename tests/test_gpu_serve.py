@@ -38,20 +38,24 @@ def test_alone_equals_in_the_mix(ptm):
         srv.release(t)
     rng = np.random.default_rng(0)
     order = rng.permutation(len(frames))
-    tickets = {}
-    for i in order:                          # all together, staggered arrivals
-        f = frames[i]
-        tickets[i] = srv.submit(f.positions, f.cell, f.pbc, species=f.species, pinned=True)
-        time.sleep(float(rng.uniform(0, 0.002)))
-    batches = set()
-    for i, t in tickets.items():
-        out = srv.wait(t, 60000)
-        info = srv.info(t)
-        assert info["submit"] <= info["start"] <= info["done"]
-        batches.add(info["batch"])
-        for k in out:
-            assert np.array_equal(out[k], alone[i][k]), (frames[i].name, k)
-    assert len(batches) < len(frames)        # frames shared launches
+    for burst in (False, True):              # staggered arrivals, then all at once
+        tickets = {}
+        for i in order:
+            f = frames[i]
+            tickets[i] = srv.submit(f.positions, f.cell, f.pbc, species=f.species, pinned=True)
+            if not burst:
+                time.sleep(float(rng.uniform(0, 0.002)))
+        batches = set()
+        for i, t in tickets.items():
+            out = srv.wait(t, 60000)
+            info = srv.info(t)
+            assert info["submit"] <= info["start"] <= info["done"]
+            batches.add(info["batch"])
+            for k in out:
+                assert np.array_equal(out[k], alone[i][k]), (frames[i].name, k, burst)
+            srv.release(t)
+        if burst:
+            assert len(batches) < len(frames)    # queued frames shared launches
     # and the device entry point agrees
     import torch
     f = frames[3]
