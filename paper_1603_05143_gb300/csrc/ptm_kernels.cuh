@@ -709,8 +709,10 @@ __device__ __noinline__ void finalize_fp64(const FrameDesc &d, const Scratch &sm
 // P64 selects the FP64 form: the same exact predicates, canonical codes and
 // lookup, then every candidate scored and the winner's outputs computed in FP64
 // (the one-frame-per-launch comparison form).
+// `live` holds the lanes of this warp that entered together (all reach the
+// warp-synchronous points below).
 template <bool F64, bool P64 = false>
-__device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, const float4 *tplw) {
+__device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, const float4 *tplw, unsigned live) {
   typedef typename RT<F64>::T T;
   double ex[P64 ? PTM_KNN : 1], ey[P64 ? PTM_KNN : 1], ez[P64 ? PTM_KNN : 1];
   T xi, yi, zi;
@@ -726,9 +728,11 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
 
   // ---- neighbours (Sec. 3)
   int cnt;
+  unsigned hmask;
   {
     if (!wrapped && knn_fast<F64>(d, sm, s, xi, yi, zi, bx, by, bz)) cnt = PTM_KNN;
     else cnt = knn_to_scratch<F64>(d, sm, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped);
+    hmask = __ballot_sync(live, cnt >= 4);       // lanes that go on to the hulls
     if (cnt < 4) { write_unmatched(d, idi); return; }
     // rows NID / DX hold (sorted index, image) of each neighbour; move them to
     // rows Q(t, 0) / Q(t, 1) (free until quantisation) and keep NID / DX for
@@ -811,21 +815,25 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
   const uint32_t mask = d.mask;
   int kmax = (mask & 16) ? 14 : ((mask & 14) ? 12 : 6);
   kmax = min(kmax, cnt);
-  if (kmax >= 6) {
-    int nf = hull_init(sm, d);
-    for (int p = 4; p <= kmax; p++) {
-      // the hull now holds neighbours 0..p-1: complete for K = 6, 12, 14.  The
-      // centre test of a snapshot rides on the visibility test of point p.
-      const bool want = (p == 6 && (mask & 1)) || (p == 12 && (mask & 14)) || (p == 14 && (mask & 16));
-      bool centre_in = false;
-      uint32_t vis = 0;
-      if (p < kmax) vis = hull_visibility(sm, nf, p, want, centre_in, d);
-      else if (want) centre_in = hull_centre_inside(sm, nf);
-      if (want && centre_in) snapshot<P64>(p, sm, d, tplw, nf, bst);
-      if (p == kmax || !vis) break;              // done, or p lies inside the hull
-      nf = hull_apply(sm, nf, vis, p, d);
-      if (nf < 0) break;
-    }
+  bool alive = kmax >= 6;
+  int nf = alive ? hull_init(sm, d) : 0;
+  for (int p = 4; p <= PTM_KNN; p++) {
+    // every insertion step starts warp-converged: a lane that finished (or took
+    // a snapshot's longer path) waits here instead of drifting into a later
+    // step alone, so the visibility tests, walks and QCP loops keep full warps
+    if (!__any_sync(hmask, alive)) break;
+    if (!alive) continue;
+    // the hull now holds neighbours 0..p-1: complete for K = 6, 12, 14.  The
+    // centre test of a snapshot rides on the visibility test of point p.
+    const bool want = (p == 6 && (mask & 1)) || (p == 12 && (mask & 14)) || (p == 14 && (mask & 16));
+    bool centre_in = false;
+    uint32_t vis = 0;
+    if (p < kmax) vis = hull_visibility(sm, nf, p, want, centre_in, d);
+    else if (want) centre_in = hull_centre_inside(sm, nf);
+    if (want && centre_in) snapshot<P64>(p, sm, d, tplw, nf, bst);
+    if (p == kmax || !vis) { alive = false; continue; }   // done, or p lies inside the hull
+    nf = hull_apply(sm, nf, vis, p, d);
+    if (nf < 0) alive = false;
   }
   if (bst.K < 0) { write_unmatched(d, idi); return; }
   if constexpr (P64) {
@@ -1074,8 +1082,9 @@ __global__ void __launch_bounds__(PTM_BLOCK, 5) k_atoms(const __grid_constant__ 
   sm.q = q; sm.nv = nv; sm.nid = nid; sm.fac = fac; sm.th = th; sm.used = used; sm.code = code;
   sm.t = threadIdx.x;
   int64_t s = (int64_t)blockIdx.x * PTM_BLOCK + threadIdx.x;
+  const unsigned live = __ballot_sync(0xffffffffu, s < d.n);
   if (s >= d.n) return;
-  classify_atom<F64, P64>(d, (int)s, sm, tplw);
+  classify_atom<F64, P64>(d, (int)s, sm, tplw, live);
 }
 
 // Persistent classification of a batch: every block pulls tiles of PTM_BLOCK
@@ -1111,9 +1120,10 @@ __global__ void __launch_bounds__(PTM_BLOCK, 5)
     if (base >= ntotal) break;
     for (int k = 0; k < tile_atoms; k += PTM_BLOCK) {
       const long long s = base + k + threadIdx.x;
+      const unsigned live = __ballot_sync(0xffffffffu, s < ntotal);
       if (s < ntotal) {
         const int f = frame_of(atom_off, nframes, s);
-        classify_atom<F64>(descs[f], (int)s, sm, tplw);
+        classify_atom<F64>(descs[f], (int)s, sm, tplw, live);
       }
     }
   }
