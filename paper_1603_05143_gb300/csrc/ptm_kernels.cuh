@@ -302,12 +302,10 @@ __device__ __forceinline__ float cand_r2(const float (&Sm)[3][3], float Gv, floa
 }
 
 // Hull of the first K neighbours is complete and contains the centre: canonical
-// code, lookup and QCP of every admissible correspondence (Algorithm 1, inner
-// loops).
-// In the FP64 form (P64) only the labelling and table entry are kept; the
-// candidates are scored later, all in FP64.
-template <bool P64>
-__device__ void snapshot(int K, const Scratch &sm, const FrameDesc &d, const float4 *tplw, int nf, Best &bst) {
+// code and lookup (Algorithm 1, inner loops).  Only the labelling and table
+// entry are kept; every snapshot's candidates are scored after the last one, in
+// one loop (score_candidates, or select_fp64 in the FP64 form).
+__device__ void snapshot(int K, const Scratch &sm, const FrameDesc &d, int nf, Best &bst) {
   if (nf != 2 * K - 4) return;                    // a neighbour is not a hull vertex
   uint64_t lab = 0, h = 0;
   if (!canonical(sm, K, nf, lab, h, d)) return;
@@ -316,25 +314,44 @@ __device__ void snapshot(int K, const Scratch &sm, const FrameDesc &d, const flo
   if (K == 6) { bst.lam6 = lab; bst.ent6 = e; }
   else if (K == 12) { bst.lam12 = lab; bst.ent12 = e; }
   else { bst.lam14 = lab; bst.ent14 = e; }
-  if constexpr (P64) { bst.K = K; return; }
-  float mx, my, mz, Gv;
-  data_moments(K, sm, mx, my, mz, Gv);
-  const int first = __ldg(&ptm_tbl[e].first), cnt = __ldg(&ptm_tbl[e].count);
-  int scored = 0;
-  for (int c = first; c < first + cnt; c++) {
-    uint64_t cand = __ldg((const unsigned long long *)&ptm_cand[c]);
-    int S = (int)(cand >> 60) & 7;
+}
+
+// FP32 QCP of every admissible correspondence of the matched snapshots, in
+// snapshot order (6, 12, 14) and table order, as one flat loop whose trips
+// start warp-converged (every lane in `qmask` calls it), so the lanes of a warp
+// run their candidates together; keeps the best and second-best RMSD^2 (the
+// first of equal values wins, Algorithm 1).
+__device__ void score_candidates(const FrameDesc &d, const Scratch &sm, const float4 *tplw, Best &bst,
+                                 unsigned qmask) {
+  int n6 = 0, n12 = 0, n14 = 0, f6 = 0, f12 = 0, f14 = 0;
+  float Gv6 = 0.f, Gv12 = 0.f, Gv14 = 0.f, mx, my, mz;
+  if (bst.ent6 >= 0) { f6 = ptm_tbl[bst.ent6].first; n6 = ptm_tbl[bst.ent6].count; data_moments(6, sm, mx, my, mz, Gv6); }
+  if (bst.ent12 >= 0) { f12 = ptm_tbl[bst.ent12].first; n12 = ptm_tbl[bst.ent12].count; data_moments(12, sm, mx, my, mz, Gv12); }
+  if (bst.ent14 >= 0) { f14 = ptm_tbl[bst.ent14].first; n14 = ptm_tbl[bst.ent14].count; data_moments(14, sm, mx, my, mz, Gv14); }
+  const int total = n6 + n12 + n14;
+  int scored = 0, points = 0;
+  for (int i = 0; __any_sync(qmask, i < total); i++) {
+    if (i >= total) continue;
+    int K, c;
+    uint64_t lab;
+    float Gv;
+    if (i < n6) { K = 6; c = f6 + i; lab = bst.lam6; Gv = Gv6; }
+    else if (i < n6 + n12) { K = 12; c = f12 + (i - n6); lab = bst.lam12; Gv = Gv12; }
+    else { K = 14; c = f14 + (i - n6 - n12); lab = bst.lam14; Gv = Gv14; }
+    const uint64_t cand = __ldg((const unsigned long long *)&ptm_cand[c]);
+    const int S = (int)(cand >> 60) & 7;
     if (!(d.mask >> S & 1)) continue;
     scored++;
+    points += K + 1;
     float Sm[3][3];
     cov_matrix(K, sm, tplw, S, lab, cand, Sm);
-    float Gw = tplw[S * 15].w;
+    const float Gw = tplw[S * 15].w;
     int fp64;
-    float r2 = cand_r2(Sm, Gv, Gw, K + 1, fp64, d);
+    const float r2 = cand_r2(Sm, Gv, Gw, K + 1, fp64, d);
     if (r2 < bst.b1) { bst.b2 = bst.b1; bst.b1 = r2; bst.K = K; bst.cand = c; bst.fp64 = fp64; }
     else if (r2 < bst.b2) bst.b2 = r2;
   }
-  if (scored) { count(d, C_CAND, scored); count(d, C_CANDPTS, (unsigned long long)scored * (K + 1)); }
+  if (scored) { count(d, C_CAND, scored); count(d, C_CANDPTS, (unsigned long long)points); }
 }
 
 // Canonical correspondence (reading R12): nibble 15 - s holds the neighbour rank
@@ -822,21 +839,28 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
     // a snapshot's longer path) waits here instead of drifting into a later
     // step alone, so the visibility tests, walks and QCP loops keep full warps
     if (!__any_sync(hmask, alive)) break;
-    if (!alive) continue;
     // the hull now holds neighbours 0..p-1: complete for K = 6, 12, 14.  The
     // centre test of a snapshot rides on the visibility test of point p.
     const bool want = (p == 6 && (mask & 1)) || (p == 12 && (mask & 14)) || (p == 14 && (mask & 16));
     bool centre_in = false;
     uint32_t vis = 0;
-    if (p < kmax) vis = hull_visibility(sm, nf, p, want, centre_in, d);
-    else if (want) centre_in = hull_centre_inside(sm, nf);
-    if (want && centre_in) snapshot<P64>(p, sm, d, tplw, nf, bst);
+    if (alive) {
+      if (p < kmax) vis = hull_visibility(sm, nf, p, want, centre_in, d);
+      else if (want) centre_in = hull_centre_inside(sm, nf);
+    }
+    if (alive && want && centre_in) snapshot(p, sm, d, nf, bst);
+    if (!alive) continue;
     if (p == kmax || !vis) { alive = false; continue; }   // done, or p lies inside the hull
     nf = hull_apply(sm, nf, vis, p, d);
     if (nf < 0) alive = false;
   }
-  if (bst.K < 0) { write_unmatched(d, idi); return; }
-  if constexpr (P64) {
+  const bool found = bst.ent6 >= 0 || bst.ent12 >= 0 || bst.ent14 >= 0;
+  const unsigned qmask = __ballot_sync(hmask, found);
+  if (!found) { write_unmatched(d, idi); return; }
+  if constexpr (!P64) {
+    score_candidates(d, sm, tplw, bst, qmask);
+    if (bst.K < 0) { write_unmatched(d, idi); return; }     // every match masked out
+  } else {
     int ns = 0;
     const int w = select_fp64(d, bst, ex, ey, ez, &ns);
     if (ns) { count(d, C_CAND, ns); }
