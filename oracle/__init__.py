@@ -225,3 +225,41 @@ def classify_frame(frame, atoms=None, mask=ALL_TEMPLATES, rmsd_max=np.inf, threa
     sp = frame.species if isinstance(species, str) and species == "frame" else species
     F = Frame(frame.positions, frame.cell, frame.pbc)
     return F.classify(atoms, species=sp, mask=mask, rmsd_max=rmsd_max, threads=threads)
+
+
+# ------------------------------------------------------------ post-processing
+# Plain definitions of the derived per-atom quantities; each reads the oracle's
+# own outputs.
+
+def von_mises(P: np.ndarray) -> np.ndarray:
+    """Von Mises shear strain of the elastic strain matrix P (Sec. 8):
+    sqrt(3/2 sum_ij P_ij^2 - 1/2 (sum_k P_kk)^2), for one (3, 3) matrix or a
+    stack (..., 3, 3).  Unmatched atoms (P = 0) give 0."""
+    P = np.asarray(P, np.float64)
+    s = 1.5 * np.sum(P * P, axis=(-2, -1)) - 0.5 * np.trace(P, axis1=-2, axis2=-1) ** 2
+    return np.sqrt(np.maximum(s, 0.0))
+
+
+def rodrigues(q: np.ndarray) -> np.ndarray:
+    """Rodrigues-Frank vector (x, y, z) / w of an orientation quaternion
+    (w, x, y, z) with w > 0 (Sec. 7: the fundamental-zone orientation projected
+    into Rodrigues-Frank space); (..., 4) -> (..., 3)."""
+    q = np.asarray(q, np.float64)
+    return q[..., 1:] / q[..., :1]
+
+
+def rmsd_histogram(structure: np.ndarray, rmsd: np.ndarray, nbins: int, rmsd_max: float) -> np.ndarray:
+    """Counts of matched atoms per structure (rows SC, FCC, HCP, ICO, BCC) and
+    RMSD bin (Sec. 5.1: the histogram from which RMSD_max is chosen).  Bin b
+    holds b <= rmsd * (nbins / rmsd_max) < b + 1, evaluated in float32 exactly
+    as the kernel does (scale rounded to float32 once, one rounded product);
+    column nbins counts the atoms at or beyond rmsd_max."""
+    structure = np.asarray(structure)
+    r = np.asarray(rmsd, np.float32)
+    scale = np.float32(nbins / rmsd_max)
+    out = np.zeros((5, nbins + 1), np.int64)
+    for S in range(1, 6):
+        v = r[(structure == S) & np.isfinite(r)]
+        b = np.floor((v * scale).astype(np.float32)).astype(np.int64)
+        out[S - 1] = np.bincount(np.minimum(b, nbins), minlength=nbins + 1)
+    return out
