@@ -89,7 +89,7 @@ typedef struct {
 /* Per-atom outputs, indexed by atom.  Any pointer may be NULL to skip it.
    Unmatched atoms (Algorithm 1: r* = infinity, structure disordered) get
    structure PTM_NONE, rmsd +INF, scale 0, quat (1,0,0,0), strain 0,
-   correspondence -1, alloy PTM_ALLOY_NONE. */
+   correspondence -1, alloy PTM_ALLOY_NONE, von_mises 0, rodrigues 0. */
 typedef struct {
   int8_t *structure;         /* n: PTM_NONE .. PTM_BCC */
   int8_t *alloy;             /* n: PTM_ALLOY_* */
@@ -102,6 +102,11 @@ typedef struct {
   int32_t *correspondence;   /* n x 15: atom index mapped to template slot 0..k
                                 (slot 0 = the atom itself), -1 beyond k; the smallest
                                 member of its orbit under the template symmetry */
+  /* derived outputs (post-processing, written only when requested) */
+  float *von_mises;          /* n: von Mises shear strain of P (Sec. 8),
+                                sqrt(3/2 sum P_ij^2 - 1/2 (tr P)^2); 0 when unmatched */
+  float *rodrigues;          /* n x 3: Rodrigues-Frank vector (x, y, z) / w of quat
+                                (Sec. 7); 0 when unmatched */
 } ptm_outputs;
 
 /* Counters of the last completed classify call (rates of the rare paths). */
@@ -268,6 +273,23 @@ ptm_status ptm_server_destroy(ptm_server *server);
    stream.  Returns PTM_ERR_INVALID_ARG for frames above the limit (or bad
    arguments) before enqueueing anything, PTM_ERR_CUDA if a launch fails. */
 ptm_status ptm_classify_frame_noalloc(const ptm_frame *frame, const ptm_outputs *out, void *stream);
+
+/* Largest bin count of ptm_rmsd_histogram. */
+#define PTM_HIST_MAX_BINS 2048
+
+/* Per-structure histogram of the RMSD of matched atoms (Sec. 5.1: the
+   histogram from which RMSD_max is chosen after the analysis), computed on the
+   device from outputs of a classify call.  structure, rmsd: DEVICE arrays of
+   n_atoms.  counts: DEVICE int64 array of 5 x (nbins + 1), overwritten: row
+   S - 1 counts structure S (PTM_SC .. PTM_BCC); column b < nbins counts atoms
+   with b <= rmsd * s < b + 1, where s = nbins / rmsd_max rounded to float32 and
+   the product is one float32 multiplication; column nbins counts atoms at or
+   beyond rmsd_max.  Unmatched atoms (structure PTM_NONE or infinite rmsd) are
+   not counted.  Asynchronous on `stream`.  PTM_ERR_INVALID_ARG for NULL
+   pointers, n_atoms < 0, nbins outside [1, PTM_HIST_MAX_BINS] or rmsd_max not
+   finite and positive. */
+ptm_status ptm_rmsd_histogram(ptm_context *ctx, int64_t n_atoms, const int8_t *structure, const float *rmsd,
+                              int nbins, double rmsd_max, int64_t *counts, void *stream);
 
 /* Measured FMA throughput of the current device, for the ALU roofline of the
    per-atom kernel (the paper has no counterpart).  kind 0 = FP32, 1 = FP64.

@@ -16,6 +16,8 @@ PTM_F32, PTM_F64 = 0, 1
 STATUS = ("PTM_OK", "PTM_ERR_INVALID_ARG", "PTM_ERR_OUT_OF_MEMORY", "PTM_ERR_CUDA", "PTM_ERR_TIMEOUT",
           "PTM_ERR_DEVICE_STATUS", "PTM_ERR_BUSY", "PTM_ERR_NOT_FOUND")
 OUTPUT_NAMES = ("structure", "alloy", "rmsd", "scale", "quat", "strain", "correspondence")
+DERIVED_NAMES = ("von_mises", "rodrigues")           # post-processing outputs, on request
+OUTPUT_FIELDS = OUTPUT_NAMES + DERIVED_NAMES          # order of ptm_outputs
 
 
 class ptm_options(C.Structure):
@@ -29,7 +31,7 @@ class ptm_frame(C.Structure):
 
 
 class ptm_outputs(C.Structure):
-    _fields_ = [(n, C.c_void_p) for n in OUTPUT_NAMES]
+    _fields_ = [(n, C.c_void_p) for n in OUTPUT_FIELDS]
 
 
 class ptm_stats(C.Structure):
@@ -93,6 +95,8 @@ def load():
         for f in ("ptm_server_create", "ptm_submit", "ptm_poll", "ptm_wait", "ptm_ticket_info", "ptm_release",
                   "ptm_server_destroy"):
             getattr(L, f).restype = C.c_int
+        L.ptm_rmsd_histogram.argtypes = [P, C.c_int64, P, P, C.c_int, C.c_double, P, P]
+        L.ptm_rmsd_histogram.restype = C.c_int
         L.ptm_measure_fma_peak.argtypes = [C.c_int, P, C.POINTER(C.c_double)]
         L.ptm_measure_fma_peak.restype = C.c_int
         L.ptm_status_string.argtypes = [C.c_int]
@@ -193,7 +197,7 @@ class PTM:
         if out is None:
             out = allocate_outputs(n, dev, outputs)
         o = ptm_outputs()
-        for name in OUTPUT_NAMES:
+        for name in OUTPUT_FIELDS:
             t = out.get(name)
             setattr(o, name, t.data_ptr() if t is not None else None)
         f = _frame(n, positions.data_ptr(), code, sp_ptr, cell, pbc, mask, rmsd_max)
@@ -216,7 +220,7 @@ class PTM:
         if out is None:
             out = allocate_outputs_host(n, outputs)
         o = ptm_outputs()
-        for name in OUTPUT_NAMES:
+        for name in OUTPUT_FIELDS:
             a = out.get(name)
             setattr(o, name, a.ctypes.data if a is not None else None)
         f = _frame(n, pos.ctypes.data, PTM_F64 if pos.dtype == np.float64 else PTM_F32,
@@ -225,6 +229,24 @@ class PTM:
         self._check(self.lib.ptm_classify_frame_host(self.h, C.byref(f), C.byref(o), C.c_void_p(st)),
                     "ptm_classify_frame_host")
         return out
+
+    def rmsd_histogram(self, structure, rmsd, nbins=100, rmsd_max=0.5, stream=None):
+        """Per-structure RMSD histogram (``ptm_rmsd_histogram``) of outputs held in
+        CUDA tensors: int64 tensor (5, nbins + 1), rows SC..BCC, last column =
+        at or beyond rmsd_max."""
+        import torch
+        n = int(structure.shape[0])
+        if rmsd.shape[0] != n or not (structure.is_cuda and rmsd.is_cuda):
+            raise ValueError("structure and rmsd must be CUDA tensors of the same length")
+        structure = structure.contiguous()
+        rmsd = rmsd.contiguous()
+        counts = torch.empty((5, nbins + 1), dtype=torch.int64, device=structure.device)
+        st = stream if stream is not None else torch.cuda.current_stream(structure.device)
+        self._check(self.lib.ptm_rmsd_histogram(self.h, n, C.c_void_p(structure.data_ptr()),
+                                                C.c_void_p(rmsd.data_ptr()), int(nbins), float(rmsd_max),
+                                                C.c_void_p(counts.data_ptr()), C.c_void_p(st.cuda_stream)),
+                    "ptm_rmsd_histogram")
+        return counts
 
     def stats(self) -> dict:
         s = ptm_stats()
@@ -281,7 +303,7 @@ def _batch_structs(frames, mask, rmsd_max, outputs):
         fr[i] = _frame(pos.shape[0], pos.data_ptr(), code, None if sp is None else sp.data_ptr(), f["cell"],
                        f.get("pbc", (True, True, True)), mask, rmsd_max)
         o = allocate_outputs(pos.shape[0], pos.device, outputs)
-        for name in OUTPUT_NAMES:
+        for name in OUTPUT_FIELDS:
             t = o.get(name)
             setattr(outs[i], name, t.data_ptr() if t is not None else None)
         keep.append((pos, sp))
@@ -337,14 +359,16 @@ def allocate_outputs(n, device, outputs=OUTPUT_NAMES):
     import torch
     shapes = {"structure": ((n,), torch.int8), "alloy": ((n,), torch.int8), "rmsd": ((n,), torch.float32),
               "scale": ((n,), torch.float32), "quat": ((n, 4), torch.float32),
-              "strain": ((n, 3, 3), torch.float32), "correspondence": ((n, 15), torch.int32)}
+              "strain": ((n, 3, 3), torch.float32), "correspondence": ((n, 15), torch.int32),
+              "von_mises": ((n,), torch.float32), "rodrigues": ((n, 3), torch.float32)}
     return {k: torch.empty(*shapes[k][0], dtype=shapes[k][1], device=device) for k in outputs}
 
 
 def allocate_outputs_host(n, outputs=OUTPUT_NAMES, pinned=False):
     shapes = {"structure": ((n,), np.int8), "alloy": ((n,), np.int8), "rmsd": ((n,), np.float32),
               "scale": ((n,), np.float32), "quat": ((n, 4), np.float32), "strain": ((n, 3, 3), np.float32),
-              "correspondence": ((n, 15), np.int32)}
+              "correspondence": ((n, 15), np.int32), "von_mises": ((n,), np.float32),
+              "rodrigues": ((n, 3), np.float32)}
     if pinned:
         import torch
         tt = {np.int8: torch.int8, np.float32: torch.float32, np.int32: torch.int32}
@@ -378,7 +402,7 @@ class Server:
         if out is None:
             out = allocate_outputs_host(n, pinned=pinned)
         o = ptm_outputs()
-        for name in OUTPUT_NAMES:
+        for name in OUTPUT_FIELDS:
             a = out.get(name)
             setattr(o, name, a.ctypes.data if a is not None else None)
         f = _frame(n, pos.ctypes.data, PTM_F64 if pos.dtype == np.float64 else PTM_F32,

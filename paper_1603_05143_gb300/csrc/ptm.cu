@@ -41,6 +41,7 @@ struct ptm_context {
   int8_t *o_struct = nullptr, *o_alloy = nullptr;
   float *o_rmsd = nullptr, *o_scale = nullptr, *o_quat = nullptr, *o_strain = nullptr;
   int32_t *o_corr = nullptr;
+  float *o_vm = nullptr, *o_rf = nullptr;
 };
 
 static ptm_status cuda_fail(ptm_context *ctx, cudaError_t e, const char *what) {
@@ -168,6 +169,7 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
       }
   hd->structure = o->structure; hd->alloy = o->alloy; hd->rmsd = o->rmsd; hd->scale = o->scale;
   hd->quat = o->quat; hd->strain = o->strain; hd->corr = o->correspondence;
+  hd->vm = o->von_mises; hd->rf = o->rodrigues;
   hd->dstat = ctx->dstat;
   hd->counters = ctx->counters;
 
@@ -276,7 +278,7 @@ ptm_status ptm_destroy(ptm_context *ctx) {
   for (int i = 0; i < 3; i++) if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   cudaFree(ctx->hpos); cudaFree(ctx->hspecies);
   cudaFree(ctx->o_struct); cudaFree(ctx->o_alloy); cudaFree(ctx->o_rmsd); cudaFree(ctx->o_scale);
-  cudaFree(ctx->o_quat); cudaFree(ctx->o_strain); cudaFree(ctx->o_corr);
+  cudaFree(ctx->o_quat); cudaFree(ctx->o_strain); cudaFree(ctx->o_corr); cudaFree(ctx->o_vm); cudaFree(ctx->o_rf);
   delete ctx;
   return PTM_OK;
 }
@@ -299,9 +301,10 @@ ptm_status ptm_classify_frame_host(ptm_context *ctx, const ptm_frame *frame, con
   if (n > ctx->cap_host_atoms) {
     cudaFree(ctx->hpos); cudaFree(ctx->hspecies);
     cudaFree(ctx->o_struct); cudaFree(ctx->o_alloy); cudaFree(ctx->o_rmsd); cudaFree(ctx->o_scale);
-    cudaFree(ctx->o_quat); cudaFree(ctx->o_strain); cudaFree(ctx->o_corr);
+    cudaFree(ctx->o_quat); cudaFree(ctx->o_strain); cudaFree(ctx->o_corr); cudaFree(ctx->o_vm); cudaFree(ctx->o_rf);
     ctx->hpos = nullptr; ctx->hspecies = nullptr; ctx->o_struct = ctx->o_alloy = nullptr;
     ctx->o_rmsd = ctx->o_scale = ctx->o_quat = ctx->o_strain = nullptr; ctx->o_corr = nullptr;
+    ctx->o_vm = ctx->o_rf = nullptr;
     ctx->cap_host_atoms = 0;
     CK(cudaMalloc(&ctx->hpos, n * 3 * 8));
     CK(cudaMalloc(&ctx->hspecies, n));
@@ -312,6 +315,8 @@ ptm_status ptm_classify_frame_host(ptm_context *ctx, const ptm_frame *frame, con
     CK(cudaMalloc(&ctx->o_quat, n * 16));
     CK(cudaMalloc(&ctx->o_strain, n * 36));
     CK(cudaMalloc(&ctx->o_corr, n * 60));
+    CK(cudaMalloc(&ctx->o_vm, n * 4));
+    CK(cudaMalloc(&ctx->o_rf, n * 12));
     ctx->cap_host_atoms = n;
   }
   CK(cudaMemcpyAsync(ctx->hpos, frame->positions, n * 3 * esz, cudaMemcpyHostToDevice, st));
@@ -327,6 +332,8 @@ ptm_status ptm_classify_frame_host(ptm_context *ctx, const ptm_frame *frame, con
   dout.quat = out->quat ? ctx->o_quat : nullptr;
   dout.strain = out->strain ? ctx->o_strain : nullptr;
   dout.correspondence = out->correspondence ? ctx->o_corr : nullptr;
+  dout.von_mises = out->von_mises ? ctx->o_vm : nullptr;
+  dout.rodrigues = out->rodrigues ? ctx->o_rf : nullptr;
   ptm_status rs = enqueue_frame(ctx, &df, &dout, st);
   if (rs != PTM_OK) return rs;
   if (out->structure) CK(cudaMemcpyAsync(out->structure, dout.structure, n, cudaMemcpyDeviceToHost, st));
@@ -336,6 +343,8 @@ ptm_status ptm_classify_frame_host(ptm_context *ctx, const ptm_frame *frame, con
   if (out->quat) CK(cudaMemcpyAsync(out->quat, dout.quat, n * 16, cudaMemcpyDeviceToHost, st));
   if (out->strain) CK(cudaMemcpyAsync(out->strain, dout.strain, n * 36, cudaMemcpyDeviceToHost, st));
   if (out->correspondence) CK(cudaMemcpyAsync(out->correspondence, dout.correspondence, n * 60, cudaMemcpyDeviceToHost, st));
+  if (out->von_mises) CK(cudaMemcpyAsync(out->von_mises, dout.von_mises, n * 4, cudaMemcpyDeviceToHost, st));
+  if (out->rodrigues) CK(cudaMemcpyAsync(out->rodrigues, dout.rodrigues, n * 12, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return PTM_OK;
 }
@@ -572,6 +581,8 @@ static void batch_layout(ptm_batch *b, unsigned char *base, BatchPlan &P, const 
     P.hd[f].structure = outs[f].structure; P.hd[f].alloy = outs[f].alloy; P.hd[f].rmsd = outs[f].rmsd;
     P.hd[f].scale = outs[f].scale; P.hd[f].quat = outs[f].quat; P.hd[f].strain = outs[f].strain;
     P.hd[f].corr = outs[f].correspondence;
+    P.hd[f].vm = outs[f].von_mises;
+    P.hd[f].rf = outs[f].rodrigues;
     P.hd[f].dstat = b->d_dstat + 4 * f;
     P.hd[f].counters = b->counters;
     P.hb[f].dstat = b->d_dstat + 4 * f;
@@ -847,6 +858,7 @@ extern "C" ptm_status ptm_classify_frame_noalloc(const ptm_frame *f, const ptm_o
       }
   desc.structure = o->structure; desc.alloy = o->alloy; desc.rmsd = o->rmsd; desc.scale = o->scale;
   desc.quat = o->quat; desc.strain = o->strain; desc.corr = o->correspondence;
+  desc.vm = o->von_mises; desc.rf = o->rodrigues;
   desc.dstat = dstat;
   desc.counters = counters;
   BinParams bp;
@@ -875,6 +887,51 @@ extern "C" ptm_status ptm_classify_frame_noalloc(const ptm_frame *f, const ptm_o
   if (f64) k_atoms<true><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
   else k_atoms<false><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
   if (cudaGetLastError() != cudaSuccess) return PTM_ERR_CUDA;
+  return PTM_OK;
+}
+
+// ------------------------------------------------------------ RMSD histogram
+// Per-structure histogram of the RMSD of matched atoms (Sec. 5.1: RMSD_max is
+// chosen from it).  Each block counts into shared memory, then adds its counts
+// to the global array.
+namespace ptm {
+__global__ void k_rmsd_hist(const int8_t *__restrict__ structure, const float *__restrict__ rmsd, int64_t n,
+                            int nbins, float scale, unsigned long long *counts) {
+  extern __shared__ unsigned int hs[];            // 5 x (nbins + 1)
+  const int nb1 = nbins + 1;
+  for (int i = threadIdx.x; i < 5 * nb1; i += blockDim.x) hs[i] = 0u;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int S = structure[i];
+    const float r = rmsd[i];
+    if (S < 1 || S > 5 || !(r < INFINITY)) continue;          // unmatched
+    const int b = min(max((int)floorf(__fmul_rn(r, scale)), 0), nbins);
+    atomicAdd(&hs[(S - 1) * nb1 + b], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 5 * nb1; i += blockDim.x)
+    if (hs[i]) atomicAdd(&counts[i], (unsigned long long)hs[i]);
+}
+}  // namespace ptm
+
+extern "C" ptm_status ptm_rmsd_histogram(ptm_context *ctx, int64_t n_atoms, const int8_t *structure, const float *rmsd,
+                                         int nbins, double rmsd_max, int64_t *counts, void *stream) {
+  using namespace ptm;
+  if (!ctx || !structure || !rmsd || !counts || n_atoms < 0 || nbins < 1 || nbins > PTM_HIST_MAX_BINS ||
+      !(rmsd_max > 0.0) || !std::isfinite(rmsd_max))
+    return PTM_ERR_INVALID_ARG;
+  CK(cudaSetDevice(ctx->device));
+  cudaGetLastError();
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(counts, 0, sizeof(int64_t) * 5 * (size_t)(nbins + 1), st));
+  if (n_atoms == 0) return PTM_OK;
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  const unsigned grid = (unsigned)std::min<int64_t>((n_atoms + 255) / 256, (int64_t)sms * 4);
+  const size_t smem = sizeof(unsigned int) * 5 * (size_t)(nbins + 1);
+  k_rmsd_hist<<<grid, 256, smem, st>>>(structure, rmsd, n_atoms, nbins, (float)(nbins / rmsd_max),
+                                       (unsigned long long *)counts);
+  CK(cudaGetLastError());
   return PTM_OK;
 }
 

@@ -566,6 +566,8 @@ __device__ void finalize(const FrameDesc &d, const Scratch &sm, const float4 *tp
     if (d.quat) { d.quat[4 * a] = 1.f; d.quat[4 * a + 1] = 0.f; d.quat[4 * a + 2] = 0.f; d.quat[4 * a + 3] = 0.f; }
     if (d.strain) for (int i = 0; i < 9; i++) d.strain[9 * a + i] = 0.f;
     if (d.corr) for (int i = 0; i < 15; i++) d.corr[15 * a + i] = -1;
+    if (d.vm) d.vm[a] = 0.f;
+    if (d.rf) for (int i = 0; i < 3; i++) d.rf[3 * a + i] = 0.f;
     return;
   }
   count(d, C_MATCHED);
@@ -580,7 +582,7 @@ __device__ void finalize(const FrameDesc &d, const Scratch &sm, const float4 *tp
   }
   // orientation in the fundamental zone: the equivalent rotation Q g with the
   // largest |w| (smallest angle); ties keep the earlier group element (Sec. 7)
-  if (d.quat) {
+  if (d.quat || d.rf) {
     float bw = -1.f, bq[4] = {1.f, 0.f, 0.f, 0.f};
     for (int g = ptm_group_off[S]; g < ptm_group_off[S + 1]; g++) {
       const float *gq = ptm_group_quat[g];
@@ -594,12 +596,14 @@ __device__ void finalize(const FrameDesc &d, const Scratch &sm, const float4 *tp
       }
     }
     float sg = bq[0] < 0.f ? -1.f : 1.f;
-    for (int i = 0; i < 4; i++) d.quat[4 * a + i] = sg * bq[i];
+    if (d.quat) for (int i = 0; i < 4; i++) d.quat[4 * a + i] = sg * bq[i];
+    // Rodrigues-Frank vector of the fundamental-zone orientation (Sec. 7)
+    if (d.rf) for (int i = 0; i < 3; i++) d.rf[3 * a + i] = (sg * bq[i + 1]) / (sg * bq[0]);
   }
   // strain (Sec. 8, Eq. 6-7): both sets barycentred and scaled to mean distance
   // 1; the isotropic templates give pinv(V) = V^T / (G_w / 3), so
   // A = 3 S^T / (G_w l_data); then P = (A A^T)^(1/2), U proper.
-  if (d.strain) {
+  if (d.strain || d.vm) {
     const float ldat = lsum / (float)(K + 1);
     const float f = 3.f / (Gw * ldat);
     float A[3][3], AA[3][3], X[3][3];
@@ -614,9 +618,20 @@ __device__ void finalize(const FrameDesc &d, const Scratch &sm, const float4 *tp
       else s2 = -s2;
     }
     const float sig[3] = {s0, s1, s2};
+    float P[3][3];
     for (int i = 0; i < 3; i++)
       for (int j = 0; j < 3; j++)
-        d.strain[9 * a + 3 * i + j] = X[i][0] * sig[0] * X[j][0] + X[i][1] * sig[1] * X[j][1] + X[i][2] * sig[2] * X[j][2];
+        P[i][j] = X[i][0] * sig[0] * X[j][0] + X[i][1] * sig[1] * X[j][1] + X[i][2] * sig[2] * X[j][2];
+    if (d.strain) for (int i = 0; i < 3; i++) for (int j = 0; j < 3; j++) d.strain[9 * a + 3 * i + j] = P[i][j];
+    // von Mises shear strain (Sec. 8) in its deviatoric form, equal to
+    // 3/2 sum P_ij^2 - 1/2 (tr P)^2 but free of its cancellation near P = I
+    if (d.vm) {
+      const float t = (P[0][0] + P[1][1] + P[2][2]) / 3.f;
+      const float e0 = P[0][0] - t, e1 = P[1][1] - t, e2 = P[2][2] - t;
+      const float off = P[0][1] * P[0][1] + P[0][2] * P[0][2] + P[1][2] * P[1][2] +
+                        P[1][0] * P[1][0] + P[2][0] * P[2][0] + P[2][1] * P[2][1];
+      d.vm[a] = sqrtf(1.5f * (e0 * e0 + e1 * e1 + e2 * e2 + off));
+    }
   }
   if (d.alloy) d.alloy[a] = alloy_label(d, sm, S, cp, a);
 }
@@ -629,6 +644,8 @@ __device__ void write_unmatched(const FrameDesc &d, int64_t a) {
   if (d.quat) { d.quat[4 * a] = 1.f; d.quat[4 * a + 1] = 0.f; d.quat[4 * a + 2] = 0.f; d.quat[4 * a + 3] = 0.f; }
   if (d.strain) for (int i = 0; i < 9; i++) d.strain[9 * a + i] = 0.f;
   if (d.corr) for (int i = 0; i < 15; i++) d.corr[15 * a + i] = -1;
+  if (d.vm) d.vm[a] = 0.f;
+  if (d.rf) for (int i = 0; i < 3; i++) d.rf[3 * a + i] = 0.f;
 }
 
 // Outputs of the winner in the FP64 form: the same steps as finalize, every
@@ -687,7 +704,7 @@ __device__ __noinline__ void finalize_fp64(const FrameDesc &d, const Scratch &sm
     d.corr[15 * a] = idi;
     for (int sl = 1; sl < 15; sl++) d.corr[15 * a + sl] = sl <= K ? sm.NID(nib(cp, 15 - sl) - 1) : -1;
   }
-  if (d.quat) {
+  if (d.quat || d.rf) {
     double bw = -1.0, bq[4] = {1.0, 0.0, 0.0, 0.0};
     for (int gi = ptm_group_off[S]; gi < ptm_group_off[S + 1]; gi++) {
       const float *gq = ptm_group_quat[gi];
@@ -701,9 +718,10 @@ __device__ __noinline__ void finalize_fp64(const FrameDesc &d, const Scratch &sm
       }
     }
     const double sg = bq[0] < 0.0 ? -1.0 : 1.0;
-    for (int i = 0; i < 4; i++) d.quat[4 * a + i] = (float)(sg * bq[i]);
+    if (d.quat) for (int i = 0; i < 4; i++) d.quat[4 * a + i] = (float)(sg * bq[i]);
+    if (d.rf) for (int i = 0; i < 3; i++) d.rf[3 * a + i] = (float)((sg * bq[i + 1]) / (sg * bq[0]));
   }
-  if (d.strain) {
+  if (d.strain || d.vm) {
     const double f = 3.0 / (Gw * (lsum / (K + 1)));
     double A[3][3], AA[3][3], X[3][3];
     for (int i = 0; i < 3; i++) for (int j = 0; j < 3; j++) A[i][j] = f * Sm[j][i];
@@ -715,9 +733,17 @@ __device__ __noinline__ void finalize_fp64(const FrameDesc &d, const Scratch &sm
       const int k = (sg[0] <= sg[1] && sg[0] <= sg[2]) ? 0 : (sg[1] <= sg[2] ? 1 : 2);
       sg[k] = -sg[k];
     }
+    double P[3][3];
     for (int i = 0; i < 3; i++)
-      for (int j = 0; j < 3; j++)
-        d.strain[9 * a + 3 * i + j] = (float)(X[i][0] * sg[0] * X[j][0] + X[i][1] * sg[1] * X[j][1] + X[i][2] * sg[2] * X[j][2]);
+      for (int j = 0; j < 3; j++) P[i][j] = X[i][0] * sg[0] * X[j][0] + X[i][1] * sg[1] * X[j][1] + X[i][2] * sg[2] * X[j][2];
+    if (d.strain) for (int i = 0; i < 3; i++) for (int j = 0; j < 3; j++) d.strain[9 * a + 3 * i + j] = (float)P[i][j];
+    if (d.vm) {
+      const double t = (P[0][0] + P[1][1] + P[2][2]) / 3.0;
+      const double e0 = P[0][0] - t, e1 = P[1][1] - t, e2 = P[2][2] - t;
+      const double off = P[0][1] * P[0][1] + P[0][2] * P[0][2] + P[1][2] * P[1][2] +
+                         P[1][0] * P[1][0] + P[2][0] * P[2][0] + P[2][1] * P[2][1];
+      d.vm[a] = (float)sqrt(1.5 * (e0 * e0 + e1 * e1 + e2 * e2 + off));
+    }
   }
   if (d.alloy) d.alloy[a] = alloy_label(d, sm, S, cp, a);
 }

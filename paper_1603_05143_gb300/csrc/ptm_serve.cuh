@@ -70,7 +70,7 @@ struct InFlight {
   int slot = 0;
 };
 
-constexpr size_t kOutBytesPerAtom = 1 + 1 + 4 + 4 + 16 + 36 + 60;
+constexpr size_t kOutBytesPerAtom = 1 + 1 + 4 + 4 + 16 + 36 + 60 + 4 + 12;
 
 size_t request_bytes(const ptm_frame &f) {
   const size_t n = (size_t)f.n_atoms;
@@ -137,7 +137,9 @@ ptm_status launch_batch(ptm_server *S, std::vector<Request *> &rs, int slot, InF
     d.scale = r->out.scale ? (float *)o : nullptr; o += 4 * n;
     d.quat = r->out.quat ? (float *)o : nullptr; o += 16 * n;
     d.strain = r->out.strain ? (float *)o : nullptr; o += 36 * n;
-    d.correspondence = r->out.correspondence ? (int32_t *)o : nullptr;
+    d.correspondence = r->out.correspondence ? (int32_t *)o : nullptr; o += 60 * n;
+    d.von_mises = r->out.von_mises ? (float *)o : nullptr; o += 4 * n;
+    d.rodrigues = r->out.rodrigues ? (float *)o : nullptr;
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "serve: inputs");
   InFlight *F = new InFlight();
@@ -187,6 +189,8 @@ ptm_status launch_batch(ptm_server *S, std::vector<Request *> &rs, int slot, InF
     if (e == cudaSuccess && r->out.strain) e = cudaMemcpyAsync(r->out.strain, d.strain, 36 * n, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && r->out.correspondence)
       e = cudaMemcpyAsync(r->out.correspondence, d.correspondence, 60 * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && r->out.von_mises) e = cudaMemcpyAsync(r->out.von_mises, d.von_mises, 4 * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && r->out.rodrigues) e = cudaMemcpyAsync(r->out.rodrigues, d.rodrigues, 12 * n, cudaMemcpyDeviceToHost, st);
   }
   if (e == cudaSuccess) e = cudaEventRecord(F->done, st);
   if (e != cudaSuccess) { batch_free(b); delete F; return cuda_fail(ctx, e, "serve: outputs"); }
