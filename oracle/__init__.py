@@ -27,6 +27,8 @@ K_OF = (6, 12, 12, 12, 14)
 NONE, SC, FCC, HCP, ICO, BCC = range(6)
 ALLOY_NONE, ALLOY_PURE, ALLOY_L10, ALLOY_L12_MAJ, ALLOY_L12_MIN, ALLOY_B2 = range(6)
 ALL_TEMPLATES = 0x1F
+ORDERINGS = {"euclidean": 0, "topological": 1}
+TOPO_N = 18
 
 _lib = None
 
@@ -67,7 +69,9 @@ def lib():
         L.ptmo_frame_free.restype = None
         L.ptmo_knn.argtypes = [P, C.c_int64, C.c_int, P, P, P, P, P]
         L.ptmo_quantise.argtypes = [C.c_int, P, P]
-        L.ptmo_classify.argtypes = [P, P, C.c_uint32, C.c_double, P, C.c_int64] + [P] * 9
+        L.ptmo_classify.argtypes = [P, P, C.c_uint32, C.c_double, C.c_int, P, C.c_int64] + [P] * 9
+        L.ptmo_voronoi_areas.argtypes = [C.c_int, P, P]
+        L.ptmo_topo_knn.argtypes = [P, C.c_int64, P, P, P]
         rc = L.ptmo_init()
         if rc:
             raise RuntimeError(f"oracle template construction failed ({rc})")
@@ -190,8 +194,19 @@ class Frame:
         m = lib().ptmo_knn(self.h, atom, k, _p(ids), _p(imgs), _p(drc), _p(dre), _p(d2))
         return ids[:m], imgs[:m], drc[:m], dre[:m], d2[:m]
 
+    def topo_knn(self, atom: int):
+        """Ids, images (k x 3) of the first min(14, m) neighbours in topological
+        order, and the Voronoi face areas of the 18 nearest by Euclidean rank."""
+        ids = np.zeros(14, np.int32)
+        imgs = np.zeros((14, 3), np.int32)
+        areas = np.zeros(TOPO_N)
+        k = lib().ptmo_topo_knn(self.h, atom, _p(ids), _p(imgs), _p(areas))
+        return ids[:k], imgs[:k], areas
+
     def classify(self, atoms=None, species=None, mask=ALL_TEMPLATES, rmsd_max=np.inf,
-                 threads: int | None = None, chunk: int = 64):
+                 threads: int | None = None, chunk: int = 64, ordering: str = "euclidean"):
+        """ordering "euclidean" (14 nearest) or "topological" (Eq. 5: the 18
+        nearest reordered by Voronoi face area, first 14 kept)."""
         atoms = np.arange(self.n, dtype=np.int64) if atoms is None else np.ascontiguousarray(atoms, np.int64)
         m = len(atoms)
         sp = None if species is None else np.ascontiguousarray(species, np.int8)
@@ -205,7 +220,7 @@ class Frame:
 
         def run(lo, hi):
             ptrs = [out[k][lo:hi].ctypes.data_as(C.c_void_p) for k in keys]
-            rc = lib().ptmo_classify(self.h, _p(sp), mask, rmsd_max,
+            rc = lib().ptmo_classify(self.h, _p(sp), mask, rmsd_max, ORDERINGS[ordering],
                                      atoms[lo:hi].ctypes.data_as(C.c_void_p), hi - lo, *ptrs)
             if rc:
                 raise RuntimeError(f"oracle classify failed ({rc})")
@@ -220,11 +235,11 @@ class Frame:
 
 
 def classify_frame(frame, atoms=None, mask=ALL_TEMPLATES, rmsd_max=np.inf, threads=None,
-                   species="frame"):
+                   species="frame", ordering="euclidean"):
     """Classify atoms of an ``inputs.Frame``-like object (positions, cell, pbc, species)."""
     sp = frame.species if isinstance(species, str) and species == "frame" else species
     F = Frame(frame.positions, frame.cell, frame.pbc)
-    return F.classify(atoms, species=sp, mask=mask, rmsd_max=rmsd_max, threads=threads)
+    return F.classify(atoms, species=sp, mask=mask, rmsd_max=rmsd_max, threads=threads, ordering=ordering)
 
 
 # ------------------------------------------------------------ post-processing
@@ -263,3 +278,13 @@ def rmsd_histogram(structure: np.ndarray, rmsd: np.ndarray, nbins: int, rmsd_max
         b = np.floor((v * scale).astype(np.float32)).astype(np.int64)
         out[S - 1] = np.bincount(np.minimum(b, nbins), minlength=nbins + 1)
     return out
+
+
+def voronoi_areas(v: np.ndarray) -> np.ndarray:
+    """Face areas of the Voronoi cell of the origin among the points v (m x 3):
+    the bisector plane of each point clipped by the others (Sec. 3, Eq. 5)."""
+    v = np.ascontiguousarray(v, np.float64)
+    a = np.zeros(len(v))
+    if lib().ptmo_voronoi_areas(len(v), _p(v), _p(a)):
+        raise ValueError("1 to 64 points")
+    return a

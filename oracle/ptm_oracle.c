@@ -846,6 +846,93 @@ static int knn(const frame_t *F, int64_t i, int kmax, cand_t *out) {
   return -1;
 }
 
+/* ---------------------------------------- topological ordering (Sec. 3, Eq. 5) */
+#define TOPO_N 18          /* neighbours whose Voronoi faces are measured (Sec. 9) */
+#define TOPO_BAND 1e-3     /* areas closer than this x the mean squared distance tie */
+
+/* Area of the face between the Voronoi cell of the origin and that of point j,
+   the cell taken among the m points v (the origin's neighbours): the bisector
+   plane x.v_j = |v_j|^2 / 2, clipped by every other half-space
+   x.v_i <= |v_i|^2 / 2.  The plane is parametrised by an orthonormal basis,
+   a square of half-width R (far outside any bounded cell) is clipped one
+   half-plane at a time, and the area is the shoelace formula; 0 when nothing
+   is left (the cells are not adjacent). */
+static double voronoi_face_area(int m, const double (*v)[3], int j, double R) {
+  double n[3] = {v[j][0], v[j][1], v[j][2]};
+  double nn = sqrt(dot3(n, n));
+  double u[3] = {n[0] / nn, n[1] / nn, n[2] / nn};
+  double a[3] = {fabs(u[0]) < 0.6 ? 1.0 : 0.0, fabs(u[0]) < 0.6 ? 0.0 : 1.0, 0.0};
+  double e1[3], e2[3];
+  cross3(u, a, e1);
+  double l1 = sqrt(dot3(e1, e1));
+  for (int c = 0; c < 3; c++) e1[c] /= l1;
+  cross3(u, e1, e2);
+  double p0[3] = {0.5 * n[0], 0.5 * n[1], 0.5 * n[2]};
+  double P[64][2], Q[64][2];
+  int np = 4;
+  P[0][0] = -R; P[0][1] = -R; P[1][0] = R; P[1][1] = -R; P[2][0] = R; P[2][1] = R; P[3][0] = -R; P[3][1] = R;
+  for (int i = 0; i < m && np > 0; i++) {
+    if (i == j) continue;
+    /* v_i . (p0 + s e1 + t e2) <= |v_i|^2 / 2   <=>   A s + B t <= Cc */
+    double A = dot3(v[i], e1), B = dot3(v[i], e2), Cc = 0.5 * dot3(v[i], v[i]) - dot3(v[i], p0);
+    int nq = 0;
+    for (int k = 0; k < np; k++) {
+      const double *x = P[k], *y = P[(k + 1) % np];
+      double fx = A * x[0] + B * x[1] - Cc, fy = A * y[0] + B * y[1] - Cc;
+      if (fx <= 0) { Q[nq][0] = x[0]; Q[nq][1] = x[1]; nq++; }
+      if ((fx < 0 && fy > 0) || (fx > 0 && fy < 0)) {
+        double t = fx / (fx - fy);
+        Q[nq][0] = x[0] + t * (y[0] - x[0]); Q[nq][1] = x[1] + t * (y[1] - x[1]); nq++;
+      }
+    }
+    np = nq;
+    memcpy(P, Q, sizeof(double) * 2 * nq);
+  }
+  double s2 = 0;
+  for (int k = 0; k < np; k++) s2 += P[k][0] * P[(k + 1) % np][1] - P[(k + 1) % np][0] * P[k][1];
+  return fabs(0.5 * s2);
+}
+
+typedef struct { double area; int rank; } topo_t;
+static int cmp_topo(const void *a, const void *b) {
+  const topo_t *x = a, *y = b;
+  if (x->area != y->area) return x->area > y->area ? -1 : 1;
+  return x->rank - y->rank;
+}
+
+/* Reorder the m Euclidean-ordered neighbours nb (m <= TOPO_N) by Eq. 5: face
+   area of the Voronoi cell descending, then distance.  Areas are grouped when
+   consecutive ones (in descending order) differ by at most TOPO_BAND x the
+   mean squared neighbour distance; inside a group the Euclidean order (distance,
+   then atom id, then image) decides.  FP64 exact neighbour vectors. */
+static void topo_order(int m, cand_t *nb, double *areas_out) {
+  double v[TOPO_N][3], mean2 = 0, dmax = 0;
+  for (int t = 0; t < m; t++) {
+    for (int c = 0; c < 3; c++) v[t][c] = nb[t].dre[c];
+    double d2 = dot3(v[t], v[t]);
+    mean2 += d2;
+    if (d2 > dmax) dmax = d2;
+  }
+  mean2 /= m;
+  double R = 10.0 * sqrt(dmax);
+  topo_t T[TOPO_N];
+  for (int t = 0; t < m; t++) { T[t].area = voronoi_face_area(m, (const double (*)[3])v, t, R); T[t].rank = t; }
+  if (areas_out) for (int t = 0; t < m; t++) areas_out[t] = T[t].area;
+  qsort(T, m, sizeof(topo_t), cmp_topo);
+  /* group ids by the band, then order by (group, Euclidean rank) */
+  int group[TOPO_N];
+  for (int t = 0, g = 0; t < m; t++) {
+    if (t > 0 && T[t - 1].area - T[t].area > TOPO_BAND * mean2) g++;
+    group[T[t].rank] = g;
+  }
+  int order[TOPO_N], k = 0;
+  for (int g = 0; k < m; g++)
+    for (int t = 0; t < m; t++) if (group[t] == g) order[k++] = t;
+  cand_t tmp[TOPO_N];
+  for (int t = 0; t < m; t++) tmp[t] = nb[order[t]];
+  memcpy(nb, tmp, sizeof(cand_t) * m);
+}
+
 /* A frame handle holds the positions (not copied), the cell and the fractional
    coordinates used to bound the image search; it is read-only afterwards, so
    several threads may classify disjoint atom lists of one frame at once. */
@@ -949,15 +1036,23 @@ static void alloy_label(int S, const uint8_t *cp, const int32_t *nid, int64_t ce
 }
 
 static void classify_atom(const frame_t *F, int64_t i, const int8_t *species, uint32_t mask,
-                          double rmsd_max, result_t *res) {
+                          double rmsd_max, int ordering, result_t *res) {
   memset(res, 0, sizeof *res);
   res->rmsd = INFINITY;
   res->quat[0] = 1.0;
   for (int s = 0; s < NMAX; s++) res->corr[s] = -1;
   for (int s = 0; s < KMAX; s++) res->nbr[s] = -1;
-  cand_t nb[KMAX];
-  int m = knn(F, i, KMAX, nb);
-  if (m < 0) return;
+  cand_t nb[TOPO_N];
+  int m;
+  if (ordering == 1) {                  /* topological: 18 nearest, reordered, first 14 kept */
+    m = knn(F, i, TOPO_N, nb);
+    if (m < 0) return;
+    topo_order(m, nb, NULL);
+    if (m > KMAX) m = KMAX;
+  } else {
+    m = knn(F, i, KMAX, nb);
+    if (m < 0) return;
+  }
   for (int t = 0; t < m; t++) res->nbr[t] = nb[t].j;
   double drc[3 * KMAX];
   int64_t q[3 * KMAX];
@@ -1089,7 +1184,7 @@ static void classify_atom(const frame_t *F, int64_t i, const int8_t *species, ui
 
 /* Classify the atoms listed in `atoms` (m entries) of a frame handle.  Outputs
    are indexed by list position; any output pointer may be NULL. */
-int ptmo_classify(void *h, const int8_t *species, uint32_t mask, double rmsd_max,
+int ptmo_classify(void *h, const int8_t *species, uint32_t mask, double rmsd_max, int ordering,
                   const int64_t *atoms, int64_t m,
                   int8_t *structure, int8_t *alloy, double *rmsd, double *scale,
                   double *quat, double *strain, int32_t *corr, int32_t *nbrs, int32_t *ncand) {
@@ -1097,7 +1192,7 @@ int ptmo_classify(void *h, const int8_t *species, uint32_t mask, double rmsd_max
   const frame_t *F = h;
   for (int64_t t = 0; t < m; t++) {
     result_t r;
-    classify_atom(F, atoms[t], species, mask, rmsd_max, &r);
+    classify_atom(F, atoms[t], species, mask, rmsd_max, ordering, &r);
     if (structure) structure[t] = r.structure;
     if (alloy) alloy[t] = r.alloy;
     if (rmsd) rmsd[t] = r.rmsd;
@@ -1109,4 +1204,26 @@ int ptmo_classify(void *h, const int8_t *species, uint32_t mask, double rmsd_max
     if (ncand) ncand[t] = r.ncand;
   }
   return 0;
+}
+
+/* Voronoi face areas of the origin's cell among m points (Sec. 3, Eq. 5). */
+int ptmo_voronoi_areas(int m, const double *v, double *area) {
+  if (m < 1 || m > 64) return -1;
+  double dmax = 0;
+  for (int t = 0; t < m; t++) { double d2 = dot3(v + 3 * t, v + 3 * t); if (d2 > dmax) dmax = d2; }
+  for (int t = 0; t < m; t++) area[t] = voronoi_face_area(m, (const double (*)[3])v, t, 10.0 * sqrt(dmax));
+  return 0;
+}
+
+/* The topological order of an atom's neighbours: ids and images of the first
+   min(14, m) of its 18 nearest after Eq. 5, and the 18 areas by Euclidean rank. */
+int ptmo_topo_knn(void *h, int64_t atom, int32_t *ids, int32_t *imgs, double *areas) {
+  const frame_t *F = h;
+  cand_t nb[TOPO_N];
+  int m = knn(F, atom, TOPO_N, nb);
+  if (m < 0) return m;
+  topo_order(m, nb, areas);
+  int k = m > KMAX ? KMAX : m;
+  for (int t = 0; t < k; t++) { ids[t] = nb[t].j; for (int c = 0; c < 3; c++) imgs[3 * t + c] = nb[t].n[c]; }
+  return k;
 }
