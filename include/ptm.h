@@ -56,6 +56,14 @@ enum { PTM_ALLOY_NONE = 0, PTM_ALLOY_PURE = 1, PTM_ALLOY_L10 = 2, PTM_ALLOY_L12_
 /* Position element types. */
 enum { PTM_F32 = 0, PTM_F64 = 1 };
 
+/* Neighbour ordering (Sec. 3, Eq. 5).  Euclidean: the 14 nearest images by
+   distance (then atom id, then image).  Topological: the 18 nearest, reordered
+   by the area of the face their Voronoi cell shares with the atom's (the cell
+   taken among those 18), larger first, then nearer; areas within 1e-3 of the
+   mean squared neighbour distance count as equal; the first 14 are used.
+   Topological ordering adds one per-atom kernel (about the cost of the rest). */
+enum { PTM_ORDER_EUCLIDEAN = 0, PTM_ORDER_TOPOLOGICAL = 1 };
+
 /* Arithmetic of the metric steps (QCP, selection, outputs).  The exact hull
    predicates, canonical codes and lookup are the same in both. */
 enum {
@@ -84,6 +92,9 @@ typedef struct {
   uint8_t pbc[3];            /* 1 = periodic along cell vector i */
   uint32_t template_mask;    /* PTM_MASK_* bits; 0 means PTM_MASK_ALL */
   double rmsd_max;           /* atoms whose best RMSD exceeds it are unmatched; INFINITY = none */
+  int ordering;              /* neighbour ordering (Sec. 3): PTM_ORDER_EUCLIDEAN (0) or
+                                PTM_ORDER_TOPOLOGICAL; topological ordering is accepted by
+                                ptm_classify_frame and ptm_classify_frame_host only */
 } ptm_frame;
 
 /* Per-atom outputs, indexed by atom.  Any pointer may be NULL to skip it.
@@ -122,7 +133,9 @@ typedef struct {
   int64_t candidates;        /* correspondences scored by QCP (symmetry-reduced, Appendix A) */
   int64_t candidate_points;  /* sum over those correspondences of the point count N = k + 1 */
   double pipeline_ms;        /* device time of the whole call (cell list + classification) */
-  double atom_kernel_ms;     /* device time of the per-atom classification kernel */
+  double atom_kernel_ms;     /* device time of the per-atom kernels (ordering + classification) */
+  int64_t topo_fp64;         /* atoms whose topological order was decided in FP64 (an area
+                                gap at the edge of the equal-area band) */
 } ptm_stats;
 
 /* Create a context on options->device (NULL options: device 0, default budget).

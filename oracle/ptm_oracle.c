@@ -879,8 +879,8 @@ static double voronoi_face_area(int m, const double (*v)[3], int j, double R) {
     for (int k = 0; k < np; k++) {
       const double *x = P[k], *y = P[(k + 1) % np];
       double fx = A * x[0] + B * x[1] - Cc, fy = A * y[0] + B * y[1] - Cc;
-      if (fx <= 0) { Q[nq][0] = x[0]; Q[nq][1] = x[1]; nq++; }
-      if ((fx < 0 && fy > 0) || (fx > 0 && fy < 0)) {
+      if (fx <= 0 && nq < 64) { Q[nq][0] = x[0]; Q[nq][1] = x[1]; nq++; }
+      if (((fx < 0 && fy > 0) || (fx > 0 && fy < 0)) && nq < 64) {
         double t = fx / (fx - fy);
         Q[nq][0] = x[0] + t * (y[0] - x[0]); Q[nq][1] = x[1] + t * (y[1] - x[1]); nq++;
       }

@@ -27,7 +27,7 @@ class ptm_options(C.Structure):
 class ptm_frame(C.Structure):
     _fields_ = [("n_atoms", C.c_int64), ("positions", C.c_void_p), ("pos_dtype", C.c_int),
                 ("species", C.c_void_p), ("cell", C.c_double * 9), ("pbc", C.c_uint8 * 3),
-                ("template_mask", C.c_uint32), ("rmsd_max", C.c_double)]
+                ("template_mask", C.c_uint32), ("rmsd_max", C.c_double), ("ordering", C.c_int)]
 
 
 class ptm_outputs(C.Structure):
@@ -37,7 +37,7 @@ class ptm_outputs(C.Structure):
 class ptm_stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("atoms", "matched", "knn_wide", "knn_fail", "sos", "qcp_fp64",
                                          "tie_fp64", "internal", "candidates", "candidate_points")] + \
-               [("pipeline_ms", C.c_double), ("atom_kernel_ms", C.c_double)]
+               [("pipeline_ms", C.c_double), ("atom_kernel_ms", C.c_double), ("topo_fp64", C.c_int64)]
 
 
 class ptm_tuning(C.Structure):
@@ -123,7 +123,10 @@ def measure_fma_peak(kind="fp32", device=0, stream=None) -> float:
     return v.value
 
 
-def _frame(n, pos_ptr, dtype_code, species_ptr, cell, pbc, mask, rmsd_max) -> ptm_frame:
+ORDERINGS = {"euclidean": 0, "topological": 1}
+
+
+def _frame(n, pos_ptr, dtype_code, species_ptr, cell, pbc, mask, rmsd_max, ordering="euclidean") -> ptm_frame:
     f = ptm_frame()
     f.n_atoms = int(n)
     f.positions = pos_ptr
@@ -136,6 +139,7 @@ def _frame(n, pos_ptr, dtype_code, species_ptr, cell, pbc, mask, rmsd_max) -> pt
         f.pbc[i] = 1 if pbc[i] else 0
     f.template_mask = int(mask)
     f.rmsd_max = float(rmsd_max) if rmsd_max is not None else math.inf
+    f.ordering = ORDERINGS[ordering]
     return f
 
 
@@ -171,7 +175,7 @@ class PTM:
 
     # ---------------------------------------------------------------- device
     def classify(self, positions, cell, pbc=(True, True, True), species=None, mask=MASK_ALL,
-                 rmsd_max=math.inf, out=None, outputs=OUTPUT_NAMES, stream=None):
+                 rmsd_max=math.inf, out=None, outputs=OUTPUT_NAMES, stream=None, ordering="euclidean"):
         """Classify every atom of a frame held in CUDA tensors (``ptm_classify_frame``).
 
         positions: (n, 3) float32 or float64 CUDA tensor; species: (n,) int8 or None.
@@ -200,7 +204,7 @@ class PTM:
         for name in OUTPUT_FIELDS:
             t = out.get(name)
             setattr(o, name, t.data_ptr() if t is not None else None)
-        f = _frame(n, positions.data_ptr(), code, sp_ptr, cell, pbc, mask, rmsd_max)
+        f = _frame(n, positions.data_ptr(), code, sp_ptr, cell, pbc, mask, rmsd_max, ordering)
         st = stream if stream is not None else torch.cuda.current_stream(dev)
         self._keep = (positions, species)
         self._check(self.lib.ptm_classify_frame(self.h, C.byref(f), C.byref(o), C.c_void_p(st.cuda_stream)),
@@ -209,7 +213,7 @@ class PTM:
 
     # ------------------------------------------------------------------ host
     def classify_host(self, positions, cell, pbc=(True, True, True), species=None, mask=MASK_ALL,
-                      rmsd_max=math.inf, out=None, outputs=OUTPUT_NAMES, stream=None):
+                      rmsd_max=math.inf, out=None, outputs=OUTPUT_NAMES, stream=None, ordering="euclidean"):
         """Same as ``classify`` for host (numpy) buffers (``ptm_classify_frame_host``):
         the library copies to and from the device and returns when done."""
         pos = np.ascontiguousarray(positions)
@@ -224,7 +228,7 @@ class PTM:
             a = out.get(name)
             setattr(o, name, a.ctypes.data if a is not None else None)
         f = _frame(n, pos.ctypes.data, PTM_F64 if pos.dtype == np.float64 else PTM_F32,
-                   sp.ctypes.data if sp is not None else None, cell, pbc, mask, rmsd_max)
+                   sp.ctypes.data if sp is not None else None, cell, pbc, mask, rmsd_max, ordering)
         st = 0 if stream is None else stream.cuda_stream
         self._check(self.lib.ptm_classify_frame_host(self.h, C.byref(f), C.byref(o), C.c_void_p(st)),
                     "ptm_classify_frame_host")

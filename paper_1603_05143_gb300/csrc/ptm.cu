@@ -16,6 +16,7 @@
 #define PTM_TBL_CONST __constant__ const
 #define PTM_TBL_GLOBAL __device__ const
 #include "ptm_kernels.cuh"
+#include "ptm_topo.cuh"
 
 // =================================================================== host
 using namespace ptm;
@@ -42,6 +43,9 @@ struct ptm_context {
   float *o_rmsd = nullptr, *o_scale = nullptr, *o_quat = nullptr, *o_strain = nullptr;
   int32_t *o_corr = nullptr;
   float *o_vm = nullptr, *o_rf = nullptr;
+  // topological order of every atom's 14 neighbours (k_topo -> k_atoms)
+  int2 *topo = nullptr;
+  size_t cap_topo = 0;
 };
 
 static ptm_status cuda_fail(ptm_context *ctx, cudaError_t e, const char *what) {
@@ -94,6 +98,7 @@ static bool finite_cell(const double *H) {
 // Enqueue the whole pipeline for one frame whose buffers are on the device.
 static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_outputs *o, cudaStream_t st) {
   if (!f || !o) return PTM_ERR_INVALID_ARG;
+  if (f->ordering != PTM_ORDER_EUCLIDEAN && f->ordering != PTM_ORDER_TOPOLOGICAL) return PTM_ERR_INVALID_ARG;
   if (f->n_atoms < 1 || f->n_atoms >= (1ll << 31) || !f->positions) return PTM_ERR_INVALID_ARG;
   if (f->pos_dtype != PTM_F32 && f->pos_dtype != PTM_F64) return PTM_ERR_INVALID_ARG;
   if (!finite_cell(f->cell)) return PTM_ERR_INVALID_ARG;
@@ -133,6 +138,14 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
   }
   ptm_status rs = grow(ctx, (size_t)n, ncell, f64);
   if (rs != PTM_OK) return rs;
+  const bool topological = f->ordering == PTM_ORDER_TOPOLOGICAL;
+  if (topological && (size_t)n > ctx->cap_topo) {
+    cudaFree(ctx->topo);
+    ctx->topo = nullptr;
+    ctx->cap_topo = 0;
+    CK(cudaMalloc(&ctx->topo, (size_t)n * PTM_KNN * sizeof(int2)));
+    ctx->cap_topo = (size_t)n;
+  }
 
   FrameDesc desc;
   FrameDesc *hd = &desc;
@@ -197,6 +210,11 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
                                ctx->cell_start, ctx->sorted, ctx->sbin, ctx->wrapv);
   const unsigned ga = (unsigned)((n + PTM_BLOCK - 1) / PTM_BLOCK);
   CK(cudaEventRecord(ctx->ev[1], st));
+  if (topological) {
+    desc.topo = ctx->topo;
+    if (f64) k_topo<true><<<ga, PTM_BLOCK, topo_smem_bytes(), st>>>(desc, ctx->topo);
+    else k_topo<false><<<ga, PTM_BLOCK, topo_smem_bytes(), st>>>(desc, ctx->topo);
+  }
   if (ctx->precision == PTM_PREC_FP64) {
     if (f64) k_atoms<true, true><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
     else k_atoms<false, true><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
@@ -279,6 +297,7 @@ ptm_status ptm_destroy(ptm_context *ctx) {
   cudaFree(ctx->hpos); cudaFree(ctx->hspecies);
   cudaFree(ctx->o_struct); cudaFree(ctx->o_alloy); cudaFree(ctx->o_rmsd); cudaFree(ctx->o_scale);
   cudaFree(ctx->o_quat); cudaFree(ctx->o_strain); cudaFree(ctx->o_corr); cudaFree(ctx->o_vm); cudaFree(ctx->o_rf);
+  cudaFree(ctx->topo);
   delete ctx;
   return PTM_OK;
 }
@@ -370,6 +389,7 @@ ptm_status ptm_get_stats(ptm_context *ctx, ptm_stats *out) {
   out->sos = (int64_t)c[C_SOS];
   out->qcp_fp64 = (int64_t)c[C_QCP64];
   out->tie_fp64 = (int64_t)c[C_TIE64];
+  out->topo_fp64 = (int64_t)c[C_TOPO64];
   out->internal = (int64_t)c[C_INTERNAL];
   return PTM_OK;
 }
@@ -382,6 +402,7 @@ ptm_status ptm_get_stats(ptm_context *ctx, ptm_stats *out) {
 static ptm_status setup_frame(const ptm_frame *f, double cell_factor, FrameDesc *desc, BinParams *bp,
                               size_t *ncell_out) {
   if (!f || f->n_atoms < 1 || f->n_atoms >= (1ll << 31) || !f->positions) return PTM_ERR_INVALID_ARG;
+  if (f->ordering != PTM_ORDER_EUCLIDEAN) return PTM_ERR_INVALID_ARG;     // batches: Euclidean only
   if (f->pos_dtype != PTM_F32 && f->pos_dtype != PTM_F64) return PTM_ERR_INVALID_ARG;
   if (!finite_cell(f->cell)) return PTM_ERR_INVALID_ARG;
   const double *H = f->cell;
@@ -670,7 +691,8 @@ extern "C" ptm_status ptm_batch_stats(ptm_batch *b, ptm_stats *out) {
   cudaGetLastError();
   out->atoms = (int64_t)c[C_ATOMS]; out->matched = (int64_t)c[C_MATCHED]; out->knn_wide = (int64_t)c[C_KNN_WIDE];
   out->knn_fail = (int64_t)c[C_KNN_FAIL]; out->sos = (int64_t)c[C_SOS]; out->qcp_fp64 = (int64_t)c[C_QCP64];
-  out->tie_fp64 = (int64_t)c[C_TIE64]; out->internal = (int64_t)c[C_INTERNAL];
+  out->tie_fp64 = (int64_t)c[C_TIE64];
+  out->topo_fp64 = (int64_t)c[C_TOPO64]; out->internal = (int64_t)c[C_INTERNAL];
   out->candidates = (int64_t)c[C_CAND]; out->candidate_points = (int64_t)c[C_CANDPTS];
   out->pipeline_ms = t_all;
   out->atom_kernel_ms = t_atom;
@@ -786,6 +808,7 @@ ptm_status noalloc_setup(int dev, unsigned char **out) {
 extern "C" ptm_status ptm_classify_frame_noalloc(const ptm_frame *f, const ptm_outputs *o, void *stream) {
   if (!f || !o) return PTM_ERR_INVALID_ARG;
   if (f->n_atoms < 1 || f->n_atoms > kNoallocAtoms || !f->positions) return PTM_ERR_INVALID_ARG;
+  if (f->ordering != PTM_ORDER_EUCLIDEAN) return PTM_ERR_INVALID_ARG;
   if (f->pos_dtype != PTM_F32 && f->pos_dtype != PTM_F64) return PTM_ERR_INVALID_ARG;
   if (!finite_cell(f->cell)) return PTM_ERR_INVALID_ARG;
   int dev = 0;

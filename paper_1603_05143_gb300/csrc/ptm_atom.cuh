@@ -59,12 +59,14 @@ struct FrameDesc {
   int32_t *corr;
   float *vm;                   // derived: von Mises shear strain
   float *rf;                   // derived: Rodrigues-Frank vector
+  const int2 *topo;            // topological order: [t][n] (sorted slot, image) of neighbour t, or NULL
   int *dstat;                  // [0] any atom wrapped, [1] overshoot (float bits, Angstrom)
   unsigned long long *counters;  // ptm_stats order: atoms, matched, knn_wide, knn_fail, sos, qcp_fp64, tie_fp64, internal, candidates, candidate_points
   int64_t atom_offset;         // first sorted slot of this frame (0 for a single frame)
 };
 
-enum { C_ATOMS = 0, C_MATCHED, C_KNN_WIDE, C_KNN_FAIL, C_SOS, C_QCP64, C_TIE64, C_INTERNAL, C_CAND, C_CANDPTS, C_NCOUNTERS };
+enum { C_ATOMS = 0, C_MATCHED, C_KNN_WIDE, C_KNN_FAIL, C_SOS, C_QCP64, C_TIE64, C_INTERNAL, C_CAND, C_CANDPTS, C_TOPO64,
+       C_NCOUNTERS };
 
 __device__ __forceinline__ void count(const FrameDesc &d, int which, unsigned long long v = 1) {
   atomicAdd(d.counters + which, v);

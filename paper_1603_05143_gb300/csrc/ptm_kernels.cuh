@@ -111,29 +111,29 @@ __device__ __forceinline__ bool search_complete(const FrameDesc &d, int R, float
   return rg > 0.f && d2_last < rg * rg * (1.f - 1e-3f);
 }
 
-// General kNN: the 14 nearest images of atom s by the full key (d2, atom id,
-// image), R growing until the 14th distance lies inside the radius the scanned
-// cells are guaranteed to cover.  Returns the neighbour count (14, fewer only
+// General kNN: the NK nearest images of atom s by the full key (d2, atom id,
+// image), R growing until the NK-th distance lies inside the radius the scanned
+// cells are guaranteed to cover.  Returns the neighbour count (NK, fewer only
 // for a small fully non-periodic system) or -1.
-template <bool F64>
+template <bool F64, int NK = PTM_KNN>
 __device__ __noinline__ int knn(const FrameDesc &d, int s, typename RT<F64>::T xi, typename RT<F64>::T yi,
                                 typename RT<F64>::T zi, int bx, int by, int bz, int wix, int wiy, int wiz,
-                                bool wrapped, typename RT<F64>::T (&Ld2)[PTM_KNN], int (&Lid)[PTM_KNN],
-                                int (&Ljs)[PTM_KNN], int (&Limg)[PTM_KNN]) {
+                                bool wrapped, typename RT<F64>::T (&Ld2)[NK], int (&Lid)[NK],
+                                int (&Ljs)[NK], int (&Limg)[NK]) {
   typedef typename RT<F64>::T T;
   const T INF = (T)INFINITY;
   for (int R = 1; R <= PTM_RMAX; R++) {
 #pragma unroll
-    for (int t = 0; t < PTM_KNN; t++) { Ld2[t] = INF; Lid[t] = 0x7fffffff; Ljs[t] = -1; Limg[t] = 0x7fffffff; }
+    for (int t = 0; t < NK; t++) { Ld2[t] = INF; Lid[t] = 0x7fffffff; Ljs[t] = -1; Limg[t] = 0x7fffffff; }
     scan_cells<F64>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, R,
                     [&](int j, T d2, int idj, int a0, int a1, int a2) {
-      if (!(d2 <= Ld2[PTM_KNN - 1])) return;
+      if (!(d2 <= Ld2[NK - 1])) return;
       const int img = img_pack(a0, a1, a2);
-      if (!key_less(d2, idj, img, Ld2[PTM_KNN - 1], Lid[PTM_KNN - 1], Limg[PTM_KNN - 1])) return;
+      if (!key_less(d2, idj, img, Ld2[NK - 1], Lid[NK - 1], Limg[NK - 1])) return;
       // insertion into the sorted list (all indices static: stays in registers)
       bool above = true;
 #pragma unroll
-      for (int t = PTM_KNN - 1; t >= 1; t--) {
+      for (int t = NK - 1; t >= 1; t--) {
         bool lt = key_less(d2, idj, img, Ld2[t - 1], Lid[t - 1], Limg[t - 1]);
         if (lt) { Ld2[t] = Ld2[t - 1]; Lid[t] = Lid[t - 1]; Ljs[t] = Ljs[t - 1]; Limg[t] = Limg[t - 1]; }
         else if (above) { Ld2[t] = d2; Lid[t] = idj; Ljs[t] = j; Limg[t] = img; }
@@ -141,14 +141,14 @@ __device__ __noinline__ int knn(const FrameDesc &d, int s, typename RT<F64>::T x
       }
       if (above) { Ld2[0] = d2; Lid[0] = idj; Ljs[0] = j; Limg[0] = img; }
     });
-    if (search_complete(d, R, (float)Ld2[PTM_KNN - 1])) {
+    if (search_complete(d, R, (float)Ld2[NK - 1])) {
       if (R > 1) count(d, C_KNN_WIDE);
-      return PTM_KNN;
+      return NK;
     }
     if (!d.pbc[0] && !d.pbc[1] && !d.pbc[2] && R >= max(d.nb[0], max(d.nb[1], d.nb[2]))) {
       int cnt = 0;
 #pragma unroll
-      for (int t = 0; t < PTM_KNN; t++) cnt += Ljs[t] >= 0;
+      for (int t = 0; t < NK; t++) cnt += Ljs[t] >= 0;
       return cnt;
     }
   }
@@ -175,33 +175,42 @@ __device__ __noinline__ int knn_to_scratch(const FrameDesc &d, const Scratch &sm
 // scratch rows NID / DX hold sorted index and image until the caller reads
 // them).  With no equal distances the distance order is the full key order.
 // Returns false when the general kNN must decide.
-template <bool F64>
-__device__ __forceinline__ bool knn_fast(const FrameDesc &d, const Scratch &sm, int s, typename RT<F64>::T xi,
-                                         typename RT<F64>::T yi, typename RT<F64>::T zi, int bx, int by, int bz) {
+template <bool F64, int NK, typename Put>
+__device__ __forceinline__ bool knn_fast_n(const FrameDesc &d, int s, typename RT<F64>::T xi,
+                                           typename RT<F64>::T yi, typename RT<F64>::T zi, int bx, int by, int bz,
+                                           Put &&put) {
   typedef typename RT<F64>::T T;
-  T L[PTM_KNN + 1];
+  T L[NK + 1];
 #pragma unroll
-  for (int t = 0; t <= PTM_KNN; t++) L[t] = (T)INFINITY;
+  for (int t = 0; t <= NK; t++) L[t] = (T)INFINITY;
   scan_cells<F64>(d, s, xi, yi, zi, bx, by, bz, 0, 0, 0, false, 1, [&](int j, T d2, int, int, int, int) {
-    if (!(d2 < L[PTM_KNN])) return;
+    if (!(d2 < L[NK])) return;
     T x = d2;
 #pragma unroll
-    for (int t = 0; t <= PTM_KNN; t++) { const T lo = fmin(L[t], x); x = fmax(L[t], x); L[t] = lo; }
+    for (int t = 0; t <= NK; t++) { const T lo = fmin(L[t], x); x = fmax(L[t], x); L[t] = lo; }
   });
-  bool distinct = L[PTM_KNN] < (T)INFINITY;
+  bool distinct = L[NK] < (T)INFINITY;
 #pragma unroll
-  for (int t = 0; t < PTM_KNN; t++) distinct &= L[t] < L[t + 1];
-  if (!distinct || !search_complete(d, 1, (float)L[PTM_KNN - 1])) return false;
-  const T last = L[PTM_KNN - 1];
+  for (int t = 0; t < NK; t++) distinct &= L[t] < L[t + 1];
+  if (!distinct || !search_complete(d, 1, (float)L[NK - 1])) return false;
+  const T last = L[NK - 1];
   scan_cells<F64>(d, s, xi, yi, zi, bx, by, bz, 0, 0, 0, false, 1, [&](int j, T d2, int, int a0, int a1, int a2) {
     if (!(d2 <= last)) return;
     int rank = 0;
 #pragma unroll
-    for (int t = 0; t < PTM_KNN - 1; t++) rank += L[t] < d2;
-    sm.NID(rank) = j;
-    sm.DX(rank) = __int_as_float(img_pack(a0, a1, a2));
+    for (int t = 0; t < NK - 1; t++) rank += L[t] < d2;
+    put(rank, j, img_pack(a0, a1, a2));
   });
   return true;
+}
+
+template <bool F64>
+__device__ __forceinline__ bool knn_fast(const FrameDesc &d, const Scratch &sm, int s, typename RT<F64>::T xi,
+                                         typename RT<F64>::T yi, typename RT<F64>::T zi, int bx, int by, int bz) {
+  return knn_fast_n<F64, PTM_KNN>(d, s, xi, yi, zi, bx, by, bz, [&](int rank, int j, int img) {
+    sm.NID(rank) = j;
+    sm.DX(rank) = __int_as_float(img);
+  });
 }
 
 // ---------------------------------------------------------- per-atom state
@@ -463,7 +472,18 @@ __device__ __noinline__ int rerank_fp64(const FrameDesc &d, int s, const Best bs
   load_atom<F64>(d, s, xi, yi, zi, idi);
   T Ld2[PTM_KNN];
   int Lid[PTM_KNN], Ljs[PTM_KNN], Limg[PTM_KNN];
-  int cnt = knn<F64>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, Ld2, Lid, Ljs, Limg);
+  int cnt;
+  if (d.topo) {
+    cnt = 0;
+    for (int t = 0; t < PTM_KNN; t++) {
+      const int2 e = d.topo[(int64_t)t * d.n + s];
+      Ljs[t] = e.x;
+      Limg[t] = e.y;
+      cnt += e.x >= 0;
+    }
+  } else {
+    cnt = knn<F64>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, Ld2, Lid, Ljs, Limg);
+  }
   if (cnt < 0) return -1;
   double ex[PTM_KNN], ey[PTM_KNN], ez[PTM_KNN];
   for (int t = 0; t < cnt; t++) vec_fp64<F64>(d, xi, yi, zi, Ljs[t], Limg[t], ex[t], ey[t], ez[t]);
@@ -773,8 +793,19 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
   int cnt;
   unsigned hmask;
   {
-    if (!wrapped && knn_fast<F64>(d, sm, s, xi, yi, zi, bx, by, bz)) cnt = PTM_KNN;
-    else cnt = knn_to_scratch<F64>(d, sm, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped);
+    if (d.topo) {                       // neighbours in topological order (Eq. 5), from k_topo
+      cnt = 0;
+      for (int t = 0; t < PTM_KNN; t++) {
+        const int2 e = d.topo[(int64_t)t * d.n + s];
+        sm.NID(t) = e.x;
+        sm.DX(t) = __int_as_float(e.y);
+        cnt += e.x >= 0;
+      }
+    } else if (!wrapped && knn_fast<F64>(d, sm, s, xi, yi, zi, bx, by, bz)) {
+      cnt = PTM_KNN;
+    } else {
+      cnt = knn_to_scratch<F64>(d, sm, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped);
+    }
     hmask = __ballot_sync(live, cnt >= 4);       // lanes that go on to the hulls
     if (cnt < 4) { write_unmatched(d, idi); return; }
     // rows NID / DX hold (sorted index, image) of each neighbour; move them to

@@ -343,6 +343,7 @@ extern "C" ptm_status ptm_submit(ptm_server *S, const ptm_frame *frame, const pt
   if (!S || !frame || !out || !ticket) return PTM_ERR_INVALID_ARG;
   if (frame->n_atoms < 1 || frame->n_atoms >= (1ll << 31) || !frame->positions) return PTM_ERR_INVALID_ARG;
   if (frame->pos_dtype != PTM_F32 && frame->pos_dtype != PTM_F64) return PTM_ERR_INVALID_ARG;
+  if (frame->ordering != PTM_ORDER_EUCLIDEAN) return PTM_ERR_INVALID_ARG;
   if (!finite_cell(frame->cell)) return PTM_ERR_INVALID_ARG;
   Request *r = new (std::nothrow) Request();
   if (!r) return PTM_ERR_OUT_OF_MEMORY;

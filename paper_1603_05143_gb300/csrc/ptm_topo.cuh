@@ -1,0 +1,200 @@
+// Topological neighbour ordering (Sec. 3, Eq. 5): for every atom, its 18
+// nearest images (the distance contract of the Euclidean path), the area of the
+// face its Voronoi cell shares with each of them (the cell taken among those 18,
+// as Sec. 9 does with the Delaunay triangulation of the centre and its 18
+// nearest), and the order "larger face first, then nearer".  The first 14 in
+// that order replace the 14 nearest for the rest of the method.
+//
+// Face area of neighbour j: the bisector plane x.v_j = |v_j|^2 / 2, clipped by
+// every other neighbour's half-space x.v_i <= |v_i|^2 / 2 (one half-plane at a
+// time, in plane coordinates), then the shoelace formula; 0 when nothing is
+// left.  Floating point cannot reproduce exact ties between equal faces (the 12
+// faces of a perfect fcc cell), so areas that follow each other in descending
+// order within TOPO_BAND x the mean squared distance form one group, ordered by
+// the Euclidean rank (distance, atom id, image).  FP32 areas decide unless a
+// gap lies within TOPO_GUARD of the band edge; then the atom's areas are
+// recomputed in FP64 from FP64 neighbour vectors.
+
+namespace ptm {
+
+#define PTM_TOPO_N 18
+#define PTM_TOPO_BAND 1e-3
+#define PTM_TOPO_GUARD 2e-5
+#define PTM_TOPO_WORDS (2 * PTM_TOPO_N + 3 * PTM_TOPO_N + PTM_TOPO_N)   // 32-bit words per thread
+
+// Area of the Voronoi face of neighbour j among the m vectors V(i, c).
+template <typename T, typename Vec>
+__device__ T topo_face_area(int m, int j, T R, Vec V) {
+  const T n0 = V(j, 0), n1 = V(j, 1), n2 = V(j, 2);
+  const T nn = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+  const T u0 = n0 / nn, u1 = n1 / nn, u2 = n2 / nn;
+  // e1 = u x a with a the axis least aligned with u, e2 = u x e1
+  const bool ax = fabs(u0) < (T)0.6;
+  const T a0 = ax ? (T)1 : (T)0, a1 = ax ? (T)0 : (T)1;
+  T e10 = u1 * (T)0 - u2 * a1, e11 = u2 * a0 - u0 * (T)0, e12 = u0 * a1 - u1 * a0;
+  const T l1 = sqrt(e10 * e10 + e11 * e11 + e12 * e12);
+  e10 /= l1; e11 /= l1; e12 /= l1;
+  const T e20 = u1 * e12 - u2 * e11, e21 = u2 * e10 - u0 * e12, e22 = u0 * e11 - u1 * e10;
+  const T p0 = n0 / 2, p1 = n1 / 2, p2 = n2 / 2;
+  // a convex polygon gains at most one vertex per clip (4 + 17 < VMAX);
+  // rounding on a nearly degenerate polygon could emit more, so writes stop at
+  // the buffer's end (the polygon then has next to no area either way)
+  constexpr int VMAX = PTM_TOPO_N + 8;
+  T P[2 * VMAX], Q[2 * VMAX];
+  int np = 4;
+  P[0] = -R; P[1] = -R; P[2] = R; P[3] = -R; P[4] = R; P[5] = R; P[6] = -R; P[7] = R;
+  for (int i = 0; i < m && np > 0; i++) {
+    if (i == j) continue;
+    const T w0 = V(i, 0), w1 = V(i, 1), w2 = V(i, 2);
+    const T A = w0 * e10 + w1 * e11 + w2 * e12, B = w0 * e20 + w1 * e21 + w2 * e22;
+    const T C = (w0 * w0 + w1 * w1 + w2 * w2) / 2 - (w0 * p0 + w1 * p1 + w2 * p2);
+    int nq = 0;
+    for (int k = 0; k < np; k++) {
+      const int k1 = k + 1 == np ? 0 : k + 1;
+      const T xs = P[2 * k], xt = P[2 * k + 1], ys = P[2 * k1], yt = P[2 * k1 + 1];
+      const T fx = A * xs + B * xt - C, fy = A * ys + B * yt - C;
+      if (fx <= 0 && nq < VMAX) { Q[2 * nq] = xs; Q[2 * nq + 1] = xt; nq++; }
+      if (((fx < 0 && fy > 0) || (fx > 0 && fy < 0)) && nq < VMAX) {
+        const T tt = fx / (fx - fy);
+        Q[2 * nq] = xs + tt * (ys - xs); Q[2 * nq + 1] = xt + tt * (yt - xt); nq++;
+      }
+    }
+    np = nq;
+    for (int k = 0; k < 2 * nq; k++) P[k] = Q[k];
+  }
+  T s2 = 0;
+  for (int k = 0; k < np; k++) {
+    const int k1 = k + 1 == np ? 0 : k + 1;
+    s2 += P[2 * k] * P[2 * k1 + 1] - P[2 * k1] * P[2 * k + 1];
+  }
+  return fabs(s2) / 2;
+}
+
+// Order o[0..m) of neighbour ranks by (area descending, rank ascending), then
+// group by the band and order each group by rank.  Returns true when a gap
+// between consecutive areas lies within the guard of the band edge.
+template <typename T>
+__device__ bool topo_order(int m, const T *area, T mean2, int *o) {
+  for (int k = 0; k < m; k++) o[k] = k;
+  for (int k = 1; k < m; k++) {                       // insertion sort, stable in rank
+    const int x = o[k];
+    int p = k;
+    while (p > 0 && area[o[p - 1]] < area[x]) { o[p] = o[p - 1]; p--; }
+    o[p] = x;
+  }
+  const T band = (T)PTM_TOPO_BAND * mean2, guard = (T)PTM_TOPO_GUARD * mean2;
+  bool near = false;
+  int g0 = 0;
+  for (int k = 1; k <= m; k++) {
+    bool split = k == m;
+    if (k < m) {
+      const T gap = area[o[k - 1]] - area[o[k]];
+      near |= fabs(gap - band) <= guard;
+      split = gap > band;
+    }
+    if (split) {                                      // group o[g0..k): order by rank
+      for (int a = g0 + 1; a < k; a++) {
+        const int x = o[a];
+        int p = a;
+        while (p > g0 && o[p - 1] > x) { o[p] = o[p - 1]; p--; }
+        o[p] = x;
+      }
+      g0 = k;
+    }
+  }
+  return near;
+}
+
+template <bool F64>
+__global__ void __launch_bounds__(PTM_BLOCK) k_topo(const __grid_constant__ FrameDesc d, int2 *__restrict__ out) {
+  typedef typename RT<F64>::T TI;
+  extern __shared__ __align__(16) unsigned char tsm_raw[];
+  int *tsm = (int *)tsm_raw;
+  const int t = threadIdx.x;
+  auto J = [&](int k) -> int & { return tsm[k * PTM_BLOCK + t]; };
+  auto IMG = [&](int k) -> int & { return tsm[(PTM_TOPO_N + k) * PTM_BLOCK + t]; };
+  auto VF = [&](int k, int c) -> float & { return ((float *)tsm)[(2 * PTM_TOPO_N + 3 * k + c) * PTM_BLOCK + t]; };
+  auto AF = [&](int k) -> float & { return ((float *)tsm)[(5 * PTM_TOPO_N + k) * PTM_BLOCK + t]; };
+  const int64_t s64 = (int64_t)blockIdx.x * PTM_BLOCK + t;
+  if (s64 >= d.n) return;
+  const int s = (int)s64;
+  TI xi, yi, zi;
+  int idi;
+  load_atom<F64>(d, s, xi, yi, zi, idi);
+  const int b = __ldg(d.sbin + s);
+  const int bz = b % d.nb[2], byx = b / d.nb[2];
+  const int by = byx % d.nb[1], bx = byx / d.nb[1];
+  const bool wrapped = d.dstat[0] != 0;
+  int wix = 0, wiy = 0, wiz = 0;
+  if (wrapped) img_unpack(__ldg(d.wrapv + s), wix, wiy, wiz);
+
+  // ---- the 18 nearest images
+  int m;
+  if (!wrapped && knn_fast_n<F64, PTM_TOPO_N>(d, s, xi, yi, zi, bx, by, bz, [&](int r, int j, int img) {
+        J(r) = j;
+        IMG(r) = img;
+      })) {
+    m = PTM_TOPO_N;
+  } else {
+    TI Ld2[PTM_TOPO_N];
+    int Lid[PTM_TOPO_N], Ljs[PTM_TOPO_N], Limg[PTM_TOPO_N];
+    m = knn<F64, PTM_TOPO_N>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, Ld2, Lid, Ljs, Limg);
+    if (m < 0) m = 0;
+    for (int k = 0; k < PTM_TOPO_N; k++) { J(k) = Ljs[k]; IMG(k) = Limg[k]; }
+  }
+  // ---- FP32 neighbour vectors: the difference of positions plus the image
+  // shift, summed without loss (error-free sums), as the metric steps use them
+  float mean2 = 0.f, dmax2 = 0.f;
+  for (int k = 0; k < m; k++) {
+    TI xj, yj, zj;
+    int idj;
+    load_atom<F64>(d, J(k), xj, yj, zj, idj);
+    int a0, a1, a2;
+    img_unpack(IMG(k), a0, a1, a2);
+    if constexpr (F64) {
+      double hx, hy, hz;
+      shift_f64(d, a0, a1, a2, hx, hy, hz);
+      VF(k, 0) = (float)((xj - xi) + hx); VF(k, 1) = (float)((yj - yi) + hy); VF(k, 2) = (float)((zj - zi) + hz);
+    } else {
+      float hx, hy, hz, lx, ly, lz, p, e1, q2, e2;
+      shift_f32(d, a0, a1, a2, hx, hy, hz, lx, ly, lz);
+      two_sum(xj, -xi, p, e1); two_sum(p, hx, q2, e2); VF(k, 0) = q2 + (e1 + (e2 + lx));
+      two_sum(yj, -yi, p, e1); two_sum(p, hy, q2, e2); VF(k, 1) = q2 + (e1 + (e2 + ly));
+      two_sum(zj, -zi, p, e1); two_sum(p, hz, q2, e2); VF(k, 2) = q2 + (e1 + (e2 + lz));
+    }
+    const float r2 = VF(k, 0) * VF(k, 0) + VF(k, 1) * VF(k, 1) + VF(k, 2) * VF(k, 2);
+    mean2 += r2;
+    dmax2 = fmaxf(dmax2, r2);
+  }
+  int o[PTM_TOPO_N];
+  if (m > 0) {
+    mean2 /= (float)m;
+    const float R = 10.f * sqrtf(dmax2);
+    auto vf = [&](int i, int c) -> float { return VF(i, c); };
+    for (int k = 0; k < m; k++) AF(k) = topo_face_area<float>(m, k, R, vf);
+    float area[PTM_TOPO_N];
+    for (int k = 0; k < m; k++) area[k] = AF(k);
+    if (topo_order<float>(m, area, mean2, o)) {
+      // a gap sits at the band edge: decide in FP64
+      count(d, C_TOPO64);
+      double v64[PTM_TOPO_N][3], a64[PTM_TOPO_N], mean64 = 0.0, dmax64 = 0.0;
+      for (int k = 0; k < m; k++) {
+        vec_fp64<F64>(d, xi, yi, zi, J(k), IMG(k), v64[k][0], v64[k][1], v64[k][2]);
+        const double r2 = v64[k][0] * v64[k][0] + v64[k][1] * v64[k][1] + v64[k][2] * v64[k][2];
+        mean64 += r2;
+        dmax64 = fmax(dmax64, r2);
+      }
+      mean64 /= m;
+      auto vd = [&](int i, int c) -> double { return v64[i][c]; };
+      for (int k = 0; k < m; k++) a64[k] = topo_face_area<double>(m, k, 10.0 * sqrt(dmax64), vd);
+      topo_order<double>(m, a64, mean64, o);
+    }
+  }
+  const int64_t n = d.n;
+  for (int k = 0; k < PTM_KNN; k++)
+    out[(int64_t)k * n + s] = k < m ? make_int2(J(o[k]), IMG(o[k])) : make_int2(-1, 0);
+}
+
+constexpr size_t topo_smem_bytes() { return (size_t)PTM_BLOCK * PTM_TOPO_WORDS * 4; }
+
+}  // namespace ptm

@@ -1,0 +1,112 @@
+"""Topological neighbour ordering (Sec. 3, Eq. 5) on the GPU against the oracle
+(GPU only): same parity bar as the Euclidean path."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1603_05143_gb300 import inputs as I
+from parity import compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ptm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1603_05143_gb300 import PTM
+    p = PTM(0)
+    yield p
+    p.close()
+
+
+def run(ptm, f, ordering="topological", mask=31):
+    import torch
+    sp = None if f.species is None else torch.from_numpy(np.ascontiguousarray(f.species, np.int8)).cuda()
+    out = ptm.classify(torch.from_numpy(np.ascontiguousarray(f.positions)).cuda(), f.cell, f.pbc, species=sp,
+                       mask=mask, ordering=ordering)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def check(ptm, f, atoms=None, mask=31):
+    g = run(ptm, f, mask=mask)
+    F = O.Frame(f.positions, f.cell, f.pbc)
+    ref = F.classify(atoms, species=f.species, mask=mask, ordering="topological")
+    st = compare(g, ref, atoms)
+    s = ptm.stats()
+    assert s["internal"] == 0
+    return st, g, ref, s
+
+
+@pytest.mark.parametrize("kind,a,reps", [("fcc", I.A_FCC_CU, 5), ("bcc", I.A_BCC_FE, 6), ("sc", I.A_SC, 6),
+                                         ("hcp", I.A_HCP, (6, 4, 4)), ("l12", I.A_L12, 5)])
+def test_perfect_lattices_match_euclidean_and_oracle(ptm, kind, a, reps):
+    f = I.crystal(kind, a, reps, rotation=I.random_rotation(I.rng_for(5)), dtype=np.float32)
+    st, g, ref, s = check(ptm, f)
+    e = run(ptm, f, ordering="euclidean")
+    for k in ("structure", "correspondence", "alloy"):
+        assert np.array_equal(g[k], e[k]), k
+    assert st["matched"] == f.n
+
+
+@pytest.mark.parametrize("sigma,dtype", [(0.1, np.float32), (0.2, np.float64), (0.28, np.float32)])
+def test_noisy_fcc_full(ptm, sigma, dtype):
+    f = I.crystal("fcc", I.A_FCC_CU, 6, sigma=sigma, seed=8, rotation=I.random_rotation(I.rng_for(6)), dtype=dtype)
+    st, g, ref, s = check(ptm, f)
+    e = run(ptm, f, ordering="euclidean")
+    if sigma >= 0.2:                 # Sec. 5.2: the area order keeps more fcc atoms when hot
+        assert np.sum(g["structure"] == 2) > np.sum(e["structure"] == 2)
+
+
+def test_polycrystal_and_mixed_phase_full(ptm):
+    for f in (I.config_polycrystal(n_target=1 << 14), I.config_mixed_phase(n_target=1 << 14)):
+        check(ptm, f)
+
+
+def test_strained_triclinic_and_masks(ptm):
+    fr = I.config_batch(seed=7, n_frames=4, n_min=2000, n_max=6000)
+    for f in fr:
+        check(ptm, f)
+    f = I.config_mixed_phase(n_target=1 << 12)
+    for m in (1, 2, 16, 6):
+        check(ptm, f, mask=m)
+
+
+def test_clusters_and_small_boxes(ptm):
+    rng = I.rng_for(9)
+    cl = [I.ico_cluster(2.556, rotation=I.random_rotation(rng), sigma=0.05, seed=i) for i in range(12)]
+    f = I.isolated_clusters(cl, dtype=np.float32)
+    check(ptm, f)
+    f = I.crystal("bcc", I.A_BCC_FE, 2, sigma=0.05, seed=3, dtype=np.float32)     # atoms see own images
+    check(ptm, f)
+
+
+def test_host_entry_and_unsupported_paths(ptm):
+    import torch
+    from paper_1603_05143_gb300 import PTMError, Server
+    f = I.config_mixed_phase(n_target=1 << 13)
+    d = run(ptm, f)
+    h = ptm.classify_host(f.positions, f.cell, f.pbc, species=f.species, ordering="topological")
+    for k in d:
+        assert np.array_equal(d[k], h[k]), k
+    # batches and servers take the Euclidean order only
+    srv = Server(ptm)
+    from paper_1603_05143_gb300.binding import _frame, ptm_outputs, PTM_F32
+    import ctypes as C
+    fr = _frame(f.n, f.positions.ctypes.data, PTM_F32, None, f.cell, f.pbc, 31, math.inf, "topological")
+    t = C.c_uint64()
+    assert ptm.lib.ptm_submit(srv.h, C.byref(fr), C.byref(ptm_outputs()), C.byref(t)) == 1
+    srv.close()
+
+
+def test_topological_full_size_sampled(ptm):
+    """The 2^20-atom polycrystal: a seeded sample checked one by one."""
+    f = I.config_polycrystal()
+    f.species = None
+    atoms = np.sort(I.rng_for(79).choice(f.n, 2000, replace=False))
+    st, g, ref, s = check(ptm, f, atoms=atoms)
+    assert st["matched"] > 0.9 * len(atoms)
