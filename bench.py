@@ -79,6 +79,8 @@ def parse():
                          "through the continuous-batching server")
     ap.add_argument("--serve-requests", type=int, default=512, help="frames per offered load (serve mode)")
     ap.add_argument("--workload", default=WORKLOAD, choices=WORKLOADS, help="frame mode: which frame")
+    ap.add_argument("--ordering", default="euclidean", choices=["euclidean", "topological"],
+                    help="frame mode: neighbour ordering (Sec. 3, Eq. 5)")
     ap.add_argument("--no-fp64-form", action="store_true", help="frame mode: skip timing the FP64 form")
     return ap.parse_args()
 
@@ -185,7 +187,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU oracle arm
-def oracle_rate(f, species, seconds, threads=None, seed=7, outputs=False):
+def oracle_rate(f, species, seconds, threads=None, seed=7, outputs=False, ordering="euclidean"):
     """Time the oracle (as it stands) on a seeded uniform sample of the frame's
     atoms, sized to take about `seconds` on `threads` host cores (all by
     default).  With outputs=True also returns (atoms, oracle outputs)."""
@@ -195,12 +197,12 @@ def oracle_rate(f, species, seconds, threads=None, seed=7, outputs=False):
     rng = np.random.default_rng(seed)
     probe = np.sort(rng.choice(f.n, 4 * threads, replace=False))
     t = time.perf_counter()
-    F.classify(probe, species=species, threads=threads, chunk=1)
+    F.classify(probe, species=species, threads=threads, chunk=1, ordering=ordering)
     per_atom = (time.perf_counter() - t) / len(probe)
     m = int(min(f.n, max(8 * threads, seconds / max(per_atom, 1e-9))))
     atoms = np.sort(rng.choice(f.n, m, replace=False))
     t = time.perf_counter()
-    ref = F.classify(atoms, species=species, threads=threads, chunk=max(1, m // (8 * threads)))
+    ref = F.classify(atoms, species=species, threads=threads, chunk=max(1, m // (8 * threads)), ordering=ordering)
     dt = time.perf_counter() - t
     if outputs:
         return m / dt, m, dt, threads, atoms, ref
@@ -254,11 +256,11 @@ def run_reference(args, world, rank, pg):
     threads = os.cpu_count() or 1
     per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        oracle_rate(f, species, per_step / 4, threads)
+        oracle_rate(f, species, per_step / 4, threads, ordering=args.ordering)
     rates, samples = [], 0
     t0 = time.perf_counter()
     for s in range(args.steps):
-        r, m, dt, th = oracle_rate(f, species, per_step, threads, seed=100 + s)
+        r, m, dt, th = oracle_rate(f, species, per_step, threads, seed=100 + s, ordering=args.ordering)
         rates.append(r)
         samples += m
     wall = time.perf_counter() - t0
@@ -266,7 +268,8 @@ def run_reference(args, world, rank, pg):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_dict(cfg, {"sample": "uniform seeded atom sample per step"}),
+            "data": "synthetic", "config": config_dict(cfg, {"sample": "uniform seeded atom sample per step",
+                                                             "ordering": args.ordering}),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{samples} atoms over {args.steps} steps, uniform seeded sample of the frame"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -290,7 +293,7 @@ def run_gpu(args, world, rank, local, pg):
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        ptm.classify(pos, f.cell, f.pbc, species=sp, out=out)
+        ptm.classify(pos, f.cell, f.pbc, species=sp, out=out, ordering=args.ordering)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -334,7 +337,7 @@ def run_gpu(args, world, rank, local, pg):
         hsp = torch.from_numpy(species).pin_memory().numpy()
         hout = allocate_outputs_host(f.n, pinned=True)
         for _ in range(2):
-            ptm.classify_host(hpos, f.cell, f.pbc, species=hsp, out=hout)
+            ptm.classify_host(hpos, f.cell, f.pbc, species=hsp, out=hout, ordering=args.ordering)
         if pg:
             pg.barrier()
         et = []
@@ -342,7 +345,7 @@ def run_gpu(args, world, rank, local, pg):
             flush.fill_(1)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            ptm.classify_host(hpos, f.cell, f.pbc, species=hsp, out=hout)
+            ptm.classify_host(hpos, f.cell, f.pbc, species=hsp, out=hout, ordering=args.ordering)
             et.append(time.perf_counter() - t0)
         tot = sum(et)
         if pg:
@@ -357,7 +360,7 @@ def run_gpu(args, world, rank, local, pg):
     if not args.no_fp64_form and rank == 0:
         p64 = PTM(local, precision="fp64")
         out64 = allocate_outputs(f.n, dev)
-        p64.classify(pos, f.cell, f.pbc, species=sp, out=out64)
+        p64.classify(pos, f.cell, f.pbc, species=sp, out=out64, ordering=args.ordering)
         torch.cuda.synchronize()
         t64 = []
         for _ in range(max(1, min(3, args.steps))):
@@ -365,7 +368,7 @@ def run_gpu(args, world, rank, local, pg):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            p64.classify(pos, f.cell, f.pbc, species=sp, out=out64)
+            p64.classify(pos, f.cell, f.pbc, species=sp, out=out64, ordering=args.ordering)
             e1.record(stream)
             e1.synchronize()
             t64.append(e0.elapsed_time(e1))
@@ -392,14 +395,16 @@ def run_gpu(args, world, rank, local, pg):
     from paper_1603_05143_gb300 import measure_fma_peak
     fma = {"fp32_tflops": measure_fma_peak("fp32", local) / 1e12, "fp64_tflops": measure_fma_peak("fp64", local) / 1e12}
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": measured_traffic() if args.workload == WORKLOAD else None, "kernel": "k_atoms",
+            "traffic": measured_traffic() if (args.workload == WORKLOAD and args.ordering == "euclidean") else None,
+            "kernel": "k_atoms" if args.ordering == "euclidean" else "k_topo + k_atoms",
             "kernel_ms": kms, "peak_note": "FP32 peak derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
             "fma_measured": fma, "frac_of_measured_fma": achieved / fma["fp32_tflops"],
             "hbm_achieved_gbs": f.n * BYTES_PER_ATOM / (kms * 1e-3) / 1e9, "hbm_peak_gbs": hbm_peak}
     cpu, errors = None, None
     if not args.no_cpu_baseline and world == 1:
-        r, m, dt, th, atoms, ref = oracle_rate(f, species, args.cpu_seconds, outputs=True)
-        r1, m1, dt1, _ = oracle_rate(f, species, min(5.0, args.cpu_seconds / 3), threads=1, seed=8)
+        r, m, dt, th, atoms, ref = oracle_rate(f, species, args.cpu_seconds, outputs=True, ordering=args.ordering)
+        r1, m1, dt1, _ = oracle_rate(f, species, min(5.0, args.cpu_seconds / 3), threads=1, seed=8,
+                                     ordering=args.ordering)
         cpu = {"value": r, "unit": UNIT, "cores": th, "kind": "oracle",
                "sample": f"{m} uniformly sampled atoms of the same frame in {dt:.1f} s",
                "single_thread": {"value": r1, "sample": f"{m1} atoms in {dt1:.1f} s"}}
@@ -409,12 +414,13 @@ def run_gpu(args, world, rank, local, pg):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_dict(cfg, {"parallelism": f"replicas{world}"}),
+            "config": config_dict(cfg, {"parallelism": f"replicas{world}", "ordering": args.ordering}),
             "latency_ms": {"p50": float(q[0]), "p99": float(q[1]), "best": float(min(times))},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "errors_vs_oracle": errors, "fp64_form": fp64_form,
-            "gpu_launches": 6 * args.steps,
-            "fallbacks": {k: s0[k] for k in ("sos", "qcp_fp64", "tie_fp64", "knn_wide", "knn_fail", "internal")},
+            "gpu_launches": (6 if args.ordering == "euclidean" else 7) * args.steps,
+            "fallbacks": {k: s0[k] for k in ("sos", "qcp_fp64", "tie_fp64", "knn_wide", "knn_fail", "internal",
+                                             "topo_fp64")},
             "matched": s0["matched"], "candidates_per_atom": s0["candidates"] / s0["atoms"]}
     print(json.dumps(line), flush=True)
     ptm.close()
