@@ -45,6 +45,7 @@ struct ptm_context {
   float *o_vm = nullptr, *o_rf = nullptr;
   // topological order of every atom's 14 neighbours (k_topo -> k_atoms)
   int2 *topo = nullptr;
+  int *topo_list = nullptr;        // atoms for the FP64 pass; [n] = their count
   size_t cap_topo = 0;
 };
 
@@ -141,9 +142,12 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
   const bool topological = f->ordering == PTM_ORDER_TOPOLOGICAL;
   if (topological && (size_t)n > ctx->cap_topo) {
     cudaFree(ctx->topo);
+    cudaFree(ctx->topo_list);
     ctx->topo = nullptr;
+    ctx->topo_list = nullptr;
     ctx->cap_topo = 0;
     CK(cudaMalloc(&ctx->topo, (size_t)n * PTM_KNN * sizeof(int2)));
+    CK(cudaMalloc(&ctx->topo_list, ((size_t)n + 1) * sizeof(int)));
     ctx->cap_topo = (size_t)n;
   }
 
@@ -212,8 +216,17 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
   CK(cudaEventRecord(ctx->ev[1], st));
   if (topological) {
     desc.topo = ctx->topo;
-    if (f64) k_topo<true><<<ga, PTM_BLOCK, topo_smem_bytes(), st>>>(desc, ctx->topo);
-    else k_topo<false><<<ga, PTM_BLOCK, topo_smem_bytes(), st>>>(desc, ctx->topo);
+    int *cnt = ctx->topo_list + ctx->cap_topo;
+    CK(cudaMemsetAsync(cnt, 0, sizeof(int), st));
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    if (f64) {
+      k_topo<true><<<ga, PTM_BLOCK, topo_smem_bytes(), st>>>(desc, ctx->topo, ctx->topo_list, cnt);
+      k_topo64<true><<<4 * sms, PTM_BLOCK, topo_smem_bytes(), st>>>(desc, ctx->topo, ctx->topo_list, cnt);
+    } else {
+      k_topo<false><<<ga, PTM_BLOCK, topo_smem_bytes(), st>>>(desc, ctx->topo, ctx->topo_list, cnt);
+      k_topo64<false><<<4 * sms, PTM_BLOCK, topo_smem_bytes(), st>>>(desc, ctx->topo, ctx->topo_list, cnt);
+    }
   }
   if (ctx->precision == PTM_PREC_FP64) {
     if (f64) k_atoms<true, true><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
@@ -298,6 +311,7 @@ ptm_status ptm_destroy(ptm_context *ctx) {
   cudaFree(ctx->o_struct); cudaFree(ctx->o_alloy); cudaFree(ctx->o_rmsd); cudaFree(ctx->o_scale);
   cudaFree(ctx->o_quat); cudaFree(ctx->o_strain); cudaFree(ctx->o_corr); cudaFree(ctx->o_vm); cudaFree(ctx->o_rf);
   cudaFree(ctx->topo);
+  cudaFree(ctx->topo_list);
   delete ctx;
   return PTM_OK;
 }

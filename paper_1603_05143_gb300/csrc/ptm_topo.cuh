@@ -13,7 +13,8 @@
 // order within TOPO_BAND x the mean squared distance form one group, ordered by
 // the Euclidean rank (distance, atom id, image).  FP32 areas decide unless a
 // gap lies within TOPO_GUARD of the band edge; then the atom's areas are
-// recomputed in FP64 from FP64 neighbour vectors.
+// recomputed in FP64 from FP64 neighbour vectors, by a second kernel over just
+// those atoms.
 
 namespace ptm {
 
@@ -105,19 +106,18 @@ __device__ bool topo_order(int m, const T *area, T mean2, int *o) {
   return near;
 }
 
-template <bool F64>
-__global__ void __launch_bounds__(PTM_BLOCK) k_topo(const __grid_constant__ FrameDesc d, int2 *__restrict__ out) {
+// One atom.  First pass (FP64PASS false): FP32 areas decide, and an atom with a
+// gap at the band edge is appended to `list` for the second pass instead of
+// being decided here, so that no warp waits on one lane's FP64 work.  Second
+// pass (true): the listed atoms, every area in FP64 from FP64 neighbour vectors.
+template <bool F64, bool FP64PASS>
+__device__ void topo_atom(const FrameDesc &d, int s, int *tsm, int2 *__restrict__ out, int *list, int *list_count) {
   typedef typename RT<F64>::T TI;
-  extern __shared__ __align__(16) unsigned char tsm_raw[];
-  int *tsm = (int *)tsm_raw;
   const int t = threadIdx.x;
   auto J = [&](int k) -> int & { return tsm[k * PTM_BLOCK + t]; };
   auto IMG = [&](int k) -> int & { return tsm[(PTM_TOPO_N + k) * PTM_BLOCK + t]; };
   auto VF = [&](int k, int c) -> float & { return ((float *)tsm)[(2 * PTM_TOPO_N + 3 * k + c) * PTM_BLOCK + t]; };
   auto AF = [&](int k) -> float & { return ((float *)tsm)[(5 * PTM_TOPO_N + k) * PTM_BLOCK + t]; };
-  const int64_t s64 = (int64_t)blockIdx.x * PTM_BLOCK + t;
-  if (s64 >= d.n) return;
-  const int s = (int)s64;
   TI xi, yi, zi;
   int idi;
   load_atom<F64>(d, s, xi, yi, zi, idi);
@@ -142,41 +142,46 @@ __global__ void __launch_bounds__(PTM_BLOCK) k_topo(const __grid_constant__ Fram
     if (m < 0) m = 0;
     for (int k = 0; k < PTM_TOPO_N; k++) { J(k) = Ljs[k]; IMG(k) = Limg[k]; }
   }
-  // ---- FP32 neighbour vectors: the difference of positions plus the image
-  // shift, summed without loss (error-free sums), as the metric steps use them
-  float mean2 = 0.f, dmax2 = 0.f;
-  for (int k = 0; k < m; k++) {
-    TI xj, yj, zj;
-    int idj;
-    load_atom<F64>(d, J(k), xj, yj, zj, idj);
-    int a0, a1, a2;
-    img_unpack(IMG(k), a0, a1, a2);
-    if constexpr (F64) {
-      double hx, hy, hz;
-      shift_f64(d, a0, a1, a2, hx, hy, hz);
-      VF(k, 0) = (float)((xj - xi) + hx); VF(k, 1) = (float)((yj - yi) + hy); VF(k, 2) = (float)((zj - zi) + hz);
-    } else {
-      float hx, hy, hz, lx, ly, lz, p, e1, q2, e2;
-      shift_f32(d, a0, a1, a2, hx, hy, hz, lx, ly, lz);
-      two_sum(xj, -xi, p, e1); two_sum(p, hx, q2, e2); VF(k, 0) = q2 + (e1 + (e2 + lx));
-      two_sum(yj, -yi, p, e1); two_sum(p, hy, q2, e2); VF(k, 1) = q2 + (e1 + (e2 + ly));
-      two_sum(zj, -zi, p, e1); two_sum(p, hz, q2, e2); VF(k, 2) = q2 + (e1 + (e2 + lz));
-    }
-    const float r2 = VF(k, 0) * VF(k, 0) + VF(k, 1) * VF(k, 1) + VF(k, 2) * VF(k, 2);
-    mean2 += r2;
-    dmax2 = fmaxf(dmax2, r2);
-  }
   int o[PTM_TOPO_N];
-  if (m > 0) {
-    mean2 /= (float)m;
-    const float R = 10.f * sqrtf(dmax2);
-    auto vf = [&](int i, int c) -> float { return VF(i, c); };
-    for (int k = 0; k < m; k++) AF(k) = topo_face_area<float>(m, k, R, vf);
-    float area[PTM_TOPO_N];
-    for (int k = 0; k < m; k++) area[k] = AF(k);
-    if (topo_order<float>(m, area, mean2, o)) {
-      // a gap sits at the band edge: decide in FP64
-      count(d, C_TOPO64);
+  if constexpr (!FP64PASS) {
+    // FP32 neighbour vectors: the difference of positions plus the image
+    // shift, summed without loss (error-free sums), as the metric steps use them
+    float mean2 = 0.f, dmax2 = 0.f;
+    for (int k = 0; k < m; k++) {
+      TI xj, yj, zj;
+      int idj;
+      load_atom<F64>(d, J(k), xj, yj, zj, idj);
+      int a0, a1, a2;
+      img_unpack(IMG(k), a0, a1, a2);
+      if constexpr (F64) {
+        double hx, hy, hz;
+        shift_f64(d, a0, a1, a2, hx, hy, hz);
+        VF(k, 0) = (float)((xj - xi) + hx); VF(k, 1) = (float)((yj - yi) + hy); VF(k, 2) = (float)((zj - zi) + hz);
+      } else {
+        float hx, hy, hz, lx, ly, lz, p, e1, q2, e2;
+        shift_f32(d, a0, a1, a2, hx, hy, hz, lx, ly, lz);
+        two_sum(xj, -xi, p, e1); two_sum(p, hx, q2, e2); VF(k, 0) = q2 + (e1 + (e2 + lx));
+        two_sum(yj, -yi, p, e1); two_sum(p, hy, q2, e2); VF(k, 1) = q2 + (e1 + (e2 + ly));
+        two_sum(zj, -zi, p, e1); two_sum(p, hz, q2, e2); VF(k, 2) = q2 + (e1 + (e2 + lz));
+      }
+      const float r2 = VF(k, 0) * VF(k, 0) + VF(k, 1) * VF(k, 1) + VF(k, 2) * VF(k, 2);
+      mean2 += r2;
+      dmax2 = fmaxf(dmax2, r2);
+    }
+    if (m > 0) {
+      mean2 /= (float)m;
+      const float R = 10.f * sqrtf(dmax2);
+      auto vf = [&](int i, int c) -> float { return VF(i, c); };
+      for (int k = 0; k < m; k++) AF(k) = topo_face_area<float>(m, k, R, vf);
+      float area[PTM_TOPO_N];
+      for (int k = 0; k < m; k++) area[k] = AF(k);
+      if (topo_order<float>(m, area, mean2, o)) {
+        count(d, C_TOPO64);                       // a gap at the band edge: the second pass decides
+        list[atomicAdd(list_count, 1)] = s;
+      }
+    }
+  } else {
+    if (m > 0) {
       double v64[PTM_TOPO_N][3], a64[PTM_TOPO_N], mean64 = 0.0, dmax64 = 0.0;
       for (int k = 0; k < m; k++) {
         vec_fp64<F64>(d, xi, yi, zi, J(k), IMG(k), v64[k][0], v64[k][1], v64[k][2]);
@@ -193,6 +198,25 @@ __global__ void __launch_bounds__(PTM_BLOCK) k_topo(const __grid_constant__ Fram
   const int64_t n = d.n;
   for (int k = 0; k < PTM_KNN; k++)
     out[(int64_t)k * n + s] = k < m ? make_int2(J(o[k]), IMG(o[k])) : make_int2(-1, 0);
+}
+
+template <bool F64>
+__global__ void __launch_bounds__(PTM_BLOCK) k_topo(const __grid_constant__ FrameDesc d, int2 *__restrict__ out,
+                                                    int *list, int *list_count) {
+  extern __shared__ __align__(16) unsigned char tsm_raw[];
+  const int64_t s = (int64_t)blockIdx.x * PTM_BLOCK + threadIdx.x;
+  if (s >= d.n) return;
+  topo_atom<F64, false>(d, (int)s, (int *)tsm_raw, out, list, list_count);
+}
+
+// Second pass over the listed atoms (grid-stride: the count is read on the device).
+template <bool F64>
+__global__ void __launch_bounds__(PTM_BLOCK) k_topo64(const __grid_constant__ FrameDesc d, int2 *__restrict__ out,
+                                                      const int *list, const int *list_count) {
+  extern __shared__ __align__(16) unsigned char tsm_raw[];
+  const int cnt = *list_count;
+  for (int i = blockIdx.x * PTM_BLOCK + threadIdx.x; i < cnt; i += gridDim.x * PTM_BLOCK)
+    topo_atom<F64, true>(d, list[i], (int *)tsm_raw, out, nullptr, nullptr);
 }
 
 constexpr size_t topo_smem_bytes() { return (size_t)PTM_BLOCK * PTM_TOPO_WORDS * 4; }
