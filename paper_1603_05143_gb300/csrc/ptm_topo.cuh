@@ -21,11 +21,14 @@ namespace ptm {
 #define PTM_TOPO_N 18
 #define PTM_TOPO_BAND 1e-3
 #define PTM_TOPO_GUARD 2e-5
-#define PTM_TOPO_WORDS (2 * PTM_TOPO_N + 3 * PTM_TOPO_N + PTM_TOPO_N)   // 32-bit words per thread
+#define PTM_TOPO_VMAX 24       // polygon buffer: 4 + 17 clips add at most 21 vertices
+// 32-bit words per thread: neighbour ids and images, FP32 vectors, two polygon buffers
+#define PTM_TOPO_WORDS (2 * PTM_TOPO_N + 3 * PTM_TOPO_N + 2 * 2 * PTM_TOPO_VMAX)
 
-// Area of the Voronoi face of neighbour j among the m vectors V(i, c).
+// Area of the Voronoi face of neighbour j among the m vectors V(i, c); P and Q
+// are polygon buffers of 2 x PTM_TOPO_VMAX values, element e at P[e * st].
 template <typename T, typename Vec>
-__device__ T topo_face_area(int m, int j, T R, Vec V) {
+__device__ T topo_face_area(int m, int j, T R, Vec V, T *P, T *Q, int st) {
   const T n0 = V(j, 0), n1 = V(j, 1), n2 = V(j, 2);
   const T nn = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
   const T u0 = n0 / nn, u1 = n1 / nn, u2 = n2 / nn;
@@ -40,10 +43,11 @@ __device__ T topo_face_area(int m, int j, T R, Vec V) {
   // a convex polygon gains at most one vertex per clip (4 + 17 < VMAX);
   // rounding on a nearly degenerate polygon could emit more, so writes stop at
   // the buffer's end (the polygon then has next to no area either way)
-  constexpr int VMAX = PTM_TOPO_N + 8;
-  T P[2 * VMAX], Q[2 * VMAX];
+  constexpr int VMAX = PTM_TOPO_VMAX;
+  T *cur = P, *nxt = Q;
   int np = 4;
-  P[0] = -R; P[1] = -R; P[2] = R; P[3] = -R; P[4] = R; P[5] = R; P[6] = -R; P[7] = R;
+  cur[0] = -R; cur[st] = -R; cur[2 * st] = R; cur[3 * st] = -R;
+  cur[4 * st] = R; cur[5 * st] = R; cur[6 * st] = -R; cur[7 * st] = R;
   for (int i = 0; i < m && np > 0; i++) {
     if (i == j) continue;
     const T w0 = V(i, 0), w1 = V(i, 1), w2 = V(i, 2);
@@ -52,21 +56,21 @@ __device__ T topo_face_area(int m, int j, T R, Vec V) {
     int nq = 0;
     for (int k = 0; k < np; k++) {
       const int k1 = k + 1 == np ? 0 : k + 1;
-      const T xs = P[2 * k], xt = P[2 * k + 1], ys = P[2 * k1], yt = P[2 * k1 + 1];
+      const T xs = cur[2 * k * st], xt = cur[(2 * k + 1) * st], ys = cur[2 * k1 * st], yt = cur[(2 * k1 + 1) * st];
       const T fx = A * xs + B * xt - C, fy = A * ys + B * yt - C;
-      if (fx <= 0 && nq < VMAX) { Q[2 * nq] = xs; Q[2 * nq + 1] = xt; nq++; }
+      if (fx <= 0 && nq < VMAX) { nxt[2 * nq * st] = xs; nxt[(2 * nq + 1) * st] = xt; nq++; }
       if (((fx < 0 && fy > 0) || (fx > 0 && fy < 0)) && nq < VMAX) {
         const T tt = fx / (fx - fy);
-        Q[2 * nq] = xs + tt * (ys - xs); Q[2 * nq + 1] = xt + tt * (yt - xt); nq++;
+        nxt[2 * nq * st] = xs + tt * (ys - xs); nxt[(2 * nq + 1) * st] = xt + tt * (yt - xt); nq++;
       }
     }
     np = nq;
-    for (int k = 0; k < 2 * nq; k++) P[k] = Q[k];
+    T *tmp = cur; cur = nxt; nxt = tmp;
   }
   T s2 = 0;
   for (int k = 0; k < np; k++) {
     const int k1 = k + 1 == np ? 0 : k + 1;
-    s2 += P[2 * k] * P[2 * k1 + 1] - P[2 * k1] * P[2 * k + 1];
+    s2 += cur[2 * k * st] * cur[(2 * k1 + 1) * st] - cur[2 * k1 * st] * cur[(2 * k + 1) * st];
   }
   return fabs(s2) / 2;
 }
@@ -117,7 +121,6 @@ __device__ void topo_atom(const FrameDesc &d, int s, int *tsm, int2 *__restrict_
   auto J = [&](int k) -> int & { return tsm[k * PTM_BLOCK + t]; };
   auto IMG = [&](int k) -> int & { return tsm[(PTM_TOPO_N + k) * PTM_BLOCK + t]; };
   auto VF = [&](int k, int c) -> float & { return ((float *)tsm)[(2 * PTM_TOPO_N + 3 * k + c) * PTM_BLOCK + t]; };
-  auto AF = [&](int k) -> float & { return ((float *)tsm)[(5 * PTM_TOPO_N + k) * PTM_BLOCK + t]; };
   TI xi, yi, zi;
   int idi;
   load_atom<F64>(d, s, xi, yi, zi, idi);
@@ -172,9 +175,11 @@ __device__ void topo_atom(const FrameDesc &d, int s, int *tsm, int2 *__restrict_
       mean2 /= (float)m;
       const float R = 10.f * sqrtf(dmax2);
       auto vf = [&](int i, int c) -> float { return VF(i, c); };
-      for (int k = 0; k < m; k++) AF(k) = topo_face_area<float>(m, k, R, vf);
+      // polygon buffers in shared memory, one word per thread per row
+      float *PB = (float *)tsm + 5 * PTM_TOPO_N * PTM_BLOCK + t;
+      float *QB = PB + 2 * PTM_TOPO_VMAX * PTM_BLOCK;
       float area[PTM_TOPO_N];
-      for (int k = 0; k < m; k++) area[k] = AF(k);
+      for (int k = 0; k < m; k++) area[k] = topo_face_area<float>(m, k, R, vf, PB, QB, PTM_BLOCK);
       if (topo_order<float>(m, area, mean2, o)) {
         count(d, C_TOPO64);                       // a gap at the band edge: the second pass decides
         list[atomicAdd(list_count, 1)] = s;
@@ -191,7 +196,8 @@ __device__ void topo_atom(const FrameDesc &d, int s, int *tsm, int2 *__restrict_
       }
       mean64 /= m;
       auto vd = [&](int i, int c) -> double { return v64[i][c]; };
-      for (int k = 0; k < m; k++) a64[k] = topo_face_area<double>(m, k, 10.0 * sqrt(dmax64), vd);
+      double P64[2 * PTM_TOPO_VMAX], Q64[2 * PTM_TOPO_VMAX];
+      for (int k = 0; k < m; k++) a64[k] = topo_face_area<double>(m, k, 10.0 * sqrt(dmax64), vd, P64, Q64, 1);
       topo_order<double>(m, a64, mean64, o);
     }
   }
