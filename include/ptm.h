@@ -93,8 +93,7 @@ typedef struct {
   uint32_t template_mask;    /* PTM_MASK_* bits; 0 means PTM_MASK_ALL */
   double rmsd_max;           /* atoms whose best RMSD exceeds it are unmatched; INFINITY = none */
   int ordering;              /* neighbour ordering (Sec. 3): PTM_ORDER_EUCLIDEAN (0) or
-                                PTM_ORDER_TOPOLOGICAL; topological ordering is accepted by
-                                ptm_classify_frame and ptm_classify_frame_host only */
+                                PTM_ORDER_TOPOLOGICAL (not by ptm_classify_frame_noalloc) */
 } ptm_frame;
 
 /* Per-atom outputs, indexed by atom.  Any pointer may be NULL to skip it.

@@ -305,7 +305,7 @@ def _batch_structs(frames, mask, rmsd_max, outputs):
             sp = sp.to(device=pos.device, dtype=torch.int8).contiguous()
         code = PTM_F64 if pos.dtype == torch.float64 else PTM_F32
         fr[i] = _frame(pos.shape[0], pos.data_ptr(), code, None if sp is None else sp.data_ptr(), f["cell"],
-                       f.get("pbc", (True, True, True)), mask, rmsd_max)
+                       f.get("pbc", (True, True, True)), mask, rmsd_max, f.get("ordering", "euclidean"))
         o = allocate_outputs(pos.shape[0], pos.device, outputs)
         for name in OUTPUT_FIELDS:
             t = o.get(name)
@@ -399,7 +399,7 @@ class Server:
         self._live = {}
 
     def submit(self, positions, cell, pbc=(True, True, True), species=None, mask=MASK_ALL, rmsd_max=math.inf,
-               out=None, pinned=False):
+               out=None, pinned=False, ordering="euclidean"):
         pos = np.ascontiguousarray(positions)
         n = pos.shape[0]
         sp = None if species is None else np.ascontiguousarray(species, np.int8)
@@ -410,7 +410,7 @@ class Server:
             a = out.get(name)
             setattr(o, name, a.ctypes.data if a is not None else None)
         f = _frame(n, pos.ctypes.data, PTM_F64 if pos.dtype == np.float64 else PTM_F32,
-                   sp.ctypes.data if sp is not None else None, cell, pbc, mask, rmsd_max)
+                   sp.ctypes.data if sp is not None else None, cell, pbc, mask, rmsd_max, ordering)
         t = C.c_uint64()
         rc = self.lib.ptm_submit(self.h, C.byref(f), C.byref(o), C.byref(t))
         if rc:

@@ -416,7 +416,7 @@ ptm_status ptm_get_stats(ptm_context *ctx, ptm_stats *out) {
 static ptm_status setup_frame(const ptm_frame *f, double cell_factor, FrameDesc *desc, BinParams *bp,
                               size_t *ncell_out) {
   if (!f || f->n_atoms < 1 || f->n_atoms >= (1ll << 31) || !f->positions) return PTM_ERR_INVALID_ARG;
-  if (f->ordering != PTM_ORDER_EUCLIDEAN) return PTM_ERR_INVALID_ARG;     // batches: Euclidean only
+  if (f->ordering != PTM_ORDER_EUCLIDEAN && f->ordering != PTM_ORDER_TOPOLOGICAL) return PTM_ERR_INVALID_ARG;
   if (f->pos_dtype != PTM_F32 && f->pos_dtype != PTM_F64) return PTM_ERR_INVALID_ARG;
   if (!finite_cell(f->cell)) return PTM_ERR_INVALID_ARG;
   const double *H = f->cell;
@@ -499,6 +499,9 @@ struct ptm_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int nsm = 152;
+  int topo = 0;                   // some frame takes the topological order
+  int2 *topo_buf = nullptr;       // per-frame segments of neighbour orders
+  int *topo_list = nullptr;       // atoms for the FP64 pass; [ntotal] = their count
   void *block = nullptr;          // the workspace (one allocation, or a pool block when served)
   bool owns_block = true;
 };
@@ -537,6 +540,22 @@ static ptm_status batch_enqueue(ptm_batch *b, cudaStream_t st) {
   k_scatter_batch<<<gb, tb, 0, st>>>(b->d_bp, b->d_atom_off, b->nframes, b->ntotal, b->atom_cell, b->atom_rank,
                                      b->atom_wrap, b->cell_start, b->sorted, b->sbin, b->wrapv);
   CK(cudaEventRecordWithFlags(b->ev[1], st, rec));
+  if (b->topo) {
+    int *cnt = b->topo_list + b->ntotal;
+    CK(cudaMemsetAsync(cnt, 0, sizeof(int), st));
+    const unsigned gt = (unsigned)((b->ntotal + PTM_BLOCK - 1) / PTM_BLOCK);
+    if (b->f64) {
+      k_topo_batch<true><<<gt, PTM_BLOCK, topo_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes, b->ntotal,
+                                                                 b->topo_list, cnt);
+      k_topo64_batch<true><<<4 * b->nsm, PTM_BLOCK, topo_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes,
+                                                                          b->topo_list, cnt);
+    } else {
+      k_topo_batch<false><<<gt, PTM_BLOCK, topo_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes, b->ntotal,
+                                                                  b->topo_list, cnt);
+      k_topo64_batch<false><<<4 * b->nsm, PTM_BLOCK, topo_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes,
+                                                                           b->topo_list, cnt);
+    }
+  }
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->nsm * b->blocks_per_sm,
                                                                        (b->ntotal + b->tile_atoms - 1) / b->tile_atoms));
   if (b->f64)
@@ -559,12 +578,15 @@ struct BatchPlan {
   int64_t ntotal = 0;
   size_t ncell = 0;
   int f64 = 0;
+  int topo = 0;                      // some frame asks for the topological order
+  std::vector<int> ordering;
 };
 
 static ptm_status batch_plan(int nframes, const ptm_frame *frames, double cell_factor, BatchPlan &P) {
   P.hd.resize(nframes);
   P.hb.resize(nframes);
   P.off.resize(nframes);
+  P.ordering.resize(nframes);
   P.f64 = frames[0].pos_dtype == PTM_F64;
   for (int f = 0; f < nframes; f++) {
     size_t nc = 0;
@@ -575,6 +597,8 @@ static ptm_status batch_plan(int nframes, const ptm_frame *frames, double cell_f
     P.hb[f].atom_off = P.ntotal;
     P.hb[f].cell_off = (int)P.ncell;
     P.hd[f].atom_offset = P.ntotal;
+    P.ordering[f] = frames[f].ordering;
+    P.topo |= frames[f].ordering == PTM_ORDER_TOPOLOGICAL;
     P.ntotal += frames[f].n_atoms;
     P.ncell += nc;
     if (P.ntotal >= (1ll << 31) || P.ncell >= (1ull << 31)) return PTM_ERR_INVALID_ARG;
@@ -583,11 +607,12 @@ static ptm_status batch_plan(int nframes, const ptm_frame *frames, double cell_f
 }
 
 // Device bytes of a batch's workspace (descriptors, sorted atoms, cell lists).
-static size_t batch_workspace_bytes(int nframes, int64_t ntotal, size_t ncell, int f64) {
+static size_t batch_workspace_bytes(int nframes, int64_t ntotal, size_t ncell, int f64, int topo) {
   const size_t n = (size_t)ntotal, rec = f64 ? sizeof(Atom64) : sizeof(float4);
   const size_t nblk = (ncell + 1 + 2 * SCAN_BLOCK - 1) / (2 * SCAN_BLOCK) + 1;
+  const size_t tb = topo ? sizeof(int2) * PTM_KNN * n + 4 * (n + 1) + 2 * 256 : 0;
   return (sizeof(FrameDesc) + sizeof(BinParams) + sizeof(int64_t) + 16) * nframes + rec * n + 20 * n +
-         8 * (ncell + 1) + 4 * nblk + 4 + 8 + 8 * C_NCOUNTERS + 16 * 256;
+         8 * (ncell + 1) + 4 * nblk + 4 + 8 + 8 * C_NCOUNTERS + 16 * 256 + tb;
 }
 
 // Carve the batch workspace out of one device block (256-byte aligned pieces)
@@ -608,7 +633,14 @@ static void batch_layout(ptm_batch *b, unsigned char *base, BatchPlan &P, const 
   b->cell_count = (int *)take(4 * (nc + 1)); b->cell_start = (int *)take(4 * (nc + 1));
   b->block_sums = (int *)take(4 * nblk); b->scan_total = (int *)take(4);
   b->queue = (unsigned long long *)take(8); b->counters = (unsigned long long *)take(8 * C_NCOUNTERS);
+  b->topo = P.topo;
+  if (P.topo) {
+    b->topo_buf = (int2 *)take(sizeof(int2) * PTM_KNN * n);
+    b->topo_list = (int *)take(4 * (n + 1));
+  }
   for (int f = 0; f < nf; f++) {
+    // frame f's topological order: rows of n_f entries from slot 14 x (first slot)
+    P.hd[f].topo = P.ordering[f] == PTM_ORDER_TOPOLOGICAL ? b->topo_buf + PTM_KNN * P.off[f] : nullptr;
     P.hd[f].sorted = b->sorted;
     P.hd[f].sbin = b->sbin;
     P.hd[f].cell_start = b->cell_start + P.hb[f].cell_off;
@@ -646,7 +678,7 @@ extern "C" ptm_status ptm_batch_create(ptm_context *ctx, int nframes, const ptm_
   b->f64 = P.f64;
   b->ntotal = P.ntotal;
   b->ncell = P.ncell;
-  cudaError_t e = cudaMalloc(&b->block, batch_workspace_bytes(nframes, P.ntotal, P.ncell, P.f64));
+  cudaError_t e = cudaMalloc(&b->block, batch_workspace_bytes(nframes, P.ntotal, P.ncell, P.f64, P.topo));
   for (int i = 0; i < 3 && e == cudaSuccess; i++) e = cudaEventCreate(&b->ev[i]);
   if (e != cudaSuccess) { rs = cuda_fail(ctx, e, "ptm_batch_create"); batch_free(b); return rs; }
   batch_layout(b, (unsigned char *)b->block, P, outs);

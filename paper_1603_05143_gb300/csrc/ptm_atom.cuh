@@ -59,7 +59,8 @@ struct FrameDesc {
   int32_t *corr;
   float *vm;                   // derived: von Mises shear strain
   float *rf;                   // derived: Rodrigues-Frank vector
-  const int2 *topo;            // topological order: [t][n] (sorted slot, image) of neighbour t, or NULL
+  const int2 *topo;            // topological order: [t][n] (sorted slot, image) of neighbour t by
+                               // frame-local slot (s - atom_offset), or NULL for the Euclidean order
   int *dstat;                  // [0] any atom wrapped, [1] overshoot (float bits, Angstrom)
   unsigned long long *counters;  // ptm_stats order: atoms, matched, knn_wide, knn_fail, sos, qcp_fp64, tie_fp64, internal, candidates, candidate_points
   int64_t atom_offset;         // first sorted slot of this frame (0 for a single frame)

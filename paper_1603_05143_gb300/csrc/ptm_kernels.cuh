@@ -476,7 +476,7 @@ __device__ __noinline__ int rerank_fp64(const FrameDesc &d, int s, const Best bs
   if (d.topo) {
     cnt = 0;
     for (int t = 0; t < PTM_KNN; t++) {
-      const int2 e = d.topo[(int64_t)t * d.n + s];
+      const int2 e = d.topo[(int64_t)t * d.n + (s - d.atom_offset)];
       Ljs[t] = e.x;
       Limg[t] = e.y;
       cnt += e.x >= 0;
@@ -796,7 +796,7 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
     if (d.topo) {                       // neighbours in topological order (Eq. 5), from k_topo
       cnt = 0;
       for (int t = 0; t < PTM_KNN; t++) {
-        const int2 e = d.topo[(int64_t)t * d.n + s];
+        const int2 e = d.topo[(int64_t)t * d.n + (s - d.atom_offset)];
         sm.NID(t) = e.x;
         sm.DX(t) = __int_as_float(e.y);
         cnt += e.x >= 0;

@@ -75,7 +75,8 @@ constexpr size_t kOutBytesPerAtom = 1 + 1 + 4 + 4 + 16 + 36 + 60 + 4 + 12;
 size_t request_bytes(const ptm_frame &f) {
   const size_t n = (size_t)f.n_atoms;
   const size_t pos = n * 3 * (f.pos_dtype == PTM_F64 ? 8 : 4);
-  const size_t ws = n * (f.pos_dtype == PTM_F64 ? 32 : 16) + 20 * n + 8 * (4 * n + 64) + sizeof(FrameDesc) + 4096;
+  const size_t ws = n * (f.pos_dtype == PTM_F64 ? 32 : 16) + 20 * n + 8 * (4 * n + 64) + sizeof(FrameDesc) + 4096 +
+                    (f.ordering == PTM_ORDER_TOPOLOGICAL ? n * (8 * PTM_KNN + 4) + 1024 : 0);
   return pos + n + n * kOutBytesPerAtom + ws;
 }
 
@@ -157,7 +158,7 @@ ptm_status launch_batch(ptm_server *S, std::vector<Request *> &rs, int slot, InF
   ptm_status rsn = batch_plan(nf, frames.data(), b->cell_factor, P);
   if (rsn != PTM_OK) { delete b; delete F; return rsn; }
   b->f64 = P.f64; b->ntotal = P.ntotal; b->ncell = P.ncell;
-  F->ws_bytes = batch_workspace_bytes(nf, P.ntotal, P.ncell, P.f64);
+  F->ws_bytes = batch_workspace_bytes(nf, P.ntotal, P.ncell, P.f64, P.topo);
   e = S->pool.alloc(F->ws_bytes, &F->ws);
   for (int i = 0; i < 3 && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(&b->ev[i], cudaEventDefault);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&F->done, cudaEventDisableTiming);
@@ -343,7 +344,7 @@ extern "C" ptm_status ptm_submit(ptm_server *S, const ptm_frame *frame, const pt
   if (!S || !frame || !out || !ticket) return PTM_ERR_INVALID_ARG;
   if (frame->n_atoms < 1 || frame->n_atoms >= (1ll << 31) || !frame->positions) return PTM_ERR_INVALID_ARG;
   if (frame->pos_dtype != PTM_F32 && frame->pos_dtype != PTM_F64) return PTM_ERR_INVALID_ARG;
-  if (frame->ordering != PTM_ORDER_EUCLIDEAN) return PTM_ERR_INVALID_ARG;
+  if (frame->ordering != PTM_ORDER_EUCLIDEAN && frame->ordering != PTM_ORDER_TOPOLOGICAL) return PTM_ERR_INVALID_ARG;
   if (!finite_cell(frame->cell)) return PTM_ERR_INVALID_ARG;
   Request *r = new (std::nothrow) Request();
   if (!r) return PTM_ERR_OUT_OF_MEMORY;

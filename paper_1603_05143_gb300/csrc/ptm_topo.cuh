@@ -201,9 +201,9 @@ __device__ void topo_atom(const FrameDesc &d, int s, int *tsm, int2 *__restrict_
       topo_order<double>(m, a64, mean64, o);
     }
   }
-  const int64_t n = d.n;
+  const int64_t n = d.n, sl = s - d.atom_offset;     // frame-local slot
   for (int k = 0; k < PTM_KNN; k++)
-    out[(int64_t)k * n + s] = k < m ? make_int2(J(o[k]), IMG(o[k])) : make_int2(-1, 0);
+    out[(int64_t)k * n + sl] = k < m ? make_int2(J(o[k]), IMG(o[k])) : make_int2(-1, 0);
 }
 
 template <bool F64>
@@ -223,6 +223,34 @@ __global__ void __launch_bounds__(PTM_BLOCK) k_topo64(const __grid_constant__ Fr
   const int cnt = *list_count;
   for (int i = blockIdx.x * PTM_BLOCK + threadIdx.x; i < cnt; i += gridDim.x * PTM_BLOCK)
     topo_atom<F64, true>(d, list[i], (int *)tsm_raw, out, nullptr, nullptr);
+}
+
+// The same two passes over a batch: every slot finds its frame (frames in the
+// Euclidean order have no topological buffer and are skipped); each frame's
+// order lands in its own segment of the batch's buffer (FrameDesc::topo).
+template <bool F64>
+__global__ void __launch_bounds__(PTM_BLOCK)
+    k_topo_batch(const FrameDesc *__restrict__ descs, const int64_t *__restrict__ atom_off, int nframes,
+                 int64_t ntotal, int *list, int *list_count) {
+  extern __shared__ __align__(16) unsigned char tsm_raw[];
+  const int64_t s = (int64_t)blockIdx.x * PTM_BLOCK + threadIdx.x;
+  if (s >= ntotal) return;
+  const FrameDesc &d = descs[frame_of(atom_off, nframes, s)];
+  if (!d.topo) return;
+  topo_atom<F64, false>(d, (int)s, (int *)tsm_raw, const_cast<int2 *>(d.topo), list, list_count);
+}
+
+template <bool F64>
+__global__ void __launch_bounds__(PTM_BLOCK)
+    k_topo64_batch(const FrameDesc *__restrict__ descs, const int64_t *__restrict__ atom_off, int nframes,
+                   const int *list, const int *list_count) {
+  extern __shared__ __align__(16) unsigned char tsm_raw[];
+  const int cnt = *list_count;
+  for (int i = blockIdx.x * PTM_BLOCK + threadIdx.x; i < cnt; i += gridDim.x * PTM_BLOCK) {
+    const int s = list[i];
+    const FrameDesc &d = descs[frame_of(atom_off, nframes, s)];
+    topo_atom<F64, true>(d, s, (int *)tsm_raw, const_cast<int2 *>(d.topo), nullptr, nullptr);
+  }
 }
 
 constexpr size_t topo_smem_bytes() { return (size_t)PTM_BLOCK * PTM_TOPO_WORDS * 4; }

@@ -85,21 +85,50 @@ def test_clusters_and_small_boxes(ptm):
     check(ptm, f)
 
 
-def test_host_entry_and_unsupported_paths(ptm):
-    import torch
-    from paper_1603_05143_gb300 import PTMError, Server
+def test_host_entry_and_noalloc_rejection(ptm):
+    import ctypes as C
+    from paper_1603_05143_gb300.binding import _frame, ptm_outputs, PTM_F32
     f = I.config_mixed_phase(n_target=1 << 13)
     d = run(ptm, f)
     h = ptm.classify_host(f.positions, f.cell, f.pbc, species=f.species, ordering="topological")
     for k in d:
         assert np.array_equal(d[k], h[k]), k
-    # batches and servers take the Euclidean order only
-    srv = Server(ptm)
-    from paper_1603_05143_gb300.binding import _frame, ptm_outputs, PTM_F32
-    import ctypes as C
+    # the allocation-free entry has no room for the ordering buffers
     fr = _frame(f.n, f.positions.ctypes.data, PTM_F32, None, f.cell, f.pbc, 31, math.inf, "topological")
-    t = C.c_uint64()
-    assert ptm.lib.ptm_submit(srv.h, C.byref(fr), C.byref(ptm_outputs()), C.byref(t)) == 1
+    assert ptm.lib.ptm_classify_frame_noalloc(C.byref(fr), C.byref(ptm_outputs()), None) == 1
+
+
+def test_batch_mixing_orderings_matches_single_frames(ptm):
+    """A batch whose frames ask for either order gives each frame the results of
+    a single-frame call with its order (the frames' ordering buffers are
+    segments of one batch buffer)."""
+    import torch
+    frames = I.config_batch(seed=12, n_frames=6, n_min=1500, n_max=9000)
+    frames.append(I.config_mixed_phase(n_target=1 << 13))
+    orders = ["topological" if i % 2 == 0 else "euclidean" for i in range(len(frames))]
+    dev = [{"positions": torch.from_numpy(f.positions).cuda(), "species": torch.from_numpy(f.species).cuda(),
+            "cell": f.cell, "pbc": f.pbc, "ordering": o} for f, o in zip(frames, orders)]
+    b = ptm.batch(dev)
+    b.run()
+    torch.cuda.synchronize()
+    for f, o, out in zip(frames, orders, b.outputs):
+        single = run(ptm, f, ordering=o)
+        for k in single:
+            assert np.array_equal(out[k].cpu().numpy(), single[k]), (f.name, o, k)
+    b.close()
+
+
+def test_server_serves_topological_frames(ptm):
+    from paper_1603_05143_gb300 import Server
+    frames = I.config_batch(seed=13, n_frames=5, n_min=1000, n_max=6000)
+    srv = Server(ptm, streams=2)
+    tickets = [srv.submit(f.positions, f.cell, f.pbc, species=f.species, ordering="topological") for f in frames]
+    for f, t in zip(frames, tickets):
+        out = srv.wait(t, 60000)
+        single = run(ptm, f)
+        for k in single:
+            assert np.array_equal(out[k], single[k]), (f.name, k)
+        srv.release(t)
     srv.close()
 
 
