@@ -17,8 +17,7 @@ ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
 def _sources():
-    return [CSRC / "ptm.cu", CSRC / "ptm_kernels.cuh", CSRC / "ptm_atom.cuh", CSRC / "ptm_serve.cuh",
-            CSRC / "ptm_peak.cuh", PKG / "tables.py", INCLUDE / "ptm.h", pathlib.Path(__file__)]
+    return sorted(CSRC.glob("*.cu*")) + [PKG / "tables.py", INCLUDE / "ptm.h", pathlib.Path(__file__)]
 
 
 def nvcc_command(out: pathlib.Path = LIB) -> list:

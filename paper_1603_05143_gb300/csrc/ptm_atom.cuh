@@ -273,18 +273,48 @@ __device__ __forceinline__ void orient_pair_filter(float ax, float ay, float az,
   sc = dc > 0x1p42f ? 1 : (dc < -0x1p42f ? -1 : 0);
 }
 
-__device__ __noinline__ int orient_centre_exact(const Scratch &sm, int a, int b, int c) {
-  const long long o = orient_raw(sm.QI(a, 0), sm.QI(a, 1), sm.QI(a, 2), sm.QI(b, 0), sm.QI(b, 1), sm.QI(b, 2),
-                                 sm.QI(c, 0), sm.QI(c, 1), sm.QI(c, 2), 0, 0, 0);
-  return (o > 0) - (o < 0);
+// Exact signs for the facets the FP32 filter left open: bit f of `openp` asks
+// for orient(a, b, c, p) (SoS when exactly 0; a positive sign sets bit f of
+// vis), bit f of `openc` for orient(a, b, c, origin) (exact, no SoS: zero
+// clears `inside`).  One normal n = (b - a) x (c - a) in 64-bit integers serves
+// both: orient(a, b, c, x) = n . (x - a).  The lanes of `wmask` take one open
+// facet each per step and step together, so the 64-bit arithmetic runs once
+// per step for the warp, with few values live (the filter loop has finished).
+__device__ __forceinline__ void hull_exact(const Scratch &sm, int p, uint32_t openp, uint32_t openc, unsigned wmask,
+                                           uint32_t &vis, bool &inside, const FrameDesc &d) {
+  uint32_t open = openp | openc;
+  while (__any_sync(wmask, open != 0)) {
+    if (!open) continue;
+    const int f = __ffs(open) - 1;
+    open &= open - 1;
+    const int v = sm.F(f);
+    const int a = v & 15, b = (v >> 4) & 15, c = (v >> 8) & 15;
+    const int ax = sm.QI(a, 0), ay = sm.QI(a, 1), az = sm.QI(a, 2);
+    const int ux = sm.QI(b, 0) - ax, uy = sm.QI(b, 1) - ay, uz = sm.QI(b, 2) - az;
+    const int vx = sm.QI(c, 0) - ax, vy = sm.QI(c, 1) - ay, vz = sm.QI(c, 2) - az;
+    const long long nx = (long long)uy * vz - (long long)uz * vy;
+    const long long ny = (long long)uz * vx - (long long)ux * vz;
+    const long long nz = (long long)ux * vy - (long long)uy * vx;
+    if (openp >> f & 1) {
+      const long long o = nx * (sm.QI(p, 0) - ax) + ny * (sm.QI(p, 1) - ay) + nz * (sm.QI(p, 2) - az);
+      int sp = (o > 0) - (o < 0);
+      if (!sp) {
+        count(d, C_SOS);
+        sp = orient_sos_slow(sm, a, b, c, p);
+      }
+      if (sp > 0) vis |= 1u << f;
+    }
+    if (openc >> f & 1) inside &= nx * ax + ny * ay + nz * az > 0;   // orient(a, b, c, origin) = -n . a < 0
+  }
 }
 
 // Facets of the current hull visible from point p (bit f set), and whether the
 // centre lies strictly inside the current hull (exact, no SoS: zero rejects),
 // computed only when `centre` is asked for.  Both use one normal per facet.
-__device__ uint32_t hull_visibility(const Scratch &sm, int nf, int p, bool centre, bool &centre_in,
+// `wmask`: the lanes of the warp that call this together.
+__device__ uint32_t hull_visibility(const Scratch &sm, int nf, int p, bool centre, bool &centre_in, unsigned wmask,
                                     const FrameDesc &d) {
-  uint32_t vis = 0;
+  uint32_t vis = 0, openp = 0, openc = 0;
   bool inside = true;
   const float px = sm.Q(p, 0), py = sm.Q(p, 1), pz = sm.Q(p, 2);
 #pragma unroll 2
@@ -294,19 +324,22 @@ __device__ uint32_t hull_visibility(const Scratch &sm, int nf, int p, bool centr
     int sp, sc;
     orient_pair_filter(sm.Q(a, 0), sm.Q(a, 1), sm.Q(a, 2), sm.Q(b, 0), sm.Q(b, 1), sm.Q(b, 2), sm.Q(c, 0),
                        sm.Q(c, 1), sm.Q(c, 2), px, py, pz, sp, sc);
-    if (!sp) sp = orient_exact_sos(sm, a, b, c, p, d);
-    if (centre && !sc) sc = orient_centre_exact(sm, a, b, c);
     if (sp > 0) vis |= 1u << f;
-    inside &= sc < 0;
+    if (!sp) openp |= 1u << f;
+    if (!sc) openc |= 1u << f;
+    inside &= sc <= 0;
   }
+  if (!centre || !inside) openc = 0;          // the centre's answer is already known
+  hull_exact(sm, p, openp, openc, wmask, vis, inside, d);
   centre_in = centre && inside;
   return vis;
 }
 
 // Centre strictly inside the current hull (for the last snapshot, where no
 // further point is inserted).
-__device__ bool hull_centre_inside(const Scratch &sm, int nf) {
+__device__ bool hull_centre_inside(const Scratch &sm, int nf, unsigned wmask, const FrameDesc &d) {
   bool inside = true;
+  uint32_t openc = 0;
 #pragma unroll 2
   for (int f = 0; f < nf; f++) {
     const int v = sm.F(f);
@@ -314,9 +347,12 @@ __device__ bool hull_centre_inside(const Scratch &sm, int nf) {
     int sp, sc;
     orient_pair_filter(sm.Q(a, 0), sm.Q(a, 1), sm.Q(a, 2), sm.Q(b, 0), sm.Q(b, 1), sm.Q(b, 2), sm.Q(c, 0),
                        sm.Q(c, 1), sm.Q(c, 2), 0.f, 0.f, 0.f, sp, sc);
-    if (!sc) sc = orient_centre_exact(sm, a, b, c);
-    inside &= sc < 0;
+    if (!sc) openc |= 1u << f;
+    inside &= sc <= 0;
   }
+  if (!inside) openc = 0;
+  uint32_t vis = 0;
+  hull_exact(sm, 0, 0, openc, wmask, vis, inside, d);
   return inside;
 }
 

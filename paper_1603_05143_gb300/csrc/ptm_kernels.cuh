@@ -165,20 +165,24 @@ __device__ __noinline__ int knn_to_scratch(const FrameDesc &d, const Scratch &sm
   typename RT<F64>::T Ld2[PTM_KNN];
   int Lid[PTM_KNN], Ljs[PTM_KNN], Limg[PTM_KNN];
   const int cnt = knn<F64>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, Ld2, Lid, Ljs, Limg);
+#pragma unroll
   for (int t = 0; t < PTM_KNN; t++) { sm.NID(t) = Ljs[t]; sm.DX(t) = __int_as_float(Limg[t]); }
   return cnt;
 }
 
-// Fast kNN for the common case (27 cells suffice, no equal distances among the
-// 15 nearest): pass 1 keeps the 15 smallest distances with a min/max network;
-// pass 2 rescans and drops each of the 14 nearest into its rank slot (the
-// scratch rows NID / DX hold sorted index and image until the caller reads
-// them).  With no equal distances the distance order is the full key order.
-// Returns false when the general kNN must decide.
-template <bool F64, int NK, typename Put>
+// Fast kNN for the common case (27 cells suffice): pass 1 keeps the NK + 1
+// smallest distances with a min/max network; pass 2 rescans and drops each of
+// the NK nearest into its rank slot.  Equal distances (an atom's mirror-image
+// neighbours in a perfect centrosymmetric lattice) form a run of slots that
+// pass 2 fills in key order (atom id, then image) by insertion; a run that
+// continues past slot NK - 1 keeps its smallest keys, as the general kNN does.
+// Slots are written through `rows`: put(r, j, img) and, while ties are ordered,
+// set(r, j, img, id) / j(r) / img(r) / id(r) (j = -1: empty).  Returns false
+// when the general kNN must decide.
+template <bool F64, int NK, typename Rows>
 __device__ __forceinline__ bool knn_fast_n(const FrameDesc &d, int s, typename RT<F64>::T xi,
                                            typename RT<F64>::T yi, typename RT<F64>::T zi, int bx, int by, int bz,
-                                           Put &&put) {
+                                           const Rows &rows) {
   typedef typename RT<F64>::T T;
   T L[NK + 1];
 #pragma unroll
@@ -189,28 +193,59 @@ __device__ __forceinline__ bool knn_fast_n(const FrameDesc &d, int s, typename R
 #pragma unroll
     for (int t = 0; t <= NK; t++) { const T lo = fmin(L[t], x); x = fmax(L[t], x); L[t] = lo; }
   });
-  bool distinct = L[NK] < (T)INFINITY;
+  if (!(L[NK] < (T)INFINITY) || !search_complete(d, 1, (float)L[NK - 1])) return false;
+  uint32_t tie = 0;                                  // bit t: L[t] == L[t + 1]
 #pragma unroll
-  for (int t = 0; t < NK; t++) distinct &= L[t] < L[t + 1];
-  if (!distinct || !search_complete(d, 1, (float)L[NK - 1])) return false;
+  for (int t = 0; t < NK; t++) tie |= (uint32_t)(L[t] == L[t + 1]) << t;
   const T last = L[NK - 1];
-  scan_cells<F64>(d, s, xi, yi, zi, bx, by, bz, 0, 0, 0, false, 1, [&](int j, T d2, int, int a0, int a1, int a2) {
-    if (!(d2 <= last)) return;
-    int rank = 0;
+  if (!tie) {                                        // distinct: distance order is key order
+    scan_cells<F64>(d, s, xi, yi, zi, bx, by, bz, 0, 0, 0, false, 1, [&](int j, T d2, int, int a0, int a1, int a2) {
+      if (!(d2 <= last)) return;
+      int rank = 0;
 #pragma unroll
-    for (int t = 0; t < NK - 1; t++) rank += L[t] < d2;
-    put(rank, j, img_pack(a0, a1, a2));
+      for (int t = 0; t < NK - 1; t++) rank += L[t] < d2;
+      rows.put(rank, j, img_pack(a0, a1, a2));
+    });
+    return true;
+  }
+  for (int r = 0; r < NK; r++) rows.set(r, -1, 0, 0);
+  scan_cells<F64>(d, s, xi, yi, zi, bx, by, bz, 0, 0, 0, false, 1, [&](int j, T d2, int idj, int a0, int a1, int a2) {
+    if (!(d2 <= last)) return;
+    int lo = 0;                                      // first slot of this distance (L[lo] == d2)
+#pragma unroll
+    for (int t = 0; t < NK - 1; t++) lo += L[t] < d2;
+    const int img = img_pack(a0, a1, a2);
+    const int hi = min(lo + __ffs(~(tie >> lo)), NK);   // its run: slots lo .. hi - 1
+    if (hi - lo == 1) { rows.put(lo, j, img); return; }
+    int r = lo;                                      // insertion point by (id, image)
+    while (r < hi && rows.j(r) >= 0 && (rows.id(r) < idj || (rows.id(r) == idj && rows.img(r) < img))) r++;
+    if (r == hi) return;                             // beyond the NK nearest
+    int e = r;                                       // first empty slot, or the run's last
+    while (e < hi - 1 && rows.j(e) >= 0) e++;
+    for (int q = e; q > r; q--) rows.set(q, rows.j(q - 1), rows.img(q - 1), rows.id(q - 1));
+    rows.set(r, j, img, idj);
   });
   return true;
 }
 
+// kNN slots in the scratch rows NID (sorted index) and DX (packed image; the
+// caller reads both), with the atom id in row DY while ties are ordered.
+struct ScratchKnnRows {
+  const Scratch &sm;
+  __device__ __forceinline__ void put(int r, int j, int img) const { sm.NID(r) = j; sm.DX(r) = __int_as_float(img); }
+  __device__ __forceinline__ void set(int r, int j, int img, int id) const {
+    put(r, j, img);
+    sm.DY(r) = __int_as_float(id);
+  }
+  __device__ __forceinline__ int j(int r) const { return sm.NID(r); }
+  __device__ __forceinline__ int img(int r) const { return __float_as_int(sm.DX(r)); }
+  __device__ __forceinline__ int id(int r) const { return __float_as_int(sm.DY(r)); }
+};
+
 template <bool F64>
 __device__ __forceinline__ bool knn_fast(const FrameDesc &d, const Scratch &sm, int s, typename RT<F64>::T xi,
                                          typename RT<F64>::T yi, typename RT<F64>::T zi, int bx, int by, int bz) {
-  return knn_fast_n<F64, PTM_KNN>(d, s, xi, yi, zi, bx, by, bz, [&](int rank, int j, int img) {
-    sm.NID(rank) = j;
-    sm.DX(rank) = __int_as_float(img);
-  });
+  return knn_fast_n<F64, PTM_KNN>(d, s, xi, yi, zi, bx, by, bz, ScratchKnnRows{sm});
 }
 
 // ---------------------------------------------------------- per-atom state
@@ -901,9 +936,11 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
     const bool want = (p == 6 && (mask & 1)) || (p == 12 && (mask & 14)) || (p == 14 && (mask & 16));
     bool centre_in = false;
     uint32_t vis = 0;
+    const unsigned vmask = __ballot_sync(hmask, alive && p < kmax);          // lanes testing point p
+    const unsigned cmask = __ballot_sync(hmask, alive && p >= kmax && want); // lanes testing only the centre
     if (alive) {
-      if (p < kmax) vis = hull_visibility(sm, nf, p, want, centre_in, d);
-      else if (want) centre_in = hull_centre_inside(sm, nf);
+      if (p < kmax) vis = hull_visibility(sm, nf, p, want, centre_in, vmask, d);
+      else if (want) centre_in = hull_centre_inside(sm, nf, cmask, d);
     }
     if (alive && want && centre_in) snapshot(p, sm, d, nf, bst);
     if (!alive) continue;

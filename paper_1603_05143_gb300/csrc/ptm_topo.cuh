@@ -110,6 +110,27 @@ __device__ bool topo_order(int m, const T *area, T mean2, int *o) {
   return near;
 }
 
+// kNN slots in the topological scratch: rows J (sorted index) and IMG (packed
+// image); while ties are ordered the atom id sits in the first rows of the FP32
+// vectors, which are written only after the kNN.
+struct TopoKnnRows {
+  int *tsm;
+  int t;
+  __device__ __forceinline__ void put(int r, int j, int img) const {
+    tsm[r * PTM_BLOCK + t] = j;
+    tsm[(PTM_TOPO_N + r) * PTM_BLOCK + t] = img;
+  }
+  __device__ __forceinline__ void set(int r, int j, int img, int id) const {
+    put(r, j, img);
+    ((float *)tsm)[(2 * PTM_TOPO_N + r) * PTM_BLOCK + t] = __int_as_float(id);
+  }
+  __device__ __forceinline__ int j(int r) const { return tsm[r * PTM_BLOCK + t]; }
+  __device__ __forceinline__ int img(int r) const { return tsm[(PTM_TOPO_N + r) * PTM_BLOCK + t]; }
+  __device__ __forceinline__ int id(int r) const {
+    return __float_as_int(((float *)tsm)[(2 * PTM_TOPO_N + r) * PTM_BLOCK + t]);
+  }
+};
+
 // One atom.  First pass (FP64PASS false): FP32 areas decide, and an atom with a
 // gap at the band edge is appended to `list` for the second pass instead of
 // being decided here, so that no warp waits on one lane's FP64 work.  Second
@@ -133,16 +154,14 @@ __device__ void topo_atom(const FrameDesc &d, int s, int *tsm, int2 *__restrict_
 
   // ---- the 18 nearest images
   int m;
-  if (!wrapped && knn_fast_n<F64, PTM_TOPO_N>(d, s, xi, yi, zi, bx, by, bz, [&](int r, int j, int img) {
-        J(r) = j;
-        IMG(r) = img;
-      })) {
+  if (!wrapped && knn_fast_n<F64, PTM_TOPO_N>(d, s, xi, yi, zi, bx, by, bz, TopoKnnRows{tsm, t})) {
     m = PTM_TOPO_N;
   } else {
     TI Ld2[PTM_TOPO_N];
     int Lid[PTM_TOPO_N], Ljs[PTM_TOPO_N], Limg[PTM_TOPO_N];
     m = knn<F64, PTM_TOPO_N>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, Ld2, Lid, Ljs, Limg);
     if (m < 0) m = 0;
+#pragma unroll
     for (int k = 0; k < PTM_TOPO_N; k++) { J(k) = Ljs[k]; IMG(k) = Limg[k]; }
   }
   int o[PTM_TOPO_N];

@@ -62,10 +62,13 @@ def test_lattices(ptm, kind, a, reps, dtype, sigma):
 
 
 def test_unrotated_perfect_lattices_exact_ties(ptm):
-    """Axis-aligned perfect lattices: coplanar facets everywhere (SoS), tied distances."""
-    for kind, a in (("fcc", I.A_FCC_CU), ("bcc", I.A_BCC_FE), ("sc", I.A_SC)):
+    """Axis-aligned perfect lattices: coplanar facets everywhere (SoS), tied
+    distances; the 14th neighbour falls inside a tied shell for fcc and hcp
+    (2 of the 6 second neighbours), so the kNN must order ties by atom id."""
+    for kind, a, reps in (("fcc", I.A_FCC_CU, 4), ("bcc", I.A_BCC_FE, 4), ("sc", I.A_SC, 4),
+                          ("hcp", I.A_HCP, (6, 4, 4))):
         for dtype in (np.float32, np.float64):
-            check(ptm, I.crystal(kind, a, 4, dtype=dtype))
+            check(ptm, I.crystal(kind, a, reps, dtype=dtype))
 
 
 @pytest.mark.parametrize("kind", ["l10", "l12", "b2"])

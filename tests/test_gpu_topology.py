@@ -53,6 +53,16 @@ def test_perfect_lattices_match_euclidean_and_oracle(ptm, kind, a, reps):
     assert st["matched"] == f.n
 
 
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_unrotated_perfect_lattices_exact_ties(ptm, dtype):
+    """Axis-aligned lattices: the 18 nearest hold whole shells of equal
+    distances (bcc: 4 of the 12 third neighbours), ordered by atom id."""
+    for kind, a in (("fcc", I.A_FCC_CU), ("bcc", I.A_BCC_FE), ("sc", I.A_SC)):
+        f = I.crystal(kind, a, 4, dtype=dtype)
+        st, g, ref, s = check(ptm, f)
+        assert st["matched"] == f.n
+
+
 @pytest.mark.parametrize("sigma,dtype", [(0.1, np.float32), (0.2, np.float64), (0.28, np.float32)])
 def test_noisy_fcc_full(ptm, sigma, dtype):
     f = I.crystal("fcc", I.A_FCC_CU, 6, sigma=sigma, seed=8, rotation=I.random_rotation(I.rng_for(6)), dtype=dtype)
