@@ -178,7 +178,7 @@ typedef struct ptm_batch ptm_batch;
    tile_atoms: atoms taken from the queue per grab (default 64, one per
    thread of a block: larger grabs measured 2-2.5x slower);
    blocks_per_sm: resident 64-thread blocks per SM for the persistent grid
-   (default 5, the shared-memory limit).  Atoms per warp are fixed at 32 (one
+   (default 7, the shared-memory limit).  Atoms per warp are fixed at 32 (one
    atom per lane). */
 typedef struct {
   double cell_factor;
@@ -209,7 +209,7 @@ ptm_status ptm_batch_stats(ptm_batch *batch, ptm_stats *out);
 ptm_status ptm_batch_destroy(ptm_batch *batch);
 
 /* Time every candidate tuning on this batch (cell_factor in {1.125, 1.25,
-   1.4}, tile_atoms in {64, 128}, blocks_per_sm in {4, 5}) and return the
+   1.4}, tile_atoms in {64, 128}, blocks_per_sm in {6, 7}) and return the
    fastest in *best.  Runs the batch (every m-th frame of it when it holds more
    than about 4 M atoms) 36 times; outputs are written with the same results
    each time. */

@@ -15,6 +15,7 @@
 
 #define PTM_TBL_CONST __constant__ const
 #define PTM_TBL_GLOBAL __device__ const
+#define PTM_TBL_ALIGN16 __attribute__((aligned(16)))
 #include "ptm_kernels.cuh"
 #include "ptm_topo.cuh"
 
@@ -284,14 +285,19 @@ ptm_status ptm_create(const ptm_options *opt, ptm_context **out) {
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
     ctx->budget = (opt && opt->hbm_budget_bytes) ? opt->hbm_budget_bytes : fr / 2;
-    const size_t smem = atom_smem_bytes();
-    if ((e = cudaFuncSetAttribute(k_atoms<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_atoms<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_atoms<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_atoms<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) {
-      rs = cuda_fail(ctx, e, "cudaFuncSetAttribute");
-      break;
+    // the per-atom kernels want every resident block's scratch in shared
+    // memory: the largest shared-memory carveout of the unified L1
+    const int smem = (int)atom_smem_bytes();
+    const void *fns[] = {(const void *)k_atoms<false>, (const void *)k_atoms<true>, (const void *)k_atoms<false, true>,
+                         (const void *)k_atoms<true, true>, (const void *)k_atoms_batch<false>,
+                         (const void *)k_atoms_batch<true>};
+    for (const void *fn : fns) {
+      if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess ||
+          (e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
+        break;
     }
+    if (e != cudaSuccess) { rs = cuda_fail(ctx, e, "cudaFuncSetAttribute"); break; }
   } while (0);
   if (rs != PTM_OK) { ptm_destroy(ctx); return rs; }
   *out = ctx;
@@ -485,7 +491,7 @@ struct ptm_batch {
   int nframes = 0, f64 = 0;
   int64_t ntotal = 0;
   size_t ncell = 0;
-  int tile_atoms = 64, blocks_per_sm = 5;
+  int tile_atoms = 64, blocks_per_sm = PTM_ATOM_BLOCKS_PER_SM;
   double cell_factor = 1.25;
   FrameDesc *d_descs = nullptr;
   BinParams *d_bp = nullptr;
@@ -763,7 +769,7 @@ extern "C" ptm_status ptm_autotune_batch(ptm_context *ctx, int nframes, const pt
   if (!ctx || !best) return PTM_ERR_INVALID_ARG;
   static const double factors[] = {1.125, 1.25, 1.4};
   static const int tiles[] = {64, 128};
-  static const int bpsm[] = {4, 5};
+  static const int bpsm[] = {PTM_ATOM_BLOCKS_PER_SM - 1, PTM_ATOM_BLOCKS_PER_SM};
   cudaStream_t st = (cudaStream_t)stream;
   // tune on every m-th frame so that at most about 4 M atoms are timed per candidate
   int64_t total = 0;

@@ -74,28 +74,36 @@ __device__ __forceinline__ void count(const FrameDesc &d, int which, unsigned lo
 }
 
 // ------------------------------------------------------------ shared scratch
+// Rows are [word][thread] (every lane its own bank).  The 42 rows of q hold the
+// quantised neighbour vectors while the hulls are built and the FP32 metric
+// vectors after them; nid holds the neighbours' sorted indices until then and
+// their atom ids after.  126 words per thread let 7 blocks of 64 threads share
+// an SM's 228 KB.
 struct Scratch {
-  float *nv;         // [42][B]  neighbour vectors for the metric steps (x[14], y[14], z[14])
-  int *nid;          // [14][B]  neighbour atom ids
-  float *q;          // [42][B]  quantised neighbour vectors (integers |q| <= 2^19, exact in FP32)
+  float *q;          // [42][B]  quantised neighbour vectors (integers |q| <= 2^19, exact in FP32),
+                     //          then the metric vectors DX / DY / DZ
+  int *nid;          // [14][B]  neighbour sorted index, then atom id
+  int *img;          // [14][B]  neighbour image (img_pack)
   uint16_t *fac;     // [24][B]  hull facets a | b << 4 | c << 8 (ccw from outside)
   uint64_t *th;      // [14][B]  third vertex of directed edge u->v, nibble v of row u (0xF none)
   uint16_t *used;    // [14][B]  directed-edge bit rows (hull horizon, Weinberg walk)
-  uint32_t *code;    // [10][B]  best Weinberg code so far (nibbles)
+  uint32_t *code;    // [9][B]   best Weinberg code so far from its third label on (nibbles)
   int t;             // thread index in block
   __device__ __forceinline__ float &Q(int p, int c) const { return q[(3 * p + c) * PTM_BLOCK + t]; }
   __device__ __forceinline__ int QI(int p, int c) const { return (int)q[(3 * p + c) * PTM_BLOCK + t]; }
-  __device__ __forceinline__ float &DX(int j) const { return nv[j * PTM_BLOCK + t]; }
-  __device__ __forceinline__ float &DY(int j) const { return nv[(PTM_KNN + j) * PTM_BLOCK + t]; }
-  __device__ __forceinline__ float &DZ(int j) const { return nv[(2 * PTM_KNN + j) * PTM_BLOCK + t]; }
+  __device__ __forceinline__ float &DX(int j) const { return Q(j, 0); }
+  __device__ __forceinline__ float &DY(int j) const { return Q(j, 1); }
+  __device__ __forceinline__ float &DZ(int j) const { return Q(j, 2); }
   __device__ __forceinline__ int &NID(int j) const { return nid[j * PTM_BLOCK + t]; }
+  __device__ __forceinline__ int &IMG(int j) const { return img[j * PTM_BLOCK + t]; }
   __device__ __forceinline__ uint16_t &F(int f) const { return fac[f * PTM_BLOCK + t]; }
   __device__ __forceinline__ uint64_t &TH(int v) const { return th[v * PTM_BLOCK + t]; }
   __device__ __forceinline__ uint16_t &U(int v) const { return used[v * PTM_BLOCK + t]; }
   __device__ __forceinline__ uint32_t &CODE(int w) const { return code[w * PTM_BLOCK + t]; }
 };
 
-constexpr int SCRATCH_WORDS = 28 + 42 + 42 + 14 + 10 + 12 + 7;   // 32-bit words per thread
+#define PTM_CODE_WORDS 9       // 71 nibbles: labels 3..73 of the longest code (labels 1, 2 are fixed)
+constexpr int SCRATCH_WORDS = 28 + 42 + 14 + 14 + PTM_CODE_WORDS + 12 + 7;   // 32-bit words per thread
 
 // -------------------------------------------------------------- small helpers
 __device__ __forceinline__ int nib(uint64_t x, int i) { return (int)((x >> (4 * i)) & 15); }
@@ -405,28 +413,29 @@ __device__ int weinberg_walk(const Scratch &sm, int K, int u, int v, bool first,
   int state = first ? 1 : 0;        // 1: writing a new best; 0: still equal
   int next = 1;
   uint32_t wbuf = 0, wcur = 0;
+  // label s of the code (s >= 2) is nibble s - 2 of the stored code: every
+  // walk starts with labels 1, 2
   auto emit = [&](int s, int L) -> bool {
+    const int n = s - 2;
     if (state == 0) {
-      if ((s & 7) == 0) wcur = sm.CODE(s >> 3);
-      int B = (wcur >> (4 * (s & 7))) & 15;
+      if ((n & 7) == 0) wcur = sm.CODE(n >> 3);
+      int B = (wcur >> (4 * (n & 7))) & 15;
       if (L > B) return false;
       if (L < B) {                                   // smaller from here on: keep the
         state = 1;                                   // equal prefix of this code word
-        wbuf = wcur & ((1u << (4 * (s & 7))) - 1u);
+        wbuf = wcur & ((1u << (4 * (n & 7))) - 1u);
       }
     }
     if (state == 1) {
-      wbuf |= (uint32_t)L << (4 * (s & 7));
-      if ((s & 7) == 7 || s == LEN - 1) { sm.CODE(s >> 3) = wbuf; wbuf = 0; }
+      wbuf |= (uint32_t)L << (4 * (n & 7));
+      if ((n & 7) == 7 || s == LEN - 1) { sm.CODE(n >> 3) = wbuf; wbuf = 0; }
     }
     return true;
   };
   lab = setnib(lab, u, next++);
-  emit(0, 1);
   sm.U(u) |= 1 << v;
   bool fresh = true;
   lab = setnib(lab, v, next++);
-  if (!emit(1, 2)) return -1;
   int s = 2;
   for (; s < LEN; s++) {
     const uint64_t tv = sm.TH(v);
@@ -517,11 +526,12 @@ __device__ bool canonical(const Scratch &sm, int K, int nf, uint64_t &labels, ui
     if (transitive) break;
   }
   if (first) return false;
-  // hash of the packed code; words past its end count as zero, as the generator packs them
+  // hash of the packed code (labels 3..LEN); words past its end count as zero,
+  // as the generator packs them
   const int LEN = 2 * (3 * K - 6) + 1;
   uint64_t h = PTM_HASH_INIT;
 #pragma unroll
-  for (int w = 0; w < 10; w++) h = (h ^ (uint64_t)(w * 8 < LEN ? sm.CODE(w) : 0u)) * PTM_HASH_MUL;
+  for (int w = 0; w < PTM_CODE_WORDS; w++) h = (h ^ (uint64_t)(w * 8 < LEN - 2 ? sm.CODE(w) : 0u)) * PTM_HASH_MUL;
   hash = h;
   return true;
 }

@@ -157,7 +157,7 @@ __device__ __noinline__ int knn(const FrameDesc &d, int s, typename RT<F64>::T x
 }
 
 // General kNN writing its result like knn_fast: sorted index of neighbour t in
-// scratch row NID(t), its packed image in row DX(t).
+// scratch row NID(t), its packed image in row IMG(t).
 template <bool F64>
 __device__ __noinline__ int knn_to_scratch(const FrameDesc &d, const Scratch &sm, int s, typename RT<F64>::T xi,
                                            typename RT<F64>::T yi, typename RT<F64>::T zi, int bx, int by, int bz,
@@ -166,7 +166,7 @@ __device__ __noinline__ int knn_to_scratch(const FrameDesc &d, const Scratch &sm
   int Lid[PTM_KNN], Ljs[PTM_KNN], Limg[PTM_KNN];
   const int cnt = knn<F64>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, Ld2, Lid, Ljs, Limg);
 #pragma unroll
-  for (int t = 0; t < PTM_KNN; t++) { sm.NID(t) = Ljs[t]; sm.DX(t) = __int_as_float(Limg[t]); }
+  for (int t = 0; t < PTM_KNN; t++) { sm.NID(t) = Ljs[t]; sm.IMG(t) = Limg[t]; }
   return cnt;
 }
 
@@ -228,18 +228,18 @@ __device__ __forceinline__ bool knn_fast_n(const FrameDesc &d, int s, typename R
   return true;
 }
 
-// kNN slots in the scratch rows NID (sorted index) and DX (packed image; the
-// caller reads both), with the atom id in row DY while ties are ordered.
+// kNN slots in the scratch rows NID (sorted index) and IMG (packed image), with
+// the atom id in row Q(r, 0) (free until quantisation) while ties are ordered.
 struct ScratchKnnRows {
   const Scratch &sm;
-  __device__ __forceinline__ void put(int r, int j, int img) const { sm.NID(r) = j; sm.DX(r) = __int_as_float(img); }
+  __device__ __forceinline__ void put(int r, int j, int img) const { sm.NID(r) = j; sm.IMG(r) = img; }
   __device__ __forceinline__ void set(int r, int j, int img, int id) const {
     put(r, j, img);
-    sm.DY(r) = __int_as_float(id);
+    sm.Q(r, 0) = __int_as_float(id);
   }
   __device__ __forceinline__ int j(int r) const { return sm.NID(r); }
-  __device__ __forceinline__ int img(int r) const { return __float_as_int(sm.DX(r)); }
-  __device__ __forceinline__ int id(int r) const { return __float_as_int(sm.DY(r)); }
+  __device__ __forceinline__ int img(int r) const { return sm.IMG(r); }
+  __device__ __forceinline__ int id(int r) const { return __float_as_int(sm.Q(r, 0)); }
 };
 
 template <bool F64>
@@ -265,7 +265,7 @@ __device__ __forceinline__ int snap_index(int K) { return K == 6 ? 0 : (K == 12 
 
 __device__ __forceinline__ int lookup(const Scratch &sm, int K, uint64_t h) {
   const int LEN = 2 * (3 * K - 6) + 1;
-  const int NW = (LEN + 7) / 8;
+  const int NW = (LEN - 2 + 7) / 8;                 // stored labels 3..LEN
   int pos = (int)(h & (PTM_TBL_NSLOTS - 1));
   for (int probe = 0; probe < PTM_TBL_NSLOTS; probe++) {
     const ptm_tbl_entry *e = &ptm_tbl[pos];
@@ -275,7 +275,7 @@ __device__ __forceinline__ int lookup(const Scratch &sm, int K, uint64_t h) {
     if (eh == h && __ldg(&e->nv) == K) {
       bool eq = true;
 #pragma unroll
-      for (int w = 0; w < 10; w++) if (w < NW) eq &= (__ldg(&e->code[w]) == sm.CODE(w));
+      for (int w = 0; w < PTM_CODE_WORDS; w++) if (w < NW) eq &= (__ldg(&e->code[w]) == sm.CODE(w));
       if (eq) return pos;
     }
     pos = (pos + 1) & (PTM_TBL_NSLOTS - 1);
@@ -296,7 +296,7 @@ __device__ __forceinline__ void cov_matrix(int K, const Scratch &sm, const float
 #pragma unroll 2
   for (int j = 0; j < K; j++) {
     const int slot = nib(cand, nib(lab, j) - 1);
-    const float4 w = tplw[S * 15 + slot];
+    const float4 w = __ldg(tplw + S * 15 + slot);
     const float x = sm.DX(j), y = sm.DY(j), z = sm.DZ(j);
     Sm[0][0] = fmaf(w.x, x, Sm[0][0]); Sm[0][1] = fmaf(w.x, y, Sm[0][1]); Sm[0][2] = fmaf(w.x, z, Sm[0][2]);
     Sm[1][0] = fmaf(w.y, x, Sm[1][0]); Sm[1][1] = fmaf(w.y, y, Sm[1][1]); Sm[1][2] = fmaf(w.y, z, Sm[1][2]);
@@ -389,7 +389,7 @@ __device__ void score_candidates(const FrameDesc &d, const Scratch &sm, const fl
     points += K + 1;
     float Sm[3][3];
     cov_matrix(K, sm, tplw, S, lab, cand, Sm);
-    const float Gw = tplw[S * 15].w;
+    const float Gw = __ldg(tplw + S * 15).w;
     int fp64;
     const float r2 = cand_r2(Sm, Gv, Gw, K + 1, fp64, d);
     if (r2 < bst.b1) { bst.b2 = bst.b1; bst.b1 = r2; bst.K = K; bst.cand = c; bst.fp64 = fp64; }
@@ -565,7 +565,7 @@ __device__ void finalize(const FrameDesc &d, const Scratch &sm, const float4 *tp
   cov_matrix(K, sm, tplw, S, lab, cand, Sm);
   float mx, my, mz, Gv;
   data_moments(K, sm, mx, my, mz, Gv);
-  const float Gw = tplw[S * 15].w;
+  const float Gw = __ldg(tplw + S * 15).w;
   float lam, q[4];
   {
     Qcp<float> o;
@@ -600,7 +600,7 @@ __device__ void finalize(const FrameDesc &d, const Scratch &sm, const float4 *tp
 #pragma unroll 2
   for (int j = 0; j < K; j++) {
     int slot = nib(cand, nib(lab, j) - 1);
-    float4 w = tplw[S * 15 + slot];
+    float4 w = __ldg(tplw + S * 15 + slot);
     float vx = sm.DX(j) - mx, vy = sm.DY(j) - my, vz = sm.DZ(j) - mz;
     float rx = R[0][0] * w.x + R[0][1] * w.y + R[0][2] * w.z;
     float ry = R[1][0] * w.x + R[1][1] * w.y + R[1][2] * w.z;
@@ -803,6 +803,42 @@ __device__ __noinline__ void finalize_fp64(const FrameDesc &d, const Scratch &sm
   if (d.alloy) d.alloy[a] = alloy_label(d, sm, S, cp, a);
 }
 
+// Neighbour vectors for the metric steps, in rows DX / DY / DZ over the
+// quantised copy (the hulls are done with it), and the neighbours' atom ids in
+// row NID over their sorted indices: the contract values, or for a shifted
+// image an error-free FP32 sum of difference and shift.
+template <bool F64>
+__device__ __forceinline__ void metric_vectors(const FrameDesc &d, const Scratch &sm, int cnt,
+                                               typename RT<F64>::T xi, typename RT<F64>::T yi,
+                                               typename RT<F64>::T zi) {
+  typedef typename RT<F64>::T T;
+#pragma unroll 2
+  for (int t = 0; t < PTM_KNN; t++) {
+    if (t >= cnt) { sm.NID(t) = -1; sm.DX(t) = sm.DY(t) = sm.DZ(t) = 0.f; continue; }
+    T xj, yj, zj;
+    int idj;
+    load_atom<F64>(d, sm.NID(t), xj, yj, zj, idj);
+    sm.NID(t) = idj;
+    int a0, a1, a2;
+    img_unpack(sm.IMG(t), a0, a1, a2);
+    if constexpr (F64) {
+      T sx, sy, sz;
+      contract_shift<F64>(d, a0, a1, a2, sx, sy, sz);
+      sm.DX(t) = (float)contract_dr(xj, xi, sx); sm.DY(t) = (float)contract_dr(yj, yi, sy);
+      sm.DZ(t) = (float)contract_dr(zj, zi, sz);
+    } else if (a0 == 0 && a1 == 0 && a2 == 0) {
+      sm.DX(t) = __fsub_rn(xj, xi); sm.DY(t) = __fsub_rn(yj, yi); sm.DZ(t) = __fsub_rn(zj, zi);
+    } else {
+      float hx, hy, hz, lx, ly, lz;
+      shift_f32(d, a0, a1, a2, hx, hy, hz, lx, ly, lz);
+      float p, e1, q2, e2;
+      two_sum(xj, -xi, p, e1); two_sum(p, hx, q2, e2); sm.DX(t) = q2 + (e1 + (e2 + lx));
+      two_sum(yj, -yi, p, e1); two_sum(p, hy, q2, e2); sm.DY(t) = q2 + (e1 + (e2 + ly));
+      two_sum(zj, -zi, p, e1); two_sum(p, hz, q2, e2); sm.DZ(t) = q2 + (e1 + (e2 + lz));
+    }
+  }
+}
+
 // ------------------------------------------------------------ one atom
 // P64 selects the FP64 form: the same exact predicates, canonical codes and
 // lookup, then every candidate scored and the winner's outputs computed in FP64
@@ -833,7 +869,7 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
       for (int t = 0; t < PTM_KNN; t++) {
         const int2 e = d.topo[(int64_t)t * d.n + (s - d.atom_offset)];
         sm.NID(t) = e.x;
-        sm.DX(t) = __int_as_float(e.y);
+        sm.IMG(t) = e.y;
         cnt += e.x >= 0;
       }
     } else if (!wrapped && knn_fast<F64>(d, sm, s, xi, yi, zi, bx, by, bz)) {
@@ -843,28 +879,24 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
     }
     hmask = __ballot_sync(live, cnt >= 4);       // lanes that go on to the hulls
     if (cnt < 4) { write_unmatched(d, idi); return; }
-    // rows NID / DX hold (sorted index, image) of each neighbour; move them to
-    // rows Q(t, 0) / Q(t, 1) (free until quantisation) and keep NID / DX for
-    // ids and vectors
-#pragma unroll
-    for (int t = 0; t < PTM_KNN; t++) { sm.Q(t, 0) = __int_as_float(sm.NID(t)); sm.Q(t, 1) = sm.DX(t); }
+    // rows NID / IMG keep (sorted index, image) of each neighbour through the
+    // hulls.  Quantised copy for the exact hull predicates (reading R7): grid
+    // 2^(e - 19) with 2^e above the largest component of the contract vectors
+    // (float32 input: kept in the Q rows between the two loops)
     T emax = 0;
 #pragma unroll 2
     for (int t = 0; t < PTM_KNN; t++) {
-      const int jt = __float_as_int(sm.Q(t, 0)), it = __float_as_int(sm.Q(t, 1));
-      sm.NID(t) = -1;
-      sm.DX(t) = sm.DY(t) = sm.DZ(t) = 0.f;
       if (t >= cnt) continue;
       T xj, yj, zj;
       int idj;
-      load_atom<F64>(d, jt, xj, yj, zj, idj);
-      sm.NID(t) = idj;
+      load_atom<F64>(d, sm.NID(t), xj, yj, zj, idj);
       int a0, a1, a2;
-      img_unpack(it, a0, a1, a2);
+      img_unpack(sm.IMG(t), a0, a1, a2);
       T sx, sy, sz;
       contract_shift<F64>(d, a0, a1, a2, sx, sy, sz);
       T cx = contract_dr(xj, xi, sx), cy = contract_dr(yj, yi, sy), cz = contract_dr(zj, zi, sz);
       emax = fmax(emax, fmax(fabs(cx), fmax(fabs(cy), fabs(cz))));
+      if constexpr (!F64) { sm.Q(t, 0) = cx; sm.Q(t, 1) = cy; sm.Q(t, 2) = cz; }
       if constexpr (P64) {
         double hx, hy, hz;
         shift_f64(d, a0, a1, a2, hx, hy, hz);
@@ -872,45 +904,26 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
         ey[t] = ((double)yj - (double)yi) + hy;
         ez[t] = ((double)zj - (double)zi) + hz;
       }
-      // neighbour vectors for the metric steps: the contract values, or for a
-      // shifted image an error-free FP32 sum of difference and shift
-      if constexpr (F64) {
-        sm.DX(t) = (float)cx; sm.DY(t) = (float)cy; sm.DZ(t) = (float)cz;
-      } else {
-        if (a0 == 0 && a1 == 0 && a2 == 0) {
-          sm.DX(t) = cx; sm.DY(t) = cy; sm.DZ(t) = cz;
-        } else {
-          float hx, hy, hz, lx, ly, lz;
-          shift_f32(d, a0, a1, a2, hx, hy, hz, lx, ly, lz);
-          float p, e1, q2, e2;
-          two_sum(xj, -xi, p, e1); two_sum(p, hx, q2, e2); sm.DX(t) = q2 + (e1 + (e2 + lx));
-          two_sum(yj, -yi, p, e1); two_sum(p, hy, q2, e2); sm.DY(t) = q2 + (e1 + (e2 + ly));
-          two_sum(zj, -zi, p, e1); two_sum(p, hz, q2, e2); sm.DZ(t) = q2 + (e1 + (e2 + lz));
-        }
-      }
     }
-    // quantised copy for the exact hull predicates (reading R7): grid 2^(e - 19)
-    // with 2^e above the largest neighbour-vector component
     int e;
     if constexpr (F64) frexp(emax, &e); else frexpf(emax, &e);
     const T sc = F64 ? (T)ldexp(1.0, PTM_QBITS - e) : (T)ldexpf(1.f, PTM_QBITS - e);
 #pragma unroll 2
     for (int t = 0; t < PTM_KNN; t++) {
       if (t >= cnt) continue;
-      const int jt = __float_as_int(sm.Q(t, 0)), it = __float_as_int(sm.Q(t, 1));
-      T xj, yj, zj;
-      int idj;
-      load_atom<F64>(d, jt, xj, yj, zj, idj);
-      int a0, a1, a2;
-      img_unpack(it, a0, a1, a2);
-      T sx, sy, sz;
-      contract_shift<F64>(d, a0, a1, a2, sx, sy, sz);
-      T cx = contract_dr(xj, xi, sx), cy = contract_dr(yj, yi, sy), cz = contract_dr(zj, zi, sz);
       if constexpr (F64) {
+        T xj, yj, zj;
+        int idj;
+        load_atom<F64>(d, sm.NID(t), xj, yj, zj, idj);
+        int a0, a1, a2;
+        img_unpack(sm.IMG(t), a0, a1, a2);
+        T sx, sy, sz;
+        contract_shift<F64>(d, a0, a1, a2, sx, sy, sz);
+        T cx = contract_dr(xj, xi, sx), cy = contract_dr(yj, yi, sy), cz = contract_dr(zj, zi, sz);
         sm.Q(t, 0) = (float)__double2int_rn(cx * sc); sm.Q(t, 1) = (float)__double2int_rn(cy * sc);
         sm.Q(t, 2) = (float)__double2int_rn(cz * sc);
       } else {
-        sm.Q(t, 0) = rintf(cx * sc); sm.Q(t, 1) = rintf(cy * sc); sm.Q(t, 2) = rintf(cz * sc);
+        sm.Q(t, 0) = rintf(sm.Q(t, 0) * sc); sm.Q(t, 1) = rintf(sm.Q(t, 1) * sc); sm.Q(t, 2) = rintf(sm.Q(t, 2) * sc);
       }
     }
   }
@@ -951,6 +964,7 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
   const bool found = bst.ent6 >= 0 || bst.ent12 >= 0 || bst.ent14 >= 0;
   const unsigned qmask = __ballot_sync(hmask, found);
   if (!found) { write_unmatched(d, idi); return; }
+  metric_vectors<F64>(d, sm, cnt, xi, yi, zi);
   if constexpr (!P64) {
     score_candidates(d, sm, tplw, bst, qmask);
     if (bst.K < 0) { write_unmatched(d, idi); return; }     // every match masked out
@@ -1174,31 +1188,38 @@ __global__ void k_scatter_batch(const BinParams *__restrict__ bp, const int64_t 
   wrapv[slot] = atom_wrap[i];
 }
 
-constexpr size_t atom_smem_bytes() {
-  return (size_t)PTM_BLOCK * SCRATCH_WORDS * 4 + 5 * 15 * sizeof(float4);
+constexpr size_t atom_smem_bytes() { return (size_t)PTM_BLOCK * SCRATCH_WORDS * 4; }
+
+// Resident blocks per SM of the per-atom kernels: 7 x (126 words x 64 threads + the
+// 1 KB the driver reserves per block) fits 228 KB of shared memory, and 7 x 64
+// threads x 146 registers the register file.
+#define PTM_ATOM_BLOCKS_PER_SM 7
+
+// Scratch rows in a block's dynamic shared memory (row layout of Scratch).
+__device__ __forceinline__ Scratch scratch_rows(unsigned char *smem) {
+  Scratch sm;
+  sm.th = (uint64_t *)smem;
+  sm.q = (float *)(sm.th + 14 * PTM_BLOCK);
+  sm.nid = (int *)(sm.q + 42 * PTM_BLOCK);
+  sm.img = sm.nid + 14 * PTM_BLOCK;
+  sm.code = (uint32_t *)(sm.img + 14 * PTM_BLOCK);
+  sm.fac = (uint16_t *)(sm.code + PTM_CODE_WORDS * PTM_BLOCK);
+  sm.used = sm.fac + 24 * PTM_BLOCK;
+  sm.t = threadIdx.x;
+  return sm;
 }
+
+// Normalised templates as float4 (x, y, z, .) in global memory, read through the
+// read-only cache (shared memory is spent on per-thread scratch).
+__device__ __forceinline__ const float4 *template_rows() { return reinterpret_cast<const float4 *>(&ptm_tpl[0][0][0]); }
 
 // The frame descriptor travels by value in the kernel parameters, so back-to-back
 // asynchronous calls never share a staging buffer.
 template <bool F64, bool P64 = false>
-__global__ void __launch_bounds__(PTM_BLOCK, 5) k_atoms(const __grid_constant__ FrameDesc d) {
+__global__ void __launch_bounds__(PTM_BLOCK, PTM_ATOM_BLOCKS_PER_SM) k_atoms(const __grid_constant__ FrameDesc d) {
   extern __shared__ __align__(16) unsigned char smem[];
-  uint64_t *th = (uint64_t *)smem;
-  float *q = (float *)(th + 14 * PTM_BLOCK);
-  float *nv = q + 42 * PTM_BLOCK;
-  int *nid = (int *)(nv + 42 * PTM_BLOCK);
-  uint32_t *code = (uint32_t *)(nid + 14 * PTM_BLOCK);
-  uint16_t *fac = (uint16_t *)(code + 10 * PTM_BLOCK);
-  uint16_t *used = fac + 24 * PTM_BLOCK;
-  float4 *tplw = (float4 *)(used + 14 * PTM_BLOCK);
-  for (int i = threadIdx.x; i < 75; i += blockDim.x) {
-    const float *w = ptm_tpl[i / 15][i % 15];
-    tplw[i] = make_float4(w[0], w[1], w[2], w[3]);
-  }
-  __syncthreads();
-  Scratch sm;
-  sm.q = q; sm.nv = nv; sm.nid = nid; sm.fac = fac; sm.th = th; sm.used = used; sm.code = code;
-  sm.t = threadIdx.x;
+  const Scratch sm = scratch_rows(smem);
+  const float4 *tplw = template_rows();
   int64_t s = (int64_t)blockIdx.x * PTM_BLOCK + threadIdx.x;
   const unsigned live = __ballot_sync(0xffffffffu, s < d.n);
   if (s >= d.n) return;
@@ -1210,26 +1231,13 @@ __global__ void __launch_bounds__(PTM_BLOCK, 5) k_atoms(const __grid_constant__ 
 // so uneven frames balance across the GPU.  Each slot finds its frame by a
 // binary search over the frames' first slots.
 template <bool F64>
-__global__ void __launch_bounds__(PTM_BLOCK, 5)
+__global__ void __launch_bounds__(PTM_BLOCK, PTM_ATOM_BLOCKS_PER_SM)
     k_atoms_batch(const FrameDesc *__restrict__ descs, const int64_t *__restrict__ atom_off, int nframes,
                   int64_t ntotal, int tile_atoms, unsigned long long *queue) {
   extern __shared__ __align__(16) unsigned char smem[];
-  uint64_t *th = (uint64_t *)smem;
-  float *q = (float *)(th + 14 * PTM_BLOCK);
-  float *nv = q + 42 * PTM_BLOCK;
-  int *nid = (int *)(nv + 42 * PTM_BLOCK);
-  uint32_t *code = (uint32_t *)(nid + 14 * PTM_BLOCK);
-  uint16_t *fac = (uint16_t *)(code + 10 * PTM_BLOCK);
-  uint16_t *used = fac + 24 * PTM_BLOCK;
-  float4 *tplw = (float4 *)(used + 14 * PTM_BLOCK);
+  const Scratch sm = scratch_rows(smem);
+  const float4 *tplw = template_rows();
   __shared__ long long tile0;
-  for (int i = threadIdx.x; i < 75; i += blockDim.x) {
-    const float *w = ptm_tpl[i / 15][i % 15];
-    tplw[i] = make_float4(w[0], w[1], w[2], w[3]);
-  }
-  Scratch sm;
-  sm.q = q; sm.nv = nv; sm.nid = nid; sm.fac = fac; sm.th = th; sm.used = used; sm.code = code;
-  sm.t = threadIdx.x;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) tile0 = (long long)atomicAdd(queue, (unsigned long long)tile_atoms);

@@ -37,7 +37,7 @@ import numpy as np
 
 TEMPLATE_NAMES = ("SC", "FCC", "HCP", "ICO", "BCC")
 K = (6, 12, 12, 12, 14)
-NIB_WORDS = 10          # 73 four-bit labels
+NIB_WORDS = 9           # labels 3..73 of the longest code, four bits each (labels 1, 2 are fixed)
 HASH_MUL = 0x100000001B3
 HASH_INIT = 0xCBF29CE484222325
 MASK64 = (1 << 64) - 1
@@ -236,8 +236,10 @@ def canonical_form(facets):
 
 
 def pack_code(code) -> list:
+    """Labels 3.. of a code as nibbles (every walk starts with labels 1, 2)."""
+    assert code[0] == 1 and code[1] == 2
     words = [0] * NIB_WORDS
-    for s, x in enumerate(code):
+    for s, x in enumerate(code[2:]):
         words[s // 8] |= (x & 15) << (4 * (s % 8))
     return words
 
@@ -335,7 +337,8 @@ def emit_header(path: pathlib.Path) -> dict:
              "#pragma once", "#include <stdint.h>",
              "/* storage qualifiers: constant memory for uniform reads, global for tables */",
              "#ifndef PTM_TBL_CONST", "#define PTM_TBL_CONST static const", "#endif",
-             "#ifndef PTM_TBL_GLOBAL", "#define PTM_TBL_GLOBAL static const", "#endif", ""]
+             "#ifndef PTM_TBL_GLOBAL", "#define PTM_TBL_GLOBAL static const", "#endif",
+             "#ifndef PTM_TBL_ALIGN16", "#define PTM_TBL_ALIGN16", "#endif", ""]
     lines.append(f"#define PTM_TBL_NSLOTS {nslots}")
     lines.append(f"#define PTM_TBL_NCAND {len(cand)}")
     lines.append(f"#define PTM_HASH_INIT 0x{HASH_INIT:016x}ULL")
@@ -344,7 +347,7 @@ def emit_header(path: pathlib.Path) -> dict:
     lines.append(f"#define PTM_GROUP_TOTAL {goff[-1]}")
     lines.append("")
     lines.append("/* normalised templates (x, y, z, .), slot 0 = centre (its .w holds sum |w|^2); Eq. 4 */")
-    lines.append("PTM_TBL_CONST float ptm_tpl[5][15][4] = {")
+    lines.append("PTM_TBL_GLOBAL float ptm_tpl[5][15][4] PTM_TBL_ALIGN16 = {")
     for w in tpl:
         gw = float(np.sum(w * w))
         # the strain fit uses pinv = V^T / (G_w / 3): every template has an isotropic
@@ -373,7 +376,7 @@ def emit_header(path: pathlib.Path) -> dict:
         for q in qs:
             lines.append("  {" + ", ".join(f"{x:.9e}f" for x in q) + "},")
     lines.append("};")
-    lines.append("typedef struct { uint64_t hash; uint32_t code[10]; uint16_t nv, first, count, pad; } ptm_tbl_entry;")
+    lines.append(f"typedef struct {{ uint64_t hash; uint32_t code[{NIB_WORDS}]; uint16_t nv, first, count, pad; }} ptm_tbl_entry;")
     lines.append("PTM_TBL_GLOBAL ptm_tbl_entry ptm_tbl[PTM_TBL_NSLOTS] = {")
     for e in slots:
         if e is None:
