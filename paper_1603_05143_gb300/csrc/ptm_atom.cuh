@@ -325,7 +325,7 @@ __device__ uint32_t hull_visibility(const Scratch &sm, int nf, int p, bool centr
   uint32_t vis = 0, openp = 0, openc = 0;
   bool inside = true;
   const float px = sm.Q(p, 0), py = sm.Q(p, 1), pz = sm.Q(p, 2);
-#pragma unroll 2
+#pragma unroll 1
   for (int f = 0; f < nf; f++) {
     const int v = sm.F(f);
     const int a = v & 15, b = (v >> 4) & 15, c = (v >> 8) & 15;
@@ -348,7 +348,7 @@ __device__ uint32_t hull_visibility(const Scratch &sm, int nf, int p, bool centr
 __device__ bool hull_centre_inside(const Scratch &sm, int nf, unsigned wmask, const FrameDesc &d) {
   bool inside = true;
   uint32_t openc = 0;
-#pragma unroll 2
+#pragma unroll 1
   for (int f = 0; f < nf; f++) {
     const int v = sm.F(f);
     const int a = v & 15, b = (v >> 4) & 15, c = (v >> 8) & 15;

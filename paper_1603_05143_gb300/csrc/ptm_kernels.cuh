@@ -85,7 +85,7 @@ __device__ __forceinline__ void scan_cells(const FrameDesc &d, int s, typename R
         const int n0 = mx + wix, n1 = my + wiy, n2 = mz + wiz;
         T sx, sy, sz;
         contract_shift<F64>(d, n0, n1, n2, sx, sy, sz);
-#pragma unroll 2
+#pragma unroll 1
         for (int j = j0; j < j1; j++) {
           T xj, yj, zj;
           int idj;
@@ -293,7 +293,7 @@ __device__ __forceinline__ void cov_matrix(int K, const Scratch &sm, const float
   for (int a = 0; a < 3; a++)
 #pragma unroll
     for (int b = 0; b < 3; b++) Sm[a][b] = 0.f;
-#pragma unroll 2
+#pragma unroll 1
   for (int j = 0; j < K; j++) {
     const int slot = nib(cand, nib(lab, j) - 1);
     const float4 w = __ldg(tplw + S * 15 + slot);
@@ -307,7 +307,7 @@ __device__ __forceinline__ void cov_matrix(int K, const Scratch &sm, const float
 // Barycentre of the centre and its first K neighbours, and G_v = sum |v - mean|^2.
 __device__ __forceinline__ void data_moments(int K, const Scratch &sm, float &mx, float &my, float &mz, float &Gv) {
   float sx = 0, sy = 0, sz = 0, g = 0;
-#pragma unroll 2
+#pragma unroll 1
   for (int j = 0; j < K; j++) {
     const float x = sm.DX(j), y = sm.DY(j), z = sm.DZ(j);
     sx += x; sy += y; sz += z;
@@ -597,7 +597,7 @@ __device__ void finalize(const FrameDesc &d, const Scratch &sm, const float4 *tp
   }
   float lsum = sqrtf(mx * mx + my * my + mz * mz);
   uint64_t corr = 0;
-#pragma unroll 2
+#pragma unroll 1
   for (int j = 0; j < K; j++) {
     int slot = nib(cand, nib(lab, j) - 1);
     float4 w = __ldg(tplw + S * 15 + slot);
@@ -812,7 +812,7 @@ __device__ __forceinline__ void metric_vectors(const FrameDesc &d, const Scratch
                                                typename RT<F64>::T xi, typename RT<F64>::T yi,
                                                typename RT<F64>::T zi) {
   typedef typename RT<F64>::T T;
-#pragma unroll 2
+#pragma unroll 1
   for (int t = 0; t < PTM_KNN; t++) {
     if (t >= cnt) { sm.NID(t) = -1; sm.DX(t) = sm.DY(t) = sm.DZ(t) = 0.f; continue; }
     T xj, yj, zj;
@@ -884,7 +884,7 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
     // 2^(e - 19) with 2^e above the largest component of the contract vectors
     // (float32 input: kept in the Q rows between the two loops)
     T emax = 0;
-#pragma unroll 2
+#pragma unroll 1
     for (int t = 0; t < PTM_KNN; t++) {
       if (t >= cnt) continue;
       T xj, yj, zj;
@@ -908,7 +908,7 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
     int e;
     if constexpr (F64) frexp(emax, &e); else frexpf(emax, &e);
     const T sc = F64 ? (T)ldexp(1.0, PTM_QBITS - e) : (T)ldexpf(1.f, PTM_QBITS - e);
-#pragma unroll 2
+#pragma unroll 1
     for (int t = 0; t < PTM_KNN; t++) {
       if (t >= cnt) continue;
       if constexpr (F64) {
