@@ -175,8 +175,10 @@ typedef struct ptm_batch ptm_batch;
 
 /* Tunables of a batch; a field <= 0 keeps its default.
    cell_factor: cell width / expected 14-neighbour radius (default 1.25);
-   tile_atoms: atoms taken from the queue per grab (default 64, one per
-   thread of a block: larger grabs measured 2-2.5x slower);
+   tile_atoms: atoms one warp takes from the queue per grab, rounded up to a
+   multiple of 32 (default 32, one per lane: each warp grabs on its own, so
+   no warp waits for another; larger grabs lengthen the tail when the queue
+   runs dry, 64 measured 10 % slower on a 2^20-atom frame);
    blocks_per_sm: resident 64-thread blocks per SM for the persistent grid
    (default 7, the shared-memory limit).  Atoms per warp are fixed at 32 (one
    atom per lane). */
@@ -209,7 +211,7 @@ ptm_status ptm_batch_stats(ptm_batch *batch, ptm_stats *out);
 ptm_status ptm_batch_destroy(ptm_batch *batch);
 
 /* Time every candidate tuning on this batch (cell_factor in {1.125, 1.25,
-   1.4}, tile_atoms in {64, 128}, blocks_per_sm in {6, 7}) and return the
+   1.4}, tile_atoms in {32, 64}, blocks_per_sm in {6, 7}) and return the
    fastest in *best.  Runs the batch (every m-th frame of it when it holds more
    than about 4 M atoms) 36 times; outputs are written with the same results
    each time. */

@@ -491,7 +491,7 @@ struct ptm_batch {
   int nframes = 0, f64 = 0;
   int64_t ntotal = 0;
   size_t ncell = 0;
-  int tile_atoms = 64, blocks_per_sm = PTM_ATOM_BLOCKS_PER_SM;
+  int tile_atoms = 32, blocks_per_sm = PTM_ATOM_BLOCKS_PER_SM;
   double cell_factor = 1.25;
   FrameDesc *d_descs = nullptr;
   BinParams *d_bp = nullptr;
@@ -562,8 +562,10 @@ static ptm_status batch_enqueue(ptm_batch *b, cudaStream_t st) {
                                                                            b->topo_list, cnt);
     }
   }
+  // two warps per block, each pulling its own tiles
+  const int64_t tiles = (b->ntotal + b->tile_atoms - 1) / b->tile_atoms;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->nsm * b->blocks_per_sm,
-                                                                       (b->ntotal + b->tile_atoms - 1) / b->tile_atoms));
+                                                                       (tiles + 1) / 2));
   if (b->f64)
     k_atoms_batch<true><<<grid, PTM_BLOCK, atom_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes,
                                                                     b->ntotal, b->tile_atoms, b->queue);
@@ -673,7 +675,7 @@ extern "C" ptm_status ptm_batch_create(ptm_context *ctx, int nframes, const ptm_
   b->nframes = nframes;
   if (tuning) {
     if (tuning->cell_factor > 0) b->cell_factor = tuning->cell_factor;
-    if (tuning->tile_atoms > 0) b->tile_atoms = (tuning->tile_atoms + PTM_BLOCK - 1) / PTM_BLOCK * PTM_BLOCK;
+    if (tuning->tile_atoms > 0) b->tile_atoms = (tuning->tile_atoms + 31) / 32 * 32;
     if (tuning->blocks_per_sm > 0) b->blocks_per_sm = tuning->blocks_per_sm;
   }
   if (!(b->cell_factor >= 0.5 && b->cell_factor <= 4.0)) { delete b; return PTM_ERR_INVALID_ARG; }
@@ -768,7 +770,7 @@ extern "C" ptm_status ptm_autotune_batch(ptm_context *ctx, int nframes, const pt
                                          const ptm_outputs *outs, void *stream, ptm_tuning *best) {
   if (!ctx || !best) return PTM_ERR_INVALID_ARG;
   static const double factors[] = {1.125, 1.25, 1.4};
-  static const int tiles[] = {64, 128};
+  static const int tiles[] = {32, 64};
   static const int bpsm[] = {PTM_ATOM_BLOCKS_PER_SM - 1, PTM_ATOM_BLOCKS_PER_SM};
   cudaStream_t st = (cudaStream_t)stream;
   // tune on every m-th frame so that at most about 4 M atoms are timed per candidate

@@ -1226,10 +1226,11 @@ __global__ void __launch_bounds__(PTM_BLOCK, PTM_ATOM_BLOCKS_PER_SM) k_atoms(con
   classify_atom<F64, P64>(d, (int)s, sm, tplw, live);
 }
 
-// Persistent classification of a batch: every block pulls tiles of PTM_BLOCK
-// consecutive sorted slots from one global queue until the batch is exhausted,
-// so uneven frames balance across the GPU.  Each slot finds its frame by a
-// binary search over the frames' first slots.
+// Persistent classification of a batch: every warp pulls tiles of tile_atoms
+// (a multiple of 32) consecutive sorted slots from one global queue until the
+// batch is exhausted, so uneven frames balance across the GPU and no warp waits
+// for the other warp of its block.  Each slot finds its frame by a binary
+// search over the frames' first slots.
 template <bool F64>
 __global__ void __launch_bounds__(PTM_BLOCK, PTM_ATOM_BLOCKS_PER_SM)
     k_atoms_batch(const FrameDesc *__restrict__ descs, const int64_t *__restrict__ atom_off, int nframes,
@@ -1237,15 +1238,14 @@ __global__ void __launch_bounds__(PTM_BLOCK, PTM_ATOM_BLOCKS_PER_SM)
   extern __shared__ __align__(16) unsigned char smem[];
   const Scratch sm = scratch_rows(smem);
   const float4 *tplw = template_rows();
-  __shared__ long long tile0;
+  const int lane = threadIdx.x & 31;
   for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) tile0 = (long long)atomicAdd(queue, (unsigned long long)tile_atoms);
-    __syncthreads();
-    const long long base = tile0;
-    if (base >= ntotal) break;
-    for (int k = 0; k < tile_atoms; k += PTM_BLOCK) {
-      const long long s = base + k + threadIdx.x;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(queue, (unsigned long long)tile_atoms);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((long long)base >= ntotal) break;
+    for (int k = 0; k < tile_atoms; k += 32) {
+      const long long s = (long long)base + k + lane;
       const unsigned live = __ballot_sync(0xffffffffu, s < ntotal);
       if (s < ntotal) {
         const int f = frame_of(atom_off, nframes, s);

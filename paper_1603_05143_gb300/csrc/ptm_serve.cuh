@@ -151,7 +151,7 @@ ptm_status launch_batch(ptm_server *S, std::vector<Request *> &rs, int slot, InF
   b->nframes = nf;
   b->owns_block = false;
   if (S->tuning.cell_factor > 0) b->cell_factor = S->tuning.cell_factor;
-  if (S->tuning.tile_atoms > 0) b->tile_atoms = (S->tuning.tile_atoms + PTM_BLOCK - 1) / PTM_BLOCK * PTM_BLOCK;
+  if (S->tuning.tile_atoms > 0) b->tile_atoms = (S->tuning.tile_atoms + 31) / 32 * 32;
   if (S->tuning.blocks_per_sm > 0) b->blocks_per_sm = S->tuning.blocks_per_sm;
   cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
   BatchPlan P;
