@@ -287,10 +287,11 @@ ptm_status ptm_create(const ptm_options *opt, ptm_context **out) {
     ctx->budget = (opt && opt->hbm_budget_bytes) ? opt->hbm_budget_bytes : fr / 2;
     // the per-atom kernels want every resident block's scratch in shared
     // memory: the largest shared-memory carveout of the unified L1
-    const int smem = (int)atom_smem_bytes();
+    const int smem = (int)std::max(atom_smem_bytes(), topo_smem_bytes());
     const void *fns[] = {(const void *)k_atoms<false>, (const void *)k_atoms<true>, (const void *)k_atoms<false, true>,
                          (const void *)k_atoms<true, true>, (const void *)k_atoms_batch<false>,
-                         (const void *)k_atoms_batch<true>};
+                         (const void *)k_atoms_batch<true>, (const void *)k_topo<false>, (const void *)k_topo<true>,
+                         (const void *)k_topo_batch<false>, (const void *)k_topo_batch<true>};
     for (const void *fn : fns) {
       if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess ||
           (e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,

@@ -21,14 +21,20 @@ namespace ptm {
 #define PTM_TOPO_N 18
 #define PTM_TOPO_BAND 1e-3
 #define PTM_TOPO_GUARD 2e-5
-#define PTM_TOPO_VMAX 24       // polygon buffer: 4 + 17 clips add at most 21 vertices
+#define PTM_TOPO_VMAX 24       // FP64 polygon buffer: 4 + 17 clips add at most 21 vertices
+// FP32 pass: polygons of up to 12 vertices in shared memory (the largest polygon met
+// while clipping an atom's 18 faces had 11 vertices in 6,000 atoms of crystals and
+// liquid); an atom whose clipping outgrows it is left to the FP64 pass
+#define PTM_TOPO_VMAX32 12
 // 32-bit words per thread: neighbour ids and images, FP32 vectors, two polygon buffers
-#define PTM_TOPO_WORDS (2 * PTM_TOPO_N + 3 * PTM_TOPO_N + 2 * 2 * PTM_TOPO_VMAX)
+#define PTM_TOPO_WORDS (2 * PTM_TOPO_N + 3 * PTM_TOPO_N + 2 * 2 * PTM_TOPO_VMAX32)
 
 // Area of the Voronoi face of neighbour j among the m vectors V(i, c); P and Q
-// are polygon buffers of 2 x PTM_TOPO_VMAX values, element e at P[e * st].
+// are polygon buffers of 2 x vmax values, element e at P[e * st].  A clip that
+// would leave more than vmax vertices sets `over` (the polygon keeps its first
+// vmax vertices).
 template <typename T, typename Vec>
-__device__ T topo_face_area(int m, int j, T R, Vec V, T *P, T *Q, int st) {
+__device__ T topo_face_area(int m, int j, T R, Vec V, T *P, T *Q, int st, int vmax, bool &over) {
   const T n0 = V(j, 0), n1 = V(j, 1), n2 = V(j, 2);
   const T nn = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
   const T u0 = n0 / nn, u1 = n1 / nn, u2 = n2 / nn;
@@ -40,10 +46,9 @@ __device__ T topo_face_area(int m, int j, T R, Vec V, T *P, T *Q, int st) {
   e10 /= l1; e11 /= l1; e12 /= l1;
   const T e20 = u1 * e12 - u2 * e11, e21 = u2 * e10 - u0 * e12, e22 = u0 * e11 - u1 * e10;
   const T p0 = n0 / 2, p1 = n1 / 2, p2 = n2 / 2;
-  // a convex polygon gains at most one vertex per clip (4 + 17 < VMAX);
+  // a convex polygon gains at most one vertex per clip (4 + 17 < PTM_TOPO_VMAX);
   // rounding on a nearly degenerate polygon could emit more, so writes stop at
   // the buffer's end (the polygon then has next to no area either way)
-  constexpr int VMAX = PTM_TOPO_VMAX;
   T *cur = P, *nxt = Q;
   int np = 4;
   cur[0] = -R; cur[st] = -R; cur[2 * st] = R; cur[3 * st] = -R;
@@ -58,13 +63,18 @@ __device__ T topo_face_area(int m, int j, T R, Vec V, T *P, T *Q, int st) {
       const int k1 = k + 1 == np ? 0 : k + 1;
       const T xs = cur[2 * k * st], xt = cur[(2 * k + 1) * st], ys = cur[2 * k1 * st], yt = cur[(2 * k1 + 1) * st];
       const T fx = A * xs + B * xt - C, fy = A * ys + B * yt - C;
-      if (fx <= 0 && nq < VMAX) { nxt[2 * nq * st] = xs; nxt[(2 * nq + 1) * st] = xt; nq++; }
-      if (((fx < 0 && fy > 0) || (fx > 0 && fy < 0)) && nq < VMAX) {
+      if (fx <= 0) {
+        if (nq < vmax) { nxt[2 * nq * st] = xs; nxt[(2 * nq + 1) * st] = xt; }
+        nq++;
+      }
+      if ((fx < 0 && fy > 0) || (fx > 0 && fy < 0)) {
         const T tt = fx / (fx - fy);
-        nxt[2 * nq * st] = xs + tt * (ys - xs); nxt[(2 * nq + 1) * st] = xt + tt * (yt - xt); nq++;
+        if (nq < vmax) { nxt[2 * nq * st] = xs + tt * (ys - xs); nxt[(2 * nq + 1) * st] = xt + tt * (yt - xt); }
+        nq++;
       }
     }
-    np = nq;
+    over |= nq > vmax;
+    np = min(nq, vmax);
     T *tmp = cur; cur = nxt; nxt = tmp;
   }
   T s2 = 0;
@@ -196,11 +206,13 @@ __device__ void topo_atom(const FrameDesc &d, int s, int *tsm, int2 *__restrict_
       auto vf = [&](int i, int c) -> float { return VF(i, c); };
       // polygon buffers in shared memory, one word per thread per row
       float *PB = (float *)tsm + 5 * PTM_TOPO_N * PTM_BLOCK + t;
-      float *QB = PB + 2 * PTM_TOPO_VMAX * PTM_BLOCK;
+      float *QB = PB + 2 * PTM_TOPO_VMAX32 * PTM_BLOCK;
       float area[PTM_TOPO_N];
-      for (int k = 0; k < m; k++) area[k] = topo_face_area<float>(m, k, R, vf, PB, QB, PTM_BLOCK);
-      if (topo_order<float>(m, area, mean2, o)) {
-        count(d, C_TOPO64);                       // a gap at the band edge: the second pass decides
+      bool over = false;
+      for (int k = 0; k < m; k++) area[k] = topo_face_area<float>(m, k, R, vf, PB, QB, PTM_BLOCK, PTM_TOPO_VMAX32, over);
+      // a gap at the band edge, or a polygon larger than the buffer: the second pass decides
+      if (topo_order<float>(m, area, mean2, o) || over) {
+        count(d, C_TOPO64);
         list[atomicAdd(list_count, 1)] = s;
       }
     }
@@ -216,7 +228,9 @@ __device__ void topo_atom(const FrameDesc &d, int s, int *tsm, int2 *__restrict_
       mean64 /= m;
       auto vd = [&](int i, int c) -> double { return v64[i][c]; };
       double P64[2 * PTM_TOPO_VMAX], Q64[2 * PTM_TOPO_VMAX];
-      for (int k = 0; k < m; k++) a64[k] = topo_face_area<double>(m, k, 10.0 * sqrt(dmax64), vd, P64, Q64, 1);
+      bool over = false;
+      for (int k = 0; k < m; k++)
+        a64[k] = topo_face_area<double>(m, k, 10.0 * sqrt(dmax64), vd, P64, Q64, 1, PTM_TOPO_VMAX, over);
       topo_order<double>(m, a64, mean64, o);
     }
   }
