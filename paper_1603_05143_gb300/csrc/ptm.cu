@@ -47,6 +47,7 @@ struct ptm_context {
   // topological order of every atom's 14 neighbours (k_topo -> k_atoms)
   int2 *topo = nullptr;
   int *topo_list = nullptr;        // atoms for the FP64 pass; [n] = their count
+  TopoSide *topo_side = nullptr;   // what the FP32 pass keeps for the FP64 pass
   size_t cap_topo = 0;
 };
 
@@ -144,11 +145,14 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
   if (topological && (size_t)n > ctx->cap_topo) {
     cudaFree(ctx->topo);
     cudaFree(ctx->topo_list);
+    cudaFree(ctx->topo_side);
     ctx->topo = nullptr;
     ctx->topo_list = nullptr;
+    ctx->topo_side = nullptr;
     ctx->cap_topo = 0;
     CK(cudaMalloc(&ctx->topo, (size_t)n * PTM_KNN * sizeof(int2)));
     CK(cudaMalloc(&ctx->topo_list, ((size_t)n + 1) * sizeof(int)));
+    CK(cudaMalloc(&ctx->topo_side, topo_side_bytes((size_t)n)));
     ctx->cap_topo = (size_t)n;
   }
 
@@ -221,12 +225,18 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
     CK(cudaMemsetAsync(cnt, 0, sizeof(int), st));
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    const int cap_side = (int)topo_side_cap(ctx->cap_topo);
+    const unsigned g64 = (unsigned)(PTM_TOPO64_BLOCKS_PER_SM * sms);
     if (f64) {
-      k_topo<true><<<ga, PTM_BLOCK, topo_smem_bytes(), st>>>(desc, ctx->topo, ctx->topo_list, cnt);
-      k_topo64<true><<<4 * sms, PTM_BLOCK, topo_smem_bytes(), st>>>(desc, ctx->topo, ctx->topo_list, cnt);
+      k_topo<true><<<ga, PTM_BLOCK, topo_smem_bytes(), st>>>(desc, ctx->topo, ctx->topo_list, cnt, ctx->topo_side,
+                                                             cap_side);
+      k_topo64<true><<<g64, PTM_BLOCK, topo64_smem_bytes(), st>>>(desc, ctx->topo, ctx->topo_list, cnt,
+                                                                  ctx->topo_side, cap_side);
     } else {
-      k_topo<false><<<ga, PTM_BLOCK, topo_smem_bytes(), st>>>(desc, ctx->topo, ctx->topo_list, cnt);
-      k_topo64<false><<<4 * sms, PTM_BLOCK, topo_smem_bytes(), st>>>(desc, ctx->topo, ctx->topo_list, cnt);
+      k_topo<false><<<ga, PTM_BLOCK, topo_smem_bytes(), st>>>(desc, ctx->topo, ctx->topo_list, cnt, ctx->topo_side,
+                                                              cap_side);
+      k_topo64<false><<<g64, PTM_BLOCK, topo64_smem_bytes(), st>>>(desc, ctx->topo, ctx->topo_list, cnt,
+                                                                   ctx->topo_side, cap_side);
     }
   }
   if (ctx->precision == PTM_PREC_FP64) {
@@ -287,11 +297,13 @@ ptm_status ptm_create(const ptm_options *opt, ptm_context **out) {
     ctx->budget = (opt && opt->hbm_budget_bytes) ? opt->hbm_budget_bytes : fr / 2;
     // the per-atom kernels want every resident block's scratch in shared
     // memory: the largest shared-memory carveout of the unified L1
-    const int smem = (int)std::max(atom_smem_bytes(), topo_smem_bytes());
+    const int smem = (int)std::max(atom_smem_bytes(), std::max(topo_smem_bytes(), topo64_smem_bytes()));
     const void *fns[] = {(const void *)k_atoms<false>, (const void *)k_atoms<true>, (const void *)k_atoms<false, true>,
                          (const void *)k_atoms<true, true>, (const void *)k_atoms_batch<false>,
                          (const void *)k_atoms_batch<true>, (const void *)k_topo<false>, (const void *)k_topo<true>,
-                         (const void *)k_topo_batch<false>, (const void *)k_topo_batch<true>};
+                         (const void *)k_topo_batch<false>, (const void *)k_topo_batch<true>,
+                         (const void *)k_topo64<false>, (const void *)k_topo64<true>,
+                         (const void *)k_topo64_batch<false>, (const void *)k_topo64_batch<true>};
     for (const void *fn : fns) {
       if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess ||
           (e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -319,6 +331,7 @@ ptm_status ptm_destroy(ptm_context *ctx) {
   cudaFree(ctx->o_quat); cudaFree(ctx->o_strain); cudaFree(ctx->o_corr); cudaFree(ctx->o_vm); cudaFree(ctx->o_rf);
   cudaFree(ctx->topo);
   cudaFree(ctx->topo_list);
+  cudaFree(ctx->topo_side);
   delete ctx;
   return PTM_OK;
 }
@@ -509,6 +522,7 @@ struct ptm_batch {
   int topo = 0;                   // some frame takes the topological order
   int2 *topo_buf = nullptr;       // per-frame segments of neighbour orders
   int *topo_list = nullptr;       // atoms for the FP64 pass; [ntotal] = their count
+  TopoSide *topo_side = nullptr;  // what the FP32 pass keeps for the FP64 pass
   void *block = nullptr;          // the workspace (one allocation, or a pool block when served)
   bool owns_block = true;
 };
@@ -551,16 +565,18 @@ static ptm_status batch_enqueue(ptm_batch *b, cudaStream_t st) {
     int *cnt = b->topo_list + b->ntotal;
     CK(cudaMemsetAsync(cnt, 0, sizeof(int), st));
     const unsigned gt = (unsigned)((b->ntotal + PTM_BLOCK - 1) / PTM_BLOCK);
+    const int cap_side = (int)topo_side_cap((size_t)b->ntotal);
+    const unsigned g64 = (unsigned)(PTM_TOPO64_BLOCKS_PER_SM * b->nsm);
     if (b->f64) {
       k_topo_batch<true><<<gt, PTM_BLOCK, topo_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes, b->ntotal,
-                                                                 b->topo_list, cnt);
-      k_topo64_batch<true><<<4 * b->nsm, PTM_BLOCK, topo_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes,
-                                                                          b->topo_list, cnt);
+                                                                 b->topo_list, cnt, b->topo_side, cap_side);
+      k_topo64_batch<true><<<g64, PTM_BLOCK, topo64_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes,
+                                                                        b->topo_list, cnt, b->topo_side, cap_side);
     } else {
       k_topo_batch<false><<<gt, PTM_BLOCK, topo_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes, b->ntotal,
-                                                                  b->topo_list, cnt);
-      k_topo64_batch<false><<<4 * b->nsm, PTM_BLOCK, topo_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes,
-                                                                           b->topo_list, cnt);
+                                                                  b->topo_list, cnt, b->topo_side, cap_side);
+      k_topo64_batch<false><<<g64, PTM_BLOCK, topo64_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes,
+                                                                         b->topo_list, cnt, b->topo_side, cap_side);
     }
   }
   // two warps per block, each pulling its own tiles
@@ -619,7 +635,7 @@ static ptm_status batch_plan(int nframes, const ptm_frame *frames, double cell_f
 static size_t batch_workspace_bytes(int nframes, int64_t ntotal, size_t ncell, int f64, int topo) {
   const size_t n = (size_t)ntotal, rec = f64 ? sizeof(Atom64) : sizeof(float4);
   const size_t nblk = (ncell + 1 + 2 * SCAN_BLOCK - 1) / (2 * SCAN_BLOCK) + 1;
-  const size_t tb = topo ? sizeof(int2) * PTM_KNN * n + 4 * (n + 1) + 2 * 256 : 0;
+  const size_t tb = topo ? sizeof(int2) * PTM_KNN * n + 4 * (n + 1) + topo_side_bytes(n) + 3 * 256 : 0;
   return (sizeof(FrameDesc) + sizeof(BinParams) + sizeof(int64_t) + 16) * nframes + rec * n + 20 * n +
          8 * (ncell + 1) + 4 * nblk + 4 + 8 + 8 * C_NCOUNTERS + 16 * 256 + tb;
 }
@@ -646,6 +662,7 @@ static void batch_layout(ptm_batch *b, unsigned char *base, BatchPlan &P, const 
   if (P.topo) {
     b->topo_buf = (int2 *)take(sizeof(int2) * PTM_KNN * n);
     b->topo_list = (int *)take(4 * (n + 1));
+    b->topo_side = (TopoSide *)take(topo_side_bytes(n));
   }
   for (int f = 0; f < nf; f++) {
     // frame f's topological order: rows of n_f entries from slot 14 x (first slot)

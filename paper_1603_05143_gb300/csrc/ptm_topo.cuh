@@ -86,10 +86,11 @@ __device__ T topo_face_area(int m, int j, T R, Vec V, T *P, T *Q, int st, int vm
 }
 
 // Order o[0..m) of neighbour ranks by (area descending, rank ascending), then
-// group by the band and order each group by rank.  Returns true when a gap
-// between consecutive areas lies within the guard of the band edge.
+// group by the band and order each group by rank.  Returns the faces (bit =
+// neighbour rank) on either side of a gap between consecutive areas that lies
+// within the guard of the band edge; 0 when every gap is clear of it.
 template <typename T>
-__device__ bool topo_order(int m, const T *area, T mean2, int *o) {
+__device__ uint32_t topo_order(int m, const T *area, T mean2, int *o) {
   for (int k = 0; k < m; k++) o[k] = k;
   for (int k = 1; k < m; k++) {                       // insertion sort, stable in rank
     const int x = o[k];
@@ -98,13 +99,13 @@ __device__ bool topo_order(int m, const T *area, T mean2, int *o) {
     o[p] = x;
   }
   const T band = (T)PTM_TOPO_BAND * mean2, guard = (T)PTM_TOPO_GUARD * mean2;
-  bool near = false;
+  uint32_t near = 0;
   int g0 = 0;
   for (int k = 1; k <= m; k++) {
     bool split = k == m;
     if (k < m) {
       const T gap = area[o[k - 1]] - area[o[k]];
-      near |= fabs(gap - band) <= guard;
+      if (fabs(gap - band) <= guard) near |= (1u << o[k - 1]) | (1u << o[k]);
       split = gap > band;
     }
     if (split) {                                      // group o[g0..k): order by rank
@@ -141,12 +142,24 @@ struct TopoKnnRows {
   }
 };
 
-// One atom.  First pass (FP64PASS false): FP32 areas decide, and an atom with a
-// gap at the band edge is appended to `list` for the second pass instead of
-// being decided here, so that no warp waits on one lane's FP64 work.  Second
-// pass (true): the listed atoms, every area in FP64 from FP64 neighbour vectors.
-template <bool F64, bool FP64PASS>
-__device__ void topo_atom(const FrameDesc &d, int s, int *tsm, int2 *__restrict__ out, int *list, int *list_count) {
+// What the FP32 pass leaves for the FP64 pass about a listed atom: its 18
+// neighbours, their FP32 face areas and the faces to recompute in FP64 (bit =
+// neighbour rank: the two faces of every gap at the band edge, or all).
+struct TopoSide {
+  int2 nb[PTM_TOPO_N];
+  float area[PTM_TOPO_N];
+  uint32_t faces;
+  uint32_t pad;
+};
+
+// One atom, FP32 areas.  An atom with an area gap at the band edge (or a
+// polygon larger than the FP32 buffers) is appended to `list` for the FP64 pass
+// instead of being decided here, so that no warp waits on one lane's FP64 work;
+// the first cap_side listed atoms leave their neighbours, areas and uncertain
+// faces in `side`.
+template <bool F64>
+__device__ void topo_atom(const FrameDesc &d, int s, int *tsm, int2 *__restrict__ out, int *list, int *list_count,
+                          TopoSide *side, int cap_side) {
   typedef typename RT<F64>::T TI;
   const int t = threadIdx.x;
   auto J = [&](int k) -> int & { return tsm[k * PTM_BLOCK + t]; };
@@ -175,63 +188,54 @@ __device__ void topo_atom(const FrameDesc &d, int s, int *tsm, int2 *__restrict_
     for (int k = 0; k < PTM_TOPO_N; k++) { J(k) = Ljs[k]; IMG(k) = Limg[k]; }
   }
   int o[PTM_TOPO_N];
-  if constexpr (!FP64PASS) {
-    // FP32 neighbour vectors: the difference of positions plus the image
-    // shift, summed without loss (error-free sums), as the metric steps use them
-    float mean2 = 0.f, dmax2 = 0.f;
-    for (int k = 0; k < m; k++) {
-      TI xj, yj, zj;
-      int idj;
-      load_atom<F64>(d, J(k), xj, yj, zj, idj);
-      int a0, a1, a2;
-      img_unpack(IMG(k), a0, a1, a2);
-      if constexpr (F64) {
-        double hx, hy, hz;
-        shift_f64(d, a0, a1, a2, hx, hy, hz);
-        VF(k, 0) = (float)((xj - xi) + hx); VF(k, 1) = (float)((yj - yi) + hy); VF(k, 2) = (float)((zj - zi) + hz);
-      } else {
-        float hx, hy, hz, lx, ly, lz, p, e1, q2, e2;
-        shift_f32(d, a0, a1, a2, hx, hy, hz, lx, ly, lz);
-        two_sum(xj, -xi, p, e1); two_sum(p, hx, q2, e2); VF(k, 0) = q2 + (e1 + (e2 + lx));
-        two_sum(yj, -yi, p, e1); two_sum(p, hy, q2, e2); VF(k, 1) = q2 + (e1 + (e2 + ly));
-        two_sum(zj, -zi, p, e1); two_sum(p, hz, q2, e2); VF(k, 2) = q2 + (e1 + (e2 + lz));
-      }
-      const float r2 = VF(k, 0) * VF(k, 0) + VF(k, 1) * VF(k, 1) + VF(k, 2) * VF(k, 2);
-      mean2 += r2;
-      dmax2 = fmaxf(dmax2, r2);
+  // FP32 neighbour vectors: the difference of positions plus the image
+  // shift, summed without loss (error-free sums), as the metric steps use them
+  float mean2 = 0.f, dmax2 = 0.f;
+  for (int k = 0; k < m; k++) {
+    TI xj, yj, zj;
+    int idj;
+    load_atom<F64>(d, J(k), xj, yj, zj, idj);
+    int a0, a1, a2;
+    img_unpack(IMG(k), a0, a1, a2);
+    if constexpr (F64) {
+      double hx, hy, hz;
+      shift_f64(d, a0, a1, a2, hx, hy, hz);
+      VF(k, 0) = (float)((xj - xi) + hx); VF(k, 1) = (float)((yj - yi) + hy); VF(k, 2) = (float)((zj - zi) + hz);
+    } else {
+      float hx, hy, hz, lx, ly, lz, p, e1, q2, e2;
+      shift_f32(d, a0, a1, a2, hx, hy, hz, lx, ly, lz);
+      two_sum(xj, -xi, p, e1); two_sum(p, hx, q2, e2); VF(k, 0) = q2 + (e1 + (e2 + lx));
+      two_sum(yj, -yi, p, e1); two_sum(p, hy, q2, e2); VF(k, 1) = q2 + (e1 + (e2 + ly));
+      two_sum(zj, -zi, p, e1); two_sum(p, hz, q2, e2); VF(k, 2) = q2 + (e1 + (e2 + lz));
     }
-    if (m > 0) {
-      mean2 /= (float)m;
-      const float R = 10.f * sqrtf(dmax2);
-      auto vf = [&](int i, int c) -> float { return VF(i, c); };
-      // polygon buffers in shared memory, one word per thread per row
-      float *PB = (float *)tsm + 5 * PTM_TOPO_N * PTM_BLOCK + t;
-      float *QB = PB + 2 * PTM_TOPO_VMAX32 * PTM_BLOCK;
-      float area[PTM_TOPO_N];
-      bool over = false;
-      for (int k = 0; k < m; k++) area[k] = topo_face_area<float>(m, k, R, vf, PB, QB, PTM_BLOCK, PTM_TOPO_VMAX32, over);
-      // a gap at the band edge, or a polygon larger than the buffer: the second pass decides
-      if (topo_order<float>(m, area, mean2, o) || over) {
-        count(d, C_TOPO64);
-        list[atomicAdd(list_count, 1)] = s;
+    const float r2 = VF(k, 0) * VF(k, 0) + VF(k, 1) * VF(k, 1) + VF(k, 2) * VF(k, 2);
+    mean2 += r2;
+    dmax2 = fmaxf(dmax2, r2);
+  }
+  if (m > 0) {
+    mean2 /= (float)m;
+    const float R = 10.f * sqrtf(dmax2);
+    auto vf = [&](int i, int c) -> float { return VF(i, c); };
+    // polygon buffers in shared memory, one word per thread per row
+    float *PB = (float *)tsm + 5 * PTM_TOPO_N * PTM_BLOCK + t;
+    float *QB = PB + 2 * PTM_TOPO_VMAX32 * PTM_BLOCK;
+    float area[PTM_TOPO_N];
+    bool over = false;
+    for (int k = 0; k < m; k++) area[k] = topo_face_area<float>(m, k, R, vf, PB, QB, PTM_BLOCK, PTM_TOPO_VMAX32, over);
+    // a gap at the band edge, or a polygon larger than the buffer: the second pass decides
+    const uint32_t near = topo_order<float>(m, area, mean2, o);
+    if (near || over) {
+      count(d, C_TOPO64);
+      const int slot = atomicAdd(list_count, 1);
+      list[slot] = s;
+      if (slot < cap_side) {                      // what the FP64 pass reuses
+        TopoSide &sd = side[slot];
+        for (int k = 0; k < PTM_TOPO_N; k++) {
+          sd.nb[k] = k < m ? make_int2(J(k), IMG(k)) : make_int2(-1, 0);
+          sd.area[k] = k < m ? area[k] : 0.f;
+        }
+        sd.faces = over ? ~0u : near;
       }
-    }
-  } else {
-    if (m > 0) {
-      double v64[PTM_TOPO_N][3], a64[PTM_TOPO_N], mean64 = 0.0, dmax64 = 0.0;
-      for (int k = 0; k < m; k++) {
-        vec_fp64<F64>(d, xi, yi, zi, J(k), IMG(k), v64[k][0], v64[k][1], v64[k][2]);
-        const double r2 = v64[k][0] * v64[k][0] + v64[k][1] * v64[k][1] + v64[k][2] * v64[k][2];
-        mean64 += r2;
-        dmax64 = fmax(dmax64, r2);
-      }
-      mean64 /= m;
-      auto vd = [&](int i, int c) -> double { return v64[i][c]; };
-      double P64[2 * PTM_TOPO_VMAX], Q64[2 * PTM_TOPO_VMAX];
-      bool over = false;
-      for (int k = 0; k < m; k++)
-        a64[k] = topo_face_area<double>(m, k, 10.0 * sqrt(dmax64), vd, P64, Q64, 1, PTM_TOPO_VMAX, over);
-      topo_order<double>(m, a64, mean64, o);
     }
   }
   const int64_t n = d.n, sl = s - d.atom_offset;     // frame-local slot
@@ -239,23 +243,96 @@ __device__ void topo_atom(const FrameDesc &d, int s, int *tsm, int2 *__restrict_
     out[(int64_t)k * n + sl] = k < m ? make_int2(J(o[k]), IMG(o[k])) : make_int2(-1, 0);
 }
 
+// FP64 pass for listed atom i (= list position), one thread: FP64 neighbour
+// vectors, and in FP64 the areas of the faces the FP32 pass could not decide
+// (the two faces of every gap at the band edge); the others keep their FP32
+// areas, whose error (measured within 2.2e-6 of the mean squared distance) is
+// far below the guard, so every gap decided from them is decided as in FP64.
+// Atoms past the side buffer find their neighbours again and recompute every
+// face.  Polygon buffers in shared memory, element e at P[e * PTM_BLOCK].  The
+// lanes of `wmask` call this together and take their faces in step, one face
+// per lane per trip, so a warp makes as many trips as its busiest lane has
+// faces (not one per face index that any lane needs).
+template <bool F64>
+__device__ void topo_atom64(const FrameDesc &d, int s, int i, const TopoSide *side, int cap_side, double *P,
+                            double *Q, int2 *__restrict__ out, unsigned wmask) {
+  typedef typename RT<F64>::T TI;
+  TI xi, yi, zi;
+  int idi;
+  load_atom<F64>(d, s, xi, yi, zi, idi);
+  int jn[PTM_TOPO_N], im[PTM_TOPO_N], m = 0;
+  double a64[PTM_TOPO_N];
+  uint32_t faces = ~0u;
+  if (i < cap_side) {
+    const TopoSide &sd = side[i];
+    for (int k = 0; k < PTM_TOPO_N; k++) {
+      const int2 e = sd.nb[k];
+      jn[k] = e.x;
+      im[k] = e.y;
+      a64[k] = (double)sd.area[k];
+      m += e.x >= 0;
+    }
+    faces = sd.faces;
+  } else {
+    const int b = __ldg(d.sbin + s);
+    const int bz = b % d.nb[2], byx = b / d.nb[2];
+    const int by = byx % d.nb[1], bx = byx / d.nb[1];
+    const bool wrapped = d.dstat[0] != 0;
+    int wix = 0, wiy = 0, wiz = 0;
+    if (wrapped) img_unpack(__ldg(d.wrapv + s), wix, wiy, wiz);
+    TI Ld2[PTM_TOPO_N];
+    int Lid[PTM_TOPO_N];
+    m = knn<F64, PTM_TOPO_N>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, Ld2, Lid, jn, im);
+    if (m < 0) m = 0;
+  }
+  int o[PTM_TOPO_N];
+  double v64[PTM_TOPO_N][3], mean64 = 0.0, dmax64 = 0.0;
+  if (m > 0) {
+    for (int k = 0; k < m; k++) {
+      vec_fp64<F64>(d, xi, yi, zi, jn[k], im[k], v64[k][0], v64[k][1], v64[k][2]);
+      const double r2 = v64[k][0] * v64[k][0] + v64[k][1] * v64[k][1] + v64[k][2] * v64[k][2];
+      mean64 += r2;
+      dmax64 = fmax(dmax64, r2);
+    }
+    mean64 /= m;
+  }
+  auto vd = [&](int a, int c) -> double { return v64[a][c]; };
+  bool over = false;
+  uint32_t todo = m > 0 ? faces & ((1u << m) - 1u) : 0u;
+  while (__any_sync(wmask, todo != 0)) {
+    if (!todo) continue;
+    const int k = __ffs(todo) - 1;
+    todo &= todo - 1;
+    a64[k] = topo_face_area<double>(m, k, 10.0 * sqrt(dmax64), vd, P, Q, PTM_BLOCK, PTM_TOPO_VMAX, over);
+  }
+  if (m > 0) topo_order<double>(m, a64, mean64, o);
+  const int64_t n = d.n, sl = s - d.atom_offset;     // frame-local slot
+  for (int k = 0; k < PTM_KNN; k++) out[(int64_t)k * n + sl] = k < m ? make_int2(jn[o[k]], im[o[k]]) : make_int2(-1, 0);
+}
+
 template <bool F64>
 __global__ void __launch_bounds__(PTM_BLOCK) k_topo(const __grid_constant__ FrameDesc d, int2 *__restrict__ out,
-                                                    int *list, int *list_count) {
+                                                    int *list, int *list_count, TopoSide *side, int cap_side) {
   extern __shared__ __align__(16) unsigned char tsm_raw[];
   const int64_t s = (int64_t)blockIdx.x * PTM_BLOCK + threadIdx.x;
   if (s >= d.n) return;
-  topo_atom<F64, false>(d, (int)s, (int *)tsm_raw, out, list, list_count);
+  topo_atom<F64>(d, (int)s, (int *)tsm_raw, out, list, list_count, side, cap_side);
 }
 
-// Second pass over the listed atoms (grid-stride: the count is read on the device).
+// Second pass over the listed atoms, one thread per atom (grid-stride over the
+// list: its length is read on the device).
 template <bool F64>
 __global__ void __launch_bounds__(PTM_BLOCK) k_topo64(const __grid_constant__ FrameDesc d, int2 *__restrict__ out,
-                                                      const int *list, const int *list_count) {
+                                                      const int *list, const int *list_count, const TopoSide *side,
+                                                      int cap_side) {
   extern __shared__ __align__(16) unsigned char tsm_raw[];
+  double *P = (double *)tsm_raw + threadIdx.x, *Q = P + 2 * PTM_TOPO_VMAX * PTM_BLOCK;
   const int cnt = *list_count;
-  for (int i = blockIdx.x * PTM_BLOCK + threadIdx.x; i < cnt; i += gridDim.x * PTM_BLOCK)
-    topo_atom<F64, true>(d, list[i], (int *)tsm_raw, out, nullptr, nullptr);
+  for (int i0 = blockIdx.x * PTM_BLOCK + (threadIdx.x & ~31); i0 < cnt; i0 += gridDim.x * PTM_BLOCK) {
+    const int i = i0 + (threadIdx.x & 31);
+    const unsigned wmask = __ballot_sync(0xffffffffu, i < cnt);
+    if (i < cnt) topo_atom64<F64>(d, list[i], i, side, cap_side, P, Q, out, wmask);
+  }
 }
 
 // The same two passes over a batch: every slot finds its frame (frames in the
@@ -264,27 +341,42 @@ __global__ void __launch_bounds__(PTM_BLOCK) k_topo64(const __grid_constant__ Fr
 template <bool F64>
 __global__ void __launch_bounds__(PTM_BLOCK)
     k_topo_batch(const FrameDesc *__restrict__ descs, const int64_t *__restrict__ atom_off, int nframes,
-                 int64_t ntotal, int *list, int *list_count) {
+                 int64_t ntotal, int *list, int *list_count, TopoSide *side, int cap_side) {
   extern __shared__ __align__(16) unsigned char tsm_raw[];
   const int64_t s = (int64_t)blockIdx.x * PTM_BLOCK + threadIdx.x;
   if (s >= ntotal) return;
   const FrameDesc &d = descs[frame_of(atom_off, nframes, s)];
   if (!d.topo) return;
-  topo_atom<F64, false>(d, (int)s, (int *)tsm_raw, const_cast<int2 *>(d.topo), list, list_count);
+  topo_atom<F64>(d, (int)s, (int *)tsm_raw, const_cast<int2 *>(d.topo), list, list_count, side, cap_side);
 }
 
 template <bool F64>
 __global__ void __launch_bounds__(PTM_BLOCK)
     k_topo64_batch(const FrameDesc *__restrict__ descs, const int64_t *__restrict__ atom_off, int nframes,
-                   const int *list, const int *list_count) {
+                   const int *list, const int *list_count, const TopoSide *side, int cap_side) {
   extern __shared__ __align__(16) unsigned char tsm_raw[];
+  double *P = (double *)tsm_raw + threadIdx.x, *Q = P + 2 * PTM_TOPO_VMAX * PTM_BLOCK;
   const int cnt = *list_count;
-  for (int i = blockIdx.x * PTM_BLOCK + threadIdx.x; i < cnt; i += gridDim.x * PTM_BLOCK) {
-    const int s = list[i];
-    const FrameDesc &d = descs[frame_of(atom_off, nframes, s)];
-    topo_atom<F64, true>(d, s, (int *)tsm_raw, const_cast<int2 *>(d.topo), nullptr, nullptr);
+  for (int i0 = blockIdx.x * PTM_BLOCK + (threadIdx.x & ~31); i0 < cnt; i0 += gridDim.x * PTM_BLOCK) {
+    const int i = i0 + (threadIdx.x & 31);
+    const unsigned wmask = __ballot_sync(0xffffffffu, i < cnt);
+    if (i < cnt) {
+      const int s = list[i];
+      const FrameDesc &d = descs[frame_of(atom_off, nframes, s)];
+      topo_atom64<F64>(d, s, i, side, cap_side, P, Q, const_cast<int2 *>(d.topo), wmask);
+    }
   }
 }
+
+// Listed atoms whose neighbours, areas and uncertain faces the FP32 pass keeps
+// for the FP64 pass (a sixteenth of the atoms: 3.6 % were listed in the
+// polycrystal, 2.6 % in the mixed-phase frame; the rest find their neighbours
+// again).
+constexpr size_t topo_side_cap(size_t n) { return n / 16 + 256; }
+constexpr size_t topo_side_bytes(size_t n) { return topo_side_cap(n) * sizeof(TopoSide); }
+// FP64 pass: two polygon buffers of 2 x PTM_TOPO_VMAX doubles per thread
+constexpr size_t topo64_smem_bytes() { return (size_t)PTM_BLOCK * 4 * PTM_TOPO_VMAX * sizeof(double); }
+#define PTM_TOPO64_BLOCKS_PER_SM 4     // 4 x (48 KB + 1 KB) of shared memory
 
 constexpr size_t topo_smem_bytes() { return (size_t)PTM_BLOCK * PTM_TOPO_WORDS * 4; }
 
