@@ -367,8 +367,13 @@ __device__ bool hull_centre_inside(const Scratch &sm, int nf, unsigned wmask, co
 // Insert point p given its visible facets (vis != 0): remove them and fan the
 // horizon to p.  Returns the new facet count, or -1 on an internal error.
 __device__ int hull_apply(const Scratch &sm, int nf, uint32_t vis, int p, const FrameDesc &d) {
-#pragma unroll
-  for (int v = 0; v < PTM_KNN; v++) sm.U(v) = 0;
+  // edge rows of the vertices of the visible facets only (no other row is read)
+  uint32_t verts = 0;
+  for (uint32_t m = vis; m; m &= m - 1) {
+    const int v = sm.F(__ffs(m) - 1);
+    verts |= (1u << (v & 15)) | (1u << ((v >> 4) & 15)) | (1u << ((v >> 8) & 15));
+  }
+  for (uint32_t m = verts; m; m &= m - 1) sm.U(__ffs(m) - 1) = 0;
   for (uint32_t m = vis; m; m &= m - 1) {
     int v = sm.F(__ffs(m) - 1);
     int a = v & 15, b = (v >> 4) & 15, c = (v >> 8) & 15;
@@ -378,7 +383,8 @@ __device__ int hull_apply(const Scratch &sm, int nf, uint32_t vis, int p, const 
   for (int f = 0; f < nf; f++)
     if (!(vis >> f & 1)) sm.F(n2++) = sm.F(f);
   int added = 0;
-  for (int u = 0; u < PTM_KNN; u++) {
+  for (uint32_t mu = verts; mu; mu &= mu - 1) {      // rows in increasing vertex order
+    const int u = __ffs(mu) - 1;
     uint32_t row = sm.U(u);
     while (row) {
       int v = __ffs(row) - 1;
