@@ -369,10 +369,10 @@ __global__ void __launch_bounds__(PTM_BLOCK)
 }
 
 // Listed atoms whose neighbours, areas and uncertain faces the FP32 pass keeps
-// for the FP64 pass (a sixteenth of the atoms: 3.6 % were listed in the
-// polycrystal, 2.6 % in the mixed-phase frame; the rest find their neighbours
-// again).
-constexpr size_t topo_side_cap(size_t n) { return n / 16 + 256; }
+// for the FP64 pass (a quarter of the atoms: 3.6 % were listed in the hot
+// polycrystal, 2.6 % in the mixed-phase frame, up to 15 % in cold crystals; the
+// rest find their neighbours again and recompute every face).
+constexpr size_t topo_side_cap(size_t n) { return n / 4 + 256; }
 constexpr size_t topo_side_bytes(size_t n) { return topo_side_cap(n) * sizeof(TopoSide); }
 // FP64 pass: two polygon buffers of 2 x PTM_TOPO_VMAX doubles per thread
 constexpr size_t topo64_smem_bytes() { return (size_t)PTM_BLOCK * 4 * PTM_TOPO_VMAX * sizeof(double); }

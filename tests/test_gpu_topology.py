@@ -95,6 +95,40 @@ def test_clusters_and_small_boxes(ptm):
     check(ptm, f)
 
 
+def _band_edge_strain(target=1e-3 + 1e-5):
+    """Uniaxial strain of a perfect fcc lattice for which the gap between its
+    two first-shell face areas is `target` x the mean squared distance (the
+    gap grows monotonically with the strain), by bisection on the oracle's
+    areas."""
+    def gap(eps):
+        f = I.crystal("fcc", I.A_FCC_CU, 3, deform=np.diag([1.0, 1.0, 1.0 + eps]), dtype=np.float64)
+        F = O.Frame(f.positions, f.cell, f.pbc)
+        ids, imgs, dr, drc, d2 = F.knn(0, O.TOPO_N)
+        v = np.asarray(drc, float).reshape(-1, 3)
+        a = np.sort(O.voronoi_areas(v))[::-1]
+        g = a[:-1] - a[1:]
+        return g[g > 1e-9 * a[0]][0] / np.mean(np.sum(v * v, 1))
+    lo, hi = 0.5e-3, 2e-3
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if gap(mid) < target else (lo, mid)
+    return 0.5 * (lo + hi)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_band_edge_lattice_every_atom_decided_in_fp64(ptm, dtype):
+    """A strained fcc lattice whose two first-shell face areas differ by the
+    band plus half the guard: every atom has a gap at the band edge, so every
+    atom goes to the FP64 pass, and the three quarters past the records the
+    FP32 pass keeps find their neighbours again and recompute every face."""
+    eps = _band_edge_strain()
+    f = I.crystal("fcc", I.A_FCC_CU, 10, deform=np.diag([1.0, 1.0, 1.0 + eps]), dtype=dtype)
+    atoms = np.sort(I.rng_for(81).choice(f.n, 400, replace=False))     # equivalent atoms: a sample
+    st, g, ref, s = check(ptm, f, atoms=atoms)
+    assert s["topo_fp64"] == f.n
+    assert st["matched"] == len(atoms) and np.all(g["structure"] == 2)
+
+
 def test_host_entry_and_noalloc_rejection(ptm):
     import ctypes as C
     from paper_1603_05143_gb300.binding import _frame, ptm_outputs, PTM_F32
