@@ -33,7 +33,7 @@ UNIT = "atoms/s"
 SM_COUNT = 152
 FP32_LANES = 128
 SM_MAX_MHZ = 2070.0
-# Algorithmic FP32 work ("Roofline"): per scored correspondence of
+# Algorithmic FP32 work, counted from the kernel's arithmetic: per scored correspondence of
 # N points, 18 (N - 1) flops for the covariance plus 232 for Horn's matrix, the
 # characteristic polynomial and 8 Newton steps; per matched atom 2000 flops for
 # the eigenvector, explicit residual, orientation and strain; per atom 126 flops
@@ -145,7 +145,10 @@ class ClockSampler:
     def __init__(self, device):
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # the raw samples go to PTM_CLOCK_LOG_DIR when set, else to the temp directory
+        import tempfile
+        log_dir = os.environ.get("PTM_CLOCK_LOG_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(log_dir, f"clocks_bench_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
