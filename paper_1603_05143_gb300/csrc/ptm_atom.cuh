@@ -472,8 +472,9 @@ __device__ int weinberg_walk(const Scratch &sm, int K, int u, int v, bool first,
 
 // Canonical code of the current K-vertex hull.  Every directed edge u->v gets
 // the key (deg u, deg v, deg w1, deg w2) with (u, v, w1) and (v, u, w2) the two
-// facets on the edge; among the edges with the largest key the smallest
-// Weinberg code wins (definition in tables.py).  Returns the labelling (nibble
+// facets on the edge, continued (for edges tied on it) by the degrees of the
+// third vertices of the facets across their four outer edges; among the edges
+// with the largest key the smallest Weinberg code wins (definition in tables.py).  Returns the labelling (nibble
 // t = label of neighbour t) and the code hash; false on an internal error.
 // Start edges are kept as a bit mask over (facet, corner) and visited by one
 // flat loop, so the threads of a warp run their walks together.
@@ -515,6 +516,29 @@ __device__ bool canonical(const Scratch &sm, int K, int nf, uint64_t &labels, ui
   // K = 12 with every degree 5 is the icosahedron, K = 6 with every degree 4 the
   // octahedron: every directed edge is equivalent, one walk suffices
   const bool transitive = (K == 12 && top == 0x5555u) || (K == 6 && top == 0x4444u);
+  // edges tied on the degrees of the edge's two facets: the key continues with
+  // the degrees of the third vertices of the facets across their outer edges
+  if (!transitive && __popcll((long long)m0) + __popc(m1) > 1) {
+    uint32_t etop = 0;
+    uint64_t n0 = 0;
+    uint32_t n1 = 0;
+    auto consider = [&](int id) {
+      const int v = sm.F(id / 3), e = id % 3;
+      const int p0 = v & 15, p1 = (v >> 4) & 15, p2 = (v >> 8) & 15;
+      const int x = e == 0 ? p0 : (e == 1 ? p1 : p2);      // edge x -> y, third vertex z
+      const int y = e == 0 ? p1 : (e == 1 ? p2 : p0);
+      const int z = e == 0 ? p2 : (e == 1 ? p0 : p1);
+      const int w = nib(sm.TH(y), x);
+      const uint32_t ext = (uint32_t)((nib(deg, nib(sm.TH(z), y)) << 12) | (nib(deg, nib(sm.TH(x), z)) << 8) |
+                                      (nib(deg, nib(sm.TH(w), x)) << 4) | nib(deg, nib(sm.TH(y), w)));
+      if (ext > etop) { etop = ext; n0 = 0; n1 = 0; }
+      if (ext == etop) { if (id < 64) n0 |= 1ull << id; else n1 |= 1u << (id - 64); }
+    };
+    for (uint64_t mm = m0; mm; mm &= mm - 1) consider(__ffsll((long long)mm) - 1);
+    for (uint32_t mm = m1; mm; mm &= mm - 1) consider(64 + __ffs(mm) - 1);
+    m0 = n0;
+    m1 = n1;
+  }
   bool first = true;
   while (m0 | m1) {
     int id;

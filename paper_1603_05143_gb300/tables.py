@@ -13,12 +13,14 @@ For each reference template of Table 1 this module builds, from geometry alone:
   slot" (Appendix A: equivalent correspondences give equal RMSD).
 
 Canonical form (one embedding, orientation-preserving; Sec. 4): every directed
-edge u->v gets the key (deg u, deg v, deg w1, deg w2), where (u, v, w1) and
-(v, u, w2) are the two facets on the edge; among the edges with the largest
-key (compared in that order) the lexicographically smallest Weinberg code is
-the canonical code and its first-visit labelling the canonical labelling.  The
-key is invariant under orientation-preserving isomorphisms, so two embedded
-graphs get the same code exactly when such an isomorphism exists.
+edge u->v gets the key (deg u, deg v, deg w1, deg w2, deg a1, deg b1, deg a2,
+deg b2), where (u, v, w1) and (v, u, w2) are the two facets on the edge and
+a1, b1, a2, b2 the third vertices of the facets across their outer edges
+(v, w1), (w1, u), (u, w2), (w2, v); among the edges with the largest key
+(compared in that order) the lexicographically smallest Weinberg code is the
+canonical code and its first-visit labelling the canonical labelling.  The key
+is invariant under orientation-preserving isomorphisms, so two embedded graphs
+get the same code exactly when such an isomorphism exists.
 
 Weinberg walk (counter-clockwise rotation seen from outside): at a new vertex
 leave by the edge after the arrival edge; at an old vertex reached along an edge
@@ -211,7 +213,9 @@ def weinberg(facets, u, v):
 
 
 def edge_key(deg, th, a, b):
-    return (deg[a], deg[b], deg[th[(a, b)]], deg[th[(b, a)]])
+    z, w = th[(a, b)], th[(b, a)]
+    return (deg[a], deg[b], deg[z], deg[w],
+            deg[th[(z, b)]], deg[th[(a, z)]], deg[th[(w, a)]], deg[th[(b, w)]])
 
 
 def canonical_form(facets):
