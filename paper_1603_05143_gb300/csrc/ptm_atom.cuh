@@ -405,38 +405,21 @@ __device__ int hull_apply(const Scratch &sm, int nf, uint32_t vis, int p, const 
   return n2;
 }
 
-// ------------------------------------------------------- canonical Weinberg code
-// Walk from u -> v over the K-vertex hull (rules in tables.py).  The emitted
-// labels are compared with the best code so far; returns +1 when this walk is
-// strictly smaller (it becomes the best and its labelling is returned), 0 when
-// equal, -1 when larger (aborted at the first larger label).
-__device__ int weinberg_walk(const Scratch &sm, int K, int u, int v, bool first, uint64_t &labels,
-                             const FrameDesc &d) {
+// ------------------------------------------------------- Weinberg code
+// Walk from u -> v over the K-vertex hull (rules in tables.py), writing the
+// code (labels 3.. as nibbles; every walk starts with labels 1, 2) to the CODE
+// rows and the first-visit labelling to `labels`.  False on an internal error.
+__device__ bool weinberg_walk(const Scratch &sm, int K, int u, int v, uint64_t &labels, const FrameDesc &d) {
   const int LEN = 2 * (3 * K - 6) + 1;
   uint64_t lab = 0;
 #pragma unroll
   for (int x = 0; x < PTM_KNN; x++) sm.U(x) = 0;
-  int state = first ? 1 : 0;        // 1: writing a new best; 0: still equal
   int next = 1;
-  uint32_t wbuf = 0, wcur = 0;
-  // label s of the code (s >= 2) is nibble s - 2 of the stored code: every
-  // walk starts with labels 1, 2
-  auto emit = [&](int s, int L) -> bool {
+  uint32_t wbuf = 0;
+  auto emit = [&](int s, int L) {
     const int n = s - 2;
-    if (state == 0) {
-      if ((n & 7) == 0) wcur = sm.CODE(n >> 3);
-      int B = (wcur >> (4 * (n & 7))) & 15;
-      if (L > B) return false;
-      if (L < B) {                                   // smaller from here on: keep the
-        state = 1;                                   // equal prefix of this code word
-        wbuf = wcur & ((1u << (4 * (n & 7))) - 1u);
-      }
-    }
-    if (state == 1) {
-      wbuf |= (uint32_t)L << (4 * (n & 7));
-      if ((n & 7) == 7 || s == LEN - 1) { sm.CODE(n >> 3) = wbuf; wbuf = 0; }
-    }
-    return true;
+    wbuf |= (uint32_t)L << (4 * (n & 7));
+    if ((n & 7) == 7 || s == LEN - 1) { sm.CODE(n >> 3) = wbuf; wbuf = 0; }
   };
   lab = setnib(lab, u, next++);
   sm.U(u) |= 1 << v;
@@ -456,28 +439,28 @@ __device__ int weinberg_walk(const Scratch &sm, int K, int u, int v, bool first,
         if (w == u || guard > 16) break;
       }
     }
-    if (w >= K) { count(d, C_INTERNAL); return -1; }
+    if (w >= K) { count(d, C_INTERNAL); return false; }
     sm.U(v) = (uint16_t)(uv | (1u << w));
     u = v;
     v = w;
     int L = nib(lab, v);
     fresh = (L == 0);
     if (fresh) { L = next++; lab = setnib(lab, v, L); }
-    if (!emit(s, L)) return -1;
+    emit(s, L);
   }
-  if (s != LEN) { count(d, C_INTERNAL); return -1; }
-  if (state == 1) { labels = lab; return 1; }
-  return 0;
+  if (s != LEN) { count(d, C_INTERNAL); return false; }
+  labels = lab;
+  return true;
 }
 
-// Canonical code of the current K-vertex hull.  Every directed edge u->v gets
-// the key (deg u, deg v, deg w1, deg w2) with (u, v, w1) and (v, u, w2) the two
-// facets on the edge, continued (for edges tied on it) by the degrees of the
-// third vertices of the facets across their four outer edges; among the edges
-// with the largest key the smallest Weinberg code wins (definition in tables.py).  Returns the labelling (nibble
-// t = label of neighbour t) and the code hash; false on an internal error.
-// Start edges are kept as a bit mask over (facet, corner) and visited by one
-// flat loop, so the threads of a warp run their walks together.
+// Weinberg code of the current K-vertex hull for the table lookup.  Every
+// directed edge u->v gets the key (deg u, deg v, deg w1, deg w2) with (u, v, w1)
+// and (v, u, w2) the two facets on the edge, continued (for edges tied on it)
+// by the degrees of the third vertices of the facets across their four outer
+// edges; the walk starts from the first edge with the largest key (definition
+// in tables.py, whose tables hold the code of every such start).  Returns the
+// labelling (nibble t = label of neighbour t) and the code hash; false on an
+// internal error.  Every lane walks once, so a warp's walks run together.
 __device__ bool canonical(const Scratch &sm, int K, int nf, uint64_t &labels, uint64_t &hash,
                           const FrameDesc &d) {
   uint64_t deg = 0;
@@ -514,7 +497,7 @@ __device__ bool canonical(const Scratch &sm, int K, int nf, uint64_t &labels, ui
     }
   }
   // K = 12 with every degree 5 is the icosahedron, K = 6 with every degree 4 the
-  // octahedron: every directed edge is equivalent, one walk suffices
+  // octahedron: every directed edge has the same key
   const bool transitive = (K == 12 && top == 0x5555u) || (K == 6 && top == 0x4444u);
   // edges tied on the degrees of the edge's two facets: the key continues with
   // the degrees of the third vertices of the facets across their outer edges
@@ -539,23 +522,17 @@ __device__ bool canonical(const Scratch &sm, int K, int nf, uint64_t &labels, ui
     m0 = n0;
     m1 = n1;
   }
-  bool first = true;
-  while (m0 | m1) {
-    int id;
-    if (m0) { id = __ffsll((long long)m0) - 1; m0 &= m0 - 1; }
-    else { id = 64 + __ffs(m1) - 1; m1 &= m1 - 1; }
+  // one walk, from the first start edge with the largest key: the tables hold
+  // the code of every such start of every template triangulation
+  if (!(m0 | m1)) return false;
+  const int id = m0 ? __ffsll((long long)m0) - 1 : 64 + __ffs(m1) - 1;
+  {
     const int v = sm.F(id / 3), e = id % 3;
     const int p0 = v & 15, p1 = (v >> 4) & 15, p2 = (v >> 8) & 15;
     const int su = e == 0 ? p0 : (e == 1 ? p1 : p2);
     const int sv = e == 0 ? p1 : (e == 1 ? p2 : p0);
-    uint64_t lab = 0;
-    const int r = weinberg_walk(sm, K, su, sv, first, lab, d);
-    if (first && r != 1) return false;
-    if (r == 1) labels = lab;
-    first = false;
-    if (transitive) break;
+    if (!weinberg_walk(sm, K, su, sv, labels, d)) return false;
   }
-  if (first) return false;
   // hash of the packed code (labels 3..LEN); words past its end count as zero,
   // as the generator packs them
   const int LEN = 2 * (3 * K - 6) + 1;

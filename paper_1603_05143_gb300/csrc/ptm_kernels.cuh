@@ -250,12 +250,12 @@ __device__ __forceinline__ bool knn_fast(const FrameDesc &d, const Scratch &sm, 
 
 // ---------------------------------------------------------- per-atom state
 // Per-atom selection state.  Plain scalars (no arrays) so that it stays in
-// registers; snapshot k = 6, 12, 14 keeps its canonical labelling and table entry.
+// registers; snapshot k = 6, 12, 14 keeps its walk labelling and table entry.
 struct Best {
   float b1, b2;                 // best and second-best FP32 RMSD^2
   int K, cand;                  // winning snapshot (6, 12, 14) and candidate index
   int fp64;                     // the winner's eigenvalue needed the FP64 solve
-  uint64_t lam6, lam12, lam14;  // canonical labelling per snapshot
+  uint64_t lam6, lam12, lam14;  // walk labelling per snapshot
   int ent6, ent12, ent14;       // table entry per snapshot, -1 = none
   __device__ __forceinline__ uint64_t lam(int K) const { return K == 6 ? lam6 : (K == 12 ? lam12 : lam14); }
   __device__ __forceinline__ int ent(int K) const { return K == 6 ? ent6 : (K == 12 ? ent12 : ent14); }
@@ -284,7 +284,7 @@ __device__ __forceinline__ int lookup(const Scratch &sm, int K, uint64_t h) {
 }
 
 // S_ab = sum_j w_{slot(j), a} dr_{j, b} for the correspondence "neighbour rank j ->
-// template slot" given by the canonical labelling and the table candidate.
+// template slot" given by the walk labelling and the table candidate.
 // Because the template barycentre is the origin and slot 0 (the centre) sits at
 // it, the data barycentre drops out of S.
 __device__ __forceinline__ void cov_matrix(int K, const Scratch &sm, const float4 *tplw, int S, uint64_t lab,
@@ -345,7 +345,7 @@ __device__ __forceinline__ float cand_r2(const float (&Sm)[3][3], float Gv, floa
   return fmaxf((Gw - o.lam * o.lam / Gv) / (float)N, 0.f);
 }
 
-// Hull of the first K neighbours is complete and contains the centre: canonical
+// Hull of the first K neighbours is complete and contains the centre: Weinberg
 // code and lookup (Algorithm 1, inner loops).  Only the labelling and table
 // entry are kept; every snapshot's candidates are scored after the last one, in
 // one loop (score_candidates, or select_fp64 in the FP64 form).
@@ -840,7 +840,7 @@ __device__ __forceinline__ void metric_vectors(const FrameDesc &d, const Scratch
 }
 
 // ------------------------------------------------------------ one atom
-// P64 selects the FP64 form: the same exact predicates, canonical codes and
+// P64 selects the FP64 form: the same exact predicates, Weinberg codes and
 // lookup, then every candidate scored and the winner's outputs computed in FP64
 // (the one-frame-per-launch comparison form).
 // `live` holds the lanes of this warp that entered together (all reach the

@@ -17,10 +17,15 @@ edge u->v gets the key (deg u, deg v, deg w1, deg w2, deg a1, deg b1, deg a2,
 deg b2), where (u, v, w1) and (v, u, w2) are the two facets on the edge and
 a1, b1, a2, b2 the third vertices of the facets across their outer edges
 (v, w1), (w1, u), (u, w2), (w2, v); among the edges with the largest key
-(compared in that order) the lexicographically smallest Weinberg code is the
-canonical code and its first-visit labelling the canonical labelling.  The key
-is invariant under orientation-preserving isomorphisms, so two embedded graphs
-get the same code exactly when such an isomorphism exists.
+(compared in that order) are the start edges.  A Weinberg walk from a start
+edge gives a code and a first-visit labelling; the key is invariant under
+orientation-preserving isomorphisms, so the codes from the start edges of two
+embedded graphs are the same set exactly when such an isomorphism exists, and
+a code determines the graph.  The tables therefore list, per template
+triangulation, the code of every start edge (starts related by an automorphism
+share one), and the kernels need one walk per hull (the paper's canonical form
+takes the smallest code over all starts; one lookup among all start codes is
+the same isomorphism test).
 
 Weinberg walk (counter-clockwise rotation seen from outside): at a new vertex
 leave by the edge after the arrival edge; at an old vertex reached along an edge
@@ -218,9 +223,12 @@ def edge_key(deg, th, a, b):
             deg[th[(z, b)]], deg[th[(a, z)]], deg[th[(w, a)]], deg[th[(b, w)]])
 
 
-def canonical_form(facets):
-    """(code, list of canonical labellings) under the edge-keyed definition of the
-    module docstring."""
+def start_codes(facets):
+    """Weinberg code -> first-visit labellings, over every start edge with the
+    largest key (definition in the module docstring).  The kernels walk from one
+    such start, whichever comes first in their facet list, so the tables hold
+    the code of each of them; starts related by an automorphism give the same
+    code."""
     deg: dict = {}
     for f in facets:
         for x in f:
@@ -228,15 +236,12 @@ def canonical_form(facets):
     th = _third(facets)
     starts = [(a, b) for f in facets for a, b in ((f[0], f[1]), (f[1], f[2]), (f[2], f[0]))]
     top = max(edge_key(deg, th, a, b) for a, b in starts)
-    starts = [(a, b) for a, b in starts if edge_key(deg, th, a, b) == top]
-    best, labs = None, []
+    out: dict = {}
     for a, b in starts:
-        code, lab = weinberg(facets, a, b)
-        if best is None or code < best:
-            best, labs = code, [lab]
-        elif code == best:
-            labs.append(lab)
-    return best, labs
+        if edge_key(deg, th, a, b) == top:
+            code, lab = weinberg(facets, a, b)
+            out.setdefault(code, []).append(lab)
+    return out
 
 
 def pack_code(code) -> list:
@@ -296,12 +301,12 @@ def build():
         tris = triangulations(w)
         raw = {}
         for t in tris:
-            code, labs = canonical_form(t)
-            for lab in labs:
-                sigma = [0] * (k + 1)            # canonical label -> slot
-                for slot, L in lab.items():
-                    sigma[L] = slot
-                raw.setdefault(code, set()).add(tuple(sigma[1:]))
+            for code, labs in start_codes(t).items():
+                for lab in labs:
+                    sigma = [0] * (k + 1)            # walk label -> slot
+                    for slot, L in lab.items():
+                        sigma[L] = slot
+                    raw.setdefault(code, set()).add(tuple(sigma[1:]))
         ncand = 0
         for code, sigmas in raw.items():
             reps = set()
