@@ -63,7 +63,9 @@ __device__ __forceinline__ double contract_d2(double a, double b, double c) {
 
 // ----------------------------------------------------------------- kNN
 // Visit every (atom, image) in the (2R+1)^3 cells around cell (bx, by, bz):
-// visit(j, d2, idj, image) with d2 by the distance contract.
+// visit(j, d2, idj, image) with d2 by the distance contract.  The cells
+// bz - R .. bz + R of a column are consecutive in the sorted order unless the
+// range wraps, and are then scanned as one range of atoms.
 template <bool F64, typename V>
 __device__ __forceinline__ void scan_cells(const FrameDesc &d, int s, typename RT<F64>::T xi,
                                            typename RT<F64>::T yi, typename RT<F64>::T zi, int bx, int by, int bz,
@@ -76,11 +78,19 @@ __device__ __forceinline__ void scan_cells(const FrameDesc &d, int s, typename R
     for (int dy = -R; dy <= R; dy++) {
       int cy = by + dy, my = 0;
       if (d.pbc[1]) { my = floordiv(cy, nby); cy -= my * nby; } else if (cy < 0 || cy >= nby) continue;
-      for (int dz = -R; dz <= R; dz++) {
-        int cz = bz + dz, mz = 0;
-        if (d.pbc[2]) { mz = floordiv(cz, nbz); cz -= mz * nbz; } else if (cz < 0 || cz >= nbz) continue;
-        const int c = (cx * nby + cy) * nbz + cz;
-        const int j0 = __ldg(d.cell_start + c), j1 = __ldg(d.cell_start + c + 1);
+      int z0 = bz - R, z1 = bz + R;
+      if (!d.pbc[2]) { z0 = max(z0, 0); z1 = min(z1, nbz - 1); }
+      const bool column = z0 >= 0 && z1 < nbz;             // no wrap: one range, image mz = 0
+      const int cbase = (cx * nby + cy) * nbz;
+      for (int r = 0; r < (column ? 1 : 2 * R + 1); r++) {
+        int ca = cbase + z0, cb = cbase + z1, mz = 0;     // cells ca .. cb
+        if (!column) {
+          int cz = bz - R + r;
+          mz = floordiv(cz, nbz);                          // periodic z (else column)
+          cz -= mz * nbz;
+          ca = cb = cbase + cz;
+        }
+        const int j0 = __ldg(d.cell_start + ca), j1 = __ldg(d.cell_start + cb + 1);
         if (j0 == j1) continue;
         const int n0 = mx + wix, n1 = my + wiy, n2 = mz + wiz;
         T sx, sy, sz;
