@@ -6,7 +6,8 @@
  * For every atom of a periodic frame the library
  *   - selects the 14 nearest neighbours, Euclidean order (Sec. 3, Table 1);
  *   - builds the convex hulls of the first 6, 12 and 14 neighbours and labels
- *     each hull graph canonically (Sec. 4);
+ *     each hull graph by a Weinberg walk, looked up among the codes of the
+ *     template triangulations (Sec. 4);
  *   - matches the labels against the SC, FCC, HCP, ICO and BCC templates and
  *     evaluates the scale-invariant RMSD (Eq. 3-4) of every admissible
  *     correspondence (Algorithm 1);
@@ -65,7 +66,7 @@ enum { PTM_F32 = 0, PTM_F64 = 1 };
 enum { PTM_ORDER_EUCLIDEAN = 0, PTM_ORDER_TOPOLOGICAL = 1 };
 
 /* Arithmetic of the metric steps (QCP, selection, outputs).  The exact hull
-   predicates, canonical codes and lookup are the same in both. */
+   predicates, Weinberg codes and lookup are the same in both. */
 enum {
   PTM_PREC_FP32 = 0,         /* FP32, with FP64 where stability needs it (the product path) */
   PTM_PREC_FP64 = 1          /* every candidate and the winner's outputs in FP64: the
