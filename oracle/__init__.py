@@ -67,7 +67,7 @@ def lib():
         L.ptmo_frame_new.restype = P
         L.ptmo_frame_free.argtypes = [P]
         L.ptmo_frame_free.restype = None
-        L.ptmo_knn.argtypes = [P, C.c_int64, C.c_int, P, P, P, P, P]
+        L.ptmo_knn.argtypes = [P, C.c_int64, C.c_int, P, P, P, P]
         L.ptmo_quantise.argtypes = [C.c_int, P, P]
         L.ptmo_classify.argtypes = [P, P, C.c_uint32, C.c_double, C.c_int, P, C.c_int64] + [P] * 9
         L.ptmo_voronoi_areas.argtypes = [C.c_int, P, P]
@@ -186,13 +186,15 @@ class Frame:
             self.h = None
 
     def knn(self, atom: int, k: int = 14):
+        """The k nearest periodic images of ``atom`` in the oracle's order (FP64
+        squared distance, then atom id, then image): ids, images (k x 3), FP64
+        contract vectors (k x 3) and squared distances."""
         ids = np.zeros(k, np.int32)
         imgs = np.zeros((k, 3), np.int32)
-        drc = np.zeros((k, 3))
-        dre = np.zeros((k, 3))
+        dr = np.zeros((k, 3))
         d2 = np.zeros(k)
-        m = lib().ptmo_knn(self.h, atom, k, _p(ids), _p(imgs), _p(drc), _p(dre), _p(d2))
-        return ids[:m], imgs[:m], drc[:m], dre[:m], d2[:m]
+        m = lib().ptmo_knn(self.h, atom, k, _p(ids), _p(imgs), _p(dr), _p(d2))
+        return ids[:m], imgs[:m], dr[:m], d2[:m]
 
     def topo_knn(self, atom: int):
         """Ids, images (k x 3) of the first min(14, m) neighbours in topological
@@ -265,10 +267,13 @@ def rodrigues(q: np.ndarray) -> np.ndarray:
 
 def rmsd_histogram(structure: np.ndarray, rmsd: np.ndarray, nbins: int, rmsd_max: float) -> np.ndarray:
     """Counts of matched atoms per structure (rows SC, FCC, HCP, ICO, BCC) and
-    RMSD bin (Sec. 5.1: the histogram from which RMSD_max is chosen).  Bin b
-    holds b <= rmsd * (nbins / rmsd_max) < b + 1, evaluated in float32 exactly
-    as the kernel does (scale rounded to float32 once, one rounded product);
-    column nbins counts the atoms at or beyond rmsd_max."""
+    RMSD bin (Sec. 5.1: the histogram from which RMSD_max is chosen).  The
+    paper fixes no binning; the rule here: the bin width factor nbins / rmsd_max
+    is rounded to float32 once, each float32 RMSD is multiplied by it in one
+    rounded float32 product, and bin b holds the atoms whose product p has
+    b <= p < b + 1 (so the decision is taken in the precision of the stored
+    RMSD); column nbins counts the atoms at or beyond rmsd_max, and unmatched
+    atoms (infinite RMSD) are not counted."""
     structure = np.asarray(structure)
     r = np.asarray(rmsd, np.float32)
     scale = np.float32(nbins / rmsd_max)

@@ -29,12 +29,14 @@
  * Readings of the paper that it follows where the paper is silent or ambiguous:
  *   R1  the centre atom belongs to both point sets (N = k + 1), at the origin.
  *   R2  the data set v is scaled by s, the template w by 1/l(w) (Eq. 3-4).
- *   R4  neighbour order by squared distance computed in the input precision by a
- *       fixed sequence of IEEE operations (the "distance contract"), ties by
- *       atom id then image vector.
+ *   R4  neighbour order by squared distance computed in FP64 (float32 positions
+ *       widened exactly) by a fixed sequence of IEEE operations without fused
+ *       multiply-add (the "distance contract"), ties by atom id then image
+ *       vector: the paper orders by distance and fixes no precision.
  *   R7  hull predicates are exact on integer coordinates quantised at 2^-19 of the
- *       largest neighbour-vector component (power-of-two grid), with Simulation
- *       of Simplicity (priority = neighbour rank) on exact zeros.
+ *       largest component of the FP64 contract vectors (power-of-two grid, round
+ *       half to even), with Simulation of Simplicity (priority = neighbour rank)
+ *       on exact zeros.
  *   R9  Weinberg walk rules, counter-clockwise rotation seen from outside.
  *   R12 the reported correspondence is the lexicographically smallest member of
  *       its orbit under the template's rotation group.
@@ -709,8 +711,8 @@ void ptmo_polar(const double *A, double *P, double *U) {
   }
 }
 
-/* ------------------------------------------------- neighbours (Sec. 3, R4) */
-typedef struct { double d2; int32_t j; int32_t n[3]; double drc[3]; double dre[3]; } cand_t;
+/* ------------------------------------------------------ neighbours (Sec. 3) */
+typedef struct { double d2; int32_t j; int32_t n[3]; double dr[3]; } cand_t;   /* dr: contract vector */
 
 static int cmp_cand(const void *a, const void *b) {
   const cand_t *x = a, *y = b;
@@ -732,34 +734,27 @@ static void shift64(const double *H, const int32_t n[3], double s[3]) {
   for (int c = 0; c < 3; c++) s[c] = ((double)n[0] * H[c] + (double)n[1] * H[3 + c]) + (double)n[2] * H[6 + c];
 }
 
-/* The distance contract: neighbour vector and squared length in the input
-   precision, one IEEE operation at a time, in this order:
-     dr_c = (x_j,c - x_i,c) + shift_c        shift rounded once to the input type
-     d2   = (dr_x dr_x + dr_y dr_y) + dr_z dr_z                                     */
+/* The distance contract: neighbour vector and squared length in FP64, one IEEE
+   operation at a time, in this order (float32 positions are first widened to
+   double, which is exact):
+     dr_c = (x_j,c - x_i,c) + shift_c
+     d2   = (dr_x dr_x + dr_y dr_y) + dr_z dr_z
+   The paper orders neighbours by distance (Sec. 3, Table 1) and fixes no
+   precision; the plain definition is the distance between the given points, so
+   the order is decided in FP64 whatever the input type.                        */
+static double posval(const frame_t *F, int64_t i, int c);
 static double contract(const frame_t *F, int64_t i, int64_t j, const int32_t n[3], double drc[3]) {
   double s[3];
   shift64(F->H, n, s);
-  if (F->f64) {
-    const double *x = F->pos;
-    double d[3];
-    for (int c = 0; c < 3; c++) { double t = x[3 * j + c] - x[3 * i + c]; d[c] = t + s[c]; drc[c] = d[c]; }
-    double a = d[0] * d[0], b = d[1] * d[1], e = d[2] * d[2];
-    double ab = a + b;
-    return ab + e;
-  } else {
-    const float *x = F->pos;
-    float d[3];
-    for (int c = 0; c < 3; c++) {
-      float t = x[3 * j + c] - x[3 * i + c];
-      float sc = (float)s[c];
-      d[c] = t + sc;
-      drc[c] = d[c];
-    }
-    float a = d[0] * d[0], b = d[1] * d[1], e = d[2] * d[2];
-    float ab = a + b;
-    float r = ab + e;
-    return (double)r;
+  double d[3];
+  for (int c = 0; c < 3; c++) {
+    double t = posval(F, j, c) - posval(F, i, c);
+    d[c] = t + s[c];
+    drc[c] = d[c];
   }
+  double a = d[0] * d[0], b = d[1] * d[1], e = d[2] * d[2];
+  double ab = a + b;
+  return ab + e;
 }
 
 static double posval(const frame_t *F, int64_t i, int c) {
@@ -820,10 +815,7 @@ static int knn(const frame_t *F, int64_t i, int kmax, cand_t *out) {
             if (d2 > R2) continue;
             if (nc == cap) { cap *= 2; c = realloc(c, sizeof(cand_t) * cap); }
             cand_t *e = &c[nc++];
-            e->d2 = d2; e->j = (int32_t)j; memcpy(e->n, n, sizeof n); memcpy(e->drc, drc, sizeof drc);
-            double s[3];
-            shift64(F->H, n, s);
-            for (int d = 0; d < 3; d++) e->dre[d] = (posval(F, j, d) - posval(F, i, d)) + s[d];
+            e->d2 = d2; e->j = (int32_t)j; memcpy(e->n, n, sizeof n); memcpy(e->dr, drc, sizeof drc);
           }
     }
     qsort(c, nc, sizeof(cand_t), cmp_cand);
@@ -908,7 +900,7 @@ static int cmp_topo(const void *a, const void *b) {
 static void topo_order(int m, cand_t *nb, double *areas_out) {
   double v[TOPO_N][3], mean2 = 0, dmax = 0;
   for (int t = 0; t < m; t++) {
-    for (int c = 0; c < 3; c++) v[t][c] = nb[t].dre[c];
+    for (int c = 0; c < 3; c++) v[t][c] = nb[t].dr[c];
     double d2 = dot3(v[t], v[t]);
     mean2 += d2;
     if (d2 > dmax) dmax = d2;
@@ -952,21 +944,20 @@ void ptmo_frame_free(void *h) {
   free(F);
 }
 
-int ptmo_knn(void *h, int64_t atom, int kmax, int32_t *ids, int32_t *imgs, double *drc,
-             double *dre, double *d2) {
+int ptmo_knn(void *h, int64_t atom, int kmax, int32_t *ids, int32_t *imgs, double *dr, double *d2) {
   const frame_t *F = h;
   cand_t c[64];
   if (kmax > 64) return -1;
   int m = knn(F, atom, kmax, c);
   for (int t = 0; t < m; t++) {
     ids[t] = c[t].j;
-    for (int d = 0; d < 3; d++) { imgs[3 * t + d] = c[t].n[d]; drc[3 * t + d] = c[t].drc[d]; dre[3 * t + d] = c[t].dre[d]; }
+    for (int d = 0; d < 3; d++) { imgs[3 * t + d] = c[t].n[d]; dr[3 * t + d] = c[t].dr[d]; }
     d2[t] = c[t].d2;
   }
   return m;
 }
 
-/* Quantisation (R7): q = rint(dr * 2^(19 - e)) with 2^e > max |dr component| over
+/* Quantisation for the exact hull predicates: q = rint(dr * 2^(19 - e)) with 2^e > max |dr component| over
    the given neighbours.  The scaling is exact; rint rounds half to even. */
 int ptmo_quantise(int m, const double *drc, int64_t *q) {
   double mx = 0;
@@ -1056,7 +1047,7 @@ static void classify_atom(const frame_t *F, int64_t i, const int8_t *species, ui
   for (int t = 0; t < m; t++) res->nbr[t] = nb[t].j;
   double drc[3 * KMAX];
   int64_t q[3 * KMAX];
-  for (int t = 0; t < m; t++) for (int d = 0; d < 3; d++) drc[3 * t + d] = nb[t].drc[d];
+  for (int t = 0; t < m; t++) for (int d = 0; d < 3; d++) drc[3 * t + d] = nb[t].dr[d];
   ptmo_quantise(m, drc, q);
 
   candidate_t best;
@@ -1107,7 +1098,7 @@ static void classify_atom(const frame_t *F, int64_t i, const int8_t *species, ui
           for (int j = 0; j <= k; j++) corr[perm[j]] = j;
           double v[3 * NMAX], w[3 * NMAX];
           for (int d = 0; d < 3; d++) v[d] = 0.0;
-          for (int j = 1; j <= k; j++) for (int d = 0; d < 3; d++) v[3 * j + d] = nb[j - 1].dre[d];
+          for (int j = 1; j <= k; j++) for (int d = 0; d < 3; d++) v[3 * j + d] = nb[j - 1].dr[d];
           for (int j = 0; j <= k; j++) for (int d = 0; d < 3; d++) w[3 * j + d] = T->w[perm[j]][d];
           candidate_t cd;
           cd.S = S;
@@ -1153,7 +1144,7 @@ static void classify_atom(const frame_t *F, int64_t i, const int8_t *species, ui
   {
     double act[NMAX][3], actn[NMAX][3], idl[NMAX][3];
     for (int d = 0; d < 3; d++) act[0][d] = 0.0;
-    for (int s = 1; s <= k; s++) for (int d = 0; d < 3; d++) act[s][d] = nb[best.cp[s] - 1].dre[d];
+    for (int s = 1; s <= k; s++) for (int d = 0; d < 3; d++) act[s][d] = nb[best.cp[s] - 1].dr[d];
     normalise(k + 1, act, actn);
     for (int s = 0; s <= k; s++) for (int d = 0; d < 3; d++) idl[s][d] = T->w[s][d];
     /* normal equations: (V^T V) A^T = V^T W */

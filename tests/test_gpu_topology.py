@@ -103,8 +103,8 @@ def _band_edge_strain(target=1e-3 + 1e-5):
     def gap(eps):
         f = I.crystal("fcc", I.A_FCC_CU, 3, deform=np.diag([1.0, 1.0, 1.0 + eps]), dtype=np.float64)
         F = O.Frame(f.positions, f.cell, f.pbc)
-        ids, imgs, dr, drc, d2 = F.knn(0, O.TOPO_N)
-        v = np.asarray(drc, float).reshape(-1, 3)
+        ids, imgs, dr, d2 = F.knn(0, O.TOPO_N)
+        v = np.asarray(dr, float).reshape(-1, 3)
         a = np.sort(O.voronoi_areas(v))[::-1]
         g = a[:-1] - a[1:]
         return g[g > 1e-9 * a[0]][0] / np.mean(np.sum(v * v, 1))

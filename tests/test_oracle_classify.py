@@ -75,6 +75,25 @@ def test_polar_matches_svd():
 
 
 # ------------------------------------------------------------------ neighbours
+def _brute_knn(x, H, i, k, reach=3, pbc=(True, True, True)):
+    """The k nearest images of atom i by an explicit sum over images in
+    [-reach, reach]^3, in FP64 (float32 positions widened first, which is
+    exact), one IEEE operation at a time; ties by (atom id, image)."""
+    x = np.asarray(x, np.float64)
+    rows = []
+    rng_ = [range(-reach, reach + 1) if p else range(1) for p in pbc]
+    for n in itertools.product(*rng_):
+        s = (n[0] * H[0] + n[1] * H[1]) + n[2] * H[2]
+        d = (x - x[i]) + s
+        d2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+        for j in range(len(x)):
+            if j == i and n == (0, 0, 0):
+                continue
+            rows.append((d2[j], j, n, d[j]))
+    rows.sort(key=lambda r: r[:3])
+    return rows[:k]
+
+
 def test_knn_matches_kdtree_orthorhombic():
     from scipy.spatial import cKDTree
     f = I.crystal("fcc", 3.615, (5, 6, 7), sigma=0.2, seed=9)
@@ -83,7 +102,7 @@ def test_knn_matches_kdtree_orthorhombic():
     tree = cKDTree(np.mod(f.positions, L), boxsize=L)
     rng = np.random.default_rng(0)
     for i in rng.choice(f.n, 60, replace=False):
-        ids, imgs, drc, dre, d2 = F.knn(int(i))
+        ids, imgs, dr, d2 = F.knn(int(i))
         dist, idx = tree.query(np.mod(f.positions[i], L), k=15)
         assert np.allclose(np.sqrt(d2), dist[1:], atol=1e-12)
         assert set(ids.tolist()) == set(idx[1:].tolist())
@@ -97,40 +116,68 @@ def test_knn_triclinic_and_tiny_box_against_image_sum():
     for reps in ((2, 2, 2), (3, 2, 2), (4, 4, 4)):
         f = I.crystal("bcc", 2.8665, reps, sigma=0.05, seed=2, rotation=R, deform=E)
         F = O.Frame(f.positions, f.cell)
-        H = f.cell
-        x = f.positions
         for i in range(0, f.n, max(1, f.n // 12)):
-            rows = []
-            for n in itertools.product(range(-3, 4), repeat=3):
-                s = (n[0] * H[0] + n[1] * H[1]) + n[2] * H[2]
-                d = (x - x[i]) + s
-                d2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
-                for j in range(f.n):
-                    if j == i and n == (0, 0, 0):
-                        continue
-                    rows.append((d2[j], j, n))
-            rows.sort()
-            ids, imgs, drc, dre, d2 = F.knn(i)
-            assert [r[1] for r in rows[:14]] == ids.tolist()
-            assert [tuple(r[2]) for r in rows[:14]] == [tuple(t) for t in imgs.tolist()]
-            assert np.array_equal(np.array([r[0] for r in rows[:14]]), d2)
+            rows = _brute_knn(f.positions, f.cell, i, 14)
+            ids, imgs, dr, d2 = F.knn(i)
+            assert [r[1] for r in rows] == ids.tolist()
+            assert [tuple(r[2]) for r in rows] == [tuple(t) for t in imgs.tolist()]
+            assert np.array_equal(np.array([r[0] for r in rows]), d2)
+            assert np.array_equal(np.array([r[3] for r in rows]), dr)
 
 
-def test_knn_float32_contract():
-    """For float32 input the distance contract runs in float32 operations."""
-    f = I.crystal("fcc", 3.615, 4, sigma=0.1, seed=8, dtype=np.float32)
+def test_knn_float32_input_ordered_in_fp64():
+    """Float32 positions: the order is that of the FP64 distances between the
+    given points (Sec. 3 orders by distance; widening float32 is exact)."""
+    rng = np.random.default_rng(8)
+    f = I.crystal("fcc", 3.615, 4, sigma=0.1, seed=8, dtype=np.float32,
+                  rotation=I.random_rotation(rng), deform=np.eye(3) + 0.03 * rng.normal(size=(3, 3)))
     F = O.Frame(f.positions, f.cell)
+    for i in (0, 17, 100, 255):
+        rows = _brute_knn(f.positions, f.cell, i, 14, reach=1)
+        ids, imgs, dr, d2 = F.knn(i)
+        assert [r[1] for r in rows] == ids.tolist()
+        assert [tuple(r[2]) for r in rows] == [tuple(t) for t in imgs.tolist()]
+        assert np.array_equal(np.array([r[0] for r in rows]), d2)
+        assert np.array_equal(np.array([r[3] for r in rows]), dr)
+
+
+def _f32_order(x, H, i, cand):
+    """Order of the candidate (j, image) pairs when the same contract runs in
+    float32 operations (the mistake the next test must catch)."""
+    x32 = np.asarray(x, np.float32)
+    keys = []
+    for j, n in cand:
+        s = ((n[0] * H[0] + n[1] * H[1]) + n[2] * H[2]).astype(np.float32)
+        d = (x32[j] - x32[i]) + s
+        keys.append(((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2], j, tuple(n)))
+    return [k[1:] for k in sorted(keys)]
+
+
+def test_knn_near_ties_follow_fp64_not_float32():
+    """A perfect (sigma = 0) rotated float32 fcc lattice: mirror-image
+    neighbours sit at distances that differ only by the float32 rounding of the
+    positions, less than the float32 rounding of d^2 itself, and the six second
+    shell neighbours straddle the 14th/15th boundary.  The oracle must follow
+    the FP64 brute force on every sampled atom, and the case must really
+    separate the precisions: a float32 contract orders them differently and
+    even picks a different set of 14."""
+    rng = np.random.default_rng(21)
+    f = I.crystal("fcc", 3.615, 3, sigma=0.0, seed=5, dtype=np.float32, rotation=I.random_rotation(rng))
     x = f.positions
-    H = f.cell
-    for i in (0, 17, 100):
-        ids, imgs, drc, dre, d2 = F.knn(i)
-        for j, n, dc, dd in zip(ids, imgs, drc, d2):
-            s64 = (n[0] * H[0] + n[1] * H[1]) + n[2] * H[2]
-            d = (x[j] - x[i]).astype(np.float32) + s64.astype(np.float32)
-            assert d.dtype == np.float32
-            assert np.array_equal(d.astype(np.float64), dc)
-            q = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]
-            assert np.float64(q) == dd
+    F = O.Frame(x, f.cell)
+    order_differs = set_differs = 0
+    for i in range(0, len(x), 3):
+        rows = _brute_knn(x, f.cell, i, 14, reach=1)
+        ids, imgs, dr, d2 = F.knn(i)
+        assert [r[1] for r in rows] == ids.tolist()
+        assert [tuple(r[2]) for r in rows] == [tuple(t) for t in imgs.tolist()]
+        assert np.array_equal(np.array([r[0] for r in rows]), d2)
+        fp64 = [(r[1], tuple(r[2])) for r in rows]
+        more = _brute_knn(x, f.cell, i, 24, reach=1)
+        f32 = _f32_order(x, f.cell, i, [(r[1], r[2]) for r in more])[:14]
+        order_differs += f32 != fp64
+        set_differs += set(f32) != set(fp64)
+    assert order_differs >= 20 and set_differs >= 10, (order_differs, set_differs)
 
 
 # ------------------------------------------------------ whole classification
@@ -192,8 +239,8 @@ def test_perfect_rotated_lattice(kind, a, S):
         assert 0 < n_alt < len(atoms)
     F = O.Frame(f.positions, f.cell)
     for t, i in enumerate(atoms[:4]):
-        ids, imgs, drc, dre, d2 = F.knn(int(i), O.K_OF[S - 1])
-        v = np.vstack([np.zeros(3), dre])
+        ids, imgs, dr, d2 = F.knn(int(i), O.K_OF[S - 1])
+        v = np.vstack([np.zeros(3), dr])
         s_exact = len(v) / np.sum(np.linalg.norm(v - v.mean(0), axis=1))
         assert abs(r["scale"][t] - s_exact) < 1e-12
     for P in r["strain"]:
@@ -219,8 +266,8 @@ def test_small_noise_sc_matches_brute_force_over_all_permutations():
         i = int(rng.integers(f.n))
         r = O.classify_frame(f, atoms=[i], species=None, mask=1)
         F = O.Frame(f.positions, f.cell)
-        ids, imgs, drc, dre, d2 = F.knn(i, 6)
-        v = np.vstack([np.zeros(3), dre])
+        ids, imgs, dr, d2 = F.knn(i, 6)
+        v = np.vstack([np.zeros(3), dr])
         best = min(_kabsch_scaled_r2(v[[0] + [1 + p for p in perm]], w)
                    for perm in itertools.permutations(range(6)))
         assert r["structure"][0] == O.SC

@@ -100,7 +100,7 @@ def test_order_follows_areas_then_distance():
     F = O.Frame(f.positions, f.cell, f.pbc)
     for atom in rng.choice(f.n, 30, replace=False):
         ids, imgs, areas = F.topo_knn(int(atom))
-        e_ids, e_imgs, _, _, d2 = F.knn(int(atom), 18)
+        e_ids, e_imgs, _, d2 = F.knn(int(atom), 18)
         rank = {(int(j), tuple(n)): r for r, (j, n) in enumerate(zip(e_ids, e_imgs))}
         r = [rank[(int(j), tuple(n))] for j, n in zip(ids, imgs)]
         a = areas[r]
