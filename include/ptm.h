@@ -58,7 +58,9 @@ enum { PTM_ALLOY_NONE = 0, PTM_ALLOY_PURE = 1, PTM_ALLOY_L10 = 2, PTM_ALLOY_L12_
 enum { PTM_F32 = 0, PTM_F64 = 1 };
 
 /* Neighbour ordering (Sec. 3, Eq. 5).  Euclidean: the 14 nearest images by
-   distance (then atom id, then image).  Topological: the 18 nearest, reordered
+   distance (then atom id, then image), distances compared in FP64 whatever the
+   position type (float32 positions are widened exactly; the library decides in
+   FP32 wherever a proven FP32 error bound separates two distances).  Topological: the 18 nearest, reordered
    by the area of the face their Voronoi cell shares with the atom's (the cell
    taken among those 18), larger first, then nearer; areas within 1e-3 of the
    mean squared neighbour distance count as equal; the first 14 are used.
@@ -136,6 +138,8 @@ typedef struct {
   double atom_kernel_ms;     /* device time of the per-atom kernels (ordering + classification) */
   int64_t topo_fp64;         /* atoms whose topological order was decided in FP64 (an area
                                 gap at the edge of the equal-area band) */
+  int64_t knn_fp64;          /* float32 input: atoms whose neighbour order needed FP64
+                                distances (two candidates within the FP32 error bound) */
 } ptm_stats;
 
 /* Create a context on options->device (NULL options: device 0, default budget).
@@ -281,8 +285,12 @@ ptm_status ptm_server_destroy(ptm_server *server);
    kernels and results as ptm_classify_frame; positions, species and outputs are
    DEVICE pointers owned by the caller.  Its workspace is one static device
    array of about 2.6 MiB that every GPU loading this library holds until the
-   process exits.  The first call on a device looks up that array's device
-   address; make that first call before any stream capture.  All calls share
+   process exits.  Its device address belongs to the CUDA context current at
+   the call: every call outside stream capture looks it up again (so a device
+   reset or a caller-made driver context is followed), and a call on a
+   capturing stream reuses the address last found for the current context, so
+   make at least one call outside capture in that context first (else
+   PTM_ERR_INVALID_ARG).  All calls share
    the array and keep its last contents (the call clears what must start at
    zero), so calls whose work overlaps on the GPU race: order them on one
    stream.  Returns PTM_ERR_INVALID_ARG for frames above the limit (or bad

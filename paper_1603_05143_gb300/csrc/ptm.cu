@@ -98,48 +98,106 @@ static bool finite_cell(const double *H) {
   return true;
 }
 
-// Enqueue the whole pipeline for one frame whose buffers are on the device.
-static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_outputs *o, cudaStream_t st) {
-  if (!f || !o) return PTM_ERR_INVALID_ARG;
+// Output pointers of a frame descriptor.
+static void set_outputs(FrameDesc *d, const ptm_outputs *o) {
+  d->structure = o->structure; d->alloy = o->alloy; d->rmsd = o->rmsd; d->scale = o->scale;
+  d->quat = o->quat; d->strain = o->strain; d->corr = o->correspondence;
+  d->vm = o->von_mises; d->rf = o->rodrigues;
+}
+
+// Most cells a frame of n atoms is given (the cell grid is coarsened until it fits).
+constexpr size_t max_cells(size_t n) { return 4 * n + 64; }
+
+// Host description of one frame: its descriptor (device pointers are filled in
+// by the caller once its workspace exists) and its binning parameters.  Shared
+// by single frames, batches and the allocation-free entry.
+static ptm_status setup_frame(const ptm_frame *f, double cell_factor, FrameDesc *desc, BinParams *bp,
+                              size_t *ncell_out) {
+  if (!f || f->n_atoms < 1 || f->n_atoms >= (1ll << 31) || !f->positions) return PTM_ERR_INVALID_ARG;
   if (f->ordering != PTM_ORDER_EUCLIDEAN && f->ordering != PTM_ORDER_TOPOLOGICAL) return PTM_ERR_INVALID_ARG;
-  if (f->n_atoms < 1 || f->n_atoms >= (1ll << 31) || !f->positions) return PTM_ERR_INVALID_ARG;
   if (f->pos_dtype != PTM_F32 && f->pos_dtype != PTM_F64) return PTM_ERR_INVALID_ARG;
   if (!finite_cell(f->cell)) return PTM_ERR_INVALID_ARG;
   const double *H = f->cell;
-  double det = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
-               H[2] * (H[3] * H[7] - H[4] * H[6]);
+  const double det = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+                     H[2] * (H[3] * H[7] - H[4] * H[6]);
   if (!(std::fabs(det) > 1e-12)) return PTM_ERR_INVALID_ARG;
   const int64_t n = f->n_atoms;
-  const int f64 = f->pos_dtype == PTM_F64;
-  double Hinv[9];
+  double Hinv[9], W[3];
   for (int i = 0; i < 3; i++)
     for (int j = 0; j < 3; j++) {
       int i1 = (j + 1) % 3, i2 = (j + 2) % 3, j1 = (i + 1) % 3, j2 = (i + 2) % 3;
       Hinv[3 * i + j] = (H[3 * i1 + j1] * H[3 * i2 + j2] - H[3 * i1 + j2] * H[3 * i2 + j1]) / det;
     }
-  double W[3];
-  for (int c = 0; c < 3; c++) {
-    double g = Hinv[c] * Hinv[c] + Hinv[3 + c] * Hinv[3 + c] + Hinv[6 + c] * Hinv[6 + c];
-    W[c] = 1.0 / std::sqrt(g);
-  }
-  // cells about 1.25x the expected 14-neighbour radius at the mean density
+  for (int c = 0; c < 3; c++) W[c] = 1.0 / std::sqrt(Hinv[c] * Hinv[c] + Hinv[3 + c] * Hinv[3 + c] + Hinv[6 + c] * Hinv[6 + c]);
   const double rho = (double)n / std::fabs(det);
-  const double r14 = std::cbrt(3.0 * 15.0 / (4.0 * M_PI * rho));
-  const double wt = 1.25 * r14;
+  const double wt = cell_factor * std::cbrt(3.0 * 15.0 / (4.0 * M_PI * rho));
   int nb[3];
   size_t ncell = 1;
   for (int c = 0; c < 3; c++) {
-    nb[c] = std::max(1, (int)std::floor(W[c] / wt));
-    nb[c] = std::min(nb[c], 1024);
+    nb[c] = std::min(std::max(1, (int)std::floor(W[c] / wt)), 1024);
     ncell *= (size_t)nb[c];
   }
-  while (ncell > (size_t)4 * n + 64) {
+  while (ncell > max_cells((size_t)n)) {
     int c = (int)(std::max_element(nb, nb + 3) - nb);
     ncell /= nb[c];
     nb[c] = std::max(1, nb[c] / 2);
     ncell *= nb[c];
   }
-  ptm_status rs = grow(ctx, (size_t)n, ncell, f64);
+  std::memset(desc, 0, sizeof(FrameDesc));
+  desc->species = f->species;
+  desc->positions = f->positions;
+  desc->n = n;
+  for (int c = 0; c < 3; c++) { desc->nb[c] = nb[c]; desc->pbc[c] = f->pbc[c] ? 1 : 0; }
+  desc->f64 = f->pos_dtype == PTM_F64;
+  desc->mask = f->template_mask ? (f->template_mask & PTM_MASK_ALL) : PTM_MASK_ALL;
+  desc->rmsd_max = std::isnan(f->rmsd_max) ? INFINITY : (float)f->rmsd_max;
+  desc->min_cell_width = (float)std::min(W[0] / nb[0], std::min(W[1] / nb[1], W[2] / nb[2]));
+  for (int i = 0; i < 9; i++) desc->H[i] = H[i];
+  // |n.H| for |n_r| <= 1 over the periodic rows r: at most the length of the
+  // vector of per-component sums of |H_rc| (rounded up a little for FP32)
+  double sm2 = 0.0;
+  for (int k = 0; k < 3; k++) {
+    double sk = 0.0;
+    for (int r = 0; r < 3; r++) if (f->pbc[r]) sk += std::fabs(H[3 * r + k]);
+    sm2 += sk * sk;
+  }
+  desc->smax = (float)(std::sqrt(sm2) * (1.0 + 1e-6));
+  for (int a = -2; a <= 2; a++)
+    for (int b = -2; b <= 2; b++)
+      for (int c = -2; c <= 2; c++) {
+        const int i = (a + 2) * 25 + (b + 2) * 5 + (c + 2);
+        for (int k = 0; k < 3; k++) {
+          volatile double t0 = (double)a * H[k];
+          volatile double t1 = (double)b * H[3 + k];
+          volatile double t2 = (double)c * H[6 + k];
+          volatile double t01 = t0 + t1;
+          const double sh = t01 + t2;
+          desc->s64[i][k] = sh;
+          desc->s32[i][k] = (float)sh;
+          desc->slo[i][k] = (float)(sh - (double)(float)sh);
+        }
+      }
+  std::memset(bp, 0, sizeof(BinParams));
+  for (int i = 0; i < 9; i++) bp->Hinv[i] = (float)Hinv[i];
+  for (int c = 0; c < 3; c++) { bp->W[c] = (float)W[c]; bp->nb[c] = nb[c]; bp->pbc[c] = desc->pbc[c]; }
+  bp->n = n;
+  bp->f64 = desc->f64;
+  bp->pos = f->positions;
+  *ncell_out = ncell;
+  return PTM_OK;
+}
+
+// Enqueue the whole pipeline for one frame whose buffers are on the device.
+static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_outputs *o, cudaStream_t st) {
+  if (!f || !o) return PTM_ERR_INVALID_ARG;
+  FrameDesc desc;
+  BinParams bp;
+  size_t ncell = 0;
+  ptm_status rs = setup_frame(f, 1.25, &desc, &bp, &ncell);
+  if (rs != PTM_OK) return rs;
+  const int64_t n = f->n_atoms;
+  const int f64 = desc.f64;
+  rs = grow(ctx, (size_t)n, ncell, f64);
   if (rs != PTM_OK) return rs;
   const bool topological = f->ordering == PTM_ORDER_TOPOLOGICAL;
   if (topological && (size_t)n > ctx->cap_topo) {
@@ -155,51 +213,13 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
     CK(cudaMalloc(&ctx->topo_side, topo_side_bytes((size_t)n)));
     ctx->cap_topo = (size_t)n;
   }
-
-  FrameDesc desc;
-  FrameDesc *hd = &desc;
-  std::memset(hd, 0, sizeof(FrameDesc));
-  hd->sorted = ctx->sorted;
-  hd->sbin = ctx->sbin;
-  hd->cell_start = ctx->cell_start;
-  hd->wrapv = ctx->wrapv;
-  hd->species = f->species;
-  hd->positions = f->positions;
-  hd->n = n;
-  for (int c = 0; c < 3; c++) { hd->nb[c] = nb[c]; hd->pbc[c] = f->pbc[c] ? 1 : 0; }
-  hd->f64 = f64;
-  hd->mask = f->template_mask ? (f->template_mask & PTM_MASK_ALL) : PTM_MASK_ALL;
-  hd->rmsd_max = std::isnan(f->rmsd_max) ? INFINITY : (float)f->rmsd_max;
-  hd->min_cell_width = (float)std::min(W[0] / nb[0], std::min(W[1] / nb[1], W[2] / nb[2]));
-  for (int i = 0; i < 9; i++) hd->H[i] = H[i];
-  // image shifts for n in [-2, 2]^3 exactly as the contract evaluates them:
-  // (n0 H0 + n1 H1) + n2 H2 in FP64 (built with -ffp-contract=off)
-  for (int a = -2; a <= 2; a++)
-    for (int b = -2; b <= 2; b++)
-      for (int c = -2; c <= 2; c++) {
-        int i = (a + 2) * 25 + (b + 2) * 5 + (c + 2);
-        for (int k = 0; k < 3; k++) {
-          volatile double t0 = (double)a * H[k];
-          volatile double t1 = (double)b * H[3 + k];
-          volatile double t2 = (double)c * H[6 + k];
-          volatile double t01 = t0 + t1;
-          double s = t01 + t2;
-          hd->s64[i][k] = s;
-          hd->s32[i][k] = (float)s;
-          hd->slo[i][k] = (float)(s - (double)(float)s);
-        }
-      }
-  hd->structure = o->structure; hd->alloy = o->alloy; hd->rmsd = o->rmsd; hd->scale = o->scale;
-  hd->quat = o->quat; hd->strain = o->strain; hd->corr = o->correspondence;
-  hd->vm = o->von_mises; hd->rf = o->rodrigues;
-  hd->dstat = ctx->dstat;
-  hd->counters = ctx->counters;
-
-  BinParams bp;
-  for (int i = 0; i < 9; i++) bp.Hinv[i] = (float)Hinv[i];
-  for (int c = 0; c < 3; c++) { bp.W[c] = (float)W[c]; bp.nb[c] = nb[c]; bp.pbc[c] = hd->pbc[c]; }
-  bp.n = n;
-  bp.f64 = f64;
+  desc.sorted = ctx->sorted;
+  desc.sbin = ctx->sbin;
+  desc.cell_start = ctx->cell_start;
+  desc.wrapv = ctx->wrapv;
+  set_outputs(&desc, o);
+  desc.dstat = ctx->dstat;
+  desc.counters = ctx->counters;
 
   cudaGetLastError();   // launch errors are read below; drop any left by earlier calls
   CK(cudaEventRecord(ctx->ev[0], st));
@@ -424,6 +444,7 @@ ptm_status ptm_get_stats(ptm_context *ctx, ptm_stats *out) {
   out->qcp_fp64 = (int64_t)c[C_QCP64];
   out->tie_fp64 = (int64_t)c[C_TIE64];
   out->topo_fp64 = (int64_t)c[C_TOPO64];
+  out->knn_fp64 = (int64_t)c[C_KNN64];
   out->internal = (int64_t)c[C_INTERNAL];
   return PTM_OK;
 }
@@ -431,75 +452,6 @@ ptm_status ptm_get_stats(ptm_context *ctx, ptm_stats *out) {
 }  // extern "C"
 
 // ================================================================== batches
-// Host description of one frame of a batch: its descriptor (device pointers are
-// filled in when the batch workspace exists) and its binning parameters.
-static ptm_status setup_frame(const ptm_frame *f, double cell_factor, FrameDesc *desc, BinParams *bp,
-                              size_t *ncell_out) {
-  if (!f || f->n_atoms < 1 || f->n_atoms >= (1ll << 31) || !f->positions) return PTM_ERR_INVALID_ARG;
-  if (f->ordering != PTM_ORDER_EUCLIDEAN && f->ordering != PTM_ORDER_TOPOLOGICAL) return PTM_ERR_INVALID_ARG;
-  if (f->pos_dtype != PTM_F32 && f->pos_dtype != PTM_F64) return PTM_ERR_INVALID_ARG;
-  if (!finite_cell(f->cell)) return PTM_ERR_INVALID_ARG;
-  const double *H = f->cell;
-  const double det = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
-                     H[2] * (H[3] * H[7] - H[4] * H[6]);
-  if (!(std::fabs(det) > 1e-12)) return PTM_ERR_INVALID_ARG;
-  const int64_t n = f->n_atoms;
-  double Hinv[9], W[3];
-  for (int i = 0; i < 3; i++)
-    for (int j = 0; j < 3; j++) {
-      int i1 = (j + 1) % 3, i2 = (j + 2) % 3, j1 = (i + 1) % 3, j2 = (i + 2) % 3;
-      Hinv[3 * i + j] = (H[3 * i1 + j1] * H[3 * i2 + j2] - H[3 * i1 + j2] * H[3 * i2 + j1]) / det;
-    }
-  for (int c = 0; c < 3; c++) W[c] = 1.0 / std::sqrt(Hinv[c] * Hinv[c] + Hinv[3 + c] * Hinv[3 + c] + Hinv[6 + c] * Hinv[6 + c]);
-  const double rho = (double)n / std::fabs(det);
-  const double wt = cell_factor * std::cbrt(3.0 * 15.0 / (4.0 * M_PI * rho));
-  int nb[3];
-  size_t ncell = 1;
-  for (int c = 0; c < 3; c++) {
-    nb[c] = std::min(std::max(1, (int)std::floor(W[c] / wt)), 1024);
-    ncell *= (size_t)nb[c];
-  }
-  while (ncell > (size_t)4 * n + 64) {
-    int c = (int)(std::max_element(nb, nb + 3) - nb);
-    ncell /= nb[c];
-    nb[c] = std::max(1, nb[c] / 2);
-    ncell *= nb[c];
-  }
-  std::memset(desc, 0, sizeof(FrameDesc));
-  desc->species = f->species;
-  desc->positions = f->positions;
-  desc->n = n;
-  for (int c = 0; c < 3; c++) { desc->nb[c] = nb[c]; desc->pbc[c] = f->pbc[c] ? 1 : 0; }
-  desc->f64 = f->pos_dtype == PTM_F64;
-  desc->mask = f->template_mask ? (f->template_mask & PTM_MASK_ALL) : PTM_MASK_ALL;
-  desc->rmsd_max = std::isnan(f->rmsd_max) ? INFINITY : (float)f->rmsd_max;
-  desc->min_cell_width = (float)std::min(W[0] / nb[0], std::min(W[1] / nb[1], W[2] / nb[2]));
-  for (int i = 0; i < 9; i++) desc->H[i] = H[i];
-  for (int a = -2; a <= 2; a++)
-    for (int b = -2; b <= 2; b++)
-      for (int c = -2; c <= 2; c++) {
-        const int i = (a + 2) * 25 + (b + 2) * 5 + (c + 2);
-        for (int k = 0; k < 3; k++) {
-          volatile double t0 = (double)a * H[k];
-          volatile double t1 = (double)b * H[3 + k];
-          volatile double t2 = (double)c * H[6 + k];
-          volatile double t01 = t0 + t1;
-          const double sh = t01 + t2;
-          desc->s64[i][k] = sh;
-          desc->s32[i][k] = (float)sh;
-          desc->slo[i][k] = (float)(sh - (double)(float)sh);
-        }
-      }
-  std::memset(bp, 0, sizeof(BinParams));
-  for (int i = 0; i < 9; i++) bp->Hinv[i] = (float)Hinv[i];
-  for (int c = 0; c < 3; c++) { bp->W[c] = (float)W[c]; bp->nb[c] = nb[c]; bp->pbc[c] = desc->pbc[c]; }
-  bp->n = n;
-  bp->f64 = desc->f64;
-  bp->pos = f->positions;
-  *ncell_out = ncell;
-  return PTM_OK;
-}
-
 struct ptm_batch {
   ptm_context *ctx = nullptr;
   int nframes = 0, f64 = 0;
@@ -671,11 +623,7 @@ static void batch_layout(ptm_batch *b, unsigned char *base, BatchPlan &P, const 
     P.hd[f].sbin = b->sbin;
     P.hd[f].cell_start = b->cell_start + P.hb[f].cell_off;
     P.hd[f].wrapv = b->wrapv;
-    P.hd[f].structure = outs[f].structure; P.hd[f].alloy = outs[f].alloy; P.hd[f].rmsd = outs[f].rmsd;
-    P.hd[f].scale = outs[f].scale; P.hd[f].quat = outs[f].quat; P.hd[f].strain = outs[f].strain;
-    P.hd[f].corr = outs[f].correspondence;
-    P.hd[f].vm = outs[f].von_mises;
-    P.hd[f].rf = outs[f].rodrigues;
+    set_outputs(&P.hd[f], &outs[f]);
     P.hd[f].dstat = b->d_dstat + 4 * f;
     P.hd[f].counters = b->counters;
     P.hb[f].dstat = b->d_dstat + 4 * f;
@@ -765,6 +713,7 @@ extern "C" ptm_status ptm_batch_stats(ptm_batch *b, ptm_stats *out) {
   out->knn_fail = (int64_t)c[C_KNN_FAIL]; out->sos = (int64_t)c[C_SOS]; out->qcp_fp64 = (int64_t)c[C_QCP64];
   out->tie_fp64 = (int64_t)c[C_TIE64];
   out->topo_fp64 = (int64_t)c[C_TOPO64]; out->internal = (int64_t)c[C_INTERNAL];
+  out->knn_fp64 = (int64_t)c[C_KNN64];
   out->candidates = (int64_t)c[C_CAND]; out->candidate_points = (int64_t)c[C_CANDPTS];
   out->pipeline_ms = t_all;
   out->atom_kernel_ms = t_atom;
@@ -835,8 +784,8 @@ extern "C" ptm_status ptm_autotune_batch(ptm_context *ctx, int nframes, const pt
 namespace {
 
 constexpr int kNoallocAtoms = PTM_NOALLOC_MAX_ATOMS;
-constexpr int kNoallocCells = 4 * kNoallocAtoms + 64;                 // the cell-count cap of the frame setup
-constexpr int kNoallocScanBlocks = (kNoallocCells + 1 + 2 * SCAN_BLOCK - 1) / (2 * SCAN_BLOCK) + 1;
+constexpr size_t kNoallocCells = max_cells(kNoallocAtoms);          // setup_frame's cap for the largest frame
+constexpr size_t kNoallocScanBlocks = (kNoallocCells + 1 + 2 * SCAN_BLOCK - 1) / (2 * SCAN_BLOCK) + 1;
 
 struct NoallocLayout {                  // byte offsets inside the static array
   static constexpr size_t sorted = 0;                                            // Atom64 records (float4 fits too)
@@ -855,24 +804,49 @@ struct NoallocLayout {                  // byte offsets inside the static array
 
 static __device__ __align__(256) unsigned char ptm_noalloc_scratch[NoallocLayout::total];
 
-// Device address of the array on each device, resolved once with that device current.
-constexpr int kMaxDevices = 64;
-unsigned char *g_noalloc_ptr[kMaxDevices] = {nullptr};
+// The array's device address belongs to the CUDA context current when it is
+// looked up.  Outside stream capture every call looks it up again (cheap, and
+// right after a device reset or with a caller-made driver context); during
+// capture, where a lookup may not be allowed, the address found last for the
+// current context is used.
+typedef int (*CtxGetCurrentFn)(void **);
+constexpr int kNoallocCtxSlots = 64;
+struct NoallocSlot { void *ctx; unsigned char *ptr; };
+NoallocSlot g_noalloc_slots[kNoallocCtxSlots] = {};
+int g_noalloc_next = 0;
+CtxGetCurrentFn g_ctx_get_current = nullptr;
 std::mutex g_noalloc_mutex;
 
-ptm_status noalloc_setup(int dev, unsigned char **out) {
-  if (dev < 0 || dev >= kMaxDevices) return PTM_ERR_INVALID_ARG;
+ptm_status noalloc_address(cudaStream_t st, unsigned char **out) {
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, ptm_noalloc_scratch) != cudaSuccess || !p) {
+  if (!g_ctx_get_current) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
       cudaGetLastError();
       return PTM_ERR_CUDA;
     }
-    g_noalloc_ptr[dev] = (unsigned char *)p;
+    g_ctx_get_current = (CtxGetCurrentFn)fn;
   }
-  *out = g_noalloc_ptr[dev];
-  return PTM_OK;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) { cudaGetLastError(); return PTM_ERR_CUDA; }
+  void *ctx = nullptr;
+  if (cap == cudaStreamCaptureStatusNone) {
+    void *p = nullptr;           // also makes the runtime's context current on a fresh thread
+    if (cudaGetSymbolAddress(&p, ptm_noalloc_scratch) != cudaSuccess || !p) { cudaGetLastError(); return PTM_ERR_CUDA; }
+    if (g_ctx_get_current(&ctx) != 0 || !ctx) return PTM_ERR_CUDA;
+    int k = 0;
+    while (k < kNoallocCtxSlots && g_noalloc_slots[k].ctx != ctx) k++;
+    if (k == kNoallocCtxSlots) { k = g_noalloc_next; g_noalloc_next = (k + 1) % kNoallocCtxSlots; }
+    g_noalloc_slots[k] = {ctx, (unsigned char *)p};
+    *out = (unsigned char *)p;
+    return PTM_OK;
+  }
+  if (g_ctx_get_current(&ctx) != 0 || !ctx) return PTM_ERR_CUDA;
+  for (int k = 0; k < kNoallocCtxSlots; k++)
+    if (g_noalloc_slots[k].ctx == ctx) { *out = g_noalloc_slots[k].ptr; return PTM_OK; }
+  return PTM_ERR_INVALID_ARG;    // captured before any call outside capture in this context
 }
 
 }  // namespace
@@ -881,43 +855,18 @@ extern "C" ptm_status ptm_classify_frame_noalloc(const ptm_frame *f, const ptm_o
   if (!f || !o) return PTM_ERR_INVALID_ARG;
   if (f->n_atoms < 1 || f->n_atoms > kNoallocAtoms || !f->positions) return PTM_ERR_INVALID_ARG;
   if (f->ordering != PTM_ORDER_EUCLIDEAN) return PTM_ERR_INVALID_ARG;
-  if (f->pos_dtype != PTM_F32 && f->pos_dtype != PTM_F64) return PTM_ERR_INVALID_ARG;
-  if (!finite_cell(f->cell)) return PTM_ERR_INVALID_ARG;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return PTM_ERR_CUDA; }
-  unsigned char *base = nullptr;
-  ptm_status rs = noalloc_setup(dev, &base);
+  FrameDesc desc;
+  BinParams bp;
+  size_t ncell = 0;
+  ptm_status rs = setup_frame(f, 1.25, &desc, &bp, &ncell);
   if (rs != PTM_OK) return rs;
+  if (ncell > kNoallocCells) return PTM_ERR_INVALID_ARG;      // cannot happen: setup_frame caps the grid
   cudaStream_t st = (cudaStream_t)stream;
-  const double *H = f->cell;
-  const double det = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
-                     H[2] * (H[3] * H[7] - H[4] * H[6]);
-  if (!(std::fabs(det) > 1e-12)) return PTM_ERR_INVALID_ARG;
+  unsigned char *base = nullptr;
+  rs = noalloc_address(st, &base);
+  if (rs != PTM_OK) return rs;
   const int64_t n = f->n_atoms;
-  const int f64 = f->pos_dtype == PTM_F64;
-  double Hinv[9];
-  for (int i = 0; i < 3; i++)
-    for (int j = 0; j < 3; j++) {
-      int i1 = (j + 1) % 3, i2 = (j + 2) % 3, j1 = (i + 1) % 3, j2 = (i + 2) % 3;
-      Hinv[3 * i + j] = (H[3 * i1 + j1] * H[3 * i2 + j2] - H[3 * i1 + j2] * H[3 * i2 + j1]) / det;
-    }
-  double W[3];
-  for (int c = 0; c < 3; c++) W[c] = 1.0 / std::sqrt(Hinv[c] * Hinv[c] + Hinv[3 + c] * Hinv[3 + c] + Hinv[6 + c] * Hinv[6 + c]);
-  const double rho = (double)n / std::fabs(det);
-  const double wt = 1.25 * std::cbrt(3.0 * 15.0 / (4.0 * M_PI * rho));
-  int nb[3];
-  size_t ncell = 1;
-  for (int c = 0; c < 3; c++) {
-    nb[c] = std::min(std::max(1, (int)std::floor(W[c] / wt)), 1024);
-    ncell *= (size_t)nb[c];
-  }
-  while (ncell > (size_t)4 * n + 64) {
-    int c = (int)(std::max_element(nb, nb + 3) - nb);
-    ncell /= nb[c];
-    nb[c] = std::max(1, nb[c] / 2);
-    ncell *= nb[c];
-  }
-  if (ncell > (size_t)kNoallocCells) return PTM_ERR_INVALID_ARG;
+  const int f64 = desc.f64;
   void *sorted = base + NoallocLayout::sorted;
   int *sbin = (int *)(base + NoallocLayout::sbin), *wrapv = (int *)(base + NoallocLayout::wrapv);
   int *atom_cell = (int *)(base + NoallocLayout::atom_cell), *atom_rank = (int *)(base + NoallocLayout::atom_rank);
@@ -925,42 +874,10 @@ extern "C" ptm_status ptm_classify_frame_noalloc(const ptm_frame *f, const ptm_o
   int *cell_count = (int *)(base + NoallocLayout::cell_count), *cell_start = (int *)(base + NoallocLayout::cell_start);
   int *block_sums = (int *)(base + NoallocLayout::block_sums), *dstat = (int *)(base + NoallocLayout::dstat);
   unsigned long long *counters = (unsigned long long *)(base + NoallocLayout::counters);
-
-  FrameDesc desc;
-  std::memset(&desc, 0, sizeof desc);
   desc.sorted = sorted; desc.sbin = sbin; desc.cell_start = cell_start; desc.wrapv = wrapv;
-  desc.species = f->species; desc.positions = f->positions; desc.n = n;
-  for (int c = 0; c < 3; c++) { desc.nb[c] = nb[c]; desc.pbc[c] = f->pbc[c] ? 1 : 0; }
-  desc.f64 = f64;
-  desc.mask = f->template_mask ? (f->template_mask & PTM_MASK_ALL) : PTM_MASK_ALL;
-  desc.rmsd_max = std::isnan(f->rmsd_max) ? INFINITY : (float)f->rmsd_max;
-  desc.min_cell_width = (float)std::min(W[0] / nb[0], std::min(W[1] / nb[1], W[2] / nb[2]));
-  for (int i = 0; i < 9; i++) desc.H[i] = H[i];
-  for (int a = -2; a <= 2; a++)
-    for (int b = -2; b <= 2; b++)
-      for (int c = -2; c <= 2; c++) {
-        const int i = (a + 2) * 25 + (b + 2) * 5 + (c + 2);
-        for (int k = 0; k < 3; k++) {
-          volatile double t0 = (double)a * H[k];
-          volatile double t1 = (double)b * H[3 + k];
-          volatile double t2 = (double)c * H[6 + k];
-          volatile double t01 = t0 + t1;
-          const double s = t01 + t2;
-          desc.s64[i][k] = s;
-          desc.s32[i][k] = (float)s;
-          desc.slo[i][k] = (float)(s - (double)(float)s);
-        }
-      }
-  desc.structure = o->structure; desc.alloy = o->alloy; desc.rmsd = o->rmsd; desc.scale = o->scale;
-  desc.quat = o->quat; desc.strain = o->strain; desc.corr = o->correspondence;
-  desc.vm = o->von_mises; desc.rf = o->rodrigues;
+  set_outputs(&desc, o);
   desc.dstat = dstat;
   desc.counters = counters;
-  BinParams bp;
-  for (int i = 0; i < 9; i++) bp.Hinv[i] = (float)Hinv[i];
-  for (int c = 0; c < 3; c++) { bp.W[c] = (float)W[c]; bp.nb[c] = nb[c]; bp.pbc[c] = desc.pbc[c]; }
-  bp.n = n;
-  bp.f64 = f64;
   cudaGetLastError();   // launch errors are read below; drop any left by earlier calls
   // the array keeps the previous call's contents: clear what must start at zero
   if (cudaMemsetAsync(cell_count, 0, (ncell + 1) * sizeof(int), st) != cudaSuccess ||

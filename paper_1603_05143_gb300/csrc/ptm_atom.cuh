@@ -45,6 +45,7 @@ struct FrameDesc {
   uint32_t mask;
   float rmsd_max;
   float min_cell_width;        // smallest perpendicular cell width (Angstrom)
+  float smax;                  // bound on the length of an image shift n.H with |n_r| <= 1 (periodic r)
   double H[9];                 // rows = cell vectors
   float s32[125][3];           // shift of image n in [-2,2]^3, FP64 value rounded to FP32
   float slo[125][3];           // FP64 shift minus s32 (compensated neighbour vectors)
@@ -62,12 +63,12 @@ struct FrameDesc {
   const int2 *topo;            // topological order: [t][n] (sorted slot, image) of neighbour t by
                                // frame-local slot (s - atom_offset), or NULL for the Euclidean order
   int *dstat;                  // [0] any atom wrapped, [1] overshoot (float bits, Angstrom)
-  unsigned long long *counters;  // ptm_stats order: atoms, matched, knn_wide, knn_fail, sos, qcp_fp64, tie_fp64, internal, candidates, candidate_points
+  unsigned long long *counters;  // the C_* counters below
   int64_t atom_offset;         // first sorted slot of this frame (0 for a single frame)
 };
 
 enum { C_ATOMS = 0, C_MATCHED, C_KNN_WIDE, C_KNN_FAIL, C_SOS, C_QCP64, C_TIE64, C_INTERNAL, C_CAND, C_CANDPTS, C_TOPO64,
-       C_NCOUNTERS };
+       C_KNN64, C_NCOUNTERS };
 
 __device__ __forceinline__ void count(const FrameDesc &d, int which, unsigned long long v = 1) {
   atomicAdd(d.counters + which, v);

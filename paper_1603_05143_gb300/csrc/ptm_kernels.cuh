@@ -18,11 +18,6 @@ template <> struct RT<true> { typedef double T; };
 
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
-template <typename T>
-__device__ __forceinline__ bool key_less(T da, int ia, int ma, T db, int ib, int mb) {
-  return da < db || (da == db && (ia < ib || (ia == ib && ma < mb)));
-}
-
 template <bool F64>
 __device__ __forceinline__ void load_atom(const FrameDesc &d, int j, typename RT<F64>::T &x,
                                           typename RT<F64>::T &y, typename RT<F64>::T &z, int &id) {
@@ -49,9 +44,13 @@ __device__ __forceinline__ void contract_shift(const FrameDesc &d, int a, int b,
   }
 }
 
-// The distance contract (Sec. 3 ordering, reading R4): in the input precision,
-// one rounded operation at a time, no fused multiply-add:
-//   dr = (x_j - x_i) + shift,  d2 = (dr_x^2 + dr_y^2) + dr_z^2
+// The distance contract (Sec. 3 orders neighbours by distance; the paper fixes
+// no precision, so the order is that of the distances between the given points
+// in FP64): dr = (x_j - x_i) + shift, d2 = (dr_x^2 + dr_y^2) + dr_z^2, one
+// rounded IEEE operation at a time, no fused multiply-add, float32 positions
+// widened exactly.  The kernels first run the same sequence in the input
+// precision (FP32 for float32 input) and decide in FP64 only where the FP32
+// values cannot order two candidates (knn_err).
 __device__ __forceinline__ float contract_dr(float xj, float xi, float s) { return __fadd_rn(__fsub_rn(xj, xi), s); }
 __device__ __forceinline__ double contract_dr(double xj, double xi, double s) { return __dadd_rn(__dsub_rn(xj, xi), s); }
 __device__ __forceinline__ float contract_d2(float a, float b, float c) {
@@ -61,11 +60,38 @@ __device__ __forceinline__ double contract_d2(double a, double b, double c) {
   return __dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(c, c));
 }
 
+// FP64 squared distance of the image (a0, a1, a2) of an atom at (xj, yj, zj):
+// the ordering key.  For float64 input it equals the input-precision value.
+template <typename T>
+__device__ __forceinline__ double key64(const FrameDesc &d, T xj, T yj, T zj, T xi, T yi, T zi, int a0, int a1,
+                                        int a2) {
+  double sx, sy, sz;
+  shift_f64(d, a0, a1, a2, sx, sy, sz);
+  return contract_d2(contract_dr((double)xj, (double)xi, sx), contract_dr((double)yj, (double)yi, sy),
+                     contract_dr((double)zj, (double)zi, sz));
+}
+
+// Bound on |d2_32 - d2_64| for an FP32 contract value v whose image shift has
+// length at most S (u = 2^-24).  Each component of the FP32 vector is within
+// 2u (|dr_c| + |s_c|) of the FP64 one (the difference, the shift's rounding to
+// FP32 and the sum each round once); squaring and the two sums add 3u v.  So
+// |d2_32 - d2_64| <= u (7 v + 4 |dr| |s|) + 8 u^2 (v + S^2); the constants
+// below leave room for |dr| estimated from v and for rounding in this bound.
+__device__ __forceinline__ float knn_err(float v, float S) {
+  const float u = 5.9604645e-8f;
+  return u * (8.5f * v + 4.5f * sqrtf(v) * S + 9.f * u * S * S);
+}
+
+__device__ __forceinline__ bool key_less64(double da, int ia, int ma, double db, int ib, int mb) {
+  return da < db || (da == db && (ia < ib || (ia == ib && ma < mb)));
+}
+
 // ----------------------------------------------------------------- kNN
 // Visit every (atom, image) in the (2R+1)^3 cells around cell (bx, by, bz):
-// visit(j, d2, idj, image) with d2 by the distance contract.  The cells
-// bz - R .. bz + R of a column are consecutive in the sorted order unless the
-// range wraps, and are then scanned as one range of atoms.
+// visit(j, d2, idj, a0, a1, a2, xj, yj, zj, sx, sy, sz) with d2 by the contract
+// in the input precision, (a0, a1, a2) the image and (sx, sy, sz) its shift.
+// The cells bz - R .. bz + R of a column are consecutive in the sorted order
+// unless the range wraps, and are then scanned as one range of atoms.
 template <bool F64, typename V>
 __device__ __forceinline__ void scan_cells(const FrameDesc &d, int s, typename RT<F64>::T xi,
                                            typename RT<F64>::T yi, typename RT<F64>::T zi, int bx, int by, int bz,
@@ -109,7 +135,7 @@ __device__ __forceinline__ void scan_cells(const FrameDesc &d, int s, typename R
           }
           if (j == s && a0 == 0 && a1 == 0 && a2 == 0) continue;
           const T ex = contract_dr(xj, xi, sx), ey = contract_dr(yj, yi, sy), ez = contract_dr(zj, zi, sz);
-          visit(j, contract_d2(ex, ey, ez), idj, a0, a1, a2);
+          visit(j, contract_d2(ex, ey, ez), idj, a0, a1, a2, xj, yj, zj, sx, sy, sz);
         }
       }
     }
@@ -121,37 +147,47 @@ __device__ __forceinline__ bool search_complete(const FrameDesc &d, int R, float
   return rg > 0.f && d2_last < rg * rg * (1.f - 1e-3f);
 }
 
-// General kNN: the NK nearest images of atom s by the full key (d2, atom id,
-// image), R growing until the NK-th distance lies inside the radius the scanned
-// cells are guaranteed to cover.  Returns the neighbour count (NK, fewer only
-// for a small fully non-periodic system) or -1.
+// General kNN: the NK nearest images of atom s by the full key (FP64 d2, atom
+// id, image), R growing until the NK-th distance lies inside the radius the
+// scanned cells are guaranteed to cover.  For float32 input a candidate whose
+// FP32 distance, less its error bound, exceeds the current NK-th key cannot
+// enter and skips the FP64 evaluation.  Returns the neighbour count (NK, fewer
+// only for a small fully non-periodic system) or -1.
 template <bool F64, int NK = PTM_KNN>
 __device__ __noinline__ int knn(const FrameDesc &d, int s, typename RT<F64>::T xi, typename RT<F64>::T yi,
                                 typename RT<F64>::T zi, int bx, int by, int bz, int wix, int wiy, int wiz,
-                                bool wrapped, typename RT<F64>::T (&Ld2)[NK], int (&Lid)[NK],
-                                int (&Ljs)[NK], int (&Limg)[NK]) {
+                                bool wrapped, double (&Ld2)[NK], int (&Lid)[NK], int (&Ljs)[NK], int (&Limg)[NK]) {
   typedef typename RT<F64>::T T;
-  const T INF = (T)INFINITY;
   for (int R = 1; R <= PTM_RMAX; R++) {
+    float last32 = INFINITY;                           // the NK-th key rounded up to FP32
 #pragma unroll
-    for (int t = 0; t < NK; t++) { Ld2[t] = INF; Lid[t] = 0x7fffffff; Ljs[t] = -1; Limg[t] = 0x7fffffff; }
+    for (int t = 0; t < NK; t++) { Ld2[t] = INFINITY; Lid[t] = 0x7fffffff; Ljs[t] = -1; Limg[t] = 0x7fffffff; }
     scan_cells<F64>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, R,
-                    [&](int j, T d2, int idj, int a0, int a1, int a2) {
-      if (!(d2 <= Ld2[NK - 1])) return;
+                    [&](int j, T d2, int idj, int a0, int a1, int a2, T xj, T yj, T zj, T sx, T sy, T sz) {
+      double key;
+      if constexpr (F64) {
+        key = d2;
+      } else {
+        const float S = sqrtf(sx * sx + sy * sy + sz * sz) * 1.0001f;
+        if (d2 - 1.25f * knn_err(d2, S) > last32) return;
+        key = key64(d, xj, yj, zj, xi, yi, zi, a0, a1, a2);
+      }
+      if (!(key <= Ld2[NK - 1])) return;
       const int img = img_pack(a0, a1, a2);
-      if (!key_less(d2, idj, img, Ld2[NK - 1], Lid[NK - 1], Limg[NK - 1])) return;
+      if (!key_less64(key, idj, img, Ld2[NK - 1], Lid[NK - 1], Limg[NK - 1])) return;
       // insertion into the sorted list (all indices static: stays in registers)
       bool above = true;
 #pragma unroll
       for (int t = NK - 1; t >= 1; t--) {
-        bool lt = key_less(d2, idj, img, Ld2[t - 1], Lid[t - 1], Limg[t - 1]);
+        bool lt = key_less64(key, idj, img, Ld2[t - 1], Lid[t - 1], Limg[t - 1]);
         if (lt) { Ld2[t] = Ld2[t - 1]; Lid[t] = Lid[t - 1]; Ljs[t] = Ljs[t - 1]; Limg[t] = Limg[t - 1]; }
-        else if (above) { Ld2[t] = d2; Lid[t] = idj; Ljs[t] = j; Limg[t] = img; }
+        else if (above) { Ld2[t] = key; Lid[t] = idj; Ljs[t] = j; Limg[t] = img; }
         above = lt;
       }
-      if (above) { Ld2[0] = d2; Lid[0] = idj; Ljs[0] = j; Limg[0] = img; }
+      if (above) { Ld2[0] = key; Lid[0] = idj; Ljs[0] = j; Limg[0] = img; }
+      if constexpr (!F64) last32 = __double2float_ru(Ld2[NK - 1]);
     });
-    if (search_complete(d, R, (float)Ld2[NK - 1])) {
+    if (search_complete(d, R, __double2float_ru(Ld2[NK - 1]))) {
       if (R > 1) count(d, C_KNN_WIDE);
       return NK;
     }
@@ -172,7 +208,7 @@ template <bool F64>
 __device__ __noinline__ int knn_to_scratch(const FrameDesc &d, const Scratch &sm, int s, typename RT<F64>::T xi,
                                            typename RT<F64>::T yi, typename RT<F64>::T zi, int bx, int by, int bz,
                                            int wix, int wiy, int wiz, bool wrapped) {
-  typename RT<F64>::T Ld2[PTM_KNN];
+  double Ld2[PTM_KNN];
   int Lid[PTM_KNN], Ljs[PTM_KNN], Limg[PTM_KNN];
   const int cnt = knn<F64>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, Ld2, Lid, Ljs, Limg);
 #pragma unroll
@@ -180,37 +216,56 @@ __device__ __noinline__ int knn_to_scratch(const FrameDesc &d, const Scratch &sm
   return cnt;
 }
 
-// Fast kNN for the common case (27 cells suffice): pass 1 keeps the NK + 1
-// smallest distances with a min/max network; pass 2 rescans and drops each of
-// the NK nearest into its rank slot.  Equal distances (an atom's mirror-image
-// neighbours in a perfect centrosymmetric lattice) form a run of slots that
-// pass 2 fills in key order (atom id, then image) by insertion; a run that
-// continues past slot NK - 1 keeps its smallest keys, as the general kNN does.
-// Slots are written through `rows`: put(r, j, img) and, while ties are ordered,
-// set(r, j, img, id) / j(r) / img(r) / id(r) (j = -1: empty).  Returns false
-// when the general kNN must decide.
+// Fast kNN for the common case (27 cells suffice).  Pass 1 keeps the NK + 1
+// smallest distances in the input precision with a min/max network.  Slots t
+// and t + 1 are "close" when those values could order their candidates
+// differently from FP64 (float32 input: the gap is within twice knn_err;
+// float64 input: equal values); close slots form runs, and the last run also
+// takes every candidate beyond slot NK - 1 within the error band.  Pass 2
+// rescans and drops each candidate into its rank slot; a run's candidates are
+// placed by insertion on the full key (FP64 d2, atom id, image), keeping the
+// smallest keys when the run crosses the last slot, so the result is the
+// general kNN's order.  Slots are written through `rows`: put(r, j, img) and,
+// inside runs, set(r, j, img, id, key) / j(r) / img(r) / id(r) / key(r)
+// (j = -1: empty).  `close_runs` receives the run mask (0: every rank decided
+// in the input precision).  Returns false when the general kNN must decide.
 template <bool F64, int NK, typename Rows>
 __device__ __forceinline__ bool knn_fast_n(const FrameDesc &d, int s, typename RT<F64>::T xi,
                                            typename RT<F64>::T yi, typename RT<F64>::T zi, int bx, int by, int bz,
-                                           const Rows &rows) {
+                                           const Rows &rows, uint32_t &close_runs) {
   typedef typename RT<F64>::T T;
   T L[NK + 1];
 #pragma unroll
   for (int t = 0; t <= NK; t++) L[t] = (T)INFINITY;
-  scan_cells<F64>(d, s, xi, yi, zi, bx, by, bz, 0, 0, 0, false, 1, [&](int j, T d2, int, int, int, int) {
+  scan_cells<F64>(d, s, xi, yi, zi, bx, by, bz, 0, 0, 0, false, 1,
+                  [&](int j, T d2, int, int, int, int, T, T, T, T, T, T) {
     if (!(d2 < L[NK])) return;
     T x = d2;
 #pragma unroll
     for (int t = 0; t <= NK; t++) { const T lo = fmin(L[t], x); x = fmax(L[t], x); L[t] = lo; }
   });
-  if (!(L[NK] < (T)INFINITY) || !search_complete(d, 1, (float)L[NK - 1])) return false;
-  uint32_t tie = 0;                                  // bit t: L[t] == L[t + 1]
+  if (!(L[NK] < (T)INFINITY)) return false;
+  uint32_t close = 0;                                // bit t: slots t and t + 1 in one run
+  T limit = L[NK - 1];                               // pass 2 admits d2 <= limit
+  if constexpr (F64) {
 #pragma unroll
-  for (int t = 0; t < NK; t++) tie |= (uint32_t)(L[t] == L[t + 1]) << t;
-  const T last = L[NK - 1];
-  if (!tie) {                                        // distinct: distance order is key order
-    scan_cells<F64>(d, s, xi, yi, zi, bx, by, bz, 0, 0, 0, false, 1, [&](int j, T d2, int, int a0, int a1, int a2) {
-      if (!(d2 <= last)) return;
+    for (int t = 0; t < NK; t++) close |= (uint32_t)(L[t] == L[t + 1]) << t;
+  } else {
+    // image shifts occur only when the 27 cells wrap around a periodic side
+    const bool shifted = (d.pbc[0] && (bx == 0 || bx >= d.nb[0] - 1)) ||
+                         (d.pbc[1] && (by == 0 || by >= d.nb[1] - 1)) ||
+                         (d.pbc[2] && (bz == 0 || bz >= d.nb[2] - 1));
+    const float S = shifted ? d.smax : 0.f;
+#pragma unroll
+    for (int t = 0; t < NK; t++) close |= (uint32_t)(L[t + 1] - L[t] <= 2.f * knn_err(L[t + 1], S)) << t;
+    if (close >> (NK - 1) & 1) limit = L[NK - 1] + 2.f * knn_err(1.01f * L[NK - 1], S);
+  }
+  if (!search_complete(d, 1, (float)limit)) return false;
+  close_runs = close;
+  if (!close) {                                      // every rank decided: distance order is key order
+    scan_cells<F64>(d, s, xi, yi, zi, bx, by, bz, 0, 0, 0, false, 1,
+                    [&](int j, T d2, int, int a0, int a1, int a2, T, T, T, T, T, T) {
+      if (!(d2 <= limit)) return;
       int rank = 0;
 #pragma unroll
       for (int t = 0; t < NK - 1; t++) rank += L[t] < d2;
@@ -218,44 +273,58 @@ __device__ __forceinline__ bool knn_fast_n(const FrameDesc &d, int s, typename R
     });
     return true;
   }
-  for (int r = 0; r < NK; r++) rows.set(r, -1, 0, 0);
-  scan_cells<F64>(d, s, xi, yi, zi, bx, by, bz, 0, 0, 0, false, 1, [&](int j, T d2, int idj, int a0, int a1, int a2) {
-    if (!(d2 <= last)) return;
-    int lo = 0;                                      // first slot of this distance (L[lo] == d2)
+  const bool crossing = (close >> (NK - 1)) & 1;
+  for (int r = 0; r < NK; r++) rows.set(r, -1, 0, 0, 0.0);
+  scan_cells<F64>(d, s, xi, yi, zi, bx, by, bz, 0, 0, 0, false, 1,
+                  [&](int j, T d2, int idj, int a0, int a1, int a2, T xj, T yj, T zj, T, T, T) {
+    if (!(d2 <= limit)) return;
+    int r0 = 0;                                      // first slot holding this value (NK - 1 beyond)
 #pragma unroll
-    for (int t = 0; t < NK - 1; t++) lo += L[t] < d2;
+    for (int t = 0; t < NK - 1; t++) r0 += L[t] < d2;
+    const uint32_t below = ~close & ((1u << r0) - 1u);
+    const int rs = below ? 32 - __clz(below) : 0;    // the run: slots rs .. hi - 1
+    const int hi = min(r0 + __ffs(~(close >> r0)), NK);
     const int img = img_pack(a0, a1, a2);
-    const int hi = min(lo + __ffs(~(tie >> lo)), NK);   // its run: slots lo .. hi - 1
-    if (hi - lo == 1) { rows.put(lo, j, img); return; }
-    int r = lo;                                      // insertion point by (id, image)
-    while (r < hi && rows.j(r) >= 0 && (rows.id(r) < idj || (rows.id(r) == idj && rows.img(r) < img))) r++;
+    if (hi - rs == 1 && !(hi == NK && crossing)) { rows.put(rs, j, img); return; }
+    double key;
+    if constexpr (F64) key = d2;
+    else key = key64(d, xj, yj, zj, xi, yi, zi, a0, a1, a2);
+    int r = rs;                                      // insertion point by (key, id, image)
+    while (r < hi && rows.j(r) >= 0 && key_less64(rows.key(r), rows.id(r), rows.img(r), key, idj, img)) r++;
     if (r == hi) return;                             // beyond the NK nearest
     int e = r;                                       // first empty slot, or the run's last
     while (e < hi - 1 && rows.j(e) >= 0) e++;
-    for (int q = e; q > r; q--) rows.set(q, rows.j(q - 1), rows.img(q - 1), rows.id(q - 1));
-    rows.set(r, j, img, idj);
+    for (int q = e; q > r; q--) rows.set(q, rows.j(q - 1), rows.img(q - 1), rows.id(q - 1), rows.key(q - 1));
+    rows.set(r, j, img, idj, key);
   });
   return true;
 }
 
-// kNN slots in the scratch rows NID (sorted index) and IMG (packed image), with
-// the atom id in row Q(r, 0) (free until quantisation) while ties are ordered.
+// kNN slots in the scratch rows NID (sorted index) and IMG (packed image); while
+// a run is ordered the atom id sits in row Q(r, 0) and the FP64 key in rows
+// Q(r, 1), Q(r, 2) (free until the neighbour vectors are written).
 struct ScratchKnnRows {
   const Scratch &sm;
   __device__ __forceinline__ void put(int r, int j, int img) const { sm.NID(r) = j; sm.IMG(r) = img; }
-  __device__ __forceinline__ void set(int r, int j, int img, int id) const {
+  __device__ __forceinline__ void set(int r, int j, int img, int id, double key) const {
     put(r, j, img);
     sm.Q(r, 0) = __int_as_float(id);
+    sm.Q(r, 1) = __int_as_float(__double2hiint(key));
+    sm.Q(r, 2) = __int_as_float(__double2loint(key));
   }
   __device__ __forceinline__ int j(int r) const { return sm.NID(r); }
   __device__ __forceinline__ int img(int r) const { return sm.IMG(r); }
   __device__ __forceinline__ int id(int r) const { return __float_as_int(sm.Q(r, 0)); }
+  __device__ __forceinline__ double key(int r) const {
+    return __hiloint2double(__float_as_int(sm.Q(r, 1)), __float_as_int(sm.Q(r, 2)));
+  }
 };
 
 template <bool F64>
 __device__ __forceinline__ bool knn_fast(const FrameDesc &d, const Scratch &sm, int s, typename RT<F64>::T xi,
-                                         typename RT<F64>::T yi, typename RT<F64>::T zi, int bx, int by, int bz) {
-  return knn_fast_n<F64, PTM_KNN>(d, s, xi, yi, zi, bx, by, bz, ScratchKnnRows{sm});
+                                         typename RT<F64>::T yi, typename RT<F64>::T zi, int bx, int by, int bz,
+                                         uint32_t &close_runs) {
+  return knn_fast_n<F64, PTM_KNN>(d, s, xi, yi, zi, bx, by, bz, ScratchKnnRows{sm}, close_runs);
 }
 
 // ---------------------------------------------------------- per-atom state
@@ -515,7 +584,7 @@ __device__ __noinline__ int rerank_fp64(const FrameDesc &d, int s, const Best bs
   T xi, yi, zi;
   int idi;
   load_atom<F64>(d, s, xi, yi, zi, idi);
-  T Ld2[PTM_KNN];
+  double Ld2[PTM_KNN];
   int Lid[PTM_KNN], Ljs[PTM_KNN], Limg[PTM_KNN];
   int cnt;
   if (d.topo) {
@@ -882,46 +951,40 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
         sm.IMG(t) = e.y;
         cnt += e.x >= 0;
       }
-    } else if (!wrapped && knn_fast<F64>(d, sm, s, xi, yi, zi, bx, by, bz)) {
+    } else if (uint32_t close_runs = 0; !wrapped && knn_fast<F64>(d, sm, s, xi, yi, zi, bx, by, bz, close_runs)) {
       cnt = PTM_KNN;
+      if (!F64 && close_runs) count(d, C_KNN64);
     } else {
       cnt = knn_to_scratch<F64>(d, sm, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped);
+      if (!F64) count(d, C_KNN64);
     }
     hmask = __ballot_sync(live, cnt >= 4);       // lanes that go on to the hulls
     if (cnt < 4) { write_unmatched(d, idi); return; }
     // rows NID / IMG keep (sorted index, image) of each neighbour through the
-    // hulls.  Quantised copy for the exact hull predicates (reading R7): grid
-    // 2^(e - 19) with 2^e above the largest component of the contract vectors
-    // (float32 input: kept in the Q rows between the two loops)
-    T emax = 0;
+    // hulls.  Quantised copy for the exact hull predicates: q = rint(dr 2^(19 - e))
+    // (half to even) on the FP64 contract vectors dr, 2^(e-1) <= max |dr_c| < 2^e
+    if constexpr (F64) {
+      T emax = 0;
 #pragma unroll 1
-    for (int t = 0; t < PTM_KNN; t++) {
-      if (t >= cnt) continue;
-      T xj, yj, zj;
-      int idj;
-      load_atom<F64>(d, sm.NID(t), xj, yj, zj, idj);
-      int a0, a1, a2;
-      img_unpack(sm.IMG(t), a0, a1, a2);
-      T sx, sy, sz;
-      contract_shift<F64>(d, a0, a1, a2, sx, sy, sz);
-      T cx = contract_dr(xj, xi, sx), cy = contract_dr(yj, yi, sy), cz = contract_dr(zj, zi, sz);
-      emax = fmax(emax, fmax(fabs(cx), fmax(fabs(cy), fabs(cz))));
-      if constexpr (!F64) { sm.Q(t, 0) = cx; sm.Q(t, 1) = cy; sm.Q(t, 2) = cz; }
-      if constexpr (P64) {
-        double hx, hy, hz;
-        shift_f64(d, a0, a1, a2, hx, hy, hz);
-        ex[t] = ((double)xj - (double)xi) + hx;
-        ey[t] = ((double)yj - (double)yi) + hy;
-        ez[t] = ((double)zj - (double)zi) + hz;
+      for (int t = 0; t < PTM_KNN; t++) {
+        if (t >= cnt) continue;
+        T xj, yj, zj;
+        int idj;
+        load_atom<F64>(d, sm.NID(t), xj, yj, zj, idj);
+        int a0, a1, a2;
+        img_unpack(sm.IMG(t), a0, a1, a2);
+        T sx, sy, sz;
+        contract_shift<F64>(d, a0, a1, a2, sx, sy, sz);
+        T cx = contract_dr(xj, xi, sx), cy = contract_dr(yj, yi, sy), cz = contract_dr(zj, zi, sz);
+        emax = fmax(emax, fmax(fabs(cx), fmax(fabs(cy), fabs(cz))));
+        if constexpr (P64) { ex[t] = cx; ey[t] = cy; ez[t] = cz; }
       }
-    }
-    int e;
-    if constexpr (F64) frexp(emax, &e); else frexpf(emax, &e);
-    const T sc = F64 ? (T)ldexp(1.0, PTM_QBITS - e) : (T)ldexpf(1.f, PTM_QBITS - e);
+      int e;
+      frexp(emax, &e);
+      const T sc = (T)ldexp(1.0, PTM_QBITS - e);
 #pragma unroll 1
-    for (int t = 0; t < PTM_KNN; t++) {
-      if (t >= cnt) continue;
-      if constexpr (F64) {
+      for (int t = 0; t < PTM_KNN; t++) {
+        if (t >= cnt) continue;
         T xj, yj, zj;
         int idj;
         load_atom<F64>(d, sm.NID(t), xj, yj, zj, idj);
@@ -932,8 +995,72 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
         T cx = contract_dr(xj, xi, sx), cy = contract_dr(yj, yi, sy), cz = contract_dr(zj, zi, sz);
         sm.Q(t, 0) = (float)__double2int_rn(cx * sc); sm.Q(t, 1) = (float)__double2int_rn(cy * sc);
         sm.Q(t, 2) = (float)__double2int_rn(cz * sc);
-      } else {
-        sm.Q(t, 0) = rintf(sm.Q(t, 0) * sc); sm.Q(t, 1) = rintf(sm.Q(t, 1) * sc); sm.Q(t, 2) = rintf(sm.Q(t, 2) * sc);
+      }
+    } else {
+      // float32 input: a neighbour in the same image whose FP32 difference is
+      // exact (the error-free sum leaves no remainder) has its FP64 vector in
+      // FP32 already and is kept in the Q rows between the two loops; the others
+      // (shifted images, inexact differences: bit t of `wide`) are evaluated in
+      // FP64 in both loops
+      float emaxf = 0.f;
+      int e64 = -100000;
+      uint32_t wide = 0;
+#pragma unroll 1
+      for (int t = 0; t < PTM_KNN; t++) {
+        if (t >= cnt) continue;
+        float xj, yj, zj;
+        int idj;
+        load_atom<false>(d, sm.NID(t), xj, yj, zj, idj);
+        int a0, a1, a2;
+        img_unpack(sm.IMG(t), a0, a1, a2);
+        float px, rx, py, ry, pz, rz;
+        two_sum(xj, -xi, px, rx); two_sum(yj, -yi, py, ry); two_sum(zj, -zi, pz, rz);
+        double cx = px, cy = py, cz = pz;
+        if ((a0 | a1 | a2) == 0 && rx == 0.f && ry == 0.f && rz == 0.f) {
+          sm.Q(t, 0) = px; sm.Q(t, 1) = py; sm.Q(t, 2) = pz;
+          emaxf = fmaxf(emaxf, fmaxf(fabsf(px), fmaxf(fabsf(py), fabsf(pz))));
+        } else {
+          wide |= 1u << t;
+          double hx, hy, hz;
+          shift_f64(d, a0, a1, a2, hx, hy, hz);
+          cx = contract_dr((double)xj, (double)xi, hx); cy = contract_dr((double)yj, (double)yi, hy);
+          cz = contract_dr((double)zj, (double)zi, hz);
+          const double m = fmax(fabs(cx), fmax(fabs(cy), fabs(cz)));
+          if (m > 0.0) { int et; frexp(m, &et); e64 = max(e64, et); }
+        }
+        if constexpr (P64) {
+          if (!(wide >> t & 1)) {
+            double hx, hy, hz;
+            shift_f64(d, a0, a1, a2, hx, hy, hz);
+            cx = contract_dr((double)xj, (double)xi, hx); cy = contract_dr((double)yj, (double)yi, hy);
+            cz = contract_dr((double)zj, (double)zi, hz);
+          }
+          ex[t] = cx; ey[t] = cy; ez[t] = cz;
+        }
+      }
+      int e;
+      frexpf(emaxf, &e);
+      if (e64 > -100000) e = emaxf > 0.f ? max(e, e64) : e64;
+      const float sc = ldexpf(1.f, PTM_QBITS - e);
+      const double sc64 = ldexp(1.0, PTM_QBITS - e);
+#pragma unroll 1
+      for (int t = 0; t < PTM_KNN; t++) {
+        if (t >= cnt) continue;
+        if (!(wide >> t & 1)) {
+          sm.Q(t, 0) = rintf(sm.Q(t, 0) * sc); sm.Q(t, 1) = rintf(sm.Q(t, 1) * sc);
+          sm.Q(t, 2) = rintf(sm.Q(t, 2) * sc);
+          continue;
+        }
+        float xj, yj, zj;
+        int idj;
+        load_atom<false>(d, sm.NID(t), xj, yj, zj, idj);
+        int a0, a1, a2;
+        img_unpack(sm.IMG(t), a0, a1, a2);
+        double hx, hy, hz;
+        shift_f64(d, a0, a1, a2, hx, hy, hz);
+        sm.Q(t, 0) = (float)__double2int_rn(contract_dr((double)xj, (double)xi, hx) * sc64);
+        sm.Q(t, 1) = (float)__double2int_rn(contract_dr((double)yj, (double)yi, hy) * sc64);
+        sm.Q(t, 2) = (float)__double2int_rn(contract_dr((double)zj, (double)zi, hz) * sc64);
       }
     }
   }

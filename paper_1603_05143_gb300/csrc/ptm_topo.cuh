@@ -122,23 +122,27 @@ __device__ uint32_t topo_order(int m, const T *area, T mean2, int *o) {
 }
 
 // kNN slots in the topological scratch: rows J (sorted index) and IMG (packed
-// image); while ties are ordered the atom id sits in the first rows of the FP32
-// vectors, which are written only after the kNN.
+// image); while a run is ordered the atom id and the FP64 key sit in the rows
+// of the FP32 vectors (3 x 18 rows), which are written only after the kNN.
 struct TopoKnnRows {
   int *tsm;
   int t;
+  __device__ __forceinline__ int &row(int k) const { return tsm[k * PTM_BLOCK + t]; }
   __device__ __forceinline__ void put(int r, int j, int img) const {
-    tsm[r * PTM_BLOCK + t] = j;
-    tsm[(PTM_TOPO_N + r) * PTM_BLOCK + t] = img;
+    row(r) = j;
+    row(PTM_TOPO_N + r) = img;
   }
-  __device__ __forceinline__ void set(int r, int j, int img, int id) const {
+  __device__ __forceinline__ void set(int r, int j, int img, int id, double key) const {
     put(r, j, img);
-    ((float *)tsm)[(2 * PTM_TOPO_N + r) * PTM_BLOCK + t] = __int_as_float(id);
+    row(2 * PTM_TOPO_N + r) = id;
+    row(3 * PTM_TOPO_N + 2 * r) = __double2hiint(key);
+    row(3 * PTM_TOPO_N + 2 * r + 1) = __double2loint(key);
   }
-  __device__ __forceinline__ int j(int r) const { return tsm[r * PTM_BLOCK + t]; }
-  __device__ __forceinline__ int img(int r) const { return tsm[(PTM_TOPO_N + r) * PTM_BLOCK + t]; }
-  __device__ __forceinline__ int id(int r) const {
-    return __float_as_int(((float *)tsm)[(2 * PTM_TOPO_N + r) * PTM_BLOCK + t]);
+  __device__ __forceinline__ int j(int r) const { return row(r); }
+  __device__ __forceinline__ int img(int r) const { return row(PTM_TOPO_N + r); }
+  __device__ __forceinline__ int id(int r) const { return row(2 * PTM_TOPO_N + r); }
+  __device__ __forceinline__ double key(int r) const {
+    return __hiloint2double(row(3 * PTM_TOPO_N + 2 * r), row(3 * PTM_TOPO_N + 2 * r + 1));
   }
 };
 
@@ -177,10 +181,12 @@ __device__ void topo_atom(const FrameDesc &d, int s, int *tsm, int2 *__restrict_
 
   // ---- the 18 nearest images
   int m;
-  if (!wrapped && knn_fast_n<F64, PTM_TOPO_N>(d, s, xi, yi, zi, bx, by, bz, TopoKnnRows{tsm, t})) {
+  uint32_t close_runs = 0;
+  if (!wrapped && knn_fast_n<F64, PTM_TOPO_N>(d, s, xi, yi, zi, bx, by, bz, TopoKnnRows{tsm, t}, close_runs)) {
     m = PTM_TOPO_N;
+    if (!F64 && close_runs) count(d, C_KNN64);
   } else {
-    TI Ld2[PTM_TOPO_N];
+    double Ld2[PTM_TOPO_N];
     int Lid[PTM_TOPO_N], Ljs[PTM_TOPO_N], Limg[PTM_TOPO_N];
     m = knn<F64, PTM_TOPO_N>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, Ld2, Lid, Ljs, Limg);
     if (m < 0) m = 0;
@@ -280,7 +286,7 @@ __device__ void topo_atom64(const FrameDesc &d, int s, int i, const TopoSide *si
     const bool wrapped = d.dstat[0] != 0;
     int wix = 0, wiy = 0, wiz = 0;
     if (wrapped) img_unpack(__ldg(d.wrapv + s), wix, wiy, wiz);
-    TI Ld2[PTM_TOPO_N];
+    double Ld2[PTM_TOPO_N];
     int Lid[PTM_TOPO_N];
     m = knn<F64, PTM_TOPO_N>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, Ld2, Lid, jn, im);
     if (m < 0) m = 0;

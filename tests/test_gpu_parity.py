@@ -113,6 +113,46 @@ def test_atoms_outside_cell(ptm):
     assert np.array_equal(g0["structure"], g1["structure"])
 
 
+def test_atoms_outside_cell_float32(ptm):
+    """Unwrapped float32 positions take the general neighbour search, whose
+    FP32 filter must keep every candidate the FP64 order can pick."""
+    f = I.crystal("bcc", I.A_BCC_FE, 4, sigma=0.0, dtype=np.float64, rotation=I.random_rotation(I.rng_for(12)))
+    rng = I.rng_for(9)
+    shift = rng.integers(-2, 3, (f.n, 3)) @ f.cell
+    g = I.Frame((f.positions + shift).astype(np.float32), f.cell, f.pbc, None, "unwrapped32")
+    check(ptm, g)
+    assert ptm.stats()["knn_fp64"] == f.n
+
+
+@pytest.mark.parametrize("kind,a,reps", [("fcc", I.A_FCC_CU, 3), ("fcc", I.A_FCC_CU, 6), ("bcc", I.A_BCC_FE, 5),
+                                         ("hcp", I.A_HCP, (5, 3, 3)), ("sc", I.A_SC, 5), ("l12", I.A_L12, 4)])
+@pytest.mark.parametrize("sigma", [0.0, 1e-6])
+def test_float32_near_ties_follow_fp64(ptm, kind, a, reps, sigma):
+    """Perfect (or 1e-6 A noise) rotated float32 lattices: mirror-image
+    neighbours differ in distance only by the float32 rounding of the
+    positions, less than the float32 rounding of d^2, so the FP32 order is not
+    the FP64 order of the oracle (which also decides the SoS priorities and the
+    reported correspondence); every atom must still match it exactly."""
+    f = I.crystal(kind, a, reps, sigma=sigma, seed=4, dtype=np.float32, rotation=I.random_rotation(I.rng_for(31)))
+    check(ptm, f)
+    assert ptm.stats()["knn_fp64"] > 0
+
+
+@pytest.mark.parametrize("sigma", [0.0, 1e-7])
+def test_float32_near_ties_across_a_long_periodic_side(ptm, sigma):
+    """An fcc slab across the x = 0 side of a 1000 A box: neighbours reached
+    through the periodic image carry a 1000 A shift, whose float32 rounding
+    moves d^2 by about as much as the gaps between mirror-image neighbours, so
+    the FP32 error bound must account for the shift."""
+    c = I.crystal("fcc", I.A_FCC_CU, (8, 4, 4), sigma=sigma, seed=6, dtype=np.float64, wrap=False)
+    pos = c.positions - np.array([4 * I.A_FCC_CU, 0.0, 0.0])
+    cell = np.diag([1000.0, 4 * I.A_FCC_CU, 4 * I.A_FCC_CU])
+    pos[:, 0] = np.mod(pos[:, 0], 1000.0)
+    f = I.Frame(pos.astype(np.float32), cell, (True, True, True), None, "slab")
+    st, g, ref = check(ptm, f)
+    assert st["matched"] > f.n // 2
+
+
 @pytest.mark.parametrize("mask", [1, 2, 4, 8, 16, 6, 14, 30, 17])
 def test_template_masks(ptm, mask):
     f = I.crystal("fcc", I.A_FCC_CU, 4, sigma=0.25, seed=3, dtype=np.float32)
