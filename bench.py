@@ -1,13 +1,18 @@
 """Throughput of per-atom Polyhedral Template Matching on one GB300.
 
-Step = one ptm_classify_frame call over the 1,048,576-atom periodic fcc
-polycrystal (16 Voronoi grains, 4 stacking-fault slabs, sigma 0.15 A, float32
-positions, all five templates, species given so the alloy rules run): cell
-list, kNN, hulls, canonical codes, QCP, orientation, strain, alloy.  Inputs are
-resident in HBM; L2 (129 MB) is flushed by writing a 256 MB buffer before every
-timed step.
+Default step (--mode batch) = one replay of the CUDA graph that classifies 256
+uneven frames (1e3 to 1e6 atoms, 33.1 M atoms in all: fcc, hcp, bcc, L1_0,
+L1_2 and sc lattices with random orientation, noise sigma in [0, 0.25] A and
+affine strain up to 5 %, triclinic cells, float32 positions, all five
+templates, species given) in one persistent launch with autotuned tiling:
+cell lists, kNN, hulls, canonical codes, QCP, orientation, strain, alloy.
+Inputs are resident in HBM and larger than L2.  The same line reports the
+end-to-end rate through the serving API with host buffers, serving latency
+at 0.8 of capacity, the FP64 one-frame-per-launch form and the oracle on a
+seeded sample.  --mode frame times one large frame (the 2^20-atom polycrystal
+or the 2^22-atom mixed-phase frame), --mode serve the Poisson serving stream.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--mode batch|frame|serve]
 
 Prints one JSON line (rank 0).  N > 1 runs one independent replica per GPU
 (the method needs no exchange between frames), launched with torch.distributed.
@@ -30,7 +35,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "atoms classified/sec (5 templates + alloy)"
 UNIT = "atoms/s"
-SM_COUNT = 152
 FP32_LANES = 128
 SM_MAX_MHZ = 2070.0
 # Algorithmic FP32 work, counted from the kernel's arithmetic: per scored correspondence of
@@ -73,11 +77,14 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", default="frame", choices=["frame", "batch", "serve"],
-                    help="frame: the 2^20-atom polycrystal (default line); batch: 256 uneven frames in one "
-                         "persistent, graph-replayed launch; serve: a Poisson stream of mixed-phase frames "
-                         "through the continuous-batching server")
+    ap.add_argument("--mode", default="batch", choices=["frame", "batch", "serve"],
+                    help="batch (default line): 256 uneven frames in one persistent, graph-replayed launch; "
+                         "frame: one large frame; serve: a Poisson stream of mixed-phase frames through the "
+                         "continuous-batching server")
     ap.add_argument("--serve-requests", type=int, default=512, help="frames per offered load (serve mode)")
+    ap.add_argument("--frame-stride", type=int, default=1,
+                    help="batch mode: keep every k-th frame (smaller cases for profiler captures)")
+    ap.add_argument("--no-autotune", action="store_true", help="batch mode: library default tuning")
     ap.add_argument("--workload", default=WORKLOAD, choices=WORKLOADS, help="frame mode: which frame")
     ap.add_argument("--ordering", default="euclidean", choices=["euclidean", "topological"],
                     help="frame mode: neighbour ordering (Sec. 3, Eq. 5)")
@@ -253,28 +260,49 @@ def errors_vs_oracle(gpu, atoms, ref):
 
 
 def run_reference(args, world, rank, pg):
+    """The oracle, as it stands, on the host cores: each step a bounded seeded
+    sample of the same workload as the GPU arm's line (rank 0 only)."""
     if rank != 0:
         return
-    f, species, cfg = workload(args.workload)
     threads = os.cpu_count() or 1
     per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
-    for _ in range(args.warmup):
-        oracle_rate(f, species, per_step / 4, threads, ordering=args.ordering)
+    if args.mode == "frame":
+        f, species, cfg = workload(args.workload)
+        cfg = config_dict(cfg, {"ordering": args.ordering})
+
+        def sample(seconds, seed):
+            r, m, dt, th = oracle_rate(f, species, seconds, threads, seed=seed, ordering=args.ordering)
+            return r, m
+        what = "uniform seeded atom sample of the frame per step"
+    else:
+        from paper_1603_05143_gb300 import inputs as I
+        frames = I.config_batch()
+        cfg = {"workload": "batch-256-frames", "frames": len(frames), "atoms": sum(f.n for f in frames),
+               "templates": "SC,FCC,HCP,ICO,BCC", "species": "given"}
+        if args.mode == "serve":
+            cfg["note"] = "serve mode: the oracle is timed on the batched frames"
+
+        def sample(seconds, seed):
+            r, m, dt, th, _ = batch_oracle(frames, seconds, threads, seed=seed)
+            return r, m
+        what = "atoms drawn uniformly (seeded) from all 256 frames, per step"
+    for w in range(args.warmup):
+        sample(per_step / 4, 50 + w)
     rates, samples = [], 0
     t0 = time.perf_counter()
-    for s in range(args.steps):
-        r, m, dt, th = oracle_rate(f, species, per_step, threads, seed=100 + s, ordering=args.ordering)
+    for k in range(args.steps):
+        r, m = sample(per_step, 100 + k)
         rates.append(r)
         samples += m
     wall = time.perf_counter() - t0
     value = float(np.mean(rates))
+    cfg = config_dict(cfg, {"sample": what})
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_dict(cfg, {"sample": "uniform seeded atom sample per step",
-                                                             "ordering": args.ordering}),
+            "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{samples} atoms over {args.steps} steps, uniform seeded sample of the frame"},
+                             "sample": f"{samples} atoms over {args.steps} steps ({what})"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -392,7 +420,7 @@ def run_gpu(args, world, rank, local, pg):
              + FLOP_PER_MATCHED * s0["matched"] + FLOP_PER_ATOM * s0["atoms"])
     achieved = flops / (kms * 1e-3) / 1e12
     clocks = clk.summary()
-    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak = fp32_peak_tflops(local)
     peaks_file = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm_peak = json.load(open(peaks_file)).get("hbm_gbs") if os.path.exists(peaks_file) else None
     from paper_1603_05143_gb300 import measure_fma_peak
@@ -400,7 +428,7 @@ def run_gpu(args, world, rank, local, pg):
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": measured_traffic() if (args.workload == WORKLOAD and args.ordering == "euclidean") else None,
             "kernel": "k_atoms" if args.ordering == "euclidean" else "k_topo + k_atoms",
-            "kernel_ms": kms, "peak_note": "FP32 peak derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
+            "kernel_ms": kms, "peak_note": f"FP32 peak derived: {sm_count(local)} SMs x 128 lanes x 2 flop x 2070 MHz",
             "fma_measured": fma, "frac_of_measured_fma": achieved / fma["fp32_tflops"],
             "hbm_achieved_gbs": f.n * BYTES_PER_ATOM / (kms * 1e-3) / 1e9, "hbm_peak_gbs": hbm_peak}
     cpu, errors = None, None
@@ -429,22 +457,95 @@ def run_gpu(args, world, rank, local, pg):
     ptm.close()
 
 
+def sm_count(local):
+    import torch
+    return torch.cuda.get_device_properties(local).multi_processor_count
+
+
+def fp32_peak_tflops(local):
+    """Derived FP32 peak: SMs x 128 FP32 lanes x 2 flop x the maximum SM clock."""
+    return sm_count(local) * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def committed_counters(name):
+    """Per-atom counters of a kernel from a committed ncu capture
+    (profiles/<name>), or None when the kernel sources changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    csrc = os.path.join(ROOT, "paper_1603_05143_gb300", "csrc")
+    src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("ptm.cu", "ptm_kernels.cuh", "ptm_atom.cuh"))
+    if hashlib.sha256(src).hexdigest() != rec.get("source_sha256"):
+        return None
+    return rec
+
+
+def batch_oracle(frames, seconds, threads=None, seed=7):
+    """The oracle (as it stands) on a seeded uniform sample of all atoms of a
+    batch, sized to take about `seconds` on `threads` host cores (single-threaded
+    oracle calls on pieces of up to 32 sampled atoms of one frame, spread over a
+    thread pool).  Returns (atoms/s, sample size, seconds,
+    threads, [(frame, atom indices, oracle outputs)])."""
+    import concurrent.futures as cf
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    sizes = np.array([f.n for f in frames])
+    first = np.concatenate([[0], np.cumsum(sizes)])
+    rng = np.random.default_rng(seed)
+    handles = {}
+
+    def one(k, atoms):
+        f = frames[k]
+        return int(k), atoms, handles[k].classify(atoms, species=f.species, threads=1)
+
+    def run(m):
+        g = np.sort(rng.choice(int(first[-1]), m, replace=False))
+        fi = np.searchsorted(first, g, side="right") - 1
+        for k in np.unique(fi):
+            if k not in handles:
+                handles[k] = oracle.Frame(frames[k].positions, frames[k].cell, frames[k].pbc)
+        t = time.perf_counter()
+        pieces = []
+        for k in np.unique(fi):
+            a = g[fi == k] - first[k]
+            pieces += [(k, a[i:i + 32]) for i in range(0, len(a), 32)]
+        with cf.ThreadPoolExecutor(threads) as ex:
+            out = list(ex.map(lambda p: one(*p), pieces))
+        return out, time.perf_counter() - t
+    _, dt = run(4 * threads)
+    m = int(max(8 * threads, seconds / max(dt / (4 * threads), 1e-9)))
+    out, dt = run(m)
+    return m / dt, m, dt, threads, out
+
+
+def batch_errors(gout, samples):
+    """errors_vs_oracle over a batch sample: the per-frame samples merged."""
+    keys = ("structure", "alloy", "rmsd", "scale", "quat", "strain", "correspondence")
+    g = {k: np.concatenate([gout[fi][k][atoms] for fi, atoms, _ in samples]) for k in keys}
+    ref = {k: np.concatenate([r[k] for _, _, r in samples]) for k in ("structure", "alloy", "rmsd", "scale",
+                                                                     "quat", "strain", "corr")}
+    return errors_vs_oracle(g, np.arange(len(g["structure"])), ref)
+
+
 def run_batch(args, world, rank, local, pg):
     """256 uneven frames (lattices, orientations, noise, strain, triclinic cells)
     classified by one persistent launch replayed from a CUDA graph."""
     import torch
-    from paper_1603_05143_gb300 import PTM, build, inputs as I
+    from paper_1603_05143_gb300 import PTM, Server, build, inputs as I
+    from paper_1603_05143_gb300.binding import allocate_outputs, allocate_outputs_host
     build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    frames = I.config_batch()
+    frames = I.config_batch()[::args.frame_stride]
     ptm = PTM(local)
     devf = [{"positions": torch.from_numpy(f.positions).to(dev), "species": torch.from_numpy(f.species).to(dev),
              "cell": f.cell, "pbc": f.pbc} for f in frames]
     ntot = sum(f.n for f in frames)
     cache = os.path.join(os.path.expanduser("~"), ".cache", "ptm_gb300", "tuning.json")
     t0 = time.perf_counter()
-    tuning = ptm.autotune(devf, cache=cache)
+    tuning = None if args.no_autotune else ptm.autotune(devf, cache=cache)
     tune_s = time.perf_counter() - t0
     b = ptm.batch(devf, tuning=tuning)
     s = torch.cuda.Stream(dev)
@@ -460,6 +561,7 @@ def run_batch(args, world, rank, local, pg):
         times, kms = [], []
         if pg:
             pg.barrier()
+        torch.cuda.synchronize()
         with ClockSampler(local) as clk:
             for _ in range(args.steps):
                 e0 = torch.cuda.Event(enable_timing=True)
@@ -470,24 +572,133 @@ def run_batch(args, world, rank, local, pg):
                 e1.synchronize()
                 times.append(e0.elapsed_time(e1))
                 kms.append(b.stats()["atom_kernel_ms"])
-    ms = sum(times) / args.steps
+        torch.cuda.synchronize()
     if pg:
-        t = torch.tensor([ms], device=dev)
+        pg.barrier()
+    total = sum(times)
+    if pg:
+        t = torch.tensor([total], device=dev)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    if rank == 0:
-        line = {"metric": METRIC, "value": world * ntot / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": "batch-256-frames", "frames": len(frames), "atoms": ntot,
-                           "min_frame": min(f.n for f in frames), "max_frame": max(f.n for f in frames),
-                           "sigma_zero_frames": sum(1 for f in frames if f.meta["sigma"] == 0),
-                           "launch": "persistent queue kernel, CUDA graph replay", "tuning": tuning,
-                           "autotune_s": round(tune_s, 1), "l2": "inputs (530 MB) larger than L2"},
-                "kernel_ms": statistics.mean(kms), "clocks": clk.summary(),
-                "fallbacks": {k: st[k] for k in ("sos", "qcp_fp64", "tie_fp64", "knn_wide", "knn_fail", "internal")},
-                "matched": st["matched"]}
-        print(json.dumps(line), flush=True)
+        total = float(t.item())
+    ms = total / args.steps
+    value = world * ntot / (ms * 1e-3)
+    gout = [{k: v.cpu().numpy() for k, v in o.items()} for o in b.outputs]
+
+    # ---- end to end: the same frames from pinned host memory through the
+    # serving API (ptm_submit / ptm_wait), all queued at once; every step copies
+    # positions and species in and every output back
+    def pin(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    e2e, serving = None, None
+    if not args.no_e2e:
+        hpos = [pin(f.positions) for f in frames]
+        hsp = [pin(f.species) for f in frames]
+        houts = [allocate_outputs_host(f.n, pinned=True) for f in frames]
+        srv = Server(ptm, tuning=tuning)
+        allidx = np.arange(len(frames))
+        _drive(srv, frames, hpos, hsp, houts, np.zeros(len(frames)), allidx)        # warm-up
+        runs = [_drive(srv, frames, hpos, hsp, houts, np.zeros(len(frames)), allidx) for _ in range(args.steps)]
+        cap = float(np.median([r["achieved_atoms_per_s"] for r in runs]))
+        same = all(np.array_equal(houts[k]["structure"], gout[k]["structure"]) and
+                   np.array_equal(houts[k]["correspondence"], gout[k]["correspondence"]) for k in allidx)
+        e2e = {"value": world * cap, "unit": UNIT, "h2d_bytes_per_step": int(sum(a.nbytes for a in hpos + hsp)),
+               "d2h_bytes_per_step": int(sum(a.nbytes for o in houts for a in o.values())),
+               "api": "ptm_submit/ptm_wait (continuous-batching server), all frames queued at once, pinned "
+                      "host positions/species in, every output out", "steps": len(runs),
+               "outputs_equal_to_batch": same}
+        # serving latency: Poisson arrivals of the batch's frames at 0.8 of that capacity
+        rng = I.rng_for(2024)
+        mean_atoms = ntot / len(frames)
+        tms, idx = I.poisson_arrivals(rng, 256, 0.8 * cap / mean_atoms, len(frames))
+        r = _drive(srv, frames, hpos, hsp, houts, tms, idx)
+        serving = {"offered_load": 0.8, "offered_atoms_per_s": 0.8 * cap, **r}
+        srv.close()
+    # ---- the one-frame-per-launch FP64 form over the same frames (comparison)
+    fp64_form = None
+    if not args.no_fp64_form and rank == 0:
+        p64 = PTM(local, precision="fp64")
+        o64 = [allocate_outputs(f.n, dev) for f in frames]
+        cur = torch.cuda.current_stream(dev)
+
+        def fp64_pass():
+            for d, o in zip(devf, o64):
+                p64.classify(d["positions"], d["cell"], d["pbc"], species=d["species"], out=o)
+        fp64_pass()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        fp64_pass()
+        e1.record(cur)
+        e1.synchronize()
+        t64 = e0.elapsed_time(e1)
+        same = all(np.array_equal(o[k].cpu().numpy(), g[k]) for o, g in zip(o64, gout)
+                   for k in ("structure", "alloy", "correspondence"))
+        fp64_form = {"value": ntot / (t64 * 1e-3), "unit": UNIT, "ms": t64,
+                     "form": "every candidate and the winner's outputs in FP64, one ptm_classify_frame per frame",
+                     "structure_alloy_correspondence_equal_to_fp32_path": same}
+        p64.close()
+    if rank != 0:
+        b.close()
+        ptm.close()
+        return
+    # ---- roofline of the per-atom kernel
+    kms_mean = statistics.mean(kms)
+    clocks = clk.summary()
+    flops = (FLOP_PER_CAND_POINT * st["candidate_points"] + FLOP_PER_CAND * st["candidates"]
+             + FLOP_PER_MATCHED * st["matched"] + FLOP_PER_ATOM * st["atoms"])
+    achieved = flops / (kms_mean * 1e-3) / 1e12
+    peak = fp32_peak_tflops(local)
+    peaks_file = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm_peak = json.load(open(peaks_file)).get("hbm_gbs") if os.path.exists(peaks_file) else None
+    from paper_1603_05143_gb300 import measure_fma_peak
+    fma = {"fp32_tflops": measure_fma_peak("fp32", local) / 1e12, "fp64_tflops": measure_fma_peak("fp64", local) / 1e12}
+    cnt = committed_counters("k_atoms_batch_counters.json")
+    issue = None
+    if cnt:
+        nsmsp = 4 * sm_count(local)
+        inst = cnt["warp_inst_per_atom"] * ntot
+        mhz = clocks.get("sm_mhz") or SM_MAX_MHZ
+        issue = {"warp_inst_per_launch": inst, "warp_inst_per_atom": cnt["warp_inst_per_atom"],
+                 "lanes_per_inst": cnt.get("thread_inst_per_inst"),
+                 "frac": inst / (nsmsp * mhz * 1e6 * kms_mean * 1e-3),
+                 "frac_at_max_clock": inst / (nsmsp * SM_MAX_MHZ * 1e6 * kms_mean * 1e-3),
+                 "clock_mhz": mhz, "source": cnt["source"]}
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": cnt["dram_bytes_per_atom"] * ntot if cnt else None,
+            "kernel": "k_atoms_batch", "kernel_ms": kms_mean,
+            "peak_note": f"FP32 peak derived: {sm_count(local)} SMs x 128 lanes x 2 flop x 2070 MHz",
+            "fma_measured": fma, "frac_of_measured_fma": achieved / fma["fp32_tflops"],
+            "issue": issue,
+            "hbm_achieved_gbs": ntot * BYTES_PER_ATOM / (kms_mean * 1e-3) / 1e9, "hbm_peak_gbs": hbm_peak}
+    cpu, errors = None, None
+    if not args.no_cpu_baseline and world == 1:
+        r, m, dt, th, samples = batch_oracle(frames, args.cpu_seconds)
+        cpu = {"value": r, "unit": UNIT, "cores": th, "kind": "oracle",
+               "sample": f"{m} atoms drawn uniformly (seeded) from all 256 frames, {dt:.1f} s"}
+        errors = batch_errors(gout, samples)
+    q = serving if serving else None
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch-256-frames" if args.frame_stride == 1 else
+                       f"batch-256-frames, every {args.frame_stride}th", "frames": len(frames), "atoms": ntot,
+                       "min_frame": min(f.n for f in frames), "max_frame": max(f.n for f in frames),
+                       "sigma_zero_frames": sum(1 for f in frames if f.meta["sigma"] == 0),
+                       "lattices": "fcc, hcp, bcc, L1_0, L1_2, sc; sigma U[0, 0.25] A; strain <= 5 %",
+                       "templates": "SC,FCC,HCP,ICO,BCC", "species": "given",
+                       "launch": "persistent queue kernel, CUDA graph replay", "tuning": tuning,
+                       "autotune_s": round(tune_s, 1), "l2": "inputs (530 MB) larger than L2",
+                       "parallelism": f"replicas{world}"},
+            "latency_ms": {"p50": q["p50_ms"], "p99": q["p99_ms"], "what": "serving, Poisson arrivals of these "
+                           "frames at 0.8 of the end-to-end capacity, submit to completion"} if q else None,
+            "serving": serving, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "errors_vs_oracle": errors, "fp64_form": fp64_form,
+            "gpu_launches": 6 * args.steps,
+            "fallbacks": {k: st[k] for k in ("sos", "qcp_fp64", "tie_fp64", "knn_fp64", "knn_wide", "knn_fail",
+                                             "internal")},
+            "matched": st["matched"], "candidates_per_atom": st["candidates"] / st["atoms"]}
+    print(json.dumps(line), flush=True)
     b.close()
     ptm.close()
 

@@ -44,10 +44,13 @@ struct ptm_context {
   float *o_rmsd = nullptr, *o_scale = nullptr, *o_quat = nullptr, *o_strain = nullptr;
   int32_t *o_corr = nullptr;
   float *o_vm = nullptr, *o_rf = nullptr;
-  // topological order of every atom's 14 neighbours (k_topo -> k_atoms)
-  int2 *topo = nullptr;
-  int *topo_list = nullptr;        // atoms for the FP64 pass; [n] = their count
-  TopoSide *topo_side = nullptr;   // what the FP32 pass keeps for the FP64 pass
+  // every atom's 14 neighbours (k_knn or k_topo -> k_atoms)
+  int2 *nbr = nullptr;
+  size_t cap_nbr = 0;
+  // topological order: atoms for the FP64 pass ([n] = their count) and what
+  // the FP32 pass keeps for it
+  int *topo_list = nullptr;
+  TopoSide *topo_side = nullptr;
   size_t cap_topo = 0;
 };
 
@@ -149,6 +152,7 @@ static ptm_status setup_frame(const ptm_frame *f, double cell_factor, FrameDesc 
   desc->n = n;
   for (int c = 0; c < 3; c++) { desc->nb[c] = nb[c]; desc->pbc[c] = f->pbc[c] ? 1 : 0; }
   desc->f64 = f->pos_dtype == PTM_F64;
+  desc->ordering = f->ordering;
   desc->mask = f->template_mask ? (f->template_mask & PTM_MASK_ALL) : PTM_MASK_ALL;
   desc->rmsd_max = std::isnan(f->rmsd_max) ? INFINITY : (float)f->rmsd_max;
   desc->min_cell_width = (float)std::min(W[0] / nb[0], std::min(W[1] / nb[1], W[2] / nb[2]));
@@ -200,15 +204,19 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
   rs = grow(ctx, (size_t)n, ncell, f64);
   if (rs != PTM_OK) return rs;
   const bool topological = f->ordering == PTM_ORDER_TOPOLOGICAL;
+  if ((size_t)n > ctx->cap_nbr) {
+    cudaFree(ctx->nbr);
+    ctx->nbr = nullptr;
+    ctx->cap_nbr = 0;
+    CK(cudaMalloc(&ctx->nbr, (size_t)n * PTM_KNN * sizeof(int2)));
+    ctx->cap_nbr = (size_t)n;
+  }
   if (topological && (size_t)n > ctx->cap_topo) {
-    cudaFree(ctx->topo);
     cudaFree(ctx->topo_list);
     cudaFree(ctx->topo_side);
-    ctx->topo = nullptr;
     ctx->topo_list = nullptr;
     ctx->topo_side = nullptr;
     ctx->cap_topo = 0;
-    CK(cudaMalloc(&ctx->topo, (size_t)n * PTM_KNN * sizeof(int2)));
     CK(cudaMalloc(&ctx->topo_list, ((size_t)n + 1) * sizeof(int)));
     CK(cudaMalloc(&ctx->topo_side, topo_side_bytes((size_t)n)));
     ctx->cap_topo = (size_t)n;
@@ -220,6 +228,7 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
   set_outputs(&desc, o);
   desc.dstat = ctx->dstat;
   desc.counters = ctx->counters;
+  desc.nbr = ctx->nbr;
 
   cudaGetLastError();   // launch errors are read below; drop any left by earlier calls
   CK(cudaEventRecord(ctx->ev[0], st));
@@ -239,8 +248,11 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
                                ctx->cell_start, ctx->sorted, ctx->sbin, ctx->wrapv);
   const unsigned ga = (unsigned)((n + PTM_BLOCK - 1) / PTM_BLOCK);
   CK(cudaEventRecord(ctx->ev[1], st));
-  if (topological) {
-    desc.topo = ctx->topo;
+  if (!topological) {
+    const unsigned gk = (unsigned)((n + PTM_KNN_BLOCK - 1) / PTM_KNN_BLOCK);
+    if (f64) k_knn<true><<<gk, PTM_KNN_BLOCK, knn_smem_bytes(), st>>>(desc);
+    else k_knn<false><<<gk, PTM_KNN_BLOCK, knn_smem_bytes(), st>>>(desc);
+  } else {
     int *cnt = ctx->topo_list + ctx->cap_topo;
     CK(cudaMemsetAsync(cnt, 0, sizeof(int), st));
     int sms = 0;
@@ -248,14 +260,14 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
     const int cap_side = (int)topo_side_cap(ctx->cap_topo);
     const unsigned g64 = (unsigned)(PTM_TOPO64_BLOCKS_PER_SM * sms);
     if (f64) {
-      k_topo<true><<<ga, PTM_BLOCK, topo_smem_bytes(), st>>>(desc, ctx->topo, ctx->topo_list, cnt, ctx->topo_side,
+      k_topo<true><<<ga, PTM_BLOCK, topo_smem_bytes(), st>>>(desc, ctx->nbr, ctx->topo_list, cnt, ctx->topo_side,
                                                              cap_side);
-      k_topo64<true><<<g64, PTM_BLOCK, topo64_smem_bytes(), st>>>(desc, ctx->topo, ctx->topo_list, cnt,
+      k_topo64<true><<<g64, PTM_BLOCK, topo64_smem_bytes(), st>>>(desc, ctx->nbr, ctx->topo_list, cnt,
                                                                   ctx->topo_side, cap_side);
     } else {
-      k_topo<false><<<ga, PTM_BLOCK, topo_smem_bytes(), st>>>(desc, ctx->topo, ctx->topo_list, cnt, ctx->topo_side,
+      k_topo<false><<<ga, PTM_BLOCK, topo_smem_bytes(), st>>>(desc, ctx->nbr, ctx->topo_list, cnt, ctx->topo_side,
                                                               cap_side);
-      k_topo64<false><<<g64, PTM_BLOCK, topo64_smem_bytes(), st>>>(desc, ctx->topo, ctx->topo_list, cnt,
+      k_topo64<false><<<g64, PTM_BLOCK, topo64_smem_bytes(), st>>>(desc, ctx->nbr, ctx->topo_list, cnt,
                                                                    ctx->topo_side, cap_side);
     }
   }
@@ -323,7 +335,9 @@ ptm_status ptm_create(const ptm_options *opt, ptm_context **out) {
                          (const void *)k_atoms_batch<true>, (const void *)k_topo<false>, (const void *)k_topo<true>,
                          (const void *)k_topo_batch<false>, (const void *)k_topo_batch<true>,
                          (const void *)k_topo64<false>, (const void *)k_topo64<true>,
-                         (const void *)k_topo64_batch<false>, (const void *)k_topo64_batch<true>};
+                         (const void *)k_topo64_batch<false>, (const void *)k_topo64_batch<true>,
+                         (const void *)k_knn<false>, (const void *)k_knn<true>, (const void *)k_knn_batch<false>,
+                         (const void *)k_knn_batch<true>};
     for (const void *fn : fns) {
       if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess ||
           (e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -349,7 +363,7 @@ ptm_status ptm_destroy(ptm_context *ctx) {
   cudaFree(ctx->hpos); cudaFree(ctx->hspecies);
   cudaFree(ctx->o_struct); cudaFree(ctx->o_alloy); cudaFree(ctx->o_rmsd); cudaFree(ctx->o_scale);
   cudaFree(ctx->o_quat); cudaFree(ctx->o_strain); cudaFree(ctx->o_corr); cudaFree(ctx->o_vm); cudaFree(ctx->o_rf);
-  cudaFree(ctx->topo);
+  cudaFree(ctx->nbr);
   cudaFree(ctx->topo_list);
   cudaFree(ctx->topo_side);
   delete ctx;
@@ -472,7 +486,7 @@ struct ptm_batch {
   cudaGraphExec_t exec = nullptr;
   int nsm = 152;
   int topo = 0;                   // some frame takes the topological order
-  int2 *topo_buf = nullptr;       // per-frame segments of neighbour orders
+  int2 *nbr_buf = nullptr;        // per-frame segments of neighbour lists
   int *topo_list = nullptr;       // atoms for the FP64 pass; [ntotal] = their count
   TopoSide *topo_side = nullptr;  // what the FP32 pass keeps for the FP64 pass
   void *block = nullptr;          // the workspace (one allocation, or a pool block when served)
@@ -513,6 +527,13 @@ static ptm_status batch_enqueue(ptm_batch *b, cudaStream_t st) {
   k_scatter_batch<<<gb, tb, 0, st>>>(b->d_bp, b->d_atom_off, b->nframes, b->ntotal, b->atom_cell, b->atom_rank,
                                      b->atom_wrap, b->cell_start, b->sorted, b->sbin, b->wrapv);
   CK(cudaEventRecordWithFlags(b->ev[1], st, rec));
+  if (b->topo != 2) {           // some frame takes the Euclidean order
+    const unsigned gk = (unsigned)((b->ntotal + PTM_KNN_BLOCK - 1) / PTM_KNN_BLOCK);
+    if (b->f64)
+      k_knn_batch<true><<<gk, PTM_KNN_BLOCK, knn_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes, b->ntotal);
+    else
+      k_knn_batch<false><<<gk, PTM_KNN_BLOCK, knn_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes, b->ntotal);
+  }
   if (b->topo) {
     int *cnt = b->topo_list + b->ntotal;
     CK(cudaMemsetAsync(cnt, 0, sizeof(int), st));
@@ -555,7 +576,8 @@ struct BatchPlan {
   int64_t ntotal = 0;
   size_t ncell = 0;
   int f64 = 0;
-  int topo = 0;                      // some frame asks for the topological order
+  int topo = 0;                      // 0: no frame, 1: some, 2: every frame in the topological order
+  int ntopo = 0;
   std::vector<int> ordering;
 };
 
@@ -575,11 +597,12 @@ static ptm_status batch_plan(int nframes, const ptm_frame *frames, double cell_f
     P.hb[f].cell_off = (int)P.ncell;
     P.hd[f].atom_offset = P.ntotal;
     P.ordering[f] = frames[f].ordering;
-    P.topo |= frames[f].ordering == PTM_ORDER_TOPOLOGICAL;
+    P.ntopo += frames[f].ordering == PTM_ORDER_TOPOLOGICAL;
     P.ntotal += frames[f].n_atoms;
     P.ncell += nc;
     if (P.ntotal >= (1ll << 31) || P.ncell >= (1ull << 31)) return PTM_ERR_INVALID_ARG;
   }
+  P.topo = P.ntopo == 0 ? 0 : (P.ntopo == nframes ? 2 : 1);
   return PTM_OK;
 }
 
@@ -587,7 +610,7 @@ static ptm_status batch_plan(int nframes, const ptm_frame *frames, double cell_f
 static size_t batch_workspace_bytes(int nframes, int64_t ntotal, size_t ncell, int f64, int topo) {
   const size_t n = (size_t)ntotal, rec = f64 ? sizeof(Atom64) : sizeof(float4);
   const size_t nblk = (ncell + 1 + 2 * SCAN_BLOCK - 1) / (2 * SCAN_BLOCK) + 1;
-  const size_t tb = topo ? sizeof(int2) * PTM_KNN * n + 4 * (n + 1) + topo_side_bytes(n) + 3 * 256 : 0;
+  const size_t tb = sizeof(int2) * PTM_KNN * n + 256 + (topo ? 4 * (n + 1) + topo_side_bytes(n) + 2 * 256 : 0);
   return (sizeof(FrameDesc) + sizeof(BinParams) + sizeof(int64_t) + 16) * nframes + rec * n + 20 * n +
          8 * (ncell + 1) + 4 * nblk + 4 + 8 + 8 * C_NCOUNTERS + 16 * 256 + tb;
 }
@@ -611,14 +634,14 @@ static void batch_layout(ptm_batch *b, unsigned char *base, BatchPlan &P, const 
   b->block_sums = (int *)take(4 * nblk); b->scan_total = (int *)take(4);
   b->queue = (unsigned long long *)take(8); b->counters = (unsigned long long *)take(8 * C_NCOUNTERS);
   b->topo = P.topo;
+  b->nbr_buf = (int2 *)take(sizeof(int2) * PTM_KNN * n);
   if (P.topo) {
-    b->topo_buf = (int2 *)take(sizeof(int2) * PTM_KNN * n);
     b->topo_list = (int *)take(4 * (n + 1));
     b->topo_side = (TopoSide *)take(topo_side_bytes(n));
   }
   for (int f = 0; f < nf; f++) {
-    // frame f's topological order: rows of n_f entries from slot 14 x (first slot)
-    P.hd[f].topo = P.ordering[f] == PTM_ORDER_TOPOLOGICAL ? b->topo_buf + PTM_KNN * P.off[f] : nullptr;
+    // frame f's neighbour list: rows of n_f entries from slot 14 x (first slot)
+    P.hd[f].nbr = b->nbr_buf + PTM_KNN * P.off[f];
     P.hd[f].sorted = b->sorted;
     P.hd[f].sbin = b->sbin;
     P.hd[f].cell_start = b->cell_start + P.hb[f].cell_off;
@@ -797,7 +820,8 @@ struct NoallocLayout {                  // byte offsets inside the static array
   static constexpr size_t cell_count = atom_wrap + sizeof(int) * kNoallocAtoms;
   static constexpr size_t cell_start = cell_count + sizeof(int) * (kNoallocCells + 1);
   static constexpr size_t block_sums = cell_start + sizeof(int) * (kNoallocCells + 1);
-  static constexpr size_t dstat = block_sums + sizeof(int) * kNoallocScanBlocks;
+  static constexpr size_t nbr = (block_sums + sizeof(int) * kNoallocScanBlocks + 15) / 16 * 16;
+  static constexpr size_t dstat = nbr + sizeof(int2) * PTM_KNN * kNoallocAtoms;
   static constexpr size_t counters = ((dstat + sizeof(int) * 8) + 7) / 8 * 8;
   static constexpr size_t total = counters + sizeof(unsigned long long) * C_NCOUNTERS;
 };
@@ -875,6 +899,7 @@ extern "C" ptm_status ptm_classify_frame_noalloc(const ptm_frame *f, const ptm_o
   int *block_sums = (int *)(base + NoallocLayout::block_sums), *dstat = (int *)(base + NoallocLayout::dstat);
   unsigned long long *counters = (unsigned long long *)(base + NoallocLayout::counters);
   desc.sorted = sorted; desc.sbin = sbin; desc.cell_start = cell_start; desc.wrapv = wrapv;
+  desc.nbr = (int2 *)(base + NoallocLayout::nbr);
   set_outputs(&desc, o);
   desc.dstat = dstat;
   desc.counters = counters;
@@ -895,6 +920,9 @@ extern "C" ptm_status ptm_classify_frame_noalloc(const ptm_frame *f, const ptm_o
   k_scan_sums<<<1, SCAN_BLOCK, 0, st>>>(block_sums, nblk, dstat + 2);
   k_scan_add<<<(nscan + 255) / 256, 256, 0, st>>>(cell_start, block_sums, nscan);
   k_scatter<<<gb, tb, 0, st>>>(f->positions, f64, n, atom_cell, atom_rank, atom_wrap, cell_start, sorted, sbin, wrapv);
+  const unsigned gk = (unsigned)((n + PTM_KNN_BLOCK - 1) / PTM_KNN_BLOCK);
+  if (f64) k_knn<true><<<gk, PTM_KNN_BLOCK, knn_smem_bytes(), st>>>(desc);
+  else k_knn<false><<<gk, PTM_KNN_BLOCK, knn_smem_bytes(), st>>>(desc);
   const unsigned ga = (unsigned)((n + PTM_BLOCK - 1) / PTM_BLOCK);
   if (f64) k_atoms<true><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
   else k_atoms<false><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);

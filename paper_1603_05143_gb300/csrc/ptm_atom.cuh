@@ -60,8 +60,10 @@ struct FrameDesc {
   int32_t *corr;
   float *vm;                   // derived: von Mises shear strain
   float *rf;                   // derived: Rodrigues-Frank vector
-  const int2 *topo;            // topological order: [t][n] (sorted slot, image) of neighbour t by
-                               // frame-local slot (s - atom_offset), or NULL for the Euclidean order
+  const int2 *nbr;             // neighbour list: [t][n] (sorted slot, image) of neighbour t of the
+                               // atom at frame-local slot s - atom_offset (slot -1: none), written
+                               // by k_knn (Euclidean order) or k_topo (topological order)
+  int ordering;                // PTM_ORDER_EUCLIDEAN or PTM_ORDER_TOPOLOGICAL
   int *dstat;                  // [0] any atom wrapped, [1] overshoot (float bits, Angstrom)
   unsigned long long *counters;  // the C_* counters below
   int64_t atom_offset;         // first sorted slot of this frame (0 for a single frame)

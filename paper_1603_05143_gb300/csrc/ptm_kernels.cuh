@@ -6,7 +6,11 @@
 //   k_bin      fractional coordinates, cell of each atom (cell list)
 //   k_scan_*   exclusive scan of the cell counts
 //   k_scatter  atoms copied into cell order as float4 (x, y, z, id)
-//   k_atoms    one thread per atom: kNN .. outputs
+//   k_knn      one thread per atom: its 14 nearest images, as a neighbour list
+//              (k_topo in ptm_topo.cuh instead for the topological order)
+//   k_atoms    one thread per atom: hulls, codes, QCP .. outputs
+// The neighbour search and the rest run as separate kernels so that the warps
+// of an SM share one phase of the method and its code.
 #pragma once
 #include "ptm_atom.cuh"
 #include "../../include/ptm.h"
@@ -202,20 +206,6 @@ __device__ __noinline__ int knn(const FrameDesc &d, int s, typename RT<F64>::T x
   return -1;
 }
 
-// General kNN writing its result like knn_fast: sorted index of neighbour t in
-// scratch row NID(t), its packed image in row IMG(t).
-template <bool F64>
-__device__ __noinline__ int knn_to_scratch(const FrameDesc &d, const Scratch &sm, int s, typename RT<F64>::T xi,
-                                           typename RT<F64>::T yi, typename RT<F64>::T zi, int bx, int by, int bz,
-                                           int wix, int wiy, int wiz, bool wrapped) {
-  double Ld2[PTM_KNN];
-  int Lid[PTM_KNN], Ljs[PTM_KNN], Limg[PTM_KNN];
-  const int cnt = knn<F64>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, Ld2, Lid, Ljs, Limg);
-#pragma unroll
-  for (int t = 0; t < PTM_KNN; t++) { sm.NID(t) = Ljs[t]; sm.IMG(t) = Limg[t]; }
-  return cnt;
-}
-
 // Fast kNN for the common case (27 cells suffice).  Pass 1 keeps the NK + 1
 // smallest distances in the input precision with a min/max network.  Slots t
 // and t + 1 are "close" when those values could order their candidates
@@ -255,10 +245,13 @@ __device__ __forceinline__ bool knn_fast_n(const FrameDesc &d, int s, typename R
     const bool shifted = (d.pbc[0] && (bx == 0 || bx >= d.nb[0] - 1)) ||
                          (d.pbc[1] && (by == 0 || by >= d.nb[1] - 1)) ||
                          (d.pbc[2] && (bz == 0 || bz >= d.nb[2] - 1));
-    const float S = shifted ? d.smax : 0.f;
+    // one band for every gap: twice the bound at the largest kept value
+    // (knn_err grows with v), without the shift term for an unshifted atom
+    const float vmax = 1.01f * L[NK];
+    const float band = shifted ? 2.f * knn_err(vmax, d.smax) : 2.f * 8.5f * 5.9604645e-8f * vmax;
 #pragma unroll
-    for (int t = 0; t < NK; t++) close |= (uint32_t)(L[t + 1] - L[t] <= 2.f * knn_err(L[t + 1], S)) << t;
-    if (close >> (NK - 1) & 1) limit = L[NK - 1] + 2.f * knn_err(1.01f * L[NK - 1], S);
+    for (int t = 0; t < NK; t++) close |= (uint32_t)(L[t + 1] - L[t] <= band) << t;
+    if (close >> (NK - 1) & 1) limit = L[NK - 1] + band;
   }
   if (!search_complete(d, 1, (float)limit)) return false;
   close_runs = close;
@@ -300,31 +293,67 @@ __device__ __forceinline__ bool knn_fast_n(const FrameDesc &d, int s, typename R
   return true;
 }
 
-// kNN slots in the scratch rows NID (sorted index) and IMG (packed image); while
-// a run is ordered the atom id sits in row Q(r, 0) and the FP64 key in rows
-// Q(r, 1), Q(r, 2) (free until the neighbour vectors are written).
-struct ScratchKnnRows {
-  const Scratch &sm;
-  __device__ __forceinline__ void put(int r, int j, int img) const { sm.NID(r) = j; sm.IMG(r) = img; }
+// kNN slots in per-thread shared-memory rows ([row][thread], stride B): row r
+// the sorted slot, row NK + r the packed image; while a run is ordered, row
+// 2 NK + r the atom id and rows 3 NK + 2 r, 3 NK + 2 r + 1 the FP64 key.
+template <int NK, int B>
+struct SmemKnnRows {
+  int *base;
+  int t;
+  static constexpr int kRows = 5 * NK;
+  __device__ __forceinline__ int &row(int k) const { return base[k * B + t]; }
+  __device__ __forceinline__ void put(int r, int j, int img) const {
+    row(r) = j;
+    row(NK + r) = img;
+  }
   __device__ __forceinline__ void set(int r, int j, int img, int id, double key) const {
     put(r, j, img);
-    sm.Q(r, 0) = __int_as_float(id);
-    sm.Q(r, 1) = __int_as_float(__double2hiint(key));
-    sm.Q(r, 2) = __int_as_float(__double2loint(key));
+    row(2 * NK + r) = id;
+    row(3 * NK + 2 * r) = __double2hiint(key);
+    row(3 * NK + 2 * r + 1) = __double2loint(key);
   }
-  __device__ __forceinline__ int j(int r) const { return sm.NID(r); }
-  __device__ __forceinline__ int img(int r) const { return sm.IMG(r); }
-  __device__ __forceinline__ int id(int r) const { return __float_as_int(sm.Q(r, 0)); }
+  __device__ __forceinline__ int j(int r) const { return row(r); }
+  __device__ __forceinline__ int img(int r) const { return row(NK + r); }
+  __device__ __forceinline__ int id(int r) const { return row(2 * NK + r); }
   __device__ __forceinline__ double key(int r) const {
-    return __hiloint2double(__float_as_int(sm.Q(r, 1)), __float_as_int(sm.Q(r, 2)));
+    return __hiloint2double(row(3 * NK + 2 * r), row(3 * NK + 2 * r + 1));
   }
 };
 
+#define PTM_KNN_BLOCK 128
+typedef SmemKnnRows<PTM_KNN, PTM_KNN_BLOCK> KnnRows;
+constexpr size_t knn_smem_bytes() { return (size_t)PTM_KNN_BLOCK * KnnRows::kRows * 4; }
+
+// The 14 nearest images of the atom at sorted slot s (Sec. 3, Table 1), written
+// to its neighbour list: fast search when 27 cells suffice, else the general
+// one.  A search that fails leaves an empty list (the atom stays unmatched).
 template <bool F64>
-__device__ __forceinline__ bool knn_fast(const FrameDesc &d, const Scratch &sm, int s, typename RT<F64>::T xi,
-                                         typename RT<F64>::T yi, typename RT<F64>::T zi, int bx, int by, int bz,
-                                         uint32_t &close_runs) {
-  return knn_fast_n<F64, PTM_KNN>(d, s, xi, yi, zi, bx, by, bz, ScratchKnnRows{sm}, close_runs);
+__device__ __forceinline__ void knn_atom(const FrameDesc &d, int s, int *smem_rows) {
+  typedef typename RT<F64>::T T;
+  T xi, yi, zi;
+  int idi;
+  load_atom<F64>(d, s, xi, yi, zi, idi);
+  const int b = __ldg(d.sbin + s);
+  const int bz = b % d.nb[2], byx = b / d.nb[2];
+  const int by = byx % d.nb[1], bx = byx / d.nb[1];
+  const bool wrapped = d.dstat[0] != 0;
+  const KnnRows rows{smem_rows, (int)threadIdx.x};
+  int2 *out = const_cast<int2 *>(d.nbr) + (s - d.atom_offset);
+  uint32_t close = 0;
+  if (!wrapped && knn_fast_n<F64, PTM_KNN>(d, s, xi, yi, zi, bx, by, bz, rows, close)) {
+    if (!F64 && close) count(d, C_KNN64);
+#pragma unroll
+    for (int t = 0; t < PTM_KNN; t++) out[(int64_t)t * d.n] = make_int2(rows.j(t), rows.img(t));
+    return;
+  }
+  int wix = 0, wiy = 0, wiz = 0;
+  if (wrapped) img_unpack(__ldg(d.wrapv + s), wix, wiy, wiz);
+  double Ld2[PTM_KNN];
+  int Lid[PTM_KNN], Ljs[PTM_KNN], Limg[PTM_KNN];
+  const int cnt = knn<F64>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, Ld2, Lid, Ljs, Limg);
+  if (!F64) count(d, C_KNN64);
+#pragma unroll
+  for (int t = 0; t < PTM_KNN; t++) out[(int64_t)t * d.n] = t < cnt ? make_int2(Ljs[t], Limg[t]) : make_int2(-1, 0);
 }
 
 // ---------------------------------------------------------- per-atom state
@@ -576,31 +605,22 @@ __device__ __forceinline__ void vec_fp64(const FrameDesc &d, typename RT<F64>::T
 
 // Rare path: the best FP32 candidates lie within PTM_BAND.  Every candidate is
 // re-scored in FP64 from neighbour vectors recomputed in FP64 from the input
-// positions.
+// positions (the neighbours read again from the atom's list).
 template <bool F64>
-__device__ __noinline__ int rerank_fp64(const FrameDesc &d, int s, const Best bst, int bx, int by, int bz,
-                                        int wix, int wiy, int wiz, bool wrapped) {
+__device__ __noinline__ int rerank_fp64(const FrameDesc &d, int s, const Best bst) {
   typedef typename RT<F64>::T T;
   T xi, yi, zi;
   int idi;
   load_atom<F64>(d, s, xi, yi, zi, idi);
-  double Ld2[PTM_KNN];
-  int Lid[PTM_KNN], Ljs[PTM_KNN], Limg[PTM_KNN];
-  int cnt;
-  if (d.topo) {
-    cnt = 0;
-    for (int t = 0; t < PTM_KNN; t++) {
-      const int2 e = d.topo[(int64_t)t * d.n + (s - d.atom_offset)];
-      Ljs[t] = e.x;
-      Limg[t] = e.y;
-      cnt += e.x >= 0;
-    }
-  } else {
-    cnt = knn<F64>(d, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped, Ld2, Lid, Ljs, Limg);
-  }
-  if (cnt < 0) return -1;
   double ex[PTM_KNN], ey[PTM_KNN], ez[PTM_KNN];
-  for (int t = 0; t < cnt; t++) vec_fp64<F64>(d, xi, yi, zi, Ljs[t], Limg[t], ex[t], ey[t], ez[t]);
+  int cnt = 0;
+  for (int t = 0; t < PTM_KNN; t++) {
+    const int2 e = d.nbr[(int64_t)t * d.n + (s - d.atom_offset)];
+    if (e.x < 0) break;
+    vec_fp64<F64>(d, xi, yi, zi, e.x, e.y, ex[t], ey[t], ez[t]);
+    cnt++;
+  }
+  if (cnt == 0) return -1;
   return select_fp64(d, bst, ex, ey, ez, nullptr);
 }
 
@@ -918,6 +938,50 @@ __device__ __forceinline__ void metric_vectors(const FrameDesc &d, const Scratch
   }
 }
 
+// FP64 contract vector of neighbour (sorted slot js, packed image img) of an
+// atom at (xi, yi, zi), float32 positions.
+__device__ __forceinline__ void vec64_row(const FrameDesc &d, float xi, float yi, float zi, int js, int img,
+                                          double (&v)[3]) {
+  float xj, yj, zj;
+  int idj;
+  load_atom<false>(d, js, xj, yj, zj, idj);
+  int a0, a1, a2;
+  img_unpack(img, a0, a1, a2);
+  double hx, hy, hz;
+  shift_f64(d, a0, a1, a2, hx, hy, hz);
+  v[0] = contract_dr((double)xj, (double)xi, hx);
+  v[1] = contract_dr((double)yj, (double)yi, hy);
+  v[2] = contract_dr((double)zj, (double)zi, hz);
+}
+
+// Quantisation of the neighbours in `wide` (float32 input, rare): the frexp
+// exponent of their largest FP64 vector component (-100000 if all are zero),
+// then q = rint(dr 2^shift) into the Q rows.  Rows are per-thread columns of
+// shared memory with stride PTM_BLOCK.
+__device__ __noinline__ int wide_exponent(const FrameDesc &d, float xi, float yi, float zi, const int *nid,
+                                          const int *img, uint32_t wide) {
+  int e64 = -100000;
+  for (; wide; wide &= wide - 1) {
+    const int t = __ffs(wide) - 1;
+    double v[3];
+    vec64_row(d, xi, yi, zi, nid[t * PTM_BLOCK], img[t * PTM_BLOCK], v);
+    const double m = fmax(fabs(v[0]), fmax(fabs(v[1]), fabs(v[2])));
+    if (m > 0.0) { int et; frexp(m, &et); e64 = max(e64, et); }
+  }
+  return e64;
+}
+
+__device__ __noinline__ void wide_quantise(const FrameDesc &d, float xi, float yi, float zi, const int *nid,
+                                           const int *img, float *q, uint32_t wide, int shift) {
+  const double sc = ldexp(1.0, shift);
+  for (; wide; wide &= wide - 1) {
+    const int t = __ffs(wide) - 1;
+    double v[3];
+    vec64_row(d, xi, yi, zi, nid[t * PTM_BLOCK], img[t * PTM_BLOCK], v);
+    for (int c = 0; c < 3; c++) q[(3 * t + c) * PTM_BLOCK] = (float)__double2int_rn(v[c] * sc);
+  }
+}
+
 // ------------------------------------------------------------ one atom
 // P64 selects the FP64 form: the same exact predicates, Weinberg codes and
 // lookup, then every candidate scored and the winner's outputs computed in FP64
@@ -931,32 +995,18 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
   T xi, yi, zi;
   int idi;
   load_atom<F64>(d, s, xi, yi, zi, idi);
-  const int b = __ldg(d.sbin + s);
-  const int bz = b % d.nb[2], byx = b / d.nb[2];
-  const int by = byx % d.nb[1], bx = byx / d.nb[1];
-  const bool wrapped = d.dstat[0] != 0;
-  int wix = 0, wiy = 0, wiz = 0;
-  if (wrapped) img_unpack(__ldg(d.wrapv + s), wix, wiy, wiz);
   count(d, C_ATOMS);
 
-  // ---- neighbours (Sec. 3)
-  int cnt;
+  // ---- neighbours (Sec. 3): the list written by k_knn or k_topo
+  int cnt = 0;
   unsigned hmask;
   {
-    if (d.topo) {                       // neighbours in topological order (Eq. 5), from k_topo
-      cnt = 0;
-      for (int t = 0; t < PTM_KNN; t++) {
-        const int2 e = d.topo[(int64_t)t * d.n + (s - d.atom_offset)];
-        sm.NID(t) = e.x;
-        sm.IMG(t) = e.y;
-        cnt += e.x >= 0;
-      }
-    } else if (uint32_t close_runs = 0; !wrapped && knn_fast<F64>(d, sm, s, xi, yi, zi, bx, by, bz, close_runs)) {
-      cnt = PTM_KNN;
-      if (!F64 && close_runs) count(d, C_KNN64);
-    } else {
-      cnt = knn_to_scratch<F64>(d, sm, s, xi, yi, zi, bx, by, bz, wix, wiy, wiz, wrapped);
-      if (!F64) count(d, C_KNN64);
+#pragma unroll 1
+    for (int t = 0; t < PTM_KNN; t++) {
+      const int2 e = __ldg(d.nbr + (int64_t)t * d.n + (s - d.atom_offset));
+      sm.NID(t) = e.x;
+      sm.IMG(t) = e.y;
+      cnt += e.x >= 0;
     }
     hmask = __ballot_sync(live, cnt >= 4);       // lanes that go on to the hulls
     if (cnt < 4) { write_unmatched(d, idi); return; }
@@ -997,13 +1047,12 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
         sm.Q(t, 2) = (float)__double2int_rn(cz * sc);
       }
     } else {
-      // float32 input: a neighbour in the same image whose FP32 difference is
-      // exact (the error-free sum leaves no remainder) has its FP64 vector in
-      // FP32 already and is kept in the Q rows between the two loops; the others
-      // (shifted images, inexact differences: bit t of `wide`) are evaluated in
-      // FP64 in both loops
+      // float32 input: a neighbour in the same image whose FP32 differences
+      // are exact (Sterbenz: |x_j - x_i| below min(|x_i|, |x_j|)) has its FP64
+      // vector in FP32 already, kept in the Q rows between the two loops; the
+      // others (bit t of `wide`: shifted images, atoms near a coordinate plane
+      // through the origin) are evaluated in FP64 out of line
       float emaxf = 0.f;
-      int e64 = -100000;
       uint32_t wide = 0;
 #pragma unroll 1
       for (int t = 0; t < PTM_KNN; t++) {
@@ -1011,56 +1060,34 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
         float xj, yj, zj;
         int idj;
         load_atom<false>(d, sm.NID(t), xj, yj, zj, idj);
-        int a0, a1, a2;
-        img_unpack(sm.IMG(t), a0, a1, a2);
-        float px, rx, py, ry, pz, rz;
-        two_sum(xj, -xi, px, rx); two_sum(yj, -yi, py, ry); two_sum(zj, -zi, pz, rz);
-        double cx = px, cy = py, cz = pz;
-        if ((a0 | a1 | a2) == 0 && rx == 0.f && ry == 0.f && rz == 0.f) {
-          sm.Q(t, 0) = px; sm.Q(t, 1) = py; sm.Q(t, 2) = pz;
-          emaxf = fmaxf(emaxf, fmaxf(fabsf(px), fmaxf(fabsf(py), fabsf(pz))));
-        } else {
-          wide |= 1u << t;
-          double hx, hy, hz;
-          shift_f64(d, a0, a1, a2, hx, hy, hz);
-          cx = contract_dr((double)xj, (double)xi, hx); cy = contract_dr((double)yj, (double)yi, hy);
-          cz = contract_dr((double)zj, (double)zi, hz);
-          const double m = fmax(fabs(cx), fmax(fabs(cy), fabs(cz)));
-          if (m > 0.0) { int et; frexp(m, &et); e64 = max(e64, et); }
-        }
-        if constexpr (P64) {
-          if (!(wide >> t & 1)) {
-            double hx, hy, hz;
-            shift_f64(d, a0, a1, a2, hx, hy, hz);
-            cx = contract_dr((double)xj, (double)xi, hx); cy = contract_dr((double)yj, (double)yi, hy);
-            cz = contract_dr((double)zj, (double)zi, hz);
-          }
-          ex[t] = cx; ey[t] = cy; ez[t] = cz;
-        }
+        const float px = __fsub_rn(xj, xi), py = __fsub_rn(yj, yi), pz = __fsub_rn(zj, zi);
+        const bool exact = sm.IMG(t) == img_pack(0, 0, 0) && fabsf(px) < fminf(fabsf(xi), fabsf(xj)) &&
+                           fabsf(py) < fminf(fabsf(yi), fabsf(yj)) && fabsf(pz) < fminf(fabsf(zi), fabsf(zj));
+        sm.Q(t, 0) = px; sm.Q(t, 1) = py; sm.Q(t, 2) = pz;
+        if (exact) emaxf = fmaxf(emaxf, fmaxf(fabsf(px), fmaxf(fabsf(py), fabsf(pz))));
+        else wide |= 1u << t;
       }
       int e;
       frexpf(emaxf, &e);
-      if (e64 > -100000) e = emaxf > 0.f ? max(e, e64) : e64;
+      if (wide) {
+        const int e64 = wide_exponent(d, xi, yi, zi, sm.nid + sm.t, sm.img + sm.t, wide);
+        if (e64 > -100000) e = emaxf > 0.f ? max(e, e64) : e64;
+      }
       const float sc = ldexpf(1.f, PTM_QBITS - e);
-      const double sc64 = ldexp(1.0, PTM_QBITS - e);
 #pragma unroll 1
       for (int t = 0; t < PTM_KNN; t++) {
-        if (t >= cnt) continue;
-        if (!(wide >> t & 1)) {
-          sm.Q(t, 0) = rintf(sm.Q(t, 0) * sc); sm.Q(t, 1) = rintf(sm.Q(t, 1) * sc);
-          sm.Q(t, 2) = rintf(sm.Q(t, 2) * sc);
-          continue;
+        if (t >= cnt || (wide >> t & 1)) continue;
+        sm.Q(t, 0) = rintf(sm.Q(t, 0) * sc); sm.Q(t, 1) = rintf(sm.Q(t, 1) * sc); sm.Q(t, 2) = rintf(sm.Q(t, 2) * sc);
+      }
+      if (wide) wide_quantise(d, xi, yi, zi, sm.nid + sm.t, sm.img + sm.t, sm.q + sm.t, wide, PTM_QBITS - e);
+      if constexpr (P64) {
+#pragma unroll 1
+        for (int t = 0; t < PTM_KNN; t++) {
+          if (t >= cnt) continue;
+          double v[3];
+          vec64_row(d, xi, yi, zi, sm.nid[t * PTM_BLOCK + sm.t], sm.img[t * PTM_BLOCK + sm.t], v);
+          ex[t] = v[0]; ey[t] = v[1]; ez[t] = v[2];
         }
-        float xj, yj, zj;
-        int idj;
-        load_atom<false>(d, sm.NID(t), xj, yj, zj, idj);
-        int a0, a1, a2;
-        img_unpack(sm.IMG(t), a0, a1, a2);
-        double hx, hy, hz;
-        shift_f64(d, a0, a1, a2, hx, hy, hz);
-        sm.Q(t, 0) = (float)__double2int_rn(contract_dr((double)xj, (double)xi, hx) * sc64);
-        sm.Q(t, 1) = (float)__double2int_rn(contract_dr((double)yj, (double)yi, hy) * sc64);
-        sm.Q(t, 2) = (float)__double2int_rn(contract_dr((double)zj, (double)zi, hz) * sc64);
       }
     }
   }
@@ -1116,7 +1143,7 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
   }
   if (bst.b2 <= bst.b1 + PTM_BAND) {
     count(d, C_TIE64);
-    const int w = rerank_fp64<F64>(d, s, bst, bx, by, bz, wix, wiy, wiz, wrapped);
+    const int w = rerank_fp64<F64>(d, s, bst);
     if (w >= 0) { bst.K = w >> 16; bst.cand = w & 0xffff; }
   }
   finalize(d, sm, tplw, bst, idi);
@@ -1361,6 +1388,29 @@ __global__ void __launch_bounds__(PTM_BLOCK, PTM_ATOM_BLOCKS_PER_SM) k_atoms(con
   const unsigned live = __ballot_sync(0xffffffffu, s < d.n);
   if (s >= d.n) return;
   classify_atom<F64, P64>(d, (int)s, sm, tplw, live);
+}
+
+// Neighbour lists of one frame (Euclidean order), one thread per atom.
+template <bool F64>
+__global__ void __launch_bounds__(PTM_KNN_BLOCK) k_knn(const __grid_constant__ FrameDesc d) {
+  extern __shared__ __align__(16) int knn_smem[];
+  const int64_t s = (int64_t)blockIdx.x * PTM_KNN_BLOCK + threadIdx.x;
+  if (s >= d.n) return;
+  knn_atom<F64>(d, (int)s, knn_smem);
+}
+
+// The same over a batch: each slot finds its frame; frames in the topological
+// order are left to k_topo_batch.
+template <bool F64>
+__global__ void __launch_bounds__(PTM_KNN_BLOCK)
+    k_knn_batch(const FrameDesc *__restrict__ descs, const int64_t *__restrict__ atom_off, int nframes,
+                int64_t ntotal) {
+  extern __shared__ __align__(16) int knn_smem[];
+  const int64_t s = (int64_t)blockIdx.x * PTM_KNN_BLOCK + threadIdx.x;
+  if (s >= ntotal) return;
+  const FrameDesc &d = descs[frame_of(atom_off, nframes, s)];
+  if (d.ordering != PTM_ORDER_EUCLIDEAN) return;
+  knn_atom<F64>(d, (int)s, knn_smem);
 }
 
 // Persistent classification of a batch: every warp pulls tiles of tile_atoms

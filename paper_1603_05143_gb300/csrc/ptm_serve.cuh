@@ -76,7 +76,8 @@ size_t request_bytes(const ptm_frame &f) {
   const size_t n = (size_t)f.n_atoms;
   const size_t pos = n * 3 * (f.pos_dtype == PTM_F64 ? 8 : 4);
   const size_t ws = n * (f.pos_dtype == PTM_F64 ? 32 : 16) + 20 * n + 8 * (4 * n + 64) + sizeof(FrameDesc) + 4096 +
-                    (f.ordering == PTM_ORDER_TOPOLOGICAL ? n * (8 * PTM_KNN + 4) + topo_side_bytes(n) + 1024 : 0);
+                    n * 8 * PTM_KNN + 256 +
+                    (f.ordering == PTM_ORDER_TOPOLOGICAL ? n * 4 + topo_side_bytes(n) + 1024 : 0);
   return pos + n + n * kOutBytesPerAtom + ws;
 }
 

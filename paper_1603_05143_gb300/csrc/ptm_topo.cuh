@@ -122,29 +122,10 @@ __device__ uint32_t topo_order(int m, const T *area, T mean2, int *o) {
 }
 
 // kNN slots in the topological scratch: rows J (sorted index) and IMG (packed
-// image); while a run is ordered the atom id and the FP64 key sit in the rows
-// of the FP32 vectors (3 x 18 rows), which are written only after the kNN.
-struct TopoKnnRows {
-  int *tsm;
-  int t;
-  __device__ __forceinline__ int &row(int k) const { return tsm[k * PTM_BLOCK + t]; }
-  __device__ __forceinline__ void put(int r, int j, int img) const {
-    row(r) = j;
-    row(PTM_TOPO_N + r) = img;
-  }
-  __device__ __forceinline__ void set(int r, int j, int img, int id, double key) const {
-    put(r, j, img);
-    row(2 * PTM_TOPO_N + r) = id;
-    row(3 * PTM_TOPO_N + 2 * r) = __double2hiint(key);
-    row(3 * PTM_TOPO_N + 2 * r + 1) = __double2loint(key);
-  }
-  __device__ __forceinline__ int j(int r) const { return row(r); }
-  __device__ __forceinline__ int img(int r) const { return row(PTM_TOPO_N + r); }
-  __device__ __forceinline__ int id(int r) const { return row(2 * PTM_TOPO_N + r); }
-  __device__ __forceinline__ double key(int r) const {
-    return __hiloint2double(row(3 * PTM_TOPO_N + 2 * r), row(3 * PTM_TOPO_N + 2 * r + 1));
-  }
-};
+// image), then (while a run is ordered) the atom id and FP64 key in the rows of
+// the FP32 vectors (3 x 18 rows), which are written only after the kNN.
+typedef SmemKnnRows<PTM_TOPO_N, PTM_BLOCK> TopoKnnRows;
+static_assert(TopoKnnRows::kRows <= 5 * PTM_TOPO_N, "kNN rows must fit the neighbour and vector rows");
 
 // What the FP32 pass leaves for the FP64 pass about a listed atom: its 18
 // neighbours, their FP32 face areas and the faces to recompute in FP64 (bit =
@@ -352,8 +333,8 @@ __global__ void __launch_bounds__(PTM_BLOCK)
   const int64_t s = (int64_t)blockIdx.x * PTM_BLOCK + threadIdx.x;
   if (s >= ntotal) return;
   const FrameDesc &d = descs[frame_of(atom_off, nframes, s)];
-  if (!d.topo) return;
-  topo_atom<F64>(d, (int)s, (int *)tsm_raw, const_cast<int2 *>(d.topo), list, list_count, side, cap_side);
+  if (d.ordering != PTM_ORDER_TOPOLOGICAL) return;
+  topo_atom<F64>(d, (int)s, (int *)tsm_raw, const_cast<int2 *>(d.nbr), list, list_count, side, cap_side);
 }
 
 template <bool F64>
@@ -369,7 +350,7 @@ __global__ void __launch_bounds__(PTM_BLOCK)
     if (i < cnt) {
       const int s = list[i];
       const FrameDesc &d = descs[frame_of(atom_off, nframes, s)];
-      topo_atom64<F64>(d, s, i, side, cap_side, P, Q, const_cast<int2 *>(d.topo), wmask);
+      topo_atom64<F64>(d, s, i, side, cap_side, P, Q, const_cast<int2 *>(d.nbr), wmask);
     }
   }
 }

@@ -4,8 +4,11 @@ allocating one (GPU only).
 ptm_classify_frame_noalloc serves callers that cannot let a library call
 cudaMalloc (applications that own all device memory, or in-situ analysis
 inside a running simulation).  It keeps its workspace in a static device
-array, so this test runs it twice in a row on different frames: leftovers of
-the first call must not leak into the second.  The file sorts last so that a
+array, so this test runs it three times in a row on different frames: a small
+float32 frame with atoms outside the cell (which sets the array's wrap and
+overshoot words), a larger float64 frame, then a smaller float32 frame with
+another cell grid and every atom inside the cell.  Leftovers of one call must
+not leak into the next, including beyond the extent of a smaller frame.  The file sorts last so that a
 run stopping at the first failure has already run every other test.
 """
 import ctypes as C
@@ -47,10 +50,15 @@ def test_noalloc_matches_allocating_entry_point():
     lib = binding.load()
     ptm = binding.PTM(0)
     stream = torch.cuda.current_stream()
-    frames = [I.crystal("l12", I.A_L12, 6, sigma=0.1, seed=3, dtype=np.float32,
-                        rotation=I.random_rotation(I.rng_for(1))),
-              I.crystal("bcc", I.A_BCC_FE, 9, sigma=0.15, seed=4, dtype=np.float64)]
-    for frame in frames:                      # two calls in a row, different frames
+    first = I.crystal("l12", I.A_L12, 6, sigma=0.1, seed=3, dtype=np.float64,
+                      rotation=I.random_rotation(I.rng_for(1)))
+    shift = I.rng_for(2).integers(-1, 2, (first.n, 3)) @ first.cell          # unwrapped positions
+    first = I.Frame((first.positions + shift).astype(np.float32), first.cell, first.pbc, first.species, "unwrapped")
+    frames = [first,
+              I.crystal("bcc", I.A_BCC_FE, 9, sigma=0.15, seed=4, dtype=np.float64),
+              I.crystal("fcc", I.A_FCC_CU, (3, 4, 5), sigma=0.05, seed=5, dtype=np.float32,
+                        rotation=I.random_rotation(I.rng_for(6)))]
+    for frame in frames:                      # three calls in a row, different frames
         f, keep = _device_frame(binding, frame, torch)
         ref = ptm.classify(keep[0], frame.cell, frame.pbc, species=keep[1])
         out, o = _outputs(binding, frame.n, torch)
