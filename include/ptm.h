@@ -135,11 +135,14 @@ typedef struct {
   int64_t candidates;        /* correspondences scored by QCP (symmetry-reduced, Appendix A) */
   int64_t candidate_points;  /* sum over those correspondences of the point count N = k + 1 */
   double pipeline_ms;        /* device time of the whole call (cell list + classification) */
-  double atom_kernel_ms;     /* device time of the per-atom kernels (ordering + classification) */
+  double atom_kernel_ms;     /* device time of the per-atom kernels (neighbour lists +
+                                classification) */
   int64_t topo_fp64;         /* atoms whose topological order was decided in FP64 (an area
                                 gap at the edge of the equal-area band) */
   int64_t knn_fp64;          /* float32 input: atoms whose neighbour order needed FP64
                                 distances (two candidates within the FP32 error bound) */
+  double classify_kernel_ms; /* device time of the classification kernel alone (hulls, codes,
+                                QCP, outputs), after the neighbour lists */
 } ptm_stats;
 
 /* Create a context on options->device (NULL options: device 0, default budget).
@@ -218,7 +221,7 @@ ptm_status ptm_batch_destroy(ptm_batch *batch);
 /* Time every candidate tuning on this batch (cell_factor in {1.125, 1.25,
    1.4}, tile_atoms in {32, 64}, blocks_per_sm in {6, 7}) and return the
    fastest in *best.  Runs the batch (every m-th frame of it when it holds more
-   than about 4 M atoms) 36 times; outputs are written with the same results
+   than about 40 M atoms) 36 times; outputs are written with the same results
    each time. */
 ptm_status ptm_autotune_batch(ptm_context *ctx, int n_frames, const ptm_frame *frames,
                               const ptm_outputs *outs, void *stream, ptm_tuning *best);

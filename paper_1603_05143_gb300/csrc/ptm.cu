@@ -35,7 +35,7 @@ struct ptm_context {
   int *dstat = nullptr;
   unsigned long long *counters = nullptr;
   cudaStream_t last_stream = nullptr;
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};   // call start, atom kernel start, end
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // call start, per-atom kernels start, end, k_atoms start
   // host-buffer entry point
   size_t cap_host_atoms = 0;
   void *hpos = nullptr;
@@ -271,6 +271,7 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
                                                                    ctx->topo_side, cap_side);
     }
   }
+  CK(cudaEventRecord(ctx->ev[3], st));
   if (ctx->precision == PTM_PREC_FP64) {
     if (f64) k_atoms<true, true><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
     else k_atoms<false, true><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
@@ -321,7 +322,7 @@ ptm_status ptm_create(const ptm_options *opt, ptm_context **out) {
     if ((e = cudaSetDevice(ctx->device)) != cudaSuccess) { rs = cuda_fail(ctx, e, "cudaSetDevice"); break; }
     if ((e = cudaMalloc(&ctx->dstat, 8 * sizeof(int))) != cudaSuccess) { rs = cuda_fail(ctx, e, "cudaMalloc"); break; }
     if ((e = cudaMalloc(&ctx->counters, C_NCOUNTERS * sizeof(unsigned long long))) != cudaSuccess) { rs = cuda_fail(ctx, e, "cudaMalloc"); break; }
-    for (int i = 0; i < 3 && e == cudaSuccess; i++) e = cudaEventCreate(&ctx->ev[i]);
+    for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaEventCreate(&ctx->ev[i]);
     if (e != cudaSuccess) { rs = cuda_fail(ctx, e, "cudaEventCreate"); break; }
     if ((e = cudaMemset(ctx->counters, 0, C_NCOUNTERS * sizeof(unsigned long long))) != cudaSuccess) { rs = cuda_fail(ctx, e, "cudaMemset"); break; }
     size_t fr = 0, tot = 0;
@@ -359,7 +360,7 @@ ptm_status ptm_destroy(ptm_context *ctx) {
   cudaFree(ctx->atom_cell); cudaFree(ctx->atom_rank); cudaFree(ctx->atom_wrap);
   cudaFree(ctx->cell_count); cudaFree(ctx->cell_start); cudaFree(ctx->block_sums);
   cudaFree(ctx->dstat); cudaFree(ctx->counters);
-  for (int i = 0; i < 3; i++) if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  for (int i = 0; i < 4; i++) if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   cudaFree(ctx->hpos); cudaFree(ctx->hspecies);
   cudaFree(ctx->o_struct); cudaFree(ctx->o_alloy); cudaFree(ctx->o_rmsd); cudaFree(ctx->o_scale);
   cudaFree(ctx->o_quat); cudaFree(ctx->o_strain); cudaFree(ctx->o_corr); cudaFree(ctx->o_vm); cudaFree(ctx->o_rf);
@@ -445,9 +446,12 @@ ptm_status ptm_get_stats(ptm_context *ctx, ptm_stats *out) {
   float t_all = 0.f, t_atom = 0.f;
   if (cudaEventElapsedTime(&t_all, ctx->ev[0], ctx->ev[2]) != cudaSuccess) t_all = -1.f;
   if (cudaEventElapsedTime(&t_atom, ctx->ev[1], ctx->ev[2]) != cudaSuccess) t_atom = -1.f;
+  float t_cls = -1.f;
+  if (cudaEventElapsedTime(&t_cls, ctx->ev[3], ctx->ev[2]) != cudaSuccess) t_cls = -1.f;
   cudaGetLastError();
   out->pipeline_ms = t_all;
   out->atom_kernel_ms = t_atom;
+  out->classify_kernel_ms = t_cls;
   out->candidates = (int64_t)c[C_CAND];
   out->candidate_points = (int64_t)c[C_CANDPTS];
   out->atoms = (int64_t)c[C_ATOMS];
@@ -481,7 +485,7 @@ struct ptm_batch {
   int *sbin = nullptr, *wrapv = nullptr, *atom_cell = nullptr, *atom_rank = nullptr, *atom_wrap = nullptr;
   int *cell_count = nullptr, *cell_start = nullptr, *block_sums = nullptr, *scan_total = nullptr;
   unsigned long long *queue = nullptr, *counters = nullptr;
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // as ptm_context::ev
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int nsm = 152;
@@ -498,7 +502,7 @@ static void batch_free(ptm_batch *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->owns_block) cudaFree(b->block);
-  for (int i = 0; i < 3; i++) if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+  for (int i = 0; i < 4; i++) if (b->ev[i]) cudaEventDestroy(b->ev[i]);
   delete b;
 }
 
@@ -552,6 +556,7 @@ static ptm_status batch_enqueue(ptm_batch *b, cudaStream_t st) {
                                                                          b->topo_list, cnt, b->topo_side, cap_side);
     }
   }
+  CK(cudaEventRecordWithFlags(b->ev[3], st, rec));
   // two warps per block, each pulling its own tiles
   const int64_t tiles = (b->ntotal + b->tile_atoms - 1) / b->tile_atoms;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->nsm * b->blocks_per_sm,
@@ -676,7 +681,7 @@ extern "C" ptm_status ptm_batch_create(ptm_context *ctx, int nframes, const ptm_
   b->ntotal = P.ntotal;
   b->ncell = P.ncell;
   cudaError_t e = cudaMalloc(&b->block, batch_workspace_bytes(nframes, P.ntotal, P.ncell, P.f64, P.topo));
-  for (int i = 0; i < 3 && e == cudaSuccess; i++) e = cudaEventCreate(&b->ev[i]);
+  for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaEventCreate(&b->ev[i]);
   if (e != cudaSuccess) { rs = cuda_fail(ctx, e, "ptm_batch_create"); batch_free(b); return rs; }
   batch_layout(b, (unsigned char *)b->block, P, outs);
   if ((e = cudaMemcpy(b->d_descs, P.hd.data(), sizeof(FrameDesc) * nframes, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -731,6 +736,9 @@ extern "C" ptm_status ptm_batch_stats(ptm_batch *b, ptm_stats *out) {
   float t_all = -1.f, t_atom = -1.f;
   if (cudaEventElapsedTime(&t_all, b->ev[0], b->ev[2]) != cudaSuccess) t_all = -1.f;
   if (cudaEventElapsedTime(&t_atom, b->ev[1], b->ev[2]) != cudaSuccess) t_atom = -1.f;
+  float t_cls = -1.f;
+  if (cudaEventElapsedTime(&t_cls, b->ev[3], b->ev[2]) != cudaSuccess) t_cls = -1.f;
+  out->classify_kernel_ms = t_cls;
   cudaGetLastError();
   out->atoms = (int64_t)c[C_ATOMS]; out->matched = (int64_t)c[C_MATCHED]; out->knn_wide = (int64_t)c[C_KNN_WIDE];
   out->knn_fail = (int64_t)c[C_KNN_FAIL]; out->sos = (int64_t)c[C_SOS]; out->qcp_fp64 = (int64_t)c[C_QCP64];
@@ -754,7 +762,7 @@ extern "C" ptm_status ptm_batch_destroy(ptm_batch *b) {
 
 // Autotuner: time every (cell size factor, queue tile, blocks per SM) candidate
 // on the caller's batch, or on every m-th frame of it when it holds more than
-// about 4 M atoms (one warm run, then the best of two timed runs), and return the
+// about 40 M atoms (one warm run, then the best of two timed runs), and return the
 // fastest.  Outputs are overwritten with identical results.
 extern "C" ptm_status ptm_autotune_batch(ptm_context *ctx, int nframes, const ptm_frame *frames,
                                          const ptm_outputs *outs, void *stream, ptm_tuning *best) {
@@ -763,10 +771,12 @@ extern "C" ptm_status ptm_autotune_batch(ptm_context *ctx, int nframes, const pt
   static const int tiles[] = {32, 64};
   static const int bpsm[] = {PTM_ATOM_BLOCKS_PER_SM - 1, PTM_ATOM_BLOCKS_PER_SM};
   cudaStream_t st = (cudaStream_t)stream;
-  // tune on every m-th frame so that at most about 4 M atoms are timed per candidate
+  // tune on every m-th frame so that at most about 40 M atoms are timed per candidate (a
+  // strided subset of a mixed batch measured a different winner than the whole)
   int64_t total = 0;
   for (int f = 0; f < nframes; f++) total += frames[f].n_atoms;
-  const int stride = (int)std::max<int64_t>(1, (total + 4000000 - 1) / 4000000);
+  const int64_t cap = 40000000;
+  const int stride = (int)std::max<int64_t>(1, (total + cap - 1) / cap);
   std::vector<ptm_frame> fs;
   std::vector<ptm_outputs> os;
   for (int f = 0; f < nframes; f += stride) { fs.push_back(frames[f]); os.push_back(outs[f]); }

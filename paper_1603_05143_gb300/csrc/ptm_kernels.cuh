@@ -1322,8 +1322,15 @@ __global__ void k_bin_batch(const BinParams *__restrict__ bp, const int64_t *__r
   int wrap;
   float over;
   const int cell = p.cell_off + bin_atom(p, p.pos, i - p.atom_off, wrap, over);
-  if (wrap != img_pack(0, 0, 0)) p.dstat[0] = 1;
-  atomicMax(p.dstat + 1, __float_as_int(over));
+  // one atomic per frame per warp (over > 0, so its bits order as integers):
+  // per-atom atomics on a frame's single status word serialise at the L2
+  const unsigned same = __match_any_sync(__activemask(), f);
+  const int omax = __reduce_max_sync(same, __float_as_int(over));
+  const bool any_wrap = __any_sync(same, wrap != img_pack(0, 0, 0));
+  if ((threadIdx.x & 31) == __ffs(same) - 1) {
+    atomicMax(p.dstat + 1, omax);
+    if (any_wrap) p.dstat[0] = 1;
+  }
   atom_cell[i] = cell;
   atom_rank[i] = atomicAdd(cell_count + cell, 1);
   atom_wrap[i] = wrap;

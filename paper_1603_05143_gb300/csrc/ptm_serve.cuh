@@ -161,7 +161,7 @@ ptm_status launch_batch(ptm_server *S, std::vector<Request *> &rs, int slot, InF
   b->f64 = P.f64; b->ntotal = P.ntotal; b->ncell = P.ncell;
   F->ws_bytes = batch_workspace_bytes(nf, P.ntotal, P.ncell, P.f64, P.topo);
   e = S->pool.alloc(F->ws_bytes, &F->ws);
-  for (int i = 0; i < 3 && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(&b->ev[i], cudaEventDefault);
+  for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(&b->ev[i], cudaEventDefault);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&F->done, cudaEventDisableTiming);
   if (e != cudaSuccess) { batch_free(b); delete F; return cuda_fail(ctx, e, "serve: workspace"); }
   b->block = F->ws;
