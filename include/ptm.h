@@ -143,6 +143,8 @@ typedef struct {
                                 distances (two candidates within the FP32 error bound) */
   double classify_kernel_ms; /* device time of the classification kernel alone (hulls, codes,
                                 QCP, outputs), after the neighbour lists */
+  int64_t excluded;          /* atoms with a non-finite coordinate or more than 100 cell periods
+                                outside the cell: left unmatched and nobody's neighbour */
 } ptm_stats;
 
 /* Create a context on options->device (NULL options: device 0, default budget).
@@ -274,6 +276,17 @@ ptm_status ptm_release(ptm_server *server, uint64_t ticket);
 
 /* Finish all queued and running frames, then free the server. */
 ptm_status ptm_server_destroy(ptm_server *server);
+
+/* Host-side fault injection for tests of the serving path (the paper has no
+   counterpart; no GPU fault is involved).  PTM_FAULT_HOLD_NEXT: the scheduler
+   does not see the completion of the next batch it launches (a lost
+   completion) until PTM_FAULT_RELEASE_HELD or ptm_server_destroy; waits on its
+   tickets run into their timeouts while other batches complete.
+   PTM_FAULT_FAIL_NEXT: the next batch launched completes with PTM_ERR_CUDA, as
+   when its completion event reports an error (the server then keeps serving).
+   PTM_ERR_INVALID_ARG for another code. */
+enum { PTM_FAULT_HOLD_NEXT = 1, PTM_FAULT_RELEASE_HELD = 2, PTM_FAULT_FAIL_NEXT = 3 };
+ptm_status ptm_server_inject(ptm_server *server, int fault);
 
 /* Largest frame accepted by ptm_classify_frame_noalloc. */
 #define PTM_NOALLOC_MAX_ATOMS 32768

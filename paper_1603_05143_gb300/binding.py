@@ -38,7 +38,7 @@ class ptm_stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("atoms", "matched", "knn_wide", "knn_fail", "sos", "qcp_fp64",
                                          "tie_fp64", "internal", "candidates", "candidate_points")] + \
                [("pipeline_ms", C.c_double), ("atom_kernel_ms", C.c_double), ("topo_fp64", C.c_int64),
-                ("knn_fp64", C.c_int64), ("classify_kernel_ms", C.c_double)]
+                ("knn_fp64", C.c_int64), ("classify_kernel_ms", C.c_double), ("excluded", C.c_int64)]
 
 
 class ptm_tuning(C.Structure):
@@ -93,8 +93,9 @@ def load():
         L.ptm_ticket_info.argtypes = [P, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         L.ptm_release.argtypes = [P, C.c_uint64]
         L.ptm_server_destroy.argtypes = [P]
+        L.ptm_server_inject.argtypes = [P, C.c_int]
         for f in ("ptm_server_create", "ptm_submit", "ptm_poll", "ptm_wait", "ptm_ticket_info", "ptm_release",
-                  "ptm_server_destroy"):
+                  "ptm_server_destroy", "ptm_server_inject"):
             getattr(L, f).restype = C.c_int
         L.ptm_rmsd_histogram.argtypes = [P, C.c_int64, P, P, C.c_int, C.c_double, P, P]
         L.ptm_rmsd_histogram.restype = C.c_int
@@ -444,6 +445,15 @@ class Server:
     def release(self, ticket):
         self.lib.ptm_release(self.h, ticket)
         self._live.pop(ticket, None)
+
+    FAULTS = {"hold_next": 1, "release_held": 2, "fail_next": 3}
+
+    def inject(self, fault: str):
+        """Host-side fault injection (``ptm_server_inject``): "hold_next",
+        "release_held" or "fail_next"."""
+        rc = self.lib.ptm_server_inject(self.h, self.FAULTS[fault])
+        if rc:
+            raise PTMError(rc, "ptm_server_inject")
 
     def close(self):
         if getattr(self, "h", None):

@@ -229,6 +229,7 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
   desc.dstat = ctx->dstat;
   desc.counters = ctx->counters;
   desc.nbr = ctx->nbr;
+  bp.counters = ctx->counters;
 
   cudaGetLastError();   // launch errors are read below; drop any left by earlier calls
   CK(cudaEventRecord(ctx->ev[0], st));
@@ -463,6 +464,7 @@ ptm_status ptm_get_stats(ptm_context *ctx, ptm_stats *out) {
   out->tie_fp64 = (int64_t)c[C_TIE64];
   out->topo_fp64 = (int64_t)c[C_TOPO64];
   out->knn_fp64 = (int64_t)c[C_KNN64];
+  out->excluded = (int64_t)c[C_EXCLUDED];
   out->internal = (int64_t)c[C_INTERNAL];
   return PTM_OK;
 }
@@ -655,6 +657,7 @@ static void batch_layout(ptm_batch *b, unsigned char *base, BatchPlan &P, const 
     P.hd[f].dstat = b->d_dstat + 4 * f;
     P.hd[f].counters = b->counters;
     P.hb[f].dstat = b->d_dstat + 4 * f;
+    P.hb[f].counters = b->counters;
   }
 }
 
@@ -744,7 +747,7 @@ extern "C" ptm_status ptm_batch_stats(ptm_batch *b, ptm_stats *out) {
   out->knn_fail = (int64_t)c[C_KNN_FAIL]; out->sos = (int64_t)c[C_SOS]; out->qcp_fp64 = (int64_t)c[C_QCP64];
   out->tie_fp64 = (int64_t)c[C_TIE64];
   out->topo_fp64 = (int64_t)c[C_TOPO64]; out->internal = (int64_t)c[C_INTERNAL];
-  out->knn_fp64 = (int64_t)c[C_KNN64];
+  out->knn_fp64 = (int64_t)c[C_KNN64]; out->excluded = (int64_t)c[C_EXCLUDED];
   out->candidates = (int64_t)c[C_CAND]; out->candidate_points = (int64_t)c[C_CANDPTS];
   out->pipeline_ms = t_all;
   out->atom_kernel_ms = t_atom;
@@ -913,6 +916,7 @@ extern "C" ptm_status ptm_classify_frame_noalloc(const ptm_frame *f, const ptm_o
   set_outputs(&desc, o);
   desc.dstat = dstat;
   desc.counters = counters;
+  bp.counters = counters;
   cudaGetLastError();   // launch errors are read below; drop any left by earlier calls
   // the array keeps the previous call's contents: clear what must start at zero
   if (cudaMemsetAsync(cell_count, 0, (ncell + 1) * sizeof(int), st) != cudaSuccess ||

@@ -70,7 +70,7 @@ struct FrameDesc {
 };
 
 enum { C_ATOMS = 0, C_MATCHED, C_KNN_WIDE, C_KNN_FAIL, C_SOS, C_QCP64, C_TIE64, C_INTERNAL, C_CAND, C_CANDPTS, C_TOPO64,
-       C_KNN64, C_NCOUNTERS };
+       C_KNN64, C_EXCLUDED, C_NCOUNTERS };
 
 __device__ __forceinline__ void count(const FrameDesc &d, int which, unsigned long long v = 1) {
   atomicAdd(d.counters + which, v);
@@ -117,6 +117,11 @@ __device__ __forceinline__ uint64_t setnib(uint64_t x, int i, int v) {
 __device__ __forceinline__ int img_pack(int a, int b, int c) {
   return ((a + 128) << 16) | ((b + 128) << 8) | (c + 128);
 }
+// Packed wrap of an atom the binning excludes (non-finite coordinate, or more
+// than PTM_FAR_PERIODS periods from the cell): image (-128, -128, -128), which
+// no valid atom packs to.
+#define PTM_FAR_PERIODS 100.f
+#define PTM_EXCLUDED 0
 __device__ __forceinline__ void img_unpack(int p, int &a, int &b, int &c) {
   a = ((p >> 16) & 255) - 128; b = ((p >> 8) & 255) - 128; c = (p & 255) - 128;
 }

@@ -339,6 +339,11 @@ __device__ __forceinline__ void knn_atom(const FrameDesc &d, int s, int *smem_ro
   const bool wrapped = d.dstat[0] != 0;
   const KnnRows rows{smem_rows, (int)threadIdx.x};
   int2 *out = const_cast<int2 *>(d.nbr) + (s - d.atom_offset);
+  if (__ldg(d.wrapv + s) == PTM_EXCLUDED) {           // excluded by the binning: no neighbours
+#pragma unroll
+    for (int t = 0; t < PTM_KNN; t++) out[(int64_t)t * d.n] = make_int2(-1, 0);
+    return;
+  }
   uint32_t close = 0;
   if (!wrapped && knn_fast_n<F64, PTM_KNN>(d, s, xi, yi, zi, bx, by, bz, rows, close)) {
     if (!F64 && close) count(d, C_KNN64);
@@ -1160,28 +1165,34 @@ struct BinParams {
   // batches only: where this frame lives
   const void *pos;   // the frame's positions
   int *dstat;        // the frame's status words
+  unsigned long long *counters;   // the call's counters (excluded atoms)
   int64_t atom_off;  // first atom of the frame in the batch order
   int cell_off;      // first cell of the frame in the batch's cell array
 };
 
 #define PTM_WRAP_TOL 1e-4f
 
-__global__ void k_bin(const void *pos, BinParams p, int *cell_count, int *atom_cell, int *atom_rank,
-                      int *atom_wrap, int *dstat) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= p.n) return;
+// Cell of one atom of frame p (shared by the single-frame and batched
+// binning), its lattice wrap (packed image) and how far it lies outside the
+// cell (Angstrom, plus a rounding slack).  An atom with a non-finite
+// coordinate, or more than PTM_FAR_PERIODS periods from the cell, is excluded:
+// it gets the marker wrap PTM_EXCLUDED (no valid image packs to it), cell 0 and
+// no overshoot, so it is nobody's neighbour and is itself left unmatched.
+__device__ __forceinline__ int bin_atom(const BinParams &p, const void *pos, int64_t li, int &wrap, float &over) {
   float x, y, z;
   if (p.f64) {
-    const double *q = (const double *)pos + 3 * i;
+    const double *q = (const double *)pos + 3 * li;
     x = (float)q[0]; y = (float)q[1]; z = (float)q[2];
   } else {
-    const float *q = (const float *)pos + 3 * i;
+    const float *q = (const float *)pos + 3 * li;
     x = q[0]; y = q[1]; z = q[2];
   }
   int bc[3], w[3];
-  float over = 0.f;
+  over = 0.f;
+  bool ok = true;
   for (int c = 0; c < 3; c++) {
     float f = x * p.Hinv[c] + y * p.Hinv[3 + c] + z * p.Hinv[6 + c];
+    ok &= fabsf(f) < PTM_FAR_PERIODS;              // false for NaN and infinities too
     w[c] = 0;
     if (p.pbc[c] && (f < -PTM_WRAP_TOL || f >= 1.f + PTM_WRAP_TOL)) {
       w[c] = (int)floorf(f);
@@ -1191,14 +1202,30 @@ __global__ void k_bin(const void *pos, BinParams p, int *cell_count, int *atom_c
     int b = (int)floorf(f * (float)p.nb[c]);
     bc[c] = min(max(b, 0), p.nb[c] - 1);
   }
-  if (w[0] | w[1] | w[2]) dstat[0] = 1;
+  if (!ok) {
+    wrap = PTM_EXCLUDED;
+    over = 0.f;
+    return 0;
+  }
   // rounding of the fractional coordinates is covered by a small extra slack
   over = fmaxf(over, 0.f) + 1e-5f * fmaxf(p.W[0], fmaxf(p.W[1], p.W[2]));
-  atomicMax(dstat + 1, __float_as_int(over));
-  int cell = (bc[0] * p.nb[1] + bc[1]) * p.nb[2] + bc[2];
+  wrap = img_pack(w[0], w[1], w[2]);
+  return (bc[0] * p.nb[1] + bc[1]) * p.nb[2] + bc[2];
+}
+
+__global__ void k_bin(const void *pos, BinParams p, int *cell_count, int *atom_cell, int *atom_rank,
+                      int *atom_wrap, int *dstat) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p.n) return;
+  int wrap;
+  float over;
+  const int cell = bin_atom(p, pos, i, wrap, over);
+  if (wrap == PTM_EXCLUDED) atomicAdd(p.counters + C_EXCLUDED, 1ull);
+  else if (wrap != img_pack(0, 0, 0)) dstat[0] = 1;
+  atomicMax(dstat + 1, __float_as_int(over));      // uniform address: the compiler aggregates per warp
   atom_cell[i] = cell;
   atom_rank[i] = atomicAdd(cell_count + cell, 1);
-  atom_wrap[i] = img_pack(w[0], w[1], w[2]);
+  atom_wrap[i] = wrap;
 }
 
 #define SCAN_BLOCK 1024
@@ -1285,34 +1312,6 @@ __device__ __forceinline__ int frame_of(const int64_t *atom_off, int nframes, in
   return lo;
 }
 
-// Cell of one atom of frame p (shared by the single-frame and batched binning).
-__device__ __forceinline__ int bin_atom(const BinParams &p, const void *pos, int64_t li, int &wrap, float &over) {
-  float x, y, z;
-  if (p.f64) {
-    const double *q = (const double *)pos + 3 * li;
-    x = (float)q[0]; y = (float)q[1]; z = (float)q[2];
-  } else {
-    const float *q = (const float *)pos + 3 * li;
-    x = q[0]; y = q[1]; z = q[2];
-  }
-  int bc[3], w[3];
-  over = 0.f;
-  for (int c = 0; c < 3; c++) {
-    float f = x * p.Hinv[c] + y * p.Hinv[3 + c] + z * p.Hinv[6 + c];
-    w[c] = 0;
-    if (p.pbc[c] && (f < -PTM_WRAP_TOL || f >= 1.f + PTM_WRAP_TOL)) {
-      w[c] = (int)floorf(f);
-      f -= (float)w[c];
-    }
-    over = fmaxf(over, fmaxf(-f, f - 1.f) * p.W[c]);
-    int b = (int)floorf(f * (float)p.nb[c]);
-    bc[c] = min(max(b, 0), p.nb[c] - 1);
-  }
-  over = fmaxf(over, 0.f) + 1e-5f * fmaxf(p.W[0], fmaxf(p.W[1], p.W[2]));
-  wrap = img_pack(w[0], w[1], w[2]);
-  return (bc[0] * p.nb[1] + bc[1]) * p.nb[2] + bc[2];
-}
-
 __global__ void k_bin_batch(const BinParams *__restrict__ bp, const int64_t *__restrict__ atom_off, int nframes,
                             int64_t ntotal, int *cell_count, int *atom_cell, int *atom_rank, int *atom_wrap) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1322,15 +1321,13 @@ __global__ void k_bin_batch(const BinParams *__restrict__ bp, const int64_t *__r
   int wrap;
   float over;
   const int cell = p.cell_off + bin_atom(p, p.pos, i - p.atom_off, wrap, over);
+  if (wrap == PTM_EXCLUDED) atomicAdd(p.counters + C_EXCLUDED, 1ull);
+  else if (wrap != img_pack(0, 0, 0)) p.dstat[0] = 1;
   // one atomic per frame per warp (over > 0, so its bits order as integers):
   // per-atom atomics on a frame's single status word serialise at the L2
   const unsigned same = __match_any_sync(__activemask(), f);
   const int omax = __reduce_max_sync(same, __float_as_int(over));
-  const bool any_wrap = __any_sync(same, wrap != img_pack(0, 0, 0));
-  if ((threadIdx.x & 31) == __ffs(same) - 1) {
-    atomicMax(p.dstat + 1, omax);
-    if (any_wrap) p.dstat[0] = 1;
-  }
+  if ((threadIdx.x & 31) == __ffs(same) - 1) atomicMax(p.dstat + 1, omax);
   atom_cell[i] = cell;
   atom_rank[i] = atomicAdd(cell_count + cell, 1);
   atom_wrap[i] = wrap;

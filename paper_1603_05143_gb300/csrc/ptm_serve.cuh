@@ -68,6 +68,7 @@ struct InFlight {
   size_t ws_bytes = 0;
   cudaEvent_t done = nullptr;
   int slot = 0;
+  bool fail = false;               // fault injection: report this batch as failed
 };
 
 constexpr size_t kOutBytesPerAtom = 1 + 1 + 4 + 4 + 16 + 36 + 60 + 4 + 12;
@@ -104,6 +105,10 @@ struct ptm_server {
   int64_t next_batch = 0;
   DevicePool pool;
   std::string error;
+  // host-side fault injection (ptm_server_inject)
+  bool hold_next = false;          // the next launched batch's completion goes unseen ...
+  InFlight *held = nullptr;        // ... while it is held here
+  int fail_next = 0;               // batches still to report as failed
 };
 
 namespace {
@@ -201,7 +206,7 @@ ptm_status launch_batch(ptm_server *S, std::vector<Request *> &rs, int slot, InF
   return PTM_OK;
 }
 
-void retire(ptm_server *S, InFlight *F) {
+void retire(ptm_server *S, InFlight *F, ptm_status status) {
   const double t = now_s();
   for (Request *r : F->reqs) {
     S->pool.release(r->pos_bytes, r->dpos);
@@ -217,6 +222,7 @@ void retire(ptm_server *S, InFlight *F) {
   for (Request *r : F->reqs) {
     S->in_use -= r->bytes;
     r->t_done = t;
+    r->status = status;
     r->state = 2;
   }
   S->slot_busy[F->slot] = false;
@@ -227,19 +233,26 @@ void serve_loop(ptm_server *S) {
   cudaSetDevice(S->ctx->device);
   std::unique_lock<std::mutex> lock(S->mu);
   for (;;) {
-    // completions
-    std::vector<InFlight *> finished;
+    // completions: a batch whose event reports an error (or that a test marked
+    // as failed) completes with PTM_ERR_CUDA instead of waiting for ever
+    std::vector<std::pair<InFlight *, ptm_status>> finished;
     for (size_t i = 0; i < S->inflight.size();) {
-      if (cudaEventQuery(S->inflight[i]->done) == cudaSuccess) {
-        finished.push_back(S->inflight[i]);
-        S->inflight.erase(S->inflight.begin() + i);
-      } else {
-        i++;
+      InFlight *F = S->inflight[i];
+      const cudaError_t q = F == S->held ? cudaErrorNotReady : cudaEventQuery(F->done);
+      if (q == cudaErrorNotReady) { i++; continue; }
+      ptm_status st = PTM_OK;
+      if (q != cudaSuccess || F->fail) {
+        st = PTM_ERR_CUDA;
+        S->error = std::string("serve: batch completion failed: ") +
+                   (q != cudaSuccess ? cudaGetErrorString(q) : "injected by ptm_server_inject");
+        if (q != cudaSuccess) cudaGetLastError();
       }
+      finished.push_back({F, st});
+      S->inflight.erase(S->inflight.begin() + i);
     }
     if (!finished.empty()) {
       lock.unlock();
-      for (InFlight *F : finished) retire(S, F);
+      for (auto &fs : finished) retire(S, fs.first, fs.second);
       lock.lock();
       continue;
     }
@@ -280,6 +293,8 @@ void serve_loop(ptm_server *S) {
       if (rs != PTM_OK) cudaStreamSynchronize(S->streams[slot]);   // copies may be in flight
       lock.lock();
       if (rs == PTM_OK) {
+        if (S->hold_next) { S->held = F; S->hold_next = false; }
+        if (S->fail_next > 0) { F->fail = true; S->fail_next--; }
         S->inflight.push_back(F);
       } else {
         S->error = S->ctx->last_error;
@@ -408,11 +423,28 @@ extern "C" ptm_status ptm_release(ptm_server *S, uint64_t ticket) {
   return PTM_OK;
 }
 
+extern "C" ptm_status ptm_server_inject(ptm_server *S, int fault) {
+  if (!S) return PTM_ERR_INVALID_ARG;
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    switch (fault) {
+      case PTM_FAULT_HOLD_NEXT: S->hold_next = true; break;
+      case PTM_FAULT_RELEASE_HELD: S->hold_next = false; S->held = nullptr; break;
+      case PTM_FAULT_FAIL_NEXT: S->fail_next++; break;
+      default: return PTM_ERR_INVALID_ARG;
+    }
+  }
+  S->cv_work.notify_all();
+  return PTM_OK;
+}
+
 extern "C" ptm_status ptm_server_destroy(ptm_server *S) {
   if (!S) return PTM_ERR_INVALID_ARG;
   {
     std::lock_guard<std::mutex> lock(S->mu);
     S->stop = true;
+    S->hold_next = false;          // a held completion is seen again, so the drain ends
+    S->held = nullptr;
   }
   S->cv_work.notify_all();
   if (S->worker.joinable()) S->worker.join();       // drains queued and in-flight work

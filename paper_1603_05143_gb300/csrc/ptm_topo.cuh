@@ -150,6 +150,11 @@ __device__ void topo_atom(const FrameDesc &d, int s, int *tsm, int2 *__restrict_
   auto J = [&](int k) -> int & { return tsm[k * PTM_BLOCK + t]; };
   auto IMG = [&](int k) -> int & { return tsm[(PTM_TOPO_N + k) * PTM_BLOCK + t]; };
   auto VF = [&](int k, int c) -> float & { return ((float *)tsm)[(2 * PTM_TOPO_N + 3 * k + c) * PTM_BLOCK + t]; };
+  const int64_t n = d.n, sl = s - d.atom_offset;     // frame-local slot
+  if (__ldg(d.wrapv + s) == PTM_EXCLUDED) {           // excluded by the binning: no neighbours
+    for (int k = 0; k < PTM_KNN; k++) out[(int64_t)k * n + sl] = make_int2(-1, 0);
+    return;
+  }
   TI xi, yi, zi;
   int idi;
   load_atom<F64>(d, s, xi, yi, zi, idi);
@@ -225,7 +230,6 @@ __device__ void topo_atom(const FrameDesc &d, int s, int *tsm, int2 *__restrict_
       }
     }
   }
-  const int64_t n = d.n, sl = s - d.atom_offset;     // frame-local slot
   for (int k = 0; k < PTM_KNN; k++)
     out[(int64_t)k * n + sl] = k < m ? make_int2(J(o[k]), IMG(o[k])) : make_int2(-1, 0);
 }
