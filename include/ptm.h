@@ -141,10 +141,12 @@ typedef struct {
                                 gap at the edge of the equal-area band) */
   int64_t knn_fp64;          /* float32 input: atoms whose neighbour order needed FP64
                                 distances (two candidates within the FP32 error bound) */
-  double classify_kernel_ms; /* device time of the classification kernel alone (hulls, codes,
+  double classify_kernel_ms; /* device time of the classification kernels (hulls, codes,
                                 QCP, outputs), after the neighbour lists */
   int64_t excluded;          /* atoms with a non-finite coordinate or more than 100 cell periods
                                 outside the cell: left unmatched and nobody's neighbour */
+  double match_kernel_ms;    /* device time of the matching kernel alone (QCP, selection,
+                                outputs): the last part of classify_kernel_ms */
 } ptm_stats;
 
 /* Create a context on options->device (NULL options: device 0, default budget).

@@ -38,7 +38,8 @@ class ptm_stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("atoms", "matched", "knn_wide", "knn_fail", "sos", "qcp_fp64",
                                          "tie_fp64", "internal", "candidates", "candidate_points")] + \
                [("pipeline_ms", C.c_double), ("atom_kernel_ms", C.c_double), ("topo_fp64", C.c_int64),
-                ("knn_fp64", C.c_int64), ("classify_kernel_ms", C.c_double), ("excluded", C.c_int64)]
+                ("knn_fp64", C.c_int64), ("classify_kernel_ms", C.c_double), ("excluded", C.c_int64),
+                ("match_kernel_ms", C.c_double)]
 
 
 class ptm_tuning(C.Structure):

@@ -35,7 +35,7 @@ struct ptm_context {
   int *dstat = nullptr;
   unsigned long long *counters = nullptr;
   cudaStream_t last_stream = nullptr;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // call start, per-atom kernels start, end, k_atoms start
+  cudaEvent_t ev[5] = {};   // call start, per-atom kernels start, end, k_hulls start, k_match start
   // host-buffer entry point
   size_t cap_host_atoms = 0;
   void *hpos = nullptr;
@@ -44,8 +44,11 @@ struct ptm_context {
   float *o_rmsd = nullptr, *o_scale = nullptr, *o_quat = nullptr, *o_strain = nullptr;
   int32_t *o_corr = nullptr;
   float *o_vm = nullptr, *o_rf = nullptr;
-  // every atom's 14 neighbours (k_knn or k_topo -> k_atoms)
+  // every atom's 14 neighbours (k_knn or k_topo -> k_hulls, k_match) and its
+  // matched snapshots (k_hulls -> k_match)
   int2 *nbr = nullptr;
+  uint64_t *lam = nullptr;
+  uint32_t *ents = nullptr;
   size_t cap_nbr = 0;
   // topological order: atoms for the FP64 pass ([n] = their count) and what
   // the FP32 pass keeps for it
@@ -205,10 +208,12 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
   if (rs != PTM_OK) return rs;
   const bool topological = f->ordering == PTM_ORDER_TOPOLOGICAL;
   if ((size_t)n > ctx->cap_nbr) {
-    cudaFree(ctx->nbr);
-    ctx->nbr = nullptr;
+    cudaFree(ctx->nbr); cudaFree(ctx->lam); cudaFree(ctx->ents);
+    ctx->nbr = nullptr; ctx->lam = nullptr; ctx->ents = nullptr;
     ctx->cap_nbr = 0;
     CK(cudaMalloc(&ctx->nbr, (size_t)n * PTM_KNN * sizeof(int2)));
+    CK(cudaMalloc(&ctx->lam, (size_t)n * 3 * sizeof(uint64_t)));
+    CK(cudaMalloc(&ctx->ents, (size_t)n * sizeof(uint32_t)));
     ctx->cap_nbr = (size_t)n;
   }
   if (topological && (size_t)n > ctx->cap_topo) {
@@ -229,6 +234,8 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
   desc.dstat = ctx->dstat;
   desc.counters = ctx->counters;
   desc.nbr = ctx->nbr;
+  desc.lam = ctx->lam;
+  desc.ents = ctx->ents;
   bp.counters = ctx->counters;
 
   cudaGetLastError();   // launch errors are read below; drop any left by earlier calls
@@ -273,12 +280,15 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
     }
   }
   CK(cudaEventRecord(ctx->ev[3], st));
+  if (f64) k_hulls<true><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
+  else k_hulls<false><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
+  CK(cudaEventRecord(ctx->ev[4], st));
   if (ctx->precision == PTM_PREC_FP64) {
-    if (f64) k_atoms<true, true><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
-    else k_atoms<false, true><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
+    if (f64) k_match<true, true><<<ga, PTM_BLOCK, match_smem_bytes(), st>>>(desc);
+    else k_match<false, true><<<ga, PTM_BLOCK, match_smem_bytes(), st>>>(desc);
   } else {
-    if (f64) k_atoms<true><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
-    else k_atoms<false><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
+    if (f64) k_match<true><<<ga, PTM_BLOCK, match_smem_bytes(), st>>>(desc);
+    else k_match<false><<<ga, PTM_BLOCK, match_smem_bytes(), st>>>(desc);
   }
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev[2], st));
@@ -323,7 +333,7 @@ ptm_status ptm_create(const ptm_options *opt, ptm_context **out) {
     if ((e = cudaSetDevice(ctx->device)) != cudaSuccess) { rs = cuda_fail(ctx, e, "cudaSetDevice"); break; }
     if ((e = cudaMalloc(&ctx->dstat, 8 * sizeof(int))) != cudaSuccess) { rs = cuda_fail(ctx, e, "cudaMalloc"); break; }
     if ((e = cudaMalloc(&ctx->counters, C_NCOUNTERS * sizeof(unsigned long long))) != cudaSuccess) { rs = cuda_fail(ctx, e, "cudaMalloc"); break; }
-    for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaEventCreate(&ctx->ev[i]);
+    for (int i = 0; i < 5 && e == cudaSuccess; i++) e = cudaEventCreate(&ctx->ev[i]);
     if (e != cudaSuccess) { rs = cuda_fail(ctx, e, "cudaEventCreate"); break; }
     if ((e = cudaMemset(ctx->counters, 0, C_NCOUNTERS * sizeof(unsigned long long))) != cudaSuccess) { rs = cuda_fail(ctx, e, "cudaMemset"); break; }
     size_t fr = 0, tot = 0;
@@ -332,9 +342,11 @@ ptm_status ptm_create(const ptm_options *opt, ptm_context **out) {
     // the per-atom kernels want every resident block's scratch in shared
     // memory: the largest shared-memory carveout of the unified L1
     const int smem = (int)std::max(atom_smem_bytes(), std::max(topo_smem_bytes(), topo64_smem_bytes()));
-    const void *fns[] = {(const void *)k_atoms<false>, (const void *)k_atoms<true>, (const void *)k_atoms<false, true>,
-                         (const void *)k_atoms<true, true>, (const void *)k_atoms_batch<false>,
-                         (const void *)k_atoms_batch<true>, (const void *)k_topo<false>, (const void *)k_topo<true>,
+    const void *fns[] = {(const void *)k_hulls<false>, (const void *)k_hulls<true>, (const void *)k_hulls_batch<false>,
+                         (const void *)k_hulls_batch<true>, (const void *)k_match<false>, (const void *)k_match<true>,
+                         (const void *)k_match<false, true>, (const void *)k_match<true, true>,
+                         (const void *)k_match_batch<false>, (const void *)k_match_batch<true>,
+                         (const void *)k_topo<false>, (const void *)k_topo<true>,
                          (const void *)k_topo_batch<false>, (const void *)k_topo_batch<true>,
                          (const void *)k_topo64<false>, (const void *)k_topo64<true>,
                          (const void *)k_topo64_batch<false>, (const void *)k_topo64_batch<true>,
@@ -361,11 +373,11 @@ ptm_status ptm_destroy(ptm_context *ctx) {
   cudaFree(ctx->atom_cell); cudaFree(ctx->atom_rank); cudaFree(ctx->atom_wrap);
   cudaFree(ctx->cell_count); cudaFree(ctx->cell_start); cudaFree(ctx->block_sums);
   cudaFree(ctx->dstat); cudaFree(ctx->counters);
-  for (int i = 0; i < 4; i++) if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  for (int i = 0; i < 5; i++) if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   cudaFree(ctx->hpos); cudaFree(ctx->hspecies);
   cudaFree(ctx->o_struct); cudaFree(ctx->o_alloy); cudaFree(ctx->o_rmsd); cudaFree(ctx->o_scale);
   cudaFree(ctx->o_quat); cudaFree(ctx->o_strain); cudaFree(ctx->o_corr); cudaFree(ctx->o_vm); cudaFree(ctx->o_rf);
-  cudaFree(ctx->nbr);
+  cudaFree(ctx->nbr); cudaFree(ctx->lam); cudaFree(ctx->ents);
   cudaFree(ctx->topo_list);
   cudaFree(ctx->topo_side);
   delete ctx;
@@ -447,12 +459,14 @@ ptm_status ptm_get_stats(ptm_context *ctx, ptm_stats *out) {
   float t_all = 0.f, t_atom = 0.f;
   if (cudaEventElapsedTime(&t_all, ctx->ev[0], ctx->ev[2]) != cudaSuccess) t_all = -1.f;
   if (cudaEventElapsedTime(&t_atom, ctx->ev[1], ctx->ev[2]) != cudaSuccess) t_atom = -1.f;
-  float t_cls = -1.f;
+  float t_cls = -1.f, t_match = -1.f;
   if (cudaEventElapsedTime(&t_cls, ctx->ev[3], ctx->ev[2]) != cudaSuccess) t_cls = -1.f;
+  if (cudaEventElapsedTime(&t_match, ctx->ev[4], ctx->ev[2]) != cudaSuccess) t_match = -1.f;
   cudaGetLastError();
   out->pipeline_ms = t_all;
   out->atom_kernel_ms = t_atom;
   out->classify_kernel_ms = t_cls;
+  out->match_kernel_ms = t_match;
   out->candidates = (int64_t)c[C_CAND];
   out->candidate_points = (int64_t)c[C_CANDPTS];
   out->atoms = (int64_t)c[C_ATOMS];
@@ -487,12 +501,14 @@ struct ptm_batch {
   int *sbin = nullptr, *wrapv = nullptr, *atom_cell = nullptr, *atom_rank = nullptr, *atom_wrap = nullptr;
   int *cell_count = nullptr, *cell_start = nullptr, *block_sums = nullptr, *scan_total = nullptr;
   unsigned long long *queue = nullptr, *counters = nullptr;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // as ptm_context::ev
+  cudaEvent_t ev[5] = {};       // as ptm_context::ev
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int nsm = 152;
   int topo = 0;                   // some frame takes the topological order
   int2 *nbr_buf = nullptr;        // per-frame segments of neighbour lists
+  uint64_t *lam_buf = nullptr;    // per-frame segments of the k_hulls -> k_match state
+  uint32_t *ents_buf = nullptr;
   int *topo_list = nullptr;       // atoms for the FP64 pass; [ntotal] = their count
   TopoSide *topo_side = nullptr;  // what the FP32 pass keeps for the FP64 pass
   void *block = nullptr;          // the workspace (one allocation, or a pool block when served)
@@ -504,7 +520,7 @@ static void batch_free(ptm_batch *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->owns_block) cudaFree(b->block);
-  for (int i = 0; i < 4; i++) if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+  for (int i = 0; i < 5; i++) if (b->ev[i]) cudaEventDestroy(b->ev[i]);
   delete b;
 }
 
@@ -520,7 +536,7 @@ static ptm_status batch_enqueue(ptm_batch *b, cudaStream_t st) {
   CK(cudaMemsetAsync(b->cell_count, 0, (b->ncell + 1) * sizeof(int), st));
   CK(cudaMemsetAsync(b->d_dstat, 0, (size_t)4 * b->nframes * sizeof(int), st));
   CK(cudaMemsetAsync(b->counters, 0, C_NCOUNTERS * sizeof(unsigned long long), st));
-  CK(cudaMemsetAsync(b->queue, 0, sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(b->queue, 0, 2 * sizeof(unsigned long long), st));
   const int tb = 256;
   const unsigned gb = (unsigned)((b->ntotal + tb - 1) / tb);
   k_bin_batch<<<gb, tb, 0, st>>>(b->d_bp, b->d_atom_off, b->nframes, b->ntotal, b->cell_count, b->atom_cell,
@@ -559,16 +575,25 @@ static ptm_status batch_enqueue(ptm_batch *b, cudaStream_t st) {
     }
   }
   CK(cudaEventRecordWithFlags(b->ev[3], st, rec));
-  // two warps per block, each pulling its own tiles
+  // persistent grids: two warps per block, each pulling its own tiles
   const int64_t tiles = (b->ntotal + b->tile_atoms - 1) / b->tile_atoms;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->nsm * b->blocks_per_sm,
                                                                        (tiles + 1) / 2));
   if (b->f64)
-    k_atoms_batch<true><<<grid, PTM_BLOCK, atom_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes,
+    k_hulls_batch<true><<<grid, PTM_BLOCK, atom_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes,
                                                                     b->ntotal, b->tile_atoms, b->queue);
   else
-    k_atoms_batch<false><<<grid, PTM_BLOCK, atom_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes,
+    k_hulls_batch<false><<<grid, PTM_BLOCK, atom_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes,
                                                                      b->ntotal, b->tile_atoms, b->queue);
+  CK(cudaEventRecordWithFlags(b->ev[4], st, rec));
+  const unsigned grid_m = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->nsm * PTM_MATCH_BLOCKS_PER_SM,
+                                                                         (tiles + 1) / 2));
+  if (b->f64)
+    k_match_batch<true><<<grid_m, PTM_BLOCK, match_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes,
+                                                                       b->ntotal, b->tile_atoms, b->queue + 1);
+  else
+    k_match_batch<false><<<grid_m, PTM_BLOCK, match_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes,
+                                                                        b->ntotal, b->tile_atoms, b->queue + 1);
   CK(cudaGetLastError());
   CK(cudaEventRecordWithFlags(b->ev[2], st, rec));
   return PTM_OK;
@@ -617,9 +642,10 @@ static ptm_status batch_plan(int nframes, const ptm_frame *frames, double cell_f
 static size_t batch_workspace_bytes(int nframes, int64_t ntotal, size_t ncell, int f64, int topo) {
   const size_t n = (size_t)ntotal, rec = f64 ? sizeof(Atom64) : sizeof(float4);
   const size_t nblk = (ncell + 1 + 2 * SCAN_BLOCK - 1) / (2 * SCAN_BLOCK) + 1;
-  const size_t tb = sizeof(int2) * PTM_KNN * n + 256 + (topo ? 4 * (n + 1) + topo_side_bytes(n) + 2 * 256 : 0);
+  const size_t tb = sizeof(int2) * PTM_KNN * n + 28 * n + 3 * 256 +
+                    (topo ? 4 * (n + 1) + topo_side_bytes(n) + 2 * 256 : 0);
   return (sizeof(FrameDesc) + sizeof(BinParams) + sizeof(int64_t) + 16) * nframes + rec * n + 20 * n +
-         8 * (ncell + 1) + 4 * nblk + 4 + 8 + 8 * C_NCOUNTERS + 16 * 256 + tb;
+         8 * (ncell + 1) + 4 * nblk + 4 + 16 + 8 * C_NCOUNTERS + 16 * 256 + tb;
 }
 
 // Carve the batch workspace out of one device block (256-byte aligned pieces)
@@ -639,9 +665,11 @@ static void batch_layout(ptm_batch *b, unsigned char *base, BatchPlan &P, const 
   b->atom_rank = (int *)take(4 * n); b->atom_wrap = (int *)take(4 * n);
   b->cell_count = (int *)take(4 * (nc + 1)); b->cell_start = (int *)take(4 * (nc + 1));
   b->block_sums = (int *)take(4 * nblk); b->scan_total = (int *)take(4);
-  b->queue = (unsigned long long *)take(8); b->counters = (unsigned long long *)take(8 * C_NCOUNTERS);
+  b->queue = (unsigned long long *)take(16); b->counters = (unsigned long long *)take(8 * C_NCOUNTERS);
   b->topo = P.topo;
   b->nbr_buf = (int2 *)take(sizeof(int2) * PTM_KNN * n);
+  b->lam_buf = (uint64_t *)take(sizeof(uint64_t) * 3 * n);
+  b->ents_buf = (uint32_t *)take(sizeof(uint32_t) * n);
   if (P.topo) {
     b->topo_list = (int *)take(4 * (n + 1));
     b->topo_side = (TopoSide *)take(topo_side_bytes(n));
@@ -649,6 +677,8 @@ static void batch_layout(ptm_batch *b, unsigned char *base, BatchPlan &P, const 
   for (int f = 0; f < nf; f++) {
     // frame f's neighbour list: rows of n_f entries from slot 14 x (first slot)
     P.hd[f].nbr = b->nbr_buf + PTM_KNN * P.off[f];
+    P.hd[f].lam = b->lam_buf + 3 * P.off[f];
+    P.hd[f].ents = b->ents_buf + P.off[f];
     P.hd[f].sorted = b->sorted;
     P.hd[f].sbin = b->sbin;
     P.hd[f].cell_start = b->cell_start + P.hb[f].cell_off;
@@ -684,7 +714,7 @@ extern "C" ptm_status ptm_batch_create(ptm_context *ctx, int nframes, const ptm_
   b->ntotal = P.ntotal;
   b->ncell = P.ncell;
   cudaError_t e = cudaMalloc(&b->block, batch_workspace_bytes(nframes, P.ntotal, P.ncell, P.f64, P.topo));
-  for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaEventCreate(&b->ev[i]);
+  for (int i = 0; i < 5 && e == cudaSuccess; i++) e = cudaEventCreate(&b->ev[i]);
   if (e != cudaSuccess) { rs = cuda_fail(ctx, e, "ptm_batch_create"); batch_free(b); return rs; }
   batch_layout(b, (unsigned char *)b->block, P, outs);
   if ((e = cudaMemcpy(b->d_descs, P.hd.data(), sizeof(FrameDesc) * nframes, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -739,9 +769,11 @@ extern "C" ptm_status ptm_batch_stats(ptm_batch *b, ptm_stats *out) {
   float t_all = -1.f, t_atom = -1.f;
   if (cudaEventElapsedTime(&t_all, b->ev[0], b->ev[2]) != cudaSuccess) t_all = -1.f;
   if (cudaEventElapsedTime(&t_atom, b->ev[1], b->ev[2]) != cudaSuccess) t_atom = -1.f;
-  float t_cls = -1.f;
+  float t_cls = -1.f, t_match = -1.f;
   if (cudaEventElapsedTime(&t_cls, b->ev[3], b->ev[2]) != cudaSuccess) t_cls = -1.f;
+  if (cudaEventElapsedTime(&t_match, b->ev[4], b->ev[2]) != cudaSuccess) t_match = -1.f;
   out->classify_kernel_ms = t_cls;
+  out->match_kernel_ms = t_match;
   cudaGetLastError();
   out->atoms = (int64_t)c[C_ATOMS]; out->matched = (int64_t)c[C_MATCHED]; out->knn_wide = (int64_t)c[C_KNN_WIDE];
   out->knn_fail = (int64_t)c[C_KNN_FAIL]; out->sos = (int64_t)c[C_SOS]; out->qcp_fp64 = (int64_t)c[C_QCP64];
@@ -834,7 +866,9 @@ struct NoallocLayout {                  // byte offsets inside the static array
   static constexpr size_t cell_start = cell_count + sizeof(int) * (kNoallocCells + 1);
   static constexpr size_t block_sums = cell_start + sizeof(int) * (kNoallocCells + 1);
   static constexpr size_t nbr = (block_sums + sizeof(int) * kNoallocScanBlocks + 15) / 16 * 16;
-  static constexpr size_t dstat = nbr + sizeof(int2) * PTM_KNN * kNoallocAtoms;
+  static constexpr size_t lam = nbr + sizeof(int2) * PTM_KNN * kNoallocAtoms;
+  static constexpr size_t ents = lam + sizeof(uint64_t) * 3 * kNoallocAtoms;
+  static constexpr size_t dstat = ents + sizeof(uint32_t) * kNoallocAtoms;
   static constexpr size_t counters = ((dstat + sizeof(int) * 8) + 7) / 8 * 8;
   static constexpr size_t total = counters + sizeof(unsigned long long) * C_NCOUNTERS;
 };
@@ -913,6 +947,8 @@ extern "C" ptm_status ptm_classify_frame_noalloc(const ptm_frame *f, const ptm_o
   unsigned long long *counters = (unsigned long long *)(base + NoallocLayout::counters);
   desc.sorted = sorted; desc.sbin = sbin; desc.cell_start = cell_start; desc.wrapv = wrapv;
   desc.nbr = (int2 *)(base + NoallocLayout::nbr);
+  desc.lam = (uint64_t *)(base + NoallocLayout::lam);
+  desc.ents = (uint32_t *)(base + NoallocLayout::ents);
   set_outputs(&desc, o);
   desc.dstat = dstat;
   desc.counters = counters;
@@ -938,8 +974,10 @@ extern "C" ptm_status ptm_classify_frame_noalloc(const ptm_frame *f, const ptm_o
   if (f64) k_knn<true><<<gk, PTM_KNN_BLOCK, knn_smem_bytes(), st>>>(desc);
   else k_knn<false><<<gk, PTM_KNN_BLOCK, knn_smem_bytes(), st>>>(desc);
   const unsigned ga = (unsigned)((n + PTM_BLOCK - 1) / PTM_BLOCK);
-  if (f64) k_atoms<true><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
-  else k_atoms<false><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
+  if (f64) k_hulls<true><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
+  else k_hulls<false><<<ga, PTM_BLOCK, atom_smem_bytes(), st>>>(desc);
+  if (f64) k_match<true><<<ga, PTM_BLOCK, match_smem_bytes(), st>>>(desc);
+  else k_match<false><<<ga, PTM_BLOCK, match_smem_bytes(), st>>>(desc);
   if (cudaGetLastError() != cudaSuccess) return PTM_ERR_CUDA;
   return PTM_OK;
 }

@@ -64,6 +64,8 @@ struct FrameDesc {
                                // atom at frame-local slot s - atom_offset (slot -1: none), written
                                // by k_knn (Euclidean order) or k_topo (topological order)
   int ordering;                // PTM_ORDER_EUCLIDEAN or PTM_ORDER_TOPOLOGICAL
+  uint64_t *lam;               // k_hulls -> k_match: [3][n] Weinberg labelling of snapshot k = 6, 12, 14
+  uint32_t *ents;              // [n] their table entries + 1, 10 bits each (0: no match)
   int *dstat;                  // [0] any atom wrapped, [1] overshoot (float bits, Angstrom)
   unsigned long long *counters;  // the C_* counters below
   int64_t atom_offset;         // first sorted slot of this frame (0 for a single frame)

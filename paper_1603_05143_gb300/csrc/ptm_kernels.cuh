@@ -8,9 +8,11 @@
 //   k_scatter  atoms copied into cell order as float4 (x, y, z, id)
 //   k_knn      one thread per atom: its 14 nearest images, as a neighbour list
 //              (k_topo in ptm_topo.cuh instead for the topological order)
-//   k_atoms    one thread per atom: hulls, codes, QCP .. outputs
-// The neighbour search and the rest run as separate kernels so that the warps
-// of an SM share one phase of the method and its code.
+//   k_hulls    one thread per atom: hulls, Weinberg codes, template lookup
+//   k_match    one thread per atom: QCP, selection, outputs
+// The phases run as separate kernels so that the warps of an SM share one
+// phase of the method and its code (the instruction cache held none of the
+// fused per-atom program).
 #pragma once
 #include "ptm_atom.cuh"
 #include "../../include/ptm.h"
@@ -321,6 +323,9 @@ struct SmemKnnRows {
 };
 
 #define PTM_KNN_BLOCK 128
+// 6 blocks of 128 threads per SM: the shared-memory rows (280 B per thread) and
+// at most 85 registers per thread fit
+#define PTM_KNN_BLOCKS_PER_SM 6
 typedef SmemKnnRows<PTM_KNN, PTM_KNN_BLOCK> KnnRows;
 constexpr size_t knn_smem_bytes() { return (size_t)PTM_KNN_BLOCK * KnnRows::kRows * 4; }
 
@@ -988,19 +993,27 @@ __device__ __noinline__ void wide_quantise(const FrameDesc &d, float xi, float y
 }
 
 // ------------------------------------------------------------ one atom
-// P64 selects the FP64 form: the same exact predicates, Weinberg codes and
-// lookup, then every candidate scored and the winner's outputs computed in FP64
-// (the one-frame-per-launch comparison form).
-// `live` holds the lanes of this warp that entered together (all reach the
-// warp-synchronous points below).
-template <bool F64, bool P64 = false>
-__device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, const float4 *tplw, unsigned live) {
+// The method for one atom runs in two kernels.  k_hulls: neighbour vectors
+// from the list, their quantised copy, the incremental hull and at k = 6, 12,
+// 14 the Weinberg code and template lookup; it leaves, per atom, the matched
+// snapshots' labellings and table entries (d.lam, d.ents).  k_match: QCP of
+// every admissible correspondence, selection and the outputs.  `live` holds
+// the lanes of this warp that entered together (all reach the warp-synchronous
+// points below).
+
+// Table entries of the snapshots k = 6, 12, 14, each + 1 in 10 bits (0 = none).
+__device__ __forceinline__ uint32_t pack_ents(int e6, int e12, int e14) {
+  return (uint32_t)(e6 + 1) | (uint32_t)(e12 + 1) << 10 | (uint32_t)(e14 + 1) << 20;
+}
+
+template <bool F64>
+__device__ void hull_atom(const FrameDesc &d, int s, const Scratch &sm, unsigned live) {
   typedef typename RT<F64>::T T;
-  double ex[P64 ? PTM_KNN : 1], ey[P64 ? PTM_KNN : 1], ez[P64 ? PTM_KNN : 1];
   T xi, yi, zi;
   int idi;
   load_atom<F64>(d, s, xi, yi, zi, idi);
   count(d, C_ATOMS);
+  const int64_t sl = s - d.atom_offset;          // frame-local slot
 
   // ---- neighbours (Sec. 3): the list written by k_knn or k_topo
   int cnt = 0;
@@ -1014,7 +1027,7 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
       cnt += e.x >= 0;
     }
     hmask = __ballot_sync(live, cnt >= 4);       // lanes that go on to the hulls
-    if (cnt < 4) { write_unmatched(d, idi); return; }
+    if (cnt < 4) { d.ents[sl] = 0; return; }
     // rows NID / IMG keep (sorted index, image) of each neighbour through the
     // hulls.  Quantised copy for the exact hull predicates: q = rint(dr 2^(19 - e))
     // (half to even) on the FP64 contract vectors dr, 2^(e-1) <= max |dr_c| < 2^e
@@ -1032,7 +1045,6 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
         contract_shift<F64>(d, a0, a1, a2, sx, sy, sz);
         T cx = contract_dr(xj, xi, sx), cy = contract_dr(yj, yi, sy), cz = contract_dr(zj, zi, sz);
         emax = fmax(emax, fmax(fabs(cx), fmax(fabs(cy), fabs(cz))));
-        if constexpr (P64) { ex[t] = cx; ey[t] = cy; ez[t] = cz; }
       }
       int e;
       frexp(emax, &e);
@@ -1085,22 +1097,11 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
         sm.Q(t, 0) = rintf(sm.Q(t, 0) * sc); sm.Q(t, 1) = rintf(sm.Q(t, 1) * sc); sm.Q(t, 2) = rintf(sm.Q(t, 2) * sc);
       }
       if (wide) wide_quantise(d, xi, yi, zi, sm.nid + sm.t, sm.img + sm.t, sm.q + sm.t, wide, PTM_QBITS - e);
-      if constexpr (P64) {
-#pragma unroll 1
-        for (int t = 0; t < PTM_KNN; t++) {
-          if (t >= cnt) continue;
-          double v[3];
-          vec64_row(d, xi, yi, zi, sm.nid[t * PTM_BLOCK + sm.t], sm.img[t * PTM_BLOCK + sm.t], v);
-          ex[t] = v[0]; ey[t] = v[1]; ez[t] = v[2];
-        }
-      }
     }
   }
 
   // ---- hulls of the first 6, 12, 14 neighbours, built incrementally (Sec. 4)
   Best bst;
-  bst.b1 = bst.b2 = INFINITY;
-  bst.K = -1; bst.cand = -1; bst.fp64 = 0;
   bst.ent6 = bst.ent12 = bst.ent14 = -1;
   bst.lam6 = bst.lam12 = bst.lam14 = 0;
   const uint32_t mask = d.mask;
@@ -1130,9 +1131,45 @@ __device__ void classify_atom(const FrameDesc &d, int s, const Scratch &sm, cons
     nf = hull_apply(sm, nf, vis, p, d);
     if (nf < 0) alive = false;
   }
-  const bool found = bst.ent6 >= 0 || bst.ent12 >= 0 || bst.ent14 >= 0;
-  const unsigned qmask = __ballot_sync(hmask, found);
-  if (!found) { write_unmatched(d, idi); return; }
+  d.ents[sl] = pack_ents(bst.ent6, bst.ent12, bst.ent14);
+  if (bst.ent6 >= 0) d.lam[sl] = bst.lam6;
+  if (bst.ent12 >= 0) d.lam[d.n + sl] = bst.lam12;
+  if (bst.ent14 >= 0) d.lam[2 * d.n + sl] = bst.lam14;
+}
+
+// P64 selects the FP64 form: every candidate scored and the winner's outputs
+// computed in FP64 (the one-frame-per-launch comparison form).
+template <bool F64, bool P64 = false>
+__device__ void match_atom(const FrameDesc &d, int s, const Scratch &sm, const float4 *tplw, unsigned live) {
+  typedef typename RT<F64>::T T;
+  const int64_t sl = s - d.atom_offset;
+  const uint32_t ents = __ldg(d.ents + sl);
+  const unsigned qmask = __ballot_sync(live, ents != 0);
+  T xi, yi, zi;
+  int idi;
+  load_atom<F64>(d, s, xi, yi, zi, idi);
+  if (!ents) { write_unmatched(d, idi); return; }
+  Best bst;
+  bst.b1 = bst.b2 = INFINITY;
+  bst.K = -1; bst.cand = -1; bst.fp64 = 0;
+  bst.ent6 = (int)(ents & 1023) - 1;
+  bst.ent12 = (int)(ents >> 10 & 1023) - 1;
+  bst.ent14 = (int)(ents >> 20 & 1023) - 1;
+  bst.lam6 = bst.ent6 >= 0 ? __ldg((const unsigned long long *)d.lam + sl) : 0;
+  bst.lam12 = bst.ent12 >= 0 ? __ldg((const unsigned long long *)d.lam + d.n + sl) : 0;
+  bst.lam14 = bst.ent14 >= 0 ? __ldg((const unsigned long long *)d.lam + 2 * d.n + sl) : 0;
+  int cnt = 0;
+#pragma unroll 1
+  for (int t = 0; t < PTM_KNN; t++) {
+    const int2 e = __ldg(d.nbr + (int64_t)t * d.n + sl);
+    sm.NID(t) = e.x;
+    sm.IMG(t) = e.y;
+    cnt += e.x >= 0;
+  }
+  double ex[P64 ? PTM_KNN : 1], ey[P64 ? PTM_KNN : 1], ez[P64 ? PTM_KNN : 1];
+  if constexpr (P64) {
+    for (int t = 0; t < cnt; t++) vec_fp64<F64>(d, xi, yi, zi, sm.NID(t), sm.IMG(t), ex[t], ey[t], ez[t]);
+  }
   metric_vectors<F64>(d, sm, cnt, xi, yi, zi);
   if constexpr (!P64) {
     score_candidates(d, sm, tplw, bst, qmask);
@@ -1357,11 +1394,17 @@ __global__ void k_scatter_batch(const BinParams *__restrict__ bp, const int64_t 
 }
 
 constexpr size_t atom_smem_bytes() { return (size_t)PTM_BLOCK * SCRATCH_WORDS * 4; }
+// k_match keeps only the neighbour vectors (42 words) and the neighbours' slots
+// and images (28 words) per thread
+constexpr int MATCH_WORDS = 42 + 14 + 14;
+constexpr size_t match_smem_bytes() { return (size_t)PTM_BLOCK * MATCH_WORDS * 4; }
 
-// Resident blocks per SM of the per-atom kernels: 7 x (126 words x 64 threads + the
-// 1 KB the driver reserves per block) fits 228 KB of shared memory, and 7 x 64
-// threads x 146 registers the register file.
+// Resident blocks per SM of k_hulls: 7 x (126 words x 64 threads + the 1 KB the
+// driver reserves per block) fits 228 KB of shared memory, and 7 x 64 threads x
+// 146 registers the register file.
 #define PTM_ATOM_BLOCKS_PER_SM 7
+// k_match: 12 x (70 words x 64 threads + 1 KB) fits, at up to 85 registers
+#define PTM_MATCH_BLOCKS_PER_SM 12
 
 // Scratch rows in a block's dynamic shared memory (row layout of Scratch).
 __device__ __forceinline__ Scratch scratch_rows(unsigned char *smem) {
@@ -1377,26 +1420,47 @@ __device__ __forceinline__ Scratch scratch_rows(unsigned char *smem) {
   return sm;
 }
 
+// The rows k_match uses (the others stay null).
+__device__ __forceinline__ Scratch match_rows(unsigned char *smem) {
+  Scratch sm;
+  sm.th = nullptr; sm.code = nullptr; sm.fac = nullptr; sm.used = nullptr;
+  sm.q = (float *)smem;
+  sm.nid = (int *)(sm.q + 42 * PTM_BLOCK);
+  sm.img = sm.nid + 14 * PTM_BLOCK;
+  sm.t = threadIdx.x;
+  return sm;
+}
+
 // Normalised templates as float4 (x, y, z, .) in global memory, read through the
 // read-only cache (shared memory is spent on per-thread scratch).
 __device__ __forceinline__ const float4 *template_rows() { return reinterpret_cast<const float4 *>(&ptm_tpl[0][0][0]); }
 
 // The frame descriptor travels by value in the kernel parameters, so back-to-back
 // asynchronous calls never share a staging buffer.
-template <bool F64, bool P64 = false>
-__global__ void __launch_bounds__(PTM_BLOCK, PTM_ATOM_BLOCKS_PER_SM) k_atoms(const __grid_constant__ FrameDesc d) {
+template <bool F64>
+__global__ void __launch_bounds__(PTM_BLOCK, PTM_ATOM_BLOCKS_PER_SM) k_hulls(const __grid_constant__ FrameDesc d) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Scratch sm = scratch_rows(smem);
-  const float4 *tplw = template_rows();
-  int64_t s = (int64_t)blockIdx.x * PTM_BLOCK + threadIdx.x;
+  const int64_t s = (int64_t)blockIdx.x * PTM_BLOCK + threadIdx.x;
   const unsigned live = __ballot_sync(0xffffffffu, s < d.n);
   if (s >= d.n) return;
-  classify_atom<F64, P64>(d, (int)s, sm, tplw, live);
+  hull_atom<F64>(d, (int)s, sm, live);
+}
+
+template <bool F64, bool P64 = false>
+__global__ void __launch_bounds__(PTM_BLOCK, PTM_MATCH_BLOCKS_PER_SM) k_match(const __grid_constant__ FrameDesc d) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Scratch sm = match_rows(smem);
+  const float4 *tplw = template_rows();
+  const int64_t s = (int64_t)blockIdx.x * PTM_BLOCK + threadIdx.x;
+  const unsigned live = __ballot_sync(0xffffffffu, s < d.n);
+  if (s >= d.n) return;
+  match_atom<F64, P64>(d, (int)s, sm, tplw, live);
 }
 
 // Neighbour lists of one frame (Euclidean order), one thread per atom.
 template <bool F64>
-__global__ void __launch_bounds__(PTM_KNN_BLOCK) k_knn(const __grid_constant__ FrameDesc d) {
+__global__ void __launch_bounds__(PTM_KNN_BLOCK, PTM_KNN_BLOCKS_PER_SM) k_knn(const __grid_constant__ FrameDesc d) {
   extern __shared__ __align__(16) int knn_smem[];
   const int64_t s = (int64_t)blockIdx.x * PTM_KNN_BLOCK + threadIdx.x;
   if (s >= d.n) return;
@@ -1406,7 +1470,7 @@ __global__ void __launch_bounds__(PTM_KNN_BLOCK) k_knn(const __grid_constant__ F
 // The same over a batch: each slot finds its frame; frames in the topological
 // order are left to k_topo_batch.
 template <bool F64>
-__global__ void __launch_bounds__(PTM_KNN_BLOCK)
+__global__ void __launch_bounds__(PTM_KNN_BLOCK, PTM_KNN_BLOCKS_PER_SM)
     k_knn_batch(const FrameDesc *__restrict__ descs, const int64_t *__restrict__ atom_off, int nframes,
                 int64_t ntotal) {
   extern __shared__ __align__(16) int knn_smem[];
@@ -1417,18 +1481,15 @@ __global__ void __launch_bounds__(PTM_KNN_BLOCK)
   knn_atom<F64>(d, (int)s, knn_smem);
 }
 
-// Persistent classification of a batch: every warp pulls tiles of tile_atoms
-// (a multiple of 32) consecutive sorted slots from one global queue until the
-// batch is exhausted, so uneven frames balance across the GPU and no warp waits
-// for the other warp of its block.  Each slot finds its frame by a binary
-// search over the frames' first slots.
-template <bool F64>
-__global__ void __launch_bounds__(PTM_BLOCK, PTM_ATOM_BLOCKS_PER_SM)
-    k_atoms_batch(const FrameDesc *__restrict__ descs, const int64_t *__restrict__ atom_off, int nframes,
-                  int64_t ntotal, int tile_atoms, unsigned long long *queue) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const Scratch sm = scratch_rows(smem);
-  const float4 *tplw = template_rows();
+// Persistent per-atom passes over a batch: every warp pulls tiles of
+// tile_atoms (a multiple of 32) consecutive sorted slots from a global queue
+// until the batch is exhausted, so uneven frames balance across the GPU and no
+// warp waits for the other warp of its block; each slot finds its frame by a
+// binary search over the frames' first slots.  fn(desc, slot, live).
+template <typename Fn>
+__device__ __forceinline__ void persistent_tiles(const FrameDesc *__restrict__ descs,
+                                                 const int64_t *__restrict__ atom_off, int nframes, int64_t ntotal,
+                                                 int tile_atoms, unsigned long long *queue, Fn &&fn) {
   const int lane = threadIdx.x & 31;
   for (;;) {
     unsigned long long base = 0;
@@ -1438,12 +1499,30 @@ __global__ void __launch_bounds__(PTM_BLOCK, PTM_ATOM_BLOCKS_PER_SM)
     for (int k = 0; k < tile_atoms; k += 32) {
       const long long s = (long long)base + k + lane;
       const unsigned live = __ballot_sync(0xffffffffu, s < ntotal);
-      if (s < ntotal) {
-        const int f = frame_of(atom_off, nframes, s);
-        classify_atom<F64>(descs[f], (int)s, sm, tplw, live);
-      }
+      if (s < ntotal) fn(descs[frame_of(atom_off, nframes, s)], (int)s, live);
     }
   }
+}
+
+template <bool F64>
+__global__ void __launch_bounds__(PTM_BLOCK, PTM_ATOM_BLOCKS_PER_SM)
+    k_hulls_batch(const FrameDesc *__restrict__ descs, const int64_t *__restrict__ atom_off, int nframes,
+                  int64_t ntotal, int tile_atoms, unsigned long long *queue) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Scratch sm = scratch_rows(smem);
+  persistent_tiles(descs, atom_off, nframes, ntotal, tile_atoms, queue,
+                   [&](const FrameDesc &d, int s, unsigned live) { hull_atom<F64>(d, s, sm, live); });
+}
+
+template <bool F64>
+__global__ void __launch_bounds__(PTM_BLOCK, PTM_MATCH_BLOCKS_PER_SM)
+    k_match_batch(const FrameDesc *__restrict__ descs, const int64_t *__restrict__ atom_off, int nframes,
+                  int64_t ntotal, int tile_atoms, unsigned long long *queue) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Scratch sm = match_rows(smem);
+  const float4 *tplw = template_rows();
+  persistent_tiles(descs, atom_off, nframes, ntotal, tile_atoms, queue,
+                   [&](const FrameDesc &d, int s, unsigned live) { match_atom<F64, false>(d, s, sm, tplw, live); });
 }
 
 }  // namespace ptm

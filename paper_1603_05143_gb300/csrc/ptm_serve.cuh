@@ -77,7 +77,7 @@ size_t request_bytes(const ptm_frame &f) {
   const size_t n = (size_t)f.n_atoms;
   const size_t pos = n * 3 * (f.pos_dtype == PTM_F64 ? 8 : 4);
   const size_t ws = n * (f.pos_dtype == PTM_F64 ? 32 : 16) + 20 * n + 8 * (4 * n + 64) + sizeof(FrameDesc) + 4096 +
-                    n * 8 * PTM_KNN + 256 +
+                    n * 8 * PTM_KNN + 28 * n + 768 +
                     (f.ordering == PTM_ORDER_TOPOLOGICAL ? n * 4 + topo_side_bytes(n) + 1024 : 0);
   return pos + n + n * kOutBytesPerAtom + ws;
 }
@@ -166,7 +166,7 @@ ptm_status launch_batch(ptm_server *S, std::vector<Request *> &rs, int slot, InF
   b->f64 = P.f64; b->ntotal = P.ntotal; b->ncell = P.ncell;
   F->ws_bytes = batch_workspace_bytes(nf, P.ntotal, P.ncell, P.f64, P.topo);
   e = S->pool.alloc(F->ws_bytes, &F->ws);
-  for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(&b->ev[i], cudaEventDefault);
+  for (int i = 0; i < 5 && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(&b->ev[i], cudaEventDefault);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&F->done, cudaEventDisableTiming);
   if (e != cudaSuccess) { batch_free(b); delete F; return cuda_fail(ctx, e, "serve: workspace"); }
   b->block = F->ws;
