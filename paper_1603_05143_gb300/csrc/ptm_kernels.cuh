@@ -127,7 +127,7 @@ __device__ __forceinline__ void scan_cells(const FrameDesc &d, int s, typename R
         const int n0 = mx + wix, n1 = my + wiy, n2 = mz + wiz;
         T sx, sy, sz;
         contract_shift<F64>(d, n0, n1, n2, sx, sy, sz);
-#pragma unroll 1
+#pragma unroll 2
         for (int j = j0; j < j1; j++) {
           T xj, yj, zj;
           int idj;
@@ -921,7 +921,7 @@ __device__ __forceinline__ void metric_vectors(const FrameDesc &d, const Scratch
                                                typename RT<F64>::T xi, typename RT<F64>::T yi,
                                                typename RT<F64>::T zi) {
   typedef typename RT<F64>::T T;
-#pragma unroll 1
+#pragma unroll 7
   for (int t = 0; t < PTM_KNN; t++) {
     if (t >= cnt) { sm.NID(t) = -1; sm.DX(t) = sm.DY(t) = sm.DZ(t) = 0.f; continue; }
     T xj, yj, zj;
@@ -1019,7 +1019,7 @@ __device__ void hull_atom(const FrameDesc &d, int s, const Scratch &sm, unsigned
   int cnt = 0;
   unsigned hmask;
   {
-#pragma unroll 1
+#pragma unroll
     for (int t = 0; t < PTM_KNN; t++) {
       const int2 e = __ldg(d.nbr + (int64_t)t * d.n + (s - d.atom_offset));
       sm.NID(t) = e.x;
@@ -1071,7 +1071,7 @@ __device__ void hull_atom(const FrameDesc &d, int s, const Scratch &sm, unsigned
       // through the origin) are evaluated in FP64 out of line
       float emaxf = 0.f;
       uint32_t wide = 0;
-#pragma unroll 1
+#pragma unroll 7
       for (int t = 0; t < PTM_KNN; t++) {
         if (t >= cnt) continue;
         float xj, yj, zj;
@@ -1091,7 +1091,7 @@ __device__ void hull_atom(const FrameDesc &d, int s, const Scratch &sm, unsigned
         if (e64 > -100000) e = emaxf > 0.f ? max(e, e64) : e64;
       }
       const float sc = ldexpf(1.f, PTM_QBITS - e);
-#pragma unroll 1
+#pragma unroll
       for (int t = 0; t < PTM_KNN; t++) {
         if (t >= cnt || (wide >> t & 1)) continue;
         sm.Q(t, 0) = rintf(sm.Q(t, 0) * sc); sm.Q(t, 1) = rintf(sm.Q(t, 1) * sc); sm.Q(t, 2) = rintf(sm.Q(t, 2) * sc);
@@ -1159,7 +1159,7 @@ __device__ void match_atom(const FrameDesc &d, int s, const Scratch &sm, const f
   bst.lam12 = bst.ent12 >= 0 ? __ldg((const unsigned long long *)d.lam + d.n + sl) : 0;
   bst.lam14 = bst.ent14 >= 0 ? __ldg((const unsigned long long *)d.lam + 2 * d.n + sl) : 0;
   int cnt = 0;
-#pragma unroll 1
+#pragma unroll
   for (int t = 0; t < PTM_KNN; t++) {
     const int2 e = __ldg(d.nbr + (int64_t)t * d.n + sl);
     sm.NID(t) = e.x;
