@@ -83,6 +83,9 @@ def parse():
                          "frame: one large frame; serve: a Poisson stream of mixed-phase frames through the "
                          "continuous-batching server")
     ap.add_argument("--serve-requests", type=int, default=512, help="frames per offered load (serve mode)")
+    ap.add_argument("--serve-streams", type=int, default=0, help="serve mode: server streams (0: library default)")
+    ap.add_argument("--serve-outputs", default="all",
+                    help="serve mode: comma-separated outputs to copy back (e.g. structure,rmsd,quat), or all")
     ap.add_argument("--frame-stride", type=int, default=1,
                     help="batch mode: keep every k-th frame (smaller cases for profiler captures)")
     ap.add_argument("--no-autotune", action="store_true", help="batch mode: library default tuning")
@@ -452,7 +455,7 @@ def run_gpu(args, world, rank, local, pg):
             "latency_ms": {"p50": float(q[0]), "p99": float(q[1]), "best": float(min(times))},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "errors_vs_oracle": errors, "fp64_form": fp64_form,
-            "gpu_launches": (8 if args.ordering == "euclidean" else 9) * args.steps,
+            "gpu_launches": int(s0["kernel_launches"]) * args.steps,
             "fallbacks": {k: s0[k] for k in ("sos", "qcp_fp64", "tie_fp64", "knn_wide", "knn_fail", "internal",
                                              "topo_fp64")},
             "matched": s0["matched"], "candidates_per_atom": s0["candidates"] / s0["atoms"]}
@@ -671,7 +674,8 @@ def run_batch(args, world, rank, local, pg):
                  "clock_mhz": mhz, "source": cnt["source"]}
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": cnt["dram_bytes_per_atom"] * ntot if cnt else None,
-            "kernel": "k_hulls_batch + k_match_batch", "kernel_ms": kms_mean,
+            "kernel": "k_hulls_batch + k_match (own launches for frames of 65536 atoms or more) + k_match_batch",
+            "kernel_ms": kms_mean,
             "neighbour_kernel": "k_knn_batch", "neighbour_kernel_ms": statistics.mean(nbr_ms),
             "peak_note": f"FP32 peak derived: {sm_count(local)} SMs x 128 lanes x 2 flop x 2070 MHz",
             "fma_measured": fma, "frac_of_measured_fma": achieved / fma["fp32_tflops"],
@@ -700,7 +704,7 @@ def run_batch(args, world, rank, local, pg):
                            "frames at 0.8 of the end-to-end capacity, submit to completion"} if q else None,
             "serving": serving, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "errors_vs_oracle": errors, "fp64_form": fp64_form,
-            "gpu_launches": 8 * args.steps,
+            "gpu_launches": int(st["kernel_launches"]) * args.steps,
             "fallbacks": {k: st[k] for k in ("sos", "qcp_fp64", "tie_fp64", "knn_fp64", "knn_wide", "knn_fail",
                                              "internal")},
             "matched": st["matched"], "candidates_per_atom": st["candidates"] / st["atoms"]}
@@ -758,7 +762,7 @@ def run_serve(args, world, rank, local, pg):
     0.8-load arrivals in order (its latency counts from each arrival)."""
     import torch
     from paper_1603_05143_gb300 import PTM, Server, build, inputs as I
-    from paper_1603_05143_gb300.binding import allocate_outputs_host
+    from paper_1603_05143_gb300.binding import OUTPUT_NAMES, allocate_outputs_host
     build.build()
     torch.cuda.set_device(local)
     t_gen = time.perf_counter()
@@ -769,10 +773,11 @@ def run_serve(args, world, rank, local, pg):
         return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     hpos = [pin(f.positions) for f in pool]
     hsp = [pin(f.species) for f in pool]
-    outs = [allocate_outputs_host(f.n, pinned=True) for f in pool]
+    names = OUTPUT_NAMES if args.serve_outputs == "all" else tuple(args.serve_outputs.split(","))
+    outs = [allocate_outputs_host(f.n, outputs=names, pinned=True) for f in pool]
     ptm = PTM(local)
     tuning = None                 # library defaults: the stream's batches change from launch to launch
-    srv = Server(ptm, tuning=tuning)
+    srv = Server(ptm, tuning=tuning, streams=args.serve_streams)
     rng = I.rng_for(2024)
     mean_atoms = float(np.mean([f.n for f in pool]))
     n_req = args.serve_requests
@@ -792,26 +797,29 @@ def run_serve(args, world, rank, local, pg):
             if load == 0.8:
                 base_req = (times[: max(32, n_req // 4)], idx[: max(32, n_req // 4)])
     srv.close()
-    # the one-frame-per-launch FP64 form, fed the same arrivals (0.8 load) in order
-    p64 = PTM(local, precision="fp64")
-    for k in range(len(pool)):
-        p64.classify_host(hpos[k], pool[k].cell, pool[k].pbc, species=hsp[k], out=outs[k])
-    lat, t0 = [], time.perf_counter()
-    b_atoms = 0
-    for ti, k in zip(*base_req):
-        dt = t0 + ti - time.perf_counter()
-        if dt > 0:
-            time.sleep(dt)
-        f = pool[k]
-        p64.classify_host(hpos[k], f.cell, f.pbc, species=hsp[k], out=outs[k])
-        lat.append((time.perf_counter() - t0 - ti) * 1e3)
-        b_atoms += f.n
-    b_span = time.perf_counter() - t0
-    p64.close()
-    lat = np.array(lat)
-    base = {"frames": len(lat), "atoms": int(b_atoms), "achieved_atoms_per_s": b_atoms / b_span,
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "offered_load": 0.8, "form": "FP64 form (PTM_PREC_FP64), one ptm_classify_frame_host call per frame"}
+    base = None
+    if not args.no_fp64_form:
+        # the one-frame-per-launch FP64 form, fed the same arrivals (0.8 load) in order
+        p64 = PTM(local, precision="fp64")
+        for k in range(len(pool)):
+            p64.classify_host(hpos[k], pool[k].cell, pool[k].pbc, species=hsp[k], out=outs[k])
+        lat, t0 = [], time.perf_counter()
+        b_atoms = 0
+        for ti, k in zip(*base_req):
+            dt = t0 + ti - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            f = pool[k]
+            p64.classify_host(hpos[k], f.cell, f.pbc, species=hsp[k], out=outs[k])
+            lat.append((time.perf_counter() - t0 - ti) * 1e3)
+            b_atoms += f.n
+        b_span = time.perf_counter() - t0
+        p64.close()
+        lat = np.array(lat)
+        base = {"frames": len(lat), "atoms": int(b_atoms), "achieved_atoms_per_s": b_atoms / b_span,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "offered_load": 0.8, "form": "FP64 form (PTM_PREC_FP64), one ptm_classify_frame_host call per frame"}
+
     st = ptm.stats()
     ptm.close()
     if rank == 0:
@@ -824,10 +832,11 @@ def run_serve(args, world, rank, local, pg):
                            "min_frame": min(sizes), "max_frame": max(sizes), "mean_frame": mean_atoms,
                            "strain_max": 0.05, "sigma_A": 0.20, "hbm_budget": "half the free device memory",
                            "io": "host pinned positions/species in, all outputs out, per frame",
-                           "l2": "inputs larger than L2", "pool_gen_s": round(gen_s, 1), "tuning": tuning},
+                           "l2": "inputs larger than L2", "pool_gen_s": round(gen_s, 1), "tuning": tuning,
+                           "streams": args.serve_streams or 2, "outputs": list(names)},
                 "serving": {"capacity": cap, "loads": loads, "one_frame_per_launch": base},
                 "e2e": {"value": world * capacity, "unit": UNIT, "h2d_bytes_per_step": int(mean_atoms * 13),
-                        "d2h_bytes_per_step": int(mean_atoms * 122)},
+                        "d2h_bytes_per_step": int(np.mean([sum(a.nbytes for a in o.values()) for o in outs]))},
                 "clocks": clk.summary(),
                 "fallbacks": {k: st[k] for k in ("sos", "qcp_fp64", "tie_fp64", "knn_wide", "knn_fail", "internal")}}
         print(json.dumps(line), flush=True)

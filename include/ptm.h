@@ -145,8 +145,9 @@ typedef struct {
                                 QCP, outputs), after the neighbour lists */
   int64_t excluded;          /* atoms with a non-finite coordinate or more than 100 cell periods
                                 outside the cell: left unmatched and nobody's neighbour */
-  double match_kernel_ms;    /* device time of the matching kernel alone (QCP, selection,
+  double match_kernel_ms;    /* device time of the matching kernels alone (QCP, selection,
                                 outputs): the last part of classify_kernel_ms */
+  int64_t kernel_launches;   /* CUDA kernels the call launched */
 } ptm_stats;
 
 /* Create a context on options->device (NULL options: device 0, default budget).

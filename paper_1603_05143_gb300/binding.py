@@ -39,7 +39,7 @@ class ptm_stats(C.Structure):
                                          "tie_fp64", "internal", "candidates", "candidate_points")] + \
                [("pipeline_ms", C.c_double), ("atom_kernel_ms", C.c_double), ("topo_fp64", C.c_int64),
                 ("knn_fp64", C.c_int64), ("classify_kernel_ms", C.c_double), ("excluded", C.c_int64),
-                ("match_kernel_ms", C.c_double)]
+                ("match_kernel_ms", C.c_double), ("kernel_launches", C.c_int64)]
 
 
 class ptm_tuning(C.Structure):

@@ -34,6 +34,8 @@ struct ptm_context {
   int *cell_count = nullptr, *cell_start = nullptr, *block_sums = nullptr;
   int *dstat = nullptr;
   unsigned long long *counters = nullptr;
+  ShiftTables *tab = nullptr;      // the current frame's image shifts
+  int launches = 0;                // kernels the last call launched
   cudaStream_t last_stream = nullptr;
   cudaEvent_t ev[5] = {};   // call start, per-atom kernels start, end, k_hulls start, k_match start
   // host-buffer entry point
@@ -118,7 +120,7 @@ constexpr size_t max_cells(size_t n) { return 4 * n + 64; }
 // by the caller once its workspace exists) and its binning parameters.  Shared
 // by single frames, batches and the allocation-free entry.
 static ptm_status setup_frame(const ptm_frame *f, double cell_factor, FrameDesc *desc, BinParams *bp,
-                              size_t *ncell_out) {
+                              size_t *ncell_out, ShiftTables *tab) {
   if (!f || f->n_atoms < 1 || f->n_atoms >= (1ll << 31) || !f->positions) return PTM_ERR_INVALID_ARG;
   if (f->ordering != PTM_ORDER_EUCLIDEAN && f->ordering != PTM_ORDER_TOPOLOGICAL) return PTM_ERR_INVALID_ARG;
   if (f->pos_dtype != PTM_F32 && f->pos_dtype != PTM_F64) return PTM_ERR_INVALID_ARG;
@@ -179,9 +181,9 @@ static ptm_status setup_frame(const ptm_frame *f, double cell_factor, FrameDesc 
           volatile double t2 = (double)c * H[6 + k];
           volatile double t01 = t0 + t1;
           const double sh = t01 + t2;
-          desc->s64[i][k] = sh;
-          desc->s32[i][k] = (float)sh;
-          desc->slo[i][k] = (float)(sh - (double)(float)sh);
+          tab->s64[i][k] = sh;
+          tab->s32[i][k] = (float)sh;
+          tab->slo[i][k] = (float)(sh - (double)(float)sh);
         }
       }
   std::memset(bp, 0, sizeof(BinParams));
@@ -199,8 +201,9 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
   if (!f || !o) return PTM_ERR_INVALID_ARG;
   FrameDesc desc;
   BinParams bp;
+  ShiftTables tab;
   size_t ncell = 0;
-  ptm_status rs = setup_frame(f, 1.25, &desc, &bp, &ncell);
+  ptm_status rs = setup_frame(f, 1.25, &desc, &bp, &ncell, &tab);
   if (rs != PTM_OK) return rs;
   const int64_t n = f->n_atoms;
   const int f64 = desc.f64;
@@ -236,6 +239,7 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
   desc.nbr = ctx->nbr;
   desc.lam = ctx->lam;
   desc.ents = ctx->ents;
+  desc.tab = ctx->tab;
   bp.counters = ctx->counters;
 
   cudaGetLastError();   // launch errors are read below; drop any left by earlier calls
@@ -243,6 +247,7 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
   CK(cudaMemsetAsync(ctx->cell_count, 0, (ncell + 1) * sizeof(int), st));
   CK(cudaMemsetAsync(ctx->dstat, 0, 4 * sizeof(int), st));
   CK(cudaMemsetAsync(ctx->counters, 0, C_NCOUNTERS * sizeof(unsigned long long), st));
+  k_put_tables<<<1, 256, 0, st>>>(tab, ctx->tab);
   const int tb = 256;
   const unsigned gb = (unsigned)((n + tb - 1) / tb);
   k_bin<<<gb, tb, 0, st>>>(f->positions, bp, ctx->cell_count, ctx->atom_cell, ctx->atom_rank, ctx->atom_wrap,
@@ -293,6 +298,8 @@ static ptm_status enqueue_frame(ptm_context *ctx, const ptm_frame *f, const ptm_
   CK(cudaGetLastError());
   CK(cudaEventRecord(ctx->ev[2], st));
   ctx->last_stream = st;
+  // k_put_tables, k_bin, three scans, k_scatter, k_knn or k_topo + k_topo64, k_hulls, k_match
+  ctx->launches = topological ? 10 : 9;
   return PTM_OK;
 }
 
@@ -333,6 +340,7 @@ ptm_status ptm_create(const ptm_options *opt, ptm_context **out) {
     if ((e = cudaSetDevice(ctx->device)) != cudaSuccess) { rs = cuda_fail(ctx, e, "cudaSetDevice"); break; }
     if ((e = cudaMalloc(&ctx->dstat, 8 * sizeof(int))) != cudaSuccess) { rs = cuda_fail(ctx, e, "cudaMalloc"); break; }
     if ((e = cudaMalloc(&ctx->counters, C_NCOUNTERS * sizeof(unsigned long long))) != cudaSuccess) { rs = cuda_fail(ctx, e, "cudaMalloc"); break; }
+    if ((e = cudaMalloc(&ctx->tab, sizeof(ShiftTables))) != cudaSuccess) { rs = cuda_fail(ctx, e, "cudaMalloc"); break; }
     for (int i = 0; i < 5 && e == cudaSuccess; i++) e = cudaEventCreate(&ctx->ev[i]);
     if (e != cudaSuccess) { rs = cuda_fail(ctx, e, "cudaEventCreate"); break; }
     if ((e = cudaMemset(ctx->counters, 0, C_NCOUNTERS * sizeof(unsigned long long))) != cudaSuccess) { rs = cuda_fail(ctx, e, "cudaMemset"); break; }
@@ -372,7 +380,7 @@ ptm_status ptm_destroy(ptm_context *ctx) {
   cudaFree(ctx->sorted); cudaFree(ctx->sbin); cudaFree(ctx->wrapv);
   cudaFree(ctx->atom_cell); cudaFree(ctx->atom_rank); cudaFree(ctx->atom_wrap);
   cudaFree(ctx->cell_count); cudaFree(ctx->cell_start); cudaFree(ctx->block_sums);
-  cudaFree(ctx->dstat); cudaFree(ctx->counters);
+  cudaFree(ctx->dstat); cudaFree(ctx->counters); cudaFree(ctx->tab);
   for (int i = 0; i < 5; i++) if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   cudaFree(ctx->hpos); cudaFree(ctx->hspecies);
   cudaFree(ctx->o_struct); cudaFree(ctx->o_alloy); cudaFree(ctx->o_rmsd); cudaFree(ctx->o_scale);
@@ -467,6 +475,7 @@ ptm_status ptm_get_stats(ptm_context *ctx, ptm_stats *out) {
   out->atom_kernel_ms = t_atom;
   out->classify_kernel_ms = t_cls;
   out->match_kernel_ms = t_match;
+  out->kernel_launches = ctx->launches;
   out->candidates = (int64_t)c[C_CAND];
   out->candidate_points = (int64_t)c[C_CANDPTS];
   out->atoms = (int64_t)c[C_ATOMS];
@@ -494,6 +503,7 @@ struct ptm_batch {
   int tile_atoms = 32, blocks_per_sm = PTM_ATOM_BLOCKS_PER_SM;
   double cell_factor = 1.25;
   FrameDesc *d_descs = nullptr;
+  ShiftTables *d_tabs = nullptr;
   BinParams *d_bp = nullptr;
   int64_t *d_atom_off = nullptr;
   int *d_dstat = nullptr;
@@ -509,6 +519,12 @@ struct ptm_batch {
   int2 *nbr_buf = nullptr;        // per-frame segments of neighbour lists
   uint64_t *lam_buf = nullptr;    // per-frame segments of the k_hulls -> k_match state
   uint32_t *ents_buf = nullptr;
+  std::vector<FrameDesc> own;     // frames with a k_match launch of their own (PTM_MATCH_OWN_LAUNCH)
+  int nsmall = 0;                 // the other frames: one persistent k_match_batch over their atoms
+  int64_t small_atoms = 0;
+  int *d_small_frames = nullptr;
+  int64_t *d_small_off = nullptr;
+  int launches = 0;               // kernels the last enqueue launched
   int *topo_list = nullptr;       // atoms for the FP64 pass; [ntotal] = their count
   TopoSide *topo_side = nullptr;  // what the FP32 pass keeps for the FP64 pass
   void *block = nullptr;          // the workspace (one allocation, or a pool block when served)
@@ -586,14 +602,25 @@ static ptm_status batch_enqueue(ptm_batch *b, cudaStream_t st) {
     k_hulls_batch<false><<<grid, PTM_BLOCK, atom_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes,
                                                                      b->ntotal, b->tile_atoms, b->queue);
   CK(cudaEventRecordWithFlags(b->ev[4], st, rec));
-  const unsigned grid_m = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->nsm * PTM_MATCH_BLOCKS_PER_SM,
-                                                                         (tiles + 1) / 2));
-  if (b->f64)
-    k_match_batch<true><<<grid_m, PTM_BLOCK, match_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes,
-                                                                       b->ntotal, b->tile_atoms, b->queue + 1);
-  else
-    k_match_batch<false><<<grid_m, PTM_BLOCK, match_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes,
-                                                                        b->ntotal, b->tile_atoms, b->queue + 1);
+  for (const FrameDesc &hd : b->own) {
+    const unsigned g = (unsigned)((hd.n + PTM_BLOCK - 1) / PTM_BLOCK);
+    if (b->f64) k_match<true><<<g, PTM_BLOCK, match_smem_bytes(), st>>>(hd);
+    else k_match<false><<<g, PTM_BLOCK, match_smem_bytes(), st>>>(hd);
+  }
+  if (b->nsmall) {
+    const int64_t stiles = (b->small_atoms + b->tile_atoms - 1) / b->tile_atoms;
+    const unsigned grid_m = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)b->nsm * PTM_MATCH_BLOCKS_PER_SM, (stiles + 1) / 2));
+    if (b->f64)
+      k_match_batch<true><<<grid_m, PTM_BLOCK, match_smem_bytes(), st>>>(b->d_descs, b->d_small_off, b->d_small_frames,
+                                                                         b->nsmall, b->small_atoms, b->tile_atoms,
+                                                                         b->queue + 1);
+    else
+      k_match_batch<false><<<grid_m, PTM_BLOCK, match_smem_bytes(), st>>>(b->d_descs, b->d_small_off,
+                                                                          b->d_small_frames, b->nsmall, b->small_atoms,
+                                                                          b->tile_atoms, b->queue + 1);
+  }
+  b->launches = 7 + (b->topo ? 2 : 0) + (int)b->own.size() + (b->nsmall ? 1 : 0) - (b->topo == 2 ? 1 : 0);
   CK(cudaGetLastError());
   CK(cudaEventRecordWithFlags(b->ev[2], st, rec));
   return PTM_OK;
@@ -603,6 +630,7 @@ static ptm_status batch_enqueue(ptm_batch *b, cudaStream_t st) {
 // offsets of every frame, total atoms and cells.
 struct BatchPlan {
   std::vector<FrameDesc> hd;
+  std::vector<ShiftTables> tabs;
   std::vector<BinParams> hb;
   std::vector<int64_t> off;
   int64_t ntotal = 0;
@@ -611,17 +639,21 @@ struct BatchPlan {
   int topo = 0;                      // 0: no frame, 1: some, 2: every frame in the topological order
   int ntopo = 0;
   std::vector<int> ordering;
+  std::vector<int> small_frames;     // frames below PTM_MATCH_OWN_LAUNCH atoms ...
+  std::vector<int64_t> small_off;    // ... and the prefix sum of their sizes
+  int64_t small_atoms = 0;
 };
 
 static ptm_status batch_plan(int nframes, const ptm_frame *frames, double cell_factor, BatchPlan &P) {
   P.hd.resize(nframes);
+  P.tabs.resize(nframes);
   P.hb.resize(nframes);
   P.off.resize(nframes);
   P.ordering.resize(nframes);
   P.f64 = frames[0].pos_dtype == PTM_F64;
   for (int f = 0; f < nframes; f++) {
     size_t nc = 0;
-    ptm_status rs = setup_frame(&frames[f], cell_factor, &P.hd[f], &P.hb[f], &nc);
+    ptm_status rs = setup_frame(&frames[f], cell_factor, &P.hd[f], &P.hb[f], &nc, &P.tabs[f]);
     if (rs == PTM_OK && (frames[f].pos_dtype == PTM_F64) != (P.f64 != 0)) rs = PTM_ERR_INVALID_ARG;
     if (rs != PTM_OK) return rs;
     P.off[f] = P.ntotal;
@@ -635,6 +667,12 @@ static ptm_status batch_plan(int nframes, const ptm_frame *frames, double cell_f
     if (P.ntotal >= (1ll << 31) || P.ncell >= (1ull << 31)) return PTM_ERR_INVALID_ARG;
   }
   P.topo = P.ntopo == 0 ? 0 : (P.ntopo == nframes ? 2 : 1);
+  for (int f = 0; f < nframes; f++)
+    if (frames[f].n_atoms < PTM_MATCH_OWN_LAUNCH) {
+      P.small_frames.push_back(f);
+      P.small_off.push_back(P.small_atoms);
+      P.small_atoms += frames[f].n_atoms;
+    }
   return PTM_OK;
 }
 
@@ -644,7 +682,9 @@ static size_t batch_workspace_bytes(int nframes, int64_t ntotal, size_t ncell, i
   const size_t nblk = (ncell + 1 + 2 * SCAN_BLOCK - 1) / (2 * SCAN_BLOCK) + 1;
   const size_t tb = sizeof(int2) * PTM_KNN * n + 28 * n + 3 * 256 +
                     (topo ? 4 * (n + 1) + topo_side_bytes(n) + 2 * 256 : 0);
-  return (sizeof(FrameDesc) + sizeof(BinParams) + sizeof(int64_t) + 16) * nframes + rec * n + 20 * n +
+  return (sizeof(FrameDesc) + sizeof(ShiftTables) + sizeof(BinParams) + 2 * sizeof(int64_t) + sizeof(int) + 16) *
+             nframes + 3 * 256 +
+         rec * n + 20 * n +
          8 * (ncell + 1) + 4 * nblk + 4 + 16 + 8 * C_NCOUNTERS + 16 * 256 + tb;
 }
 
@@ -657,7 +697,10 @@ static void batch_layout(ptm_batch *b, unsigned char *base, BatchPlan &P, const 
   const size_t nblk = (nc + 1 + 2 * SCAN_BLOCK - 1) / (2 * SCAN_BLOCK) + 1;
   const int nf = b->nframes;
   b->d_descs = (FrameDesc *)take(sizeof(FrameDesc) * nf);
+  b->d_tabs = (ShiftTables *)take(sizeof(ShiftTables) * nf);
   b->d_bp = (BinParams *)take(sizeof(BinParams) * nf);
+  b->d_small_frames = (int *)take(sizeof(int) * nf);
+  b->d_small_off = (int64_t *)take(sizeof(int64_t) * nf);
   b->d_atom_off = (int64_t *)take(sizeof(int64_t) * nf);
   b->d_dstat = (int *)take(sizeof(int) * 4 * nf);
   b->sorted = take((P.f64 ? sizeof(Atom64) : sizeof(float4)) * n);
@@ -679,6 +722,7 @@ static void batch_layout(ptm_batch *b, unsigned char *base, BatchPlan &P, const 
     P.hd[f].nbr = b->nbr_buf + PTM_KNN * P.off[f];
     P.hd[f].lam = b->lam_buf + 3 * P.off[f];
     P.hd[f].ents = b->ents_buf + P.off[f];
+    P.hd[f].tab = b->d_tabs + f;
     P.hd[f].sorted = b->sorted;
     P.hd[f].sbin = b->sbin;
     P.hd[f].cell_start = b->cell_start + P.hb[f].cell_off;
@@ -689,6 +733,10 @@ static void batch_layout(ptm_batch *b, unsigned char *base, BatchPlan &P, const 
     P.hb[f].dstat = b->d_dstat + 4 * f;
     P.hb[f].counters = b->counters;
   }
+  b->own.clear();
+  for (int f = 0; f < nf; f++) if (P.hd[f].n >= PTM_MATCH_OWN_LAUNCH) b->own.push_back(P.hd[f]);
+  b->nsmall = (int)P.small_frames.size();
+  b->small_atoms = P.small_atoms;
 }
 
 extern "C" ptm_status ptm_batch_create(ptm_context *ctx, int nframes, const ptm_frame *frames, const ptm_outputs *outs,
@@ -718,6 +766,11 @@ extern "C" ptm_status ptm_batch_create(ptm_context *ctx, int nframes, const ptm_
   if (e != cudaSuccess) { rs = cuda_fail(ctx, e, "ptm_batch_create"); batch_free(b); return rs; }
   batch_layout(b, (unsigned char *)b->block, P, outs);
   if ((e = cudaMemcpy(b->d_descs, P.hd.data(), sizeof(FrameDesc) * nframes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(b->d_tabs, P.tabs.data(), sizeof(ShiftTables) * nframes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (b->nsmall && (e = cudaMemcpy(b->d_small_frames, P.small_frames.data(), sizeof(int) * b->nsmall,
+                                    cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (b->nsmall && (e = cudaMemcpy(b->d_small_off, P.small_off.data(), sizeof(int64_t) * b->nsmall,
+                                    cudaMemcpyHostToDevice)) != cudaSuccess) ||
       (e = cudaMemcpy(b->d_bp, P.hb.data(), sizeof(BinParams) * nframes, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(b->d_atom_off, P.off.data(), sizeof(int64_t) * nframes, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemset(b->counters, 0, 8 * C_NCOUNTERS)) != cudaSuccess) {
@@ -774,6 +827,7 @@ extern "C" ptm_status ptm_batch_stats(ptm_batch *b, ptm_stats *out) {
   if (cudaEventElapsedTime(&t_match, b->ev[4], b->ev[2]) != cudaSuccess) t_match = -1.f;
   out->classify_kernel_ms = t_cls;
   out->match_kernel_ms = t_match;
+  out->kernel_launches = b->launches;
   cudaGetLastError();
   out->atoms = (int64_t)c[C_ATOMS]; out->matched = (int64_t)c[C_MATCHED]; out->knn_wide = (int64_t)c[C_KNN_WIDE];
   out->knn_fail = (int64_t)c[C_KNN_FAIL]; out->sos = (int64_t)c[C_SOS]; out->qcp_fp64 = (int64_t)c[C_QCP64];
@@ -868,7 +922,8 @@ struct NoallocLayout {                  // byte offsets inside the static array
   static constexpr size_t nbr = (block_sums + sizeof(int) * kNoallocScanBlocks + 15) / 16 * 16;
   static constexpr size_t lam = nbr + sizeof(int2) * PTM_KNN * kNoallocAtoms;
   static constexpr size_t ents = lam + sizeof(uint64_t) * 3 * kNoallocAtoms;
-  static constexpr size_t dstat = ents + sizeof(uint32_t) * kNoallocAtoms;
+  static constexpr size_t tab = (ents + sizeof(uint32_t) * kNoallocAtoms + 15) / 16 * 16;
+  static constexpr size_t dstat = tab + sizeof(ShiftTables);
   static constexpr size_t counters = ((dstat + sizeof(int) * 8) + 7) / 8 * 8;
   static constexpr size_t total = counters + sizeof(unsigned long long) * C_NCOUNTERS;
 };
@@ -928,8 +983,9 @@ extern "C" ptm_status ptm_classify_frame_noalloc(const ptm_frame *f, const ptm_o
   if (f->ordering != PTM_ORDER_EUCLIDEAN) return PTM_ERR_INVALID_ARG;
   FrameDesc desc;
   BinParams bp;
+  ShiftTables tab;
   size_t ncell = 0;
-  ptm_status rs = setup_frame(f, 1.25, &desc, &bp, &ncell);
+  ptm_status rs = setup_frame(f, 1.25, &desc, &bp, &ncell, &tab);
   if (rs != PTM_OK) return rs;
   if (ncell > kNoallocCells) return PTM_ERR_INVALID_ARG;      // cannot happen: setup_frame caps the grid
   cudaStream_t st = (cudaStream_t)stream;
@@ -949,6 +1005,7 @@ extern "C" ptm_status ptm_classify_frame_noalloc(const ptm_frame *f, const ptm_o
   desc.nbr = (int2 *)(base + NoallocLayout::nbr);
   desc.lam = (uint64_t *)(base + NoallocLayout::lam);
   desc.ents = (uint32_t *)(base + NoallocLayout::ents);
+  desc.tab = (ShiftTables *)(base + NoallocLayout::tab);
   set_outputs(&desc, o);
   desc.dstat = dstat;
   desc.counters = counters;
@@ -961,6 +1018,7 @@ extern "C" ptm_status ptm_classify_frame_noalloc(const ptm_frame *f, const ptm_o
     cudaGetLastError();
     return PTM_ERR_CUDA;
   }
+  k_put_tables<<<1, 256, 0, st>>>(tab, (ShiftTables *)desc.tab);
   const int tb = 256;
   const unsigned gb = (unsigned)((n + tb - 1) / tb);
   k_bin<<<gb, tb, 0, st>>>(f->positions, bp, cell_count, atom_cell, atom_rank, atom_wrap, dstat);

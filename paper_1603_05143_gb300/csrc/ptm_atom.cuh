@@ -30,6 +30,15 @@ namespace ptm {
 
 struct Atom64 { double x, y, z; long long id; };
 
+// Shift n.H of each lattice image n in [-2,2]^3, in device memory beside the
+// frame's descriptor: the FP64 value, its FP32 rounding and the FP32 rounding of
+// the remainder (compensated neighbour vectors).
+struct ShiftTables {
+  float s32[125][3];
+  float slo[125][3];
+  double s64[125][3];
+};
+
 // Device-resident description of one frame (filled by the host).
 struct FrameDesc {
   const void *sorted;          // float4 (x, y, z, id bits) or Atom64, cell-sorted (ids are frame-local)
@@ -47,9 +56,7 @@ struct FrameDesc {
   float min_cell_width;        // smallest perpendicular cell width (Angstrom)
   float smax;                  // bound on the length of an image shift n.H with |n_r| <= 1 (periodic r)
   double H[9];                 // rows = cell vectors
-  float s32[125][3];           // shift of image n in [-2,2]^3, FP64 value rounded to FP32
-  float slo[125][3];           // FP64 shift minus s32 (compensated neighbour vectors)
-  double s64[125][3];          // FP64 shift
+  const struct ShiftTables *tab;   // shifts of the images n in [-2,2]^3 (device memory)
   // outputs (by atom id)
   int8_t *structure;
   int8_t *alloy;
@@ -133,8 +140,9 @@ __device__ __forceinline__ void shift_f32(const FrameDesc &d, int a, int b, int 
                                           float &sz, float &lx, float &ly, float &lz) {
   if (a >= -2 && a <= 2 && b >= -2 && b <= 2 && c >= -2 && c <= 2) {
     int i = (a + 2) * 25 + (b + 2) * 5 + (c + 2);
-    sx = d.s32[i][0]; sy = d.s32[i][1]; sz = d.s32[i][2];
-    lx = d.slo[i][0]; ly = d.slo[i][1]; lz = d.slo[i][2];
+    const ShiftTables &t = *d.tab;
+    sx = t.s32[i][0]; sy = t.s32[i][1]; sz = t.s32[i][2];
+    lx = t.slo[i][0]; ly = t.slo[i][1]; lz = t.slo[i][2];
   } else {
     double s[3];
     for (int k = 0; k < 3; k++)
@@ -149,7 +157,8 @@ __device__ __forceinline__ void shift_f64(const FrameDesc &d, int a, int b, int 
                                           double &sz) {
   if (a >= -2 && a <= 2 && b >= -2 && b <= 2 && c >= -2 && c <= 2) {
     int i = (a + 2) * 25 + (b + 2) * 5 + (c + 2);
-    sx = d.s64[i][0]; sy = d.s64[i][1]; sz = d.s64[i][2];
+    const ShiftTables &t = *d.tab;
+    sx = t.s64[i][0]; sy = t.s64[i][1]; sz = t.s64[i][2];
   } else {
     double s[3];
     for (int k = 0; k < 3; k++)

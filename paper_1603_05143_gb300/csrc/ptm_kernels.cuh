@@ -1192,6 +1192,14 @@ __device__ void match_atom(const FrameDesc &d, int s, const Scratch &sm, const f
 }
 
 // ------------------------------------------------------------------ kernels
+// Copies a frame's shift tables, passed by value, into device memory: stream
+// ordered, so back-to-back asynchronous calls never share a host staging buffer.
+__global__ void k_put_tables(const __grid_constant__ ShiftTables t, ShiftTables *out) {
+  const float *src = reinterpret_cast<const float *>(&t);
+  float *dst = reinterpret_cast<float *>(out);
+  for (int i = threadIdx.x; i < (int)(sizeof(ShiftTables) / 4); i += blockDim.x) dst[i] = src[i];
+}
+
 struct BinParams {
   float Hinv[9];     // fractional = x . Hinv
   float W[3];        // perpendicular cell widths
@@ -1403,8 +1411,13 @@ constexpr size_t match_smem_bytes() { return (size_t)PTM_BLOCK * MATCH_WORDS * 4
 // driver reserves per block) fits 228 KB of shared memory, and 7 x 64 threads x
 // 146 registers the register file.
 #define PTM_ATOM_BLOCKS_PER_SM 7
-// k_match: 12 x (70 words x 64 threads + 1 KB) fits, at up to 85 registers
-#define PTM_MATCH_BLOCKS_PER_SM 12
+// k_match: 11 x (70 words x 64 threads + two descriptor copies + 1 KB) fits, at up
+// to 93 registers
+#define PTM_MATCH_BLOCKS_PER_SM 11
+// Frames of a batch with at least this many atoms get a k_match launch of their
+// own: a descriptor in the kernel parameters costs no loads, one in memory adds
+// one before every address (k_match ran 35 % slower on a 2^20-atom frame)
+#define PTM_MATCH_OWN_LAUNCH 65536
 
 // Scratch rows in a block's dynamic shared memory (row layout of Scratch).
 __device__ __forceinline__ Scratch scratch_rows(unsigned char *smem) {
@@ -1452,10 +1465,10 @@ __global__ void __launch_bounds__(PTM_BLOCK, PTM_MATCH_BLOCKS_PER_SM) k_match(co
   extern __shared__ __align__(16) unsigned char smem[];
   const Scratch sm = match_rows(smem);
   const float4 *tplw = template_rows();
-  const int64_t s = (int64_t)blockIdx.x * PTM_BLOCK + threadIdx.x;
+  const int64_t s = (int64_t)blockIdx.x * PTM_BLOCK + threadIdx.x;     // frame-local slot
   const unsigned live = __ballot_sync(0xffffffffu, s < d.n);
   if (s >= d.n) return;
-  match_atom<F64, P64>(d, (int)s, sm, tplw, live);
+  match_atom<F64, P64>(d, (int)(s + d.atom_offset), sm, tplw, live);
 }
 
 // Neighbour lists of one frame (Euclidean order), one thread per atom.
@@ -1482,24 +1495,54 @@ __global__ void __launch_bounds__(PTM_KNN_BLOCK, PTM_KNN_BLOCKS_PER_SM)
 }
 
 // Persistent per-atom passes over a batch: every warp pulls tiles of
-// tile_atoms (a multiple of 32) consecutive sorted slots from a global queue
-// until the batch is exhausted, so uneven frames balance across the GPU and no
-// warp waits for the other warp of its block; each slot finds its frame by a
-// binary search over the frames' first slots.  fn(desc, slot, live).
+// tile_atoms (a multiple of 32) consecutive slots from a global queue until the
+// batch is exhausted, so uneven frames balance across the GPU and no warp waits
+// for the other warp of its block.  The slots are the batch's sorted slots, or
+// with a map (map_frames, map_off, nmap) a virtual numbering of the listed
+// frames' atoms only: virtual slot v of listed frame k = frame_of(map_off, ...)
+// is sorted slot atom_offset + v - map_off[k] of frame map_frames[k].  With
+// `head` (this warp's slot of shared memory) a tile whose slots all belong to
+// one frame reads that frame's descriptor from a shared copy, made when the
+// frame changes.  fn(desc, slot, live).
 template <typename Fn>
 __device__ __forceinline__ void persistent_tiles(const FrameDesc *__restrict__ descs,
                                                  const int64_t *__restrict__ atom_off, int nframes, int64_t ntotal,
-                                                 int tile_atoms, unsigned long long *queue, Fn &&fn) {
+                                                 const int *__restrict__ map_frames, int tile_atoms,
+                                                 unsigned long long *queue, FrameDesc *head, Fn &&fn) {
   const int lane = threadIdx.x & 31;
+  int cached = -1;
   for (;;) {
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(queue, (unsigned long long)tile_atoms);
     base = __shfl_sync(0xffffffffu, base, 0);
     if ((long long)base >= ntotal) break;
     for (int k = 0; k < tile_atoms; k += 32) {
-      const long long s = (long long)base + k + lane;
+      long long s = (long long)base + k + lane;
       const unsigned live = __ballot_sync(0xffffffffu, s < ntotal);
-      if (s < ntotal) fn(descs[frame_of(atom_off, nframes, s)], (int)s, live);
+      int f = -1;
+      if (s < ntotal) {
+        f = frame_of(atom_off, nframes, s);
+        if (map_frames) {
+          s += (long long)__ldg((const long long *)&descs[__ldg(map_frames + f)].atom_offset) -
+               (long long)__ldg((const long long *)atom_off + f);
+          f = __ldg(map_frames + f);
+        }
+      }
+      const FrameDesc *dp = descs + f;
+      if (head) {
+        const int f0 = __shfl_sync(0xffffffffu, f, 0);          // lane 0 is live whenever any lane is
+        if (__all_sync(0xffffffffu, f == f0 || !(live >> lane & 1))) {
+          if (f0 != cached) {
+            const int *src = reinterpret_cast<const int *>(descs + f0);
+            int *dst = reinterpret_cast<int *>(head);
+            for (int w = lane; w < (int)(sizeof(FrameDesc) / 4); w += 32) dst[w] = __ldg(src + w);
+            __syncwarp();
+            cached = f0;
+          }
+          dp = head;
+        }
+      }
+      if (live >> lane & 1) fn(*dp, (int)s, live);
     }
   }
 }
@@ -1510,18 +1553,23 @@ __global__ void __launch_bounds__(PTM_BLOCK, PTM_ATOM_BLOCKS_PER_SM)
                   int64_t ntotal, int tile_atoms, unsigned long long *queue) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Scratch sm = scratch_rows(smem);
-  persistent_tiles(descs, atom_off, nframes, ntotal, tile_atoms, queue,
+  persistent_tiles(descs, atom_off, nframes, ntotal, nullptr, tile_atoms, queue, nullptr,
                    [&](const FrameDesc &d, int s, unsigned live) { hull_atom<F64>(d, s, sm, live); });
 }
 
+// k_match over the atoms of the batch's smaller frames (the larger ones get a
+// k_match launch each, with their descriptor in the kernel parameters): map_off
+// is the prefix sum of the listed frames' sizes, map_frames their indices.
 template <bool F64>
 __global__ void __launch_bounds__(PTM_BLOCK, PTM_MATCH_BLOCKS_PER_SM)
-    k_match_batch(const FrameDesc *__restrict__ descs, const int64_t *__restrict__ atom_off, int nframes,
-                  int64_t ntotal, int tile_atoms, unsigned long long *queue) {
+    k_match_batch(const FrameDesc *__restrict__ descs, const int64_t *__restrict__ map_off,
+                  const int *__restrict__ map_frames, int nmap, int64_t nslots, int tile_atoms,
+                  unsigned long long *queue) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Scratch sm = match_rows(smem);
   const float4 *tplw = template_rows();
-  persistent_tiles(descs, atom_off, nframes, ntotal, tile_atoms, queue,
+  __shared__ FrameDesc heads[PTM_BLOCK / 32];
+  persistent_tiles(descs, map_off, nmap, nslots, map_frames, tile_atoms, queue, &heads[threadIdx.x >> 5],
                    [&](const FrameDesc &d, int s, unsigned live) { match_atom<F64, false>(d, s, sm, tplw, live); });
 }
 

@@ -76,7 +76,8 @@ constexpr size_t kOutBytesPerAtom = 1 + 1 + 4 + 4 + 16 + 36 + 60 + 4 + 12;
 size_t request_bytes(const ptm_frame &f) {
   const size_t n = (size_t)f.n_atoms;
   const size_t pos = n * 3 * (f.pos_dtype == PTM_F64 ? 8 : 4);
-  const size_t ws = n * (f.pos_dtype == PTM_F64 ? 32 : 16) + 20 * n + 8 * (4 * n + 64) + sizeof(FrameDesc) + 4096 +
+  const size_t ws = n * (f.pos_dtype == PTM_F64 ? 32 : 16) + 20 * n + 8 * (4 * n + 64) + sizeof(FrameDesc) +
+                    sizeof(ShiftTables) + 4096 +
                     n * 8 * PTM_KNN + 28 * n + 768 +
                     (f.ordering == PTM_ORDER_TOPOLOGICAL ? n * 4 + topo_side_bytes(n) + 1024 : 0);
   return pos + n + n * kOutBytesPerAtom + ws;
@@ -172,15 +173,27 @@ ptm_status launch_batch(ptm_server *S, std::vector<Request *> &rs, int slot, InF
   b->block = F->ws;
   batch_layout(b, (unsigned char *)F->ws, P, outs.data());
   // descriptors through this slot's pinned staging (free: the slot's previous batch is done)
-  const size_t need = sizeof(FrameDesc) * nf + sizeof(BinParams) * nf + sizeof(int64_t) * nf;
+  const size_t need = (sizeof(FrameDesc) + sizeof(ShiftTables) + sizeof(BinParams) + 2 * sizeof(int64_t) +
+                       sizeof(int)) * nf;
   unsigned char *hs = (unsigned char *)S->staging[slot];
   if (need > S->staging_bytes) { batch_free(b); delete F; return PTM_ERR_INVALID_ARG; }
+  unsigned char *h_tab = hs + sizeof(FrameDesc) * nf, *h_bp = h_tab + sizeof(ShiftTables) * nf;
+  unsigned char *h_off = h_bp + sizeof(BinParams) * nf;
+  unsigned char *h_soff = h_off + sizeof(int64_t) * nf, *h_sfr = h_soff + sizeof(int64_t) * nf;
   std::memcpy(hs, P.hd.data(), sizeof(FrameDesc) * nf);
-  std::memcpy(hs + sizeof(FrameDesc) * nf, P.hb.data(), sizeof(BinParams) * nf);
-  std::memcpy(hs + (sizeof(FrameDesc) + sizeof(BinParams)) * nf, P.off.data(), sizeof(int64_t) * nf);
+  std::memcpy(h_tab, P.tabs.data(), sizeof(ShiftTables) * nf);
+  std::memcpy(h_bp, P.hb.data(), sizeof(BinParams) * nf);
+  std::memcpy(h_off, P.off.data(), sizeof(int64_t) * nf);
+  std::memcpy(h_soff, P.small_off.data(), sizeof(int64_t) * P.small_off.size());
+  std::memcpy(h_sfr, P.small_frames.data(), sizeof(int) * P.small_frames.size());
   e = cudaMemcpyAsync(b->d_descs, hs, sizeof(FrameDesc) * nf, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_bp, hs + sizeof(FrameDesc) * nf, sizeof(BinParams) * nf, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_atom_off, hs + (sizeof(FrameDesc) + sizeof(BinParams)) * nf, sizeof(int64_t) * nf, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_tabs, h_tab, sizeof(ShiftTables) * nf, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_bp, h_bp, sizeof(BinParams) * nf, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_atom_off, h_off, sizeof(int64_t) * nf, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && b->nsmall)
+    e = cudaMemcpyAsync(b->d_small_off, h_soff, sizeof(int64_t) * b->nsmall, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && b->nsmall)
+    e = cudaMemcpyAsync(b->d_small_frames, h_sfr, sizeof(int) * b->nsmall, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) { batch_free(b); delete F; return cuda_fail(ctx, e, "serve: descriptors"); }
   rsn = batch_enqueue(b, st);
   if (rsn != PTM_OK) { batch_free(b); delete F; return rsn; }
@@ -333,7 +346,8 @@ extern "C" ptm_status ptm_server_create(ptm_context *ctx, const ptm_server_optio
   if (opt && opt->streams > 0) S->nslots = std::min(opt->streams, 8);
   if (opt && opt->max_batch_atoms > 0) S->max_batch_atoms = opt->max_batch_atoms;
   if (opt) S->tuning = opt->tuning;
-  S->staging_bytes = (sizeof(FrameDesc) + sizeof(BinParams) + sizeof(int64_t)) * (size_t)S->max_batch;
+  S->staging_bytes = (sizeof(FrameDesc) + sizeof(ShiftTables) + sizeof(BinParams) + 2 * sizeof(int64_t) +
+                      sizeof(int)) * (size_t)S->max_batch;
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < S->nslots && e == cudaSuccess; i++) {
     cudaStream_t st = nullptr;
