@@ -516,9 +516,11 @@ __device__ void score_candidates(const FrameDesc &d, const Scratch &sm, const fl
   if (scored) { count(d, C_CAND, scored); count(d, C_CANDPTS, (unsigned long long)points); }
 }
 
-// Canonical correspondence (reading R12): nibble 15 - s holds the neighbour rank
-// of template slot s; the orbit minimum under the template rotation group, read
-// slot 1 first, is the numerically smallest packing.
+// Canonical correspondence: the paper leaves open which of the equivalent
+// correspondences of a match is reported; this library reports the smallest
+// member of its orbit under the template's rotation group.  Nibble 15 - s holds
+// the neighbour rank of template slot s, so the orbit minimum, read slot 1
+// first, is the numerically smallest packing.
 __device__ uint64_t canonical_corr(int S, int K, uint64_t corr) {
   uint64_t best = ~0ull;
   const int g0 = ptm_group_off[S], g1 = ptm_group_off[S + 1];
@@ -543,8 +545,9 @@ __device__ __forceinline__ uint64_t corr_of(int K, uint64_t lab, uint64_t cand) 
 
 
 // FP64 selection over every candidate of the matched snapshots (Algorithm 1,
-// inner loops), from FP64 neighbour vectors: ties within PTM_TIE go to the
-// earlier template, then to the smaller canonical correspondence (reading R13).
+// inner loops), from FP64 neighbour vectors.  Exact ties, which the paper does
+// not resolve, are read as: RMSD^2 within PTM_TIE goes to the earlier template
+// (SC, FCC, HCP, ICO, BCC), then to the smaller canonical correspondence.
 // Returns (K << 16) | candidate index, or -1; *scored counts the candidates.
 __device__ __noinline__ int select_fp64(const FrameDesc &d, const Best &bst, const double (&ex)[PTM_KNN],
                                         const double (&ey)[PTM_KNN], const double (&ez)[PTM_KNN], int *scored) {
