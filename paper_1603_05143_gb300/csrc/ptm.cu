@@ -886,8 +886,9 @@ extern "C" ptm_status ptm_autotune_batch(ptm_context *ctx, int nframes, const pt
           if (rs != PTM_OK) break;
           if (r >= 1) {
             float m = 0.f;
-            if (cudaEventSynchronize(b->ev[2]) != cudaSuccess ||
-                cudaEventElapsedTime(&m, b->ev[0], b->ev[2]) != cudaSuccess) { rs = PTM_ERR_CUDA; break; }
+            cudaError_t e = cudaEventSynchronize(b->ev[2]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&m, b->ev[0], b->ev[2]);
+            if (e != cudaSuccess) { rs = cuda_fail(ctx, e, "ptm_autotune_batch"); break; }
             ms = std::min(ms, m);
           }
         }

@@ -1522,6 +1522,7 @@ __device__ __forceinline__ void persistent_tiles(const FrameDesc *__restrict__ d
     for (int k = 0; k < tile_atoms; k += 32) {
       long long s = (long long)base + k + lane;
       const unsigned live = __ballot_sync(0xffffffffu, s < ntotal);
+      if (!live) break;                  // the rest of a tile past the end (warp-uniform)
       int f = -1;
       if (s < ntotal) {
         f = frame_of(atom_off, nframes, s);

@@ -54,6 +54,32 @@ def test_batch_equals_single_frames(ptm):
     b.close()
 
 
+@pytest.mark.parametrize("tile", [32, 64, 96])
+def test_batch_with_large_frames_and_tiles(ptm, tile):
+    """Frames of 65536 atoms or more take their own matching launch, the
+    others the shared persistent one; tiles of 64 and 96 slots leave chunks
+    past the end of the atoms: every frame still equals its single-frame
+    result."""
+    import torch
+    frames = I.config_batch(seed=12, n_frames=5, n_min=300, n_max=3000)
+    frames.insert(2, I.crystal("bcc", I.A_BCC_FE, 33, sigma=0.1, seed=4, dtype=np.float32,
+                               rotation=I.random_rotation(I.rng_for(6))))        # 71874 atoms
+    frames.append(I.crystal("fcc", I.A_FCC_CU, 26, sigma=0.12, seed=5, dtype=np.float32))   # 70304 atoms
+    dev = _dev(frames)
+    b = ptm.batch(dev, tuning={"tile_atoms": tile})
+    b.run()
+    torch.cuda.synchronize()
+    st = b.stats()
+    assert st["internal"] == 0 and st["atoms"] == sum(f.n for f in frames)
+    assert st["kernel_launches"] == 8 + 2                 # two frames with their own k_match
+    for f, d, o in zip(frames, dev, b.outputs):
+        ref = ptm.classify(d["positions"], f.cell, f.pbc, species=d["species"])
+        torch.cuda.synchronize()
+        for k in ref:
+            assert torch.equal(ref[k], o[k]), (f.name, k)
+    b.close()
+
+
 def test_batch_graph_replay_follows_positions(ptm):
     import torch
     frames = I.config_batch(seed=7, n_frames=6, n_min=500, n_max=5000)
