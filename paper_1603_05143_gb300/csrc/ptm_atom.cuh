@@ -135,6 +135,13 @@ __device__ __forceinline__ void img_unpack(int p, int &a, int &b, int &c) {
   a = ((p >> 16) & 255) - 128; b = ((p >> 8) & 255) - 128; c = (p & 255) - 128;
 }
 
+// Shift n.H in FP64 of an image outside the tables (out of line: rare).
+__device__ __noinline__ void shift_far(const FrameDesc &d, int a, int b, int c, double (&s)[3]) {
+  for (int k = 0; k < 3; k++)
+    s[k] = __dadd_rn(__dadd_rn(__dmul_rn((double)a, d.H[k]), __dmul_rn((double)b, d.H[3 + k])),
+                     __dmul_rn((double)c, d.H[6 + k]));
+}
+
 // Shift of lattice image n, rounded from FP64 exactly as the contract states.
 __device__ __forceinline__ void shift_f32(const FrameDesc &d, int a, int b, int c, float &sx, float &sy,
                                           float &sz, float &lx, float &ly, float &lz) {
@@ -145,9 +152,7 @@ __device__ __forceinline__ void shift_f32(const FrameDesc &d, int a, int b, int 
     lx = t.slo[i][0]; ly = t.slo[i][1]; lz = t.slo[i][2];
   } else {
     double s[3];
-    for (int k = 0; k < 3; k++)
-      s[k] = __dadd_rn(__dadd_rn(__dmul_rn((double)a, d.H[k]), __dmul_rn((double)b, d.H[3 + k])),
-                       __dmul_rn((double)c, d.H[6 + k]));
+    shift_far(d, a, b, c, s);
     sx = (float)s[0]; sy = (float)s[1]; sz = (float)s[2];
     lx = (float)(s[0] - (double)sx); ly = (float)(s[1] - (double)sy); lz = (float)(s[2] - (double)sz);
   }
@@ -161,9 +166,7 @@ __device__ __forceinline__ void shift_f64(const FrameDesc &d, int a, int b, int 
     sx = t.s64[i][0]; sy = t.s64[i][1]; sz = t.s64[i][2];
   } else {
     double s[3];
-    for (int k = 0; k < 3; k++)
-      s[k] = __dadd_rn(__dadd_rn(__dmul_rn((double)a, d.H[k]), __dmul_rn((double)b, d.H[3 + k])),
-                       __dmul_rn((double)c, d.H[6 + k]));
+    shift_far(d, a, b, c, s);
     sx = s[0]; sy = s[1]; sz = s[2];
   }
 }
