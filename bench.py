@@ -46,27 +46,15 @@ FLOP_PER_CAND_POINT = 18.0
 FLOP_PER_CAND = 232.0 - 18.0
 FLOP_PER_MATCHED = 2000.0
 FLOP_PER_ATOM = 126.0
-# Algorithmic DRAM bytes of the classification kernel (k_atoms) per atom: its
-# cell-sorted record (16 B), its neighbour list (14 x 8 B), the species byte
-# and the outputs (1 + 1 + 4 + 4 + 16 + 36 + 60 B); neighbours' records are
-# re-read from cache.
-BYTES_PER_ATOM = 16 + 112 + 1 + 122
+# Algorithmic DRAM bytes per atom of the per-atom pipeline: its cell-sorted
+# record (16 B), the species byte and the outputs (1 + 1 + 4 + 4 + 16 + 36 +
+# 60 B).  The neighbour list (14 x 8 B, written by the neighbour kernel and read
+# by the two classification kernels) and the hull results (28 B) are
+# intermediates: they show up in the measured traffic, not here.
+BYTES_PER_ATOM = 16 + 1 + 122
 WORKLOAD = "polycrystal-1048576"
-
-
-def measured_traffic():
-    """DRAM bytes per k_atoms launch from the committed ncu capture, or None when
-    the kernel sources changed since that capture."""
-    import hashlib
-    path = os.path.join(ROOT, "profiles", "k_atoms_traffic.json")
-    if not os.path.exists(path):
-        return None
-    rec = json.load(open(path))
-    csrc = os.path.join(ROOT, "paper_1603_05143_gb300", "csrc")
-    src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("ptm.cu", "ptm_kernels.cuh", "ptm_atom.cuh"))
-    if hashlib.sha256(src).hexdigest() != rec.get("source_sha256"):
-        return None
-    return rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]
+BATCH_WORKLOAD = "batch-256-frames"
+COUNTERS = "per_atom_counters.json"
 
 
 def parse():
@@ -336,7 +324,7 @@ def run_gpu(args, world, rank, local, pg):
     st = ptm.stats()
     assert st["internal"] == 0 and st["atoms"] == f.n, st
 
-    times, kernel_ms, nbr_ms, stats = [], [], [], []
+    times, kernel_ms, nbr_ms, match_ms, stats = [], [], [], [], []
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
@@ -353,6 +341,7 @@ def run_gpu(args, world, rank, local, pg):
             s = ptm.stats()
             kernel_ms.append(s["classify_kernel_ms"])
             nbr_ms.append(s["atom_kernel_ms"] - s["classify_kernel_ms"])
+            match_ms.append(s["match_kernel_ms"])
             stats.append(s)
         torch.cuda.synchronize()
     if pg:
@@ -421,22 +410,23 @@ def run_gpu(args, world, rank, local, pg):
 
     s0 = stats[-1]
     kms = statistics.mean(kernel_ms)
+    mms = statistics.mean(match_ms)
     flops = (FLOP_PER_CAND_POINT * s0["candidate_points"] + FLOP_PER_CAND * s0["candidates"]
              + FLOP_PER_MATCHED * s0["matched"] + FLOP_PER_ATOM * s0["atoms"])
-    achieved = flops / (kms * 1e-3) / 1e12
     clocks = clk.summary()
-    peak = fp32_peak_tflops(local)
     peaks_file = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm_peak = json.load(open(peaks_file)).get("hbm_gbs") if os.path.exists(peaks_file) else None
     from paper_1603_05143_gb300 import measure_fma_peak
     fma = {"fp32_tflops": measure_fma_peak("fp32", local) / 1e12, "fp64_tflops": measure_fma_peak("fp64", local) / 1e12}
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": measured_traffic() if (args.workload == WORKLOAD and args.ordering == "euclidean") else None,
-            "kernel": "k_hulls + k_match", "kernel_ms": kms,
-            "neighbour_kernels_ms": statistics.mean(nbr_ms),
-            "neighbour_kernels": "k_knn" if args.ordering == "euclidean" else "k_topo + k_topo64", "peak_note": f"FP32 peak derived: {sm_count(local)} SMs x 128 lanes x 2 flop x 2070 MHz",
-            "fma_measured": fma, "frac_of_measured_fma": achieved / fma["fp32_tflops"],
-            "hbm_achieved_gbs": f.n * BYTES_PER_ATOM / (kms * 1e-3) / 1e9, "hbm_peak_gbs": hbm_peak}
+    topo = args.ordering == "topological"
+    phases = {("k_topo + k_topo64" if topo else "k_knn"): statistics.mean(nbr_ms), "k_hulls": kms - mms,
+              "k_match": mms}
+    counters = committed_counters(args.workload) if not topo else None
+    pipe_ms = sum(phases.values())
+    roof = roofline(local, clocks, f.n, phases, counters, flops,
+                    {"classify_ms": kms, "classify_kernels": "k_hulls + k_match",
+                     "more": {"fma_measured": fma, "hbm_achieved_gbs": f.n * BYTES_PER_ATOM / (pipe_ms * 1e-3) / 1e9,
+                              "hbm_peak_gbs": hbm_peak}})
     cpu, errors = None, None
     if not args.no_cpu_baseline and world == 1:
         r, m, dt, th, atoms, ref = oracle_rate(f, species, args.cpu_seconds, outputs=True, ordering=args.ordering)
@@ -473,19 +463,66 @@ def fp32_peak_tflops(local):
     return sm_count(local) * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 
-def committed_counters(name):
-    """Per-atom counters of a kernel from a committed ncu capture
-    (profiles/<name>), or None when the kernel sources changed since."""
+def committed_counters(workload):
+    """Per-atom ncu counters of the per-atom kernels on `workload`, from the
+    committed capture (profiles/per_atom_counters.json), or None when the
+    kernel sources changed since that capture."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", name)
+    path = os.path.join(ROOT, "profiles", COUNTERS)
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
     csrc = os.path.join(ROOT, "paper_1603_05143_gb300", "csrc")
-    src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("ptm.cu", "ptm_kernels.cuh", "ptm_atom.cuh"))
+    src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in rec["sources"])
     if hashlib.sha256(src).hexdigest() != rec.get("source_sha256"):
         return None
-    return rec
+    return rec["workloads"].get(workload)
+
+
+def roofline(local, clocks, atoms, phase_ms, counters, flops, extra):
+    """Roofline of the dominant per-atom kernel.  The path is integer- and
+    control-bound (exact hull predicates, graph walks, table lookups), so the
+    bound is instruction issue: warp instructions (the committed ncu count per
+    atom x the atoms of this launch) / the kernel's CUDA-event time, against
+    SMSPs x 1 warp instruction per clock x the sampled SM clock.  Every kernel
+    of the step gets the same figures; the algorithmic FP32 flops of the
+    classification kernels are reported beside them.  Without a current
+    capture the FP32 form stands alone."""
+    nsmsp = 4 * sm_count(local)
+    mhz = clocks.get("sm_mhz") or SM_MAX_MHZ
+    slots = nsmsp * mhz * 1e6                       # warp-instruction issue slots per second
+    total = sum(phase_ms.values())
+    kernels = {}
+    for name, ms in phase_ms.items():
+        e = {"ms": ms, "share_of_kernels": ms / total}
+        c = (counters or {}).get("kernels", {}).get(name)
+        if c:
+            lanes = c["thread_inst_per_atom"] / c["warp_inst_per_atom"]
+            frac = c["warp_inst_per_atom"] * atoms / (slots * ms * 1e-3)
+            e.update(warp_inst_per_atom=c["warp_inst_per_atom"], lanes_per_inst=lanes, issue_frac=frac,
+                     lane_issue_frac=frac * lanes / 32, dram_bytes_per_atom=c["dram_bytes_per_atom"])
+        kernels[name] = e
+    peak32 = fp32_peak_tflops(local)
+    ach32 = flops / (extra["classify_ms"] * 1e-3) / 1e12
+    fp32 = {"achieved": ach32, "peak": peak32, "unit": "TFLOP/s", "frac": ach32 / peak32,
+            "kernels": extra["classify_kernels"], "kernel_ms": extra["classify_ms"],
+            "peak_note": f"FP32 peak derived: {sm_count(local)} SMs x 128 lanes x 2 flop x 2070 MHz",
+            "work": "algorithmic FP32 flops: covariance, Horn matrix, characteristic polynomial and Newton "
+                    "steps per scored candidate; eigenvector, residual, orientation and strain per match"}
+    dom = max(phase_ms, key=phase_ms.get)
+    d = kernels[dom]
+    if "issue_frac" not in d:
+        return {"bound": "alu", "achieved": ach32, "peak": peak32, "unit": "TFLOP/s", "frac": ach32 / peak32,
+                "traffic": None, "kernel": extra["classify_kernels"], "kernels": kernels, "fp32": fp32,
+                "note": "no current ncu capture of these kernels on this workload: FP32 form only", **extra["more"]}
+    ach = d["warp_inst_per_atom"] * atoms / (d["ms"] * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": slots / 1e12, "unit": "Twarp-inst/s",
+            "frac": ach * 1e12 / slots, "traffic": d["dram_bytes_per_atom"] * atoms, "kernel": dom,
+            "kernel_ms": d["ms"], "lane_issue_frac": d["lane_issue_frac"],
+            "work": f"warp instructions: ncu smsp__inst_executed.sum per atom on {counters['captured']} "
+                    f"(profiles/{COUNTERS}) x {atoms} atoms",
+            "peak_note": f"{nsmsp} SMSPs x 1 warp instruction per clock x {mhz:.0f} MHz (sampled SM clock)",
+            "kernels": kernels, "fp32": fp32, **extra["more"]}
 
 
 def batch_oracle(frames, seconds, threads=None, seed=7):
@@ -564,7 +601,7 @@ def run_batch(args, world, rank, local, pg):
         s.synchronize()
         st = b.stats()
         assert st["internal"] == 0 and st["atoms"] == ntot, st
-        times, kms, nbr_ms = [], [], []
+        times, kms, nbr_ms, match_ms = [], [], [], []
         if pg:
             pg.barrier()
         torch.cuda.synchronize()
@@ -580,6 +617,7 @@ def run_batch(args, world, rank, local, pg):
                 bs = b.stats()
                 kms.append(bs["classify_kernel_ms"])
                 nbr_ms.append(bs["atom_kernel_ms"] - bs["classify_kernel_ms"])
+                match_ms.append(bs["match_kernel_ms"])
         torch.cuda.synchronize()
     if pg:
         pg.barrier()
@@ -616,8 +654,7 @@ def run_batch(args, world, rank, local, pg):
                "outputs_equal_to_batch": same}
         # serving latency: Poisson arrivals of the batch's frames at 0.8 of that capacity
         rng = I.rng_for(2024)
-        mean_atoms = ntot / len(frames)
-        tms, idx = I.poisson_arrivals(rng, 256, 0.8 * cap / mean_atoms, len(frames))
+        tms, idx = offered_stream(rng, 256, 0.8 * cap, [f.n for f in frames])
         r = _drive(srv, frames, hpos, hsp, houts, tms, idx)
         serving = {"offered_load": 0.8, "offered_atoms_per_s": 0.8 * cap, **r}
         srv.close()
@@ -650,37 +687,25 @@ def run_batch(args, world, rank, local, pg):
         b.close()
         ptm.close()
         return
-    # ---- roofline of the per-atom kernel
+    # ---- roofline of the dominant per-atom kernel
     kms_mean = statistics.mean(kms)
+    mms = statistics.mean(match_ms)
     clocks = clk.summary()
     flops = (FLOP_PER_CAND_POINT * st["candidate_points"] + FLOP_PER_CAND * st["candidates"]
              + FLOP_PER_MATCHED * st["matched"] + FLOP_PER_ATOM * st["atoms"])
-    achieved = flops / (kms_mean * 1e-3) / 1e12
-    peak = fp32_peak_tflops(local)
     peaks_file = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm_peak = json.load(open(peaks_file)).get("hbm_gbs") if os.path.exists(peaks_file) else None
     from paper_1603_05143_gb300 import measure_fma_peak
     fma = {"fp32_tflops": measure_fma_peak("fp32", local) / 1e12, "fp64_tflops": measure_fma_peak("fp64", local) / 1e12}
-    cnt = committed_counters("k_atoms_batch_counters.json")
-    issue = None
-    if cnt:
-        nsmsp = 4 * sm_count(local)
-        inst = cnt["warp_inst_per_atom"] * ntot
-        mhz = clocks.get("sm_mhz") or SM_MAX_MHZ
-        issue = {"warp_inst_per_launch": inst, "warp_inst_per_atom": cnt["warp_inst_per_atom"],
-                 "lanes_per_inst": cnt.get("thread_inst_per_inst"),
-                 "frac": inst / (nsmsp * mhz * 1e6 * kms_mean * 1e-3),
-                 "frac_at_max_clock": inst / (nsmsp * SM_MAX_MHZ * 1e6 * kms_mean * 1e-3),
-                 "clock_mhz": mhz, "source": cnt["source"]}
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": cnt["dram_bytes_per_atom"] * ntot if cnt else None,
-            "kernel": "k_hulls_batch + k_match (own launches for frames of 65536 atoms or more) + k_match_batch",
-            "kernel_ms": kms_mean,
-            "neighbour_kernel": "k_knn_batch", "neighbour_kernel_ms": statistics.mean(nbr_ms),
-            "peak_note": f"FP32 peak derived: {sm_count(local)} SMs x 128 lanes x 2 flop x 2070 MHz",
-            "fma_measured": fma, "frac_of_measured_fma": achieved / fma["fp32_tflops"],
-            "issue": issue,
-            "hbm_achieved_gbs": ntot * BYTES_PER_ATOM / (kms_mean * 1e-3) / 1e9, "hbm_peak_gbs": hbm_peak}
+    phases = {"k_knn_batch": statistics.mean(nbr_ms), "k_hulls_batch": kms_mean - mms,
+              "k_match + k_match_batch": mms}
+    pipe_ms = sum(phases.values())
+    roof = roofline(local, clocks, ntot, phases, committed_counters(BATCH_WORKLOAD), flops,
+                    {"classify_ms": kms_mean,
+                     "classify_kernels": "k_hulls_batch + k_match (own launches for frames of 65536 atoms or more) "
+                                         "+ k_match_batch",
+                     "more": {"fma_measured": fma, "hbm_achieved_gbs": ntot * BYTES_PER_ATOM / (pipe_ms * 1e-3) / 1e9,
+                              "hbm_peak_gbs": hbm_peak}})
     cpu, errors = None, None
     if not args.no_cpu_baseline and world == 1:
         r, m, dt, th, samples = batch_oracle(frames, args.cpu_seconds)
@@ -711,6 +736,19 @@ def run_batch(args, world, rank, local, pg):
     print(json.dumps(line), flush=True)
     b.close()
     ptm.close()
+
+
+def offered_stream(rng, n, atoms_per_s, sizes):
+    """n Poisson arrivals with frames drawn uniformly from a pool of `sizes`,
+    the times scaled so that the sampled stream itself offers atoms_per_s
+    (its atoms over its arrival span): a short sample of a heavy-tailed pool
+    would otherwise offer well off the nominal load."""
+    from paper_1603_05143_gb300 import inputs as I
+    sizes = np.asarray(sizes, dtype=np.float64)
+    t, idx = I.poisson_arrivals(rng, n, atoms_per_s / sizes.mean(), len(sizes))
+    if t[-1] > 0:
+        t = t * (sizes[idx].sum() / atoms_per_s) / t[-1]
+    return t, idx
 
 
 def _drive(srv, pool, hpos, hsp, outs, times, idx, timeout_s=600.0):
@@ -747,7 +785,9 @@ def _drive(srv, pool, hpos, hsp, outs, times, idx, timeout_s=600.0):
     atoms = sum(pool[k].n for k in idx)
     span = max(r["done"] for r in rec) - min(r["submit"] for r in rec)
     lat = np.array([r["done"] - r["submit"] for r in rec]) * 1e3
+    arrivals = float(np.max(times) - np.min(times))     # the sampled stream's own arrival rate
     return {"frames": len(times), "atoms": int(atoms), "achieved_atoms_per_s": atoms / span,
+            "arrival_atoms_per_s": atoms / arrivals if arrivals > 0 else None,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "batches": len({r["batch"] for r in rec})}
 
@@ -789,8 +829,7 @@ def run_serve(args, world, rank, local, pg):
         capacity = cap["achieved_atoms_per_s"]
         loads = []
         for load in (0.5, 0.8, 0.95):
-            rate_hz = load * capacity / mean_atoms
-            times, idx = I.poisson_arrivals(rng, n_req, rate_hz, len(pool))
+            times, idx = offered_stream(rng, n_req, load * capacity, [f.n for f in pool])
             r = _drive(srv, pool, hpos, hsp, outs, times, idx)
             r.update(offered_load=load, offered_atoms_per_s=load * capacity)
             loads.append(r)
