@@ -100,6 +100,17 @@ def dist_setup(args):
     return world, rank, local, pg
 
 
+def max_over_ranks(x, pg, dev=None):
+    """The largest of every rank's x (the job's time is its slowest
+    replica's); x itself on a single process."""
+    if not pg:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
 WORKLOADS = ("polycrystal-1048576", "mixed-phase-4194304", "fcc-4000")
 
 
@@ -257,7 +268,7 @@ def run_reference(args, world, rank, pg):
     if rank != 0:
         return
     threads = os.cpu_count() or 1
-    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    per_step = min(args.cpu_seconds, max(2.0, 60.0 / max(1, args.steps + args.warmup)))
     if args.mode == "frame":
         f, species, cfg = workload(args.workload)
         cfg = config_dict(cfg, {"ordering": args.ordering})
@@ -347,10 +358,7 @@ def run_gpu(args, world, rank, local, pg):
     if pg:
         pg.barrier()
     total = sum(times)
-    if pg:
-        t = torch.tensor([total], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total = float(t.item())
+    total = max_over_ranks(total, pg, dev)
     ms = total / args.steps
     value = world * f.n / (ms * 1e-3)
 
@@ -373,10 +381,7 @@ def run_gpu(args, world, rank, local, pg):
             ptm.classify_host(hpos, f.cell, f.pbc, species=hsp, out=hout, ordering=args.ordering)
             et.append(time.perf_counter() - t0)
         tot = sum(et)
-        if pg:
-            t = torch.tensor([tot], device=dev)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            tot = float(t.item())
+        tot = max_over_ranks(tot, pg, dev)
         e2e = {"value": world * f.n * args.steps / tot, "unit": UNIT,
                "h2d_bytes_per_step": int(hpos.nbytes + hsp.nbytes),
                "d2h_bytes_per_step": int(sum(a.nbytes for a in hout.values()))}
@@ -622,10 +627,7 @@ def run_batch(args, world, rank, local, pg):
     if pg:
         pg.barrier()
     total = sum(times)
-    if pg:
-        t = torch.tensor([total], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total = float(t.item())
+    total = max_over_ranks(total, pg, dev)
     ms = total / args.steps
     value = world * ntot / (ms * 1e-3)
     gout = [{k: v.cpu().numpy() for k, v in o.items()} for o in b.outputs]

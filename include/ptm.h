@@ -303,7 +303,7 @@ ptm_status ptm_server_inject(ptm_server *server, int fault);
    needed: the call runs on the current device, on `stream`, with the same
    kernels and results as ptm_classify_frame; positions, species and outputs are
    DEVICE pointers owned by the caller.  Its workspace is one static device
-   array of about 2.6 MiB that every GPU loading this library holds until the
+   array of about 7.0 MiB that every GPU loading this library holds until the
    process exits.  Its device address belongs to the CUDA context current at
    the call: every call outside stream capture looks it up again (so a device
    reset or a caller-made driver context is followed), and a call on a
