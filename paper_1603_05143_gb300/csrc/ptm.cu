@@ -525,6 +525,9 @@ struct ptm_batch {
   int *d_small_frames = nullptr;
   int64_t *d_small_off = nullptr;
   int launches = 0;               // kernels the last enqueue launched
+  cudaStream_t side[PTM_MATCH_SIDE_STREAMS] = {};   // the own k_match launches fork onto these
+  cudaEvent_t fork = nullptr, join[PTM_MATCH_SIDE_STREAMS] = {};
+  int nside = 0;
   int *topo_list = nullptr;       // atoms for the FP64 pass; [ntotal] = their count
   TopoSide *topo_side = nullptr;  // what the FP32 pass keeps for the FP64 pass
   void *block = nullptr;          // the workspace (one allocation, or a pool block when served)
@@ -533,11 +536,30 @@ struct ptm_batch {
 
 static void batch_free(ptm_batch *b) {
   if (!b) return;
+  for (int i = 0; i < b->nside; i++) {
+    if (b->join[i]) cudaEventDestroy(b->join[i]);
+    if (b->side[i]) cudaStreamDestroy(b->side[i]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->owns_block) cudaFree(b->block);
   for (int i = 0; i < 5; i++) if (b->ev[i]) cudaEventDestroy(b->ev[i]);
   delete b;
+}
+
+// Side streams and fork / join events for a batch with two or more own
+// k_match launches (created outside any stream capture).
+static cudaError_t batch_side_init(ptm_batch *b) {
+  const int want = (int)std::min<size_t>(PTM_MATCH_SIDE_STREAMS, b->own.size() > 1 ? b->own.size() - 1 : 0);
+  cudaError_t e = cudaSuccess;
+  if (want && !b->fork) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int i = 0; i < want && e == cudaSuccess; i++) {
+    e = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) b->nside = i + 1;
+  }
+  return e;
 }
 
 // Enqueue one pass over the whole batch: binning of every frame, one scan over
@@ -602,10 +624,20 @@ static ptm_status batch_enqueue(ptm_batch *b, cudaStream_t st) {
     k_hulls_batch<false><<<grid, PTM_BLOCK, atom_smem_bytes(), st>>>(b->d_descs, b->d_atom_off, b->nframes,
                                                                      b->ntotal, b->tile_atoms, b->queue);
   CK(cudaEventRecordWithFlags(b->ev[4], st, rec));
-  for (const FrameDesc &hd : b->own) {
+  // the frames' own k_match launches alternate between the batch stream and
+  // the side streams, so that one launch's last wave overlaps the next launch
+  const int ns = b->nside;
+  if (ns) {
+    CK(cudaEventRecord(b->fork, st));
+    for (int i = 0; i < ns; i++) CK(cudaStreamWaitEvent(b->side[i], b->fork, 0));
+  }
+  for (size_t k = 0; k < b->own.size(); k++) {
+    const FrameDesc &hd = b->own[k];
+    const int w = (int)(k % (size_t)(ns + 1));
+    cudaStream_t sk = w == 0 ? st : b->side[w - 1];
     const unsigned g = (unsigned)((hd.n + PTM_BLOCK - 1) / PTM_BLOCK);
-    if (b->f64) k_match<true><<<g, PTM_BLOCK, match_smem_bytes(), st>>>(hd);
-    else k_match<false><<<g, PTM_BLOCK, match_smem_bytes(), st>>>(hd);
+    if (b->f64) k_match<true><<<g, PTM_BLOCK, match_smem_bytes(), sk>>>(hd);
+    else k_match<false><<<g, PTM_BLOCK, match_smem_bytes(), sk>>>(hd);
   }
   if (b->nsmall) {
     const int64_t stiles = (b->small_atoms + b->tile_atoms - 1) / b->tile_atoms;
@@ -619,6 +651,12 @@ static ptm_status batch_enqueue(ptm_batch *b, cudaStream_t st) {
       k_match_batch<false><<<grid_m, PTM_BLOCK, match_smem_bytes(), st>>>(b->d_descs, b->d_small_off,
                                                                           b->d_small_frames, b->nsmall, b->small_atoms,
                                                                           b->tile_atoms, b->queue + 1);
+  }
+  if (ns) {
+    for (int i = 0; i < ns; i++) {
+      CK(cudaEventRecord(b->join[i], b->side[i]));
+      CK(cudaStreamWaitEvent(st, b->join[i], 0));
+    }
   }
   b->launches = 7 + (b->topo ? 2 : 0) + (int)b->own.size() + (b->nsmall ? 1 : 0) - (b->topo == 2 ? 1 : 0);
   CK(cudaGetLastError());
@@ -765,7 +803,8 @@ extern "C" ptm_status ptm_batch_create(ptm_context *ctx, int nframes, const ptm_
   for (int i = 0; i < 5 && e == cudaSuccess; i++) e = cudaEventCreate(&b->ev[i]);
   if (e != cudaSuccess) { rs = cuda_fail(ctx, e, "ptm_batch_create"); batch_free(b); return rs; }
   batch_layout(b, (unsigned char *)b->block, P, outs);
-  if ((e = cudaMemcpy(b->d_descs, P.hd.data(), sizeof(FrameDesc) * nframes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+  if ((e = batch_side_init(b)) != cudaSuccess ||
+      (e = cudaMemcpy(b->d_descs, P.hd.data(), sizeof(FrameDesc) * nframes, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(b->d_tabs, P.tabs.data(), sizeof(ShiftTables) * nframes, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (b->nsmall && (e = cudaMemcpy(b->d_small_frames, P.small_frames.data(), sizeof(int) * b->nsmall,
                                     cudaMemcpyHostToDevice)) != cudaSuccess) ||

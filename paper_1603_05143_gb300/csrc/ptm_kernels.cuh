@@ -1418,9 +1418,12 @@ constexpr size_t match_smem_bytes() { return (size_t)PTM_BLOCK * MATCH_WORDS * 4
 // to 93 registers
 #define PTM_MATCH_BLOCKS_PER_SM 11
 // Frames of a batch with at least this many atoms get a k_match launch of their
-// own: a descriptor in the kernel parameters costs no loads, one in memory adds
-// one before every address (k_match ran 35 % slower on a 2^20-atom frame)
+// own (on a 2^20-atom frame the persistent k_match_batch took 0.47 ms more than
+// such a launch's 1.47 ms); the own launches alternate between the batch's stream and
+// PTM_MATCH_SIDE_STREAMS side streams, so that each launch's last wave overlaps
+// the next launch (the batch of 256 frames: matching 60.6 -> 48.8 ms)
 #define PTM_MATCH_OWN_LAUNCH 65536
+#define PTM_MATCH_SIDE_STREAMS 2
 
 // Scratch rows in a block's dynamic shared memory (row layout of Scratch).
 __device__ __forceinline__ Scratch scratch_rows(unsigned char *smem) {

@@ -172,6 +172,7 @@ ptm_status launch_batch(ptm_server *S, std::vector<Request *> &rs, int slot, InF
   if (e != cudaSuccess) { batch_free(b); delete F; return cuda_fail(ctx, e, "serve: workspace"); }
   b->block = F->ws;
   batch_layout(b, (unsigned char *)F->ws, P, outs.data());
+  if ((e = batch_side_init(b)) != cudaSuccess) { batch_free(b); delete F; return cuda_fail(ctx, e, "serve: streams"); }
   // descriptors through this slot's pinned staging (free: the slot's previous batch is done)
   const size_t need = (sizeof(FrameDesc) + sizeof(ShiftTables) + sizeof(BinParams) + 2 * sizeof(int64_t) +
                        sizeof(int)) * nf;
