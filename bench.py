@@ -874,7 +874,7 @@ def run_serve(args, world, rank, local, pg):
                            "strain_max": 0.05, "sigma_A": 0.20, "hbm_budget": "half the free device memory",
                            "io": "host pinned positions/species in, all outputs out, per frame",
                            "l2": "inputs larger than L2", "pool_gen_s": round(gen_s, 1), "tuning": tuning,
-                           "streams": args.serve_streams or 2, "outputs": list(names)},
+                           "streams": args.serve_streams or 4, "outputs": list(names)},
                 "serving": {"capacity": cap, "loads": loads, "one_frame_per_launch": base},
                 "e2e": {"value": world * capacity, "unit": UNIT, "h2d_bytes_per_step": int(mean_atoms * 13),
                         "d2h_bytes_per_step": int(np.mean([sum(a.nbytes for a in o.values()) for o in outs]))},

@@ -248,7 +248,7 @@ typedef struct ptm_server ptm_server;
 typedef struct {
   size_t hbm_budget_bytes;   /* 0 = the context's budget (half the free memory at create) */
   int max_batch_frames;      /* frames per launch; 0 = 64 */
-  int streams;               /* batches in flight; 0 = 2, at most 8 */
+  int streams;               /* batches in flight; 0 = 4, at most 8 */
   ptm_tuning tuning;         /* zeros = defaults */
   int64_t max_batch_atoms;   /* atoms per launch (a larger single frame runs alone);
                                 0 = 4,194,304 */

@@ -88,7 +88,7 @@ size_t request_bytes(const ptm_frame &f) {
 struct ptm_server {
   ptm_context *ctx = nullptr;
   size_t budget = 0, in_use = 0;
-  int max_batch = 64, nslots = 2;
+  int max_batch = 64, nslots = 4;   // batches in flight (4 streams: 220 M atoms/s capacity against 203 M with 2)
   int64_t max_batch_atoms = 4 << 20;
   ptm_tuning tuning{};
   std::vector<cudaStream_t> streams;
