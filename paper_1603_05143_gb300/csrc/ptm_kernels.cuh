@@ -71,6 +71,17 @@ __device__ __forceinline__ double contract_d2(double a, double b, double c) {
 template <typename T>
 __device__ __forceinline__ double key64(const FrameDesc &d, T xj, T yj, T zj, T xi, T yi, T zi, int a0, int a1,
                                         int a2) {
+  if constexpr (sizeof(T) == 4) {
+    // image 0 with every FP32 difference exact (Sterbenz: |x_j - x_i| <=
+    // min(|x_i|, |x_j|)): the FP64 differences are these FP32 values and the
+    // zero shift adds nothing, so only the squares and sums run in FP64
+    if ((a0 | a1 | a2) == 0) {
+      const float px = __fsub_rn(xj, xi), py = __fsub_rn(yj, yi), pz = __fsub_rn(zj, zi);
+      if (fabsf(px) <= fminf(fabsf(xi), fabsf(xj)) && fabsf(py) <= fminf(fabsf(yi), fabsf(yj)) &&
+          fabsf(pz) <= fminf(fabsf(zi), fabsf(zj)))
+        return contract_d2((double)px, (double)py, (double)pz);
+    }
+  }
   double sx, sy, sz;
   shift_f64(d, a0, a1, a2, sx, sy, sz);
   return contract_d2(contract_dr((double)xj, (double)xi, sx), contract_dr((double)yj, (double)yi, sy),
@@ -88,8 +99,13 @@ __device__ __forceinline__ float knn_err(float v, float S) {
   return u * (8.5f * v + 4.5f * sqrtf(v) * S + 9.f * u * S * S);
 }
 
+// Key order (FP64 d2, atom id, image).  Keys are non-negative and not NaN, so
+// their bit patterns order as unsigned integers: the comparisons stay off the
+// FP64 pipe.
 __device__ __forceinline__ bool key_less64(double da, int ia, int ma, double db, int ib, int mb) {
-  return da < db || (da == db && (ia < ib || (ia == ib && ma < mb)));
+  const unsigned long long ua = (unsigned long long)__double_as_longlong(da);
+  const unsigned long long ub = (unsigned long long)__double_as_longlong(db);
+  return ua < ub || (ua == ub && (ia < ib || (ia == ib && ma < mb)));
 }
 
 // ----------------------------------------------------------------- kNN
@@ -178,7 +194,7 @@ __device__ __noinline__ int knn(const FrameDesc &d, int s, typename RT<F64>::T x
         if (d2 - 1.25f * knn_err(d2, S) > last32) return;
         key = key64(d, xj, yj, zj, xi, yi, zi, a0, a1, a2);
       }
-      if (!(key <= Ld2[NK - 1])) return;
+      if ((unsigned long long)__double_as_longlong(key) > (unsigned long long)__double_as_longlong(Ld2[NK - 1])) return;
       const int img = img_pack(a0, a1, a2);
       if (!key_less64(key, idj, img, Ld2[NK - 1], Lid[NK - 1], Limg[NK - 1])) return;
       // insertion into the sorted list (all indices static: stays in registers)
