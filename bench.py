@@ -654,9 +654,9 @@ def run_batch(args, world, rank, local, pg):
                "api": "ptm_submit/ptm_wait (continuous-batching server), all frames queued at once, pinned "
                       "host positions/species in, every output out", "steps": len(runs),
                "outputs_equal_to_batch": same}
-        # serving latency: Poisson arrivals of the batch's frames at 0.8 of that capacity
+        # serving latency: 1024 Poisson arrivals, frames drawn from the batch, at 0.8 of that capacity
         rng = I.rng_for(2024)
-        tms, idx = offered_stream(rng, 256, 0.8 * cap, [f.n for f in frames])
+        tms, idx = offered_stream(rng, 1024, 0.8 * cap, [f.n for f in frames])
         r = _drive(srv, frames, hpos, hsp, houts, tms, idx)
         serving = {"offered_load": 0.8, "offered_atoms_per_s": 0.8 * cap, **r}
         srv.close()

@@ -224,7 +224,7 @@ ptm_status ptm_batch_stats(ptm_batch *batch, ptm_stats *out);
 ptm_status ptm_batch_destroy(ptm_batch *batch);
 
 /* Time every candidate tuning on this batch (cell_factor in {1.125, 1.25,
-   1.4}, tile_atoms in {32, 64}, blocks_per_sm in {6, 7}) and return the
+   1.4}, tile_atoms in {32, 64}, blocks_per_sm in {7, 8}) and return the
    fastest in *best.  Runs the batch (every m-th frame of it when it holds more
    than about 40 M atoms) 36 times; outputs are written with the same results
    each time. */

@@ -86,16 +86,16 @@ __device__ __forceinline__ void count(const FrameDesc &d, int which, unsigned lo
 }
 
 // ------------------------------------------------------------ shared scratch
-// Rows are [word][thread] (every lane its own bank).  The 42 rows of q hold the
-// quantised neighbour vectors while the hulls are built and the FP32 metric
-// vectors after them; nid holds the neighbours' sorted indices until then and
-// their atom ids after.  126 words per thread let 7 blocks of 64 threads share
-// an SM's 228 KB.
+// Rows are [word][thread] (every lane its own bank).  In k_hulls the 42 rows of
+// q hold the quantised neighbour vectors while the hulls are built, beside the
+// rotation system, code, facet and edge rows: 98 words per thread let 8 blocks
+// of 64 threads share an SM's 228 KB.  k_match uses only q (the FP32 metric
+// vectors), nid (the neighbours' sorted indices, then their atom ids) and img.
 struct Scratch {
   float *q;          // [42][B]  quantised neighbour vectors (integers |q| <= 2^19, exact in FP32),
                      //          then the metric vectors DX / DY / DZ
-  int *nid;          // [14][B]  neighbour sorted index, then atom id
-  int *img;          // [14][B]  neighbour image (img_pack)
+  int *nid;          // [14][B]  neighbour sorted index, then atom id (k_match)
+  int *img;          // [14][B]  neighbour image (img_pack) (k_match)
   uint16_t *fac;     // [24][B]  hull facets a | b << 4 | c << 8 (ccw from outside)
   uint64_t *th;      // [14][B]  third vertex of directed edge u->v, nibble v of row u (0xF none)
   uint16_t *used;    // [14][B]  directed-edge bit rows (hull horizon, Weinberg walk)
@@ -115,7 +115,7 @@ struct Scratch {
 };
 
 #define PTM_CODE_WORDS 9       // 71 nibbles: labels 3..73 of the longest code (labels 1, 2 are fixed)
-constexpr int SCRATCH_WORDS = 28 + 42 + 14 + 14 + PTM_CODE_WORDS + 12 + 7;   // 32-bit words per thread
+constexpr int SCRATCH_WORDS = 28 + 42 + PTM_CODE_WORDS + 12 + 7;   // 32-bit words per k_hulls thread
 
 // -------------------------------------------------------------- small helpers
 __device__ __forceinline__ int nib(uint64_t x, int i) { return (int)((x >> (4 * i)) & 15); }

@@ -985,28 +985,31 @@ __device__ __forceinline__ void vec64_row(const FrameDesc &d, float xi, float yi
 
 // Quantisation of the neighbours in `wide` (float32 input, rare): the frexp
 // exponent of their largest FP64 vector component (-100000 if all are zero),
-// then q = rint(dr 2^shift) into the Q rows.  Rows are per-thread columns of
-// shared memory with stride PTM_BLOCK.
-__device__ __noinline__ int wide_exponent(const FrameDesc &d, float xi, float yi, float zi, const int *nid,
-                                          const int *img, uint32_t wide) {
+// then q = rint(dr 2^shift) into the Q rows.  Neighbour t of the atom is the
+// list entry nb[t * nst]; the Q rows are per-thread columns of shared memory
+// with stride PTM_BLOCK.
+__device__ __noinline__ int wide_exponent(const FrameDesc &d, float xi, float yi, float zi, const int2 *nb,
+                                          int64_t nst, uint32_t wide) {
   int e64 = -100000;
   for (; wide; wide &= wide - 1) {
     const int t = __ffs(wide) - 1;
+    const int2 e = __ldg(nb + t * nst);
     double v[3];
-    vec64_row(d, xi, yi, zi, nid[t * PTM_BLOCK], img[t * PTM_BLOCK], v);
+    vec64_row(d, xi, yi, zi, e.x, e.y, v);
     const double m = fmax(fabs(v[0]), fmax(fabs(v[1]), fabs(v[2])));
     if (m > 0.0) { int et; frexp(m, &et); e64 = max(e64, et); }
   }
   return e64;
 }
 
-__device__ __noinline__ void wide_quantise(const FrameDesc &d, float xi, float yi, float zi, const int *nid,
-                                           const int *img, float *q, uint32_t wide, int shift) {
+__device__ __noinline__ void wide_quantise(const FrameDesc &d, float xi, float yi, float zi, const int2 *nb,
+                                           int64_t nst, float *q, uint32_t wide, int shift) {
   const double sc = ldexp(1.0, shift);
   for (; wide; wide &= wide - 1) {
     const int t = __ffs(wide) - 1;
+    const int2 e = __ldg(nb + t * nst);
     double v[3];
-    vec64_row(d, xi, yi, zi, nid[t * PTM_BLOCK], img[t * PTM_BLOCK], v);
+    vec64_row(d, xi, yi, zi, e.x, e.y, v);
     for (int c = 0; c < 3; c++) q[(3 * t + c) * PTM_BLOCK] = (float)__double2int_rn(v[c] * sc);
   }
 }
@@ -1034,32 +1037,27 @@ __device__ void hull_atom(const FrameDesc &d, int s, const Scratch &sm, unsigned
   count(d, C_ATOMS);
   const int64_t sl = s - d.atom_offset;          // frame-local slot
 
-  // ---- neighbours (Sec. 3): the list written by k_knn or k_topo
+  // ---- neighbours (Sec. 3): the list written by k_knn or k_topo, read in
+  // place (entry t at nb[t * n]; the valid entries form a prefix).
+  // Quantised copy for the exact hull predicates: q = rint(dr 2^(19 - e))
+  // (half to even) on the FP64 contract vectors dr, 2^(e-1) <= max |dr_c| < 2^e
+  const int2 *nb = d.nbr + sl;
+  const int64_t nst = d.n;
   int cnt = 0;
   unsigned hmask;
   {
-#pragma unroll
-    for (int t = 0; t < PTM_KNN; t++) {
-      const int2 e = __ldg(d.nbr + (int64_t)t * d.n + (s - d.atom_offset));
-      sm.NID(t) = e.x;
-      sm.IMG(t) = e.y;
-      cnt += e.x >= 0;
-    }
-    hmask = __ballot_sync(live, cnt >= 4);       // lanes that go on to the hulls
-    if (cnt < 4) { d.ents[sl] = 0; return; }
-    // rows NID / IMG keep (sorted index, image) of each neighbour through the
-    // hulls.  Quantised copy for the exact hull predicates: q = rint(dr 2^(19 - e))
-    // (half to even) on the FP64 contract vectors dr, 2^(e-1) <= max |dr_c| < 2^e
     if constexpr (F64) {
       T emax = 0;
 #pragma unroll 1
       for (int t = 0; t < PTM_KNN; t++) {
-        if (t >= cnt) continue;
+        const int2 e = __ldg(nb + t * nst);
+        if (e.x < 0) continue;
+        cnt++;
         T xj, yj, zj;
         int idj;
-        load_atom<F64>(d, sm.NID(t), xj, yj, zj, idj);
+        load_atom<F64>(d, e.x, xj, yj, zj, idj);
         int a0, a1, a2;
-        img_unpack(sm.IMG(t), a0, a1, a2);
+        img_unpack(e.y, a0, a1, a2);
         T sx, sy, sz;
         contract_shift<F64>(d, a0, a1, a2, sx, sy, sz);
         T cx = contract_dr(xj, xi, sx), cy = contract_dr(yj, yi, sy), cz = contract_dr(zj, zi, sz);
@@ -1071,11 +1069,12 @@ __device__ void hull_atom(const FrameDesc &d, int s, const Scratch &sm, unsigned
 #pragma unroll 1
       for (int t = 0; t < PTM_KNN; t++) {
         if (t >= cnt) continue;
+        const int2 en = __ldg(nb + t * nst);
         T xj, yj, zj;
         int idj;
-        load_atom<F64>(d, sm.NID(t), xj, yj, zj, idj);
+        load_atom<F64>(d, en.x, xj, yj, zj, idj);
         int a0, a1, a2;
-        img_unpack(sm.IMG(t), a0, a1, a2);
+        img_unpack(en.y, a0, a1, a2);
         T sx, sy, sz;
         contract_shift<F64>(d, a0, a1, a2, sx, sy, sz);
         T cx = contract_dr(xj, xi, sx), cy = contract_dr(yj, yi, sy), cz = contract_dr(zj, zi, sz);
@@ -1092,12 +1091,14 @@ __device__ void hull_atom(const FrameDesc &d, int s, const Scratch &sm, unsigned
       uint32_t wide = 0;
 #pragma unroll 7
       for (int t = 0; t < PTM_KNN; t++) {
-        if (t >= cnt) continue;
+        const int2 e = __ldg(nb + t * nst);
+        if (e.x < 0) continue;
+        cnt++;
         float xj, yj, zj;
         int idj;
-        load_atom<false>(d, sm.NID(t), xj, yj, zj, idj);
+        load_atom<false>(d, e.x, xj, yj, zj, idj);
         const float px = __fsub_rn(xj, xi), py = __fsub_rn(yj, yi), pz = __fsub_rn(zj, zi);
-        const bool exact = sm.IMG(t) == img_pack(0, 0, 0) && fabsf(px) < fminf(fabsf(xi), fabsf(xj)) &&
+        const bool exact = e.y == img_pack(0, 0, 0) && fabsf(px) < fminf(fabsf(xi), fabsf(xj)) &&
                            fabsf(py) < fminf(fabsf(yi), fabsf(yj)) && fabsf(pz) < fminf(fabsf(zi), fabsf(zj));
         sm.Q(t, 0) = px; sm.Q(t, 1) = py; sm.Q(t, 2) = pz;
         if (exact) emaxf = fmaxf(emaxf, fmaxf(fabsf(px), fmaxf(fabsf(py), fabsf(pz))));
@@ -1106,7 +1107,7 @@ __device__ void hull_atom(const FrameDesc &d, int s, const Scratch &sm, unsigned
       int e;
       frexpf(emaxf, &e);
       if (wide) {
-        const int e64 = wide_exponent(d, xi, yi, zi, sm.nid + sm.t, sm.img + sm.t, wide);
+        const int e64 = wide_exponent(d, xi, yi, zi, nb, nst, wide);
         if (e64 > -100000) e = emaxf > 0.f ? max(e, e64) : e64;
       }
       const float sc = ldexpf(1.f, PTM_QBITS - e);
@@ -1115,8 +1116,10 @@ __device__ void hull_atom(const FrameDesc &d, int s, const Scratch &sm, unsigned
         if (t >= cnt || (wide >> t & 1)) continue;
         sm.Q(t, 0) = rintf(sm.Q(t, 0) * sc); sm.Q(t, 1) = rintf(sm.Q(t, 1) * sc); sm.Q(t, 2) = rintf(sm.Q(t, 2) * sc);
       }
-      if (wide) wide_quantise(d, xi, yi, zi, sm.nid + sm.t, sm.img + sm.t, sm.q + sm.t, wide, PTM_QBITS - e);
+      if (wide) wide_quantise(d, xi, yi, zi, nb, nst, sm.q + sm.t, wide, PTM_QBITS - e);
     }
+    hmask = __ballot_sync(live, cnt >= 4);       // lanes that go on to the hulls
+    if (cnt < 4) { d.ents[sl] = 0; return; }
   }
 
   // ---- hulls of the first 6, 12, 14 neighbours, built incrementally (Sec. 4)
@@ -1426,10 +1429,10 @@ constexpr size_t atom_smem_bytes() { return (size_t)PTM_BLOCK * SCRATCH_WORDS * 
 constexpr int MATCH_WORDS = 42 + 14 + 14;
 constexpr size_t match_smem_bytes() { return (size_t)PTM_BLOCK * MATCH_WORDS * 4; }
 
-// Resident blocks per SM of k_hulls: 7 x (126 words x 64 threads + the 1 KB the
-// driver reserves per block) fits 228 KB of shared memory, and 7 x 64 threads x
-// 146 registers the register file.
-#define PTM_ATOM_BLOCKS_PER_SM 7
+// Resident blocks per SM of k_hulls: 8 x (98 words x 64 threads + the 1 KB the
+// driver reserves per block) fits 228 KB of shared memory, and 8 x 64 threads x
+// 128 registers the register file.
+#define PTM_ATOM_BLOCKS_PER_SM 8
 // k_match: 11 x (70 words x 64 threads + two descriptor copies + 1 KB) fits, at up
 // to 93 registers
 #define PTM_MATCH_BLOCKS_PER_SM 11
@@ -1441,14 +1444,15 @@ constexpr size_t match_smem_bytes() { return (size_t)PTM_BLOCK * MATCH_WORDS * 4
 #define PTM_MATCH_OWN_LAUNCH 65536
 #define PTM_MATCH_SIDE_STREAMS 2
 
-// Scratch rows in a block's dynamic shared memory (row layout of Scratch).
+// Scratch rows of k_hulls in a block's dynamic shared memory (row layout of
+// Scratch without the nid / img rows).
 __device__ __forceinline__ Scratch scratch_rows(unsigned char *smem) {
   Scratch sm;
   sm.th = (uint64_t *)smem;
   sm.q = (float *)(sm.th + 14 * PTM_BLOCK);
-  sm.nid = (int *)(sm.q + 42 * PTM_BLOCK);
-  sm.img = sm.nid + 14 * PTM_BLOCK;
-  sm.code = (uint32_t *)(sm.img + 14 * PTM_BLOCK);
+  sm.nid = nullptr;                 // k_hulls reads the neighbour list in place
+  sm.img = nullptr;
+  sm.code = (uint32_t *)(sm.q + 42 * PTM_BLOCK);
   sm.fac = (uint16_t *)(sm.code + PTM_CODE_WORDS * PTM_BLOCK);
   sm.used = sm.fac + 24 * PTM_BLOCK;
   sm.t = threadIdx.x;
