@@ -242,15 +242,38 @@ __device__ __forceinline__ bool knn_fast_n(const FrameDesc &d, int s, typename R
                                            typename RT<F64>::T yi, typename RT<F64>::T zi, int bx, int by, int bz,
                                            const Rows &rows, uint32_t &close_runs) {
   typedef typename RT<F64>::T T;
+  // float32 input, 14 neighbours: the network also carries each value's
+  // candidate as (sorted slot << 5 | image index), so that an atom whose ranks
+  // are all decided needs no second scan (slots below 2^27)
+  constexpr bool CARRY = !F64 && NK == PTM_KNN;
   T L[NK + 1];
+  uint32_t C[CARRY ? NK + 1 : 1];
 #pragma unroll
   for (int t = 0; t <= NK; t++) L[t] = (T)INFINITY;
+  if constexpr (CARRY) {
+#pragma unroll
+    for (int t = 0; t <= NK; t++) C[t] = 0u;
+  }
   scan_cells<F64>(d, s, xi, yi, zi, bx, by, bz, 0, 0, 0, false, 1,
-                  [&](int j, T d2, int, int, int, int, T, T, T, T, T, T) {
+                  [&](int j, T d2, int, int a0, int a1, int a2, T, T, T, T, T, T) {
     if (!(d2 < L[NK])) return;
     T x = d2;
+    if constexpr (CARRY) {
+      uint32_t xc = ((uint32_t)j << 5) | (uint32_t)((a0 + 1) * 9 + (a1 + 1) * 3 + (a2 + 1));
 #pragma unroll
-    for (int t = 0; t <= NK; t++) { const T lo = fmin(L[t], x); x = fmax(L[t], x); L[t] = lo; }
+      for (int t = 0; t <= NK; t++) {
+        const bool sw = x < L[t];
+        const T lo = sw ? x : L[t];
+        const uint32_t lc = sw ? xc : C[t];
+        x = sw ? L[t] : x;
+        xc = sw ? C[t] : xc;
+        L[t] = lo;
+        C[t] = lc;
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t <= NK; t++) { const T lo = fmin(L[t], x); x = fmax(L[t], x); L[t] = lo; }
+    }
   });
   if (!(L[NK] < (T)INFINITY)) return false;
   uint32_t close = 0;                                // bit t: slots t and t + 1 in one run
@@ -273,6 +296,16 @@ __device__ __forceinline__ bool knn_fast_n(const FrameDesc &d, int s, typename R
   }
   if (!search_complete(d, 1, (float)limit)) return false;
   close_runs = close;
+  if constexpr (CARRY) {
+    if (!close && d.atom_offset + d.n <= (1ll << 27)) {    // every rank decided, the candidates at hand
+#pragma unroll
+      for (int t = 0; t < NK; t++) {
+        const int k = (int)(C[t] & 31u);
+        rows.put(t, (int)(C[t] >> 5), img_pack(k / 9 - 1, (k / 3) % 3 - 1, k % 3 - 1));
+      }
+      return true;
+    }
+  }
   if (!close) {                                      // every rank decided: distance order is key order
     scan_cells<F64>(d, s, xi, yi, zi, bx, by, bz, 0, 0, 0, false, 1,
                     [&](int j, T d2, int, int a0, int a1, int a2, T, T, T, T, T, T) {
@@ -936,19 +969,20 @@ __device__ __noinline__ void finalize_fp64(const FrameDesc &d, const Scratch &sm
 // row NID over their sorted indices: the contract values, or for a shifted
 // image an error-free FP32 sum of difference and shift.
 template <bool F64>
-__device__ __forceinline__ void metric_vectors(const FrameDesc &d, const Scratch &sm, int cnt,
+__device__ __forceinline__ void metric_vectors(const FrameDesc &d, const Scratch &sm, const int2 *nb, int64_t nst,
                                                typename RT<F64>::T xi, typename RT<F64>::T yi,
                                                typename RT<F64>::T zi) {
   typedef typename RT<F64>::T T;
 #pragma unroll 7
   for (int t = 0; t < PTM_KNN; t++) {
-    if (t >= cnt) { sm.NID(t) = -1; sm.DX(t) = sm.DY(t) = sm.DZ(t) = 0.f; continue; }
+    const int2 e = __ldg(nb + t * nst);
+    if (e.x < 0) { sm.NID(t) = -1; sm.DX(t) = sm.DY(t) = sm.DZ(t) = 0.f; continue; }
     T xj, yj, zj;
     int idj;
-    load_atom<F64>(d, sm.NID(t), xj, yj, zj, idj);
+    load_atom<F64>(d, e.x, xj, yj, zj, idj);
     sm.NID(t) = idj;
     int a0, a1, a2;
-    img_unpack(sm.IMG(t), a0, a1, a2);
+    img_unpack(e.y, a0, a1, a2);
     if constexpr (F64) {
       T sx, sy, sz;
       contract_shift<F64>(d, a0, a1, a2, sx, sy, sz);
@@ -1180,19 +1214,17 @@ __device__ void match_atom(const FrameDesc &d, int s, const Scratch &sm, const f
   bst.lam6 = bst.ent6 >= 0 ? __ldg((const unsigned long long *)d.lam + sl) : 0;
   bst.lam12 = bst.ent12 >= 0 ? __ldg((const unsigned long long *)d.lam + d.n + sl) : 0;
   bst.lam14 = bst.ent14 >= 0 ? __ldg((const unsigned long long *)d.lam + 2 * d.n + sl) : 0;
-  int cnt = 0;
-#pragma unroll
-  for (int t = 0; t < PTM_KNN; t++) {
-    const int2 e = __ldg(d.nbr + (int64_t)t * d.n + sl);
-    sm.NID(t) = e.x;
-    sm.IMG(t) = e.y;
-    cnt += e.x >= 0;
-  }
+  const int2 *nb = d.nbr + sl;                   // the neighbour list, entry t at nb[t * n]
+  const int64_t nst = d.n;
   double ex[P64 ? PTM_KNN : 1], ey[P64 ? PTM_KNN : 1], ez[P64 ? PTM_KNN : 1];
   if constexpr (P64) {
-    for (int t = 0; t < cnt; t++) vec_fp64<F64>(d, xi, yi, zi, sm.NID(t), sm.IMG(t), ex[t], ey[t], ez[t]);
+    for (int t = 0; t < PTM_KNN; t++) {
+      const int2 e = __ldg(nb + t * nst);
+      if (e.x < 0) break;                          // the valid entries form a prefix
+      vec_fp64<F64>(d, xi, yi, zi, e.x, e.y, ex[t], ey[t], ez[t]);
+    }
   }
-  metric_vectors<F64>(d, sm, cnt, xi, yi, zi);
+  metric_vectors<F64>(d, sm, nb, nst, xi, yi, zi);
   if constexpr (!P64) {
     score_candidates(d, sm, tplw, bst, qmask);
     if (bst.K < 0) { write_unmatched(d, idi); return; }     // every match masked out
@@ -1424,16 +1456,16 @@ __global__ void k_scatter_batch(const BinParams *__restrict__ bp, const int64_t 
 }
 
 constexpr size_t atom_smem_bytes() { return (size_t)PTM_BLOCK * SCRATCH_WORDS * 4; }
-// k_match keeps only the neighbour vectors (42 words) and the neighbours' slots
-// and images (28 words) per thread
-constexpr int MATCH_WORDS = 42 + 14 + 14;
+// k_match keeps only the neighbour vectors (42 words) and the neighbours' atom
+// ids (14 words) per thread; the images are read from the neighbour list
+constexpr int MATCH_WORDS = 42 + 14;
 constexpr size_t match_smem_bytes() { return (size_t)PTM_BLOCK * MATCH_WORDS * 4; }
 
 // Resident blocks per SM of k_hulls: 8 x (98 words x 64 threads + the 1 KB the
 // driver reserves per block) fits 228 KB of shared memory, and 8 x 64 threads x
 // 128 registers the register file.
 #define PTM_ATOM_BLOCKS_PER_SM 8
-// k_match: 11 x (70 words x 64 threads + two descriptor copies + 1 KB) fits, at up
+// k_match: 11 x (56 words x 64 threads + two descriptor copies + 1 KB) fits, at up
 // to 93 registers
 #define PTM_MATCH_BLOCKS_PER_SM 11
 // Frames of a batch with at least this many atoms get a k_match launch of their
@@ -1465,7 +1497,7 @@ __device__ __forceinline__ Scratch match_rows(unsigned char *smem) {
   sm.th = nullptr; sm.code = nullptr; sm.fac = nullptr; sm.used = nullptr;
   sm.q = (float *)smem;
   sm.nid = (int *)(sm.q + 42 * PTM_BLOCK);
-  sm.img = sm.nid + 14 * PTM_BLOCK;
+  sm.img = nullptr;                 // images are read from the neighbour list
   sm.t = threadIdx.x;
   return sm;
 }
