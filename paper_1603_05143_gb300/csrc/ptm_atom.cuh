@@ -347,7 +347,7 @@ __device__ uint32_t hull_visibility(const Scratch &sm, int nf, int p, bool centr
   uint32_t vis = 0, openp = 0, openc = 0;
   bool inside = true;
   const float px = sm.Q(p, 0), py = sm.Q(p, 1), pz = sm.Q(p, 2);
-#pragma unroll 1
+#pragma unroll 2
   for (int f = 0; f < nf; f++) {
     const int v = sm.F(f);
     const int a = v & 15, b = (v >> 4) & 15, c = (v >> 8) & 15;

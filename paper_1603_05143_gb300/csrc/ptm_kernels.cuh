@@ -120,10 +120,12 @@ __device__ __forceinline__ void scan_cells(const FrameDesc &d, int s, typename R
                                            int wix, int wiy, int wiz, bool wrapped, int R, V &&visit) {
   typedef typename RT<F64>::T T;
   const int nbx = d.nb[0], nby = d.nb[1], nbz = d.nb[2];
-  for (int dx = -R; dx <= R; dx++) {
+  for (int ix = 0; ix <= 2 * R; ix++) {
+    const int dx = ix <= R ? ix : R - ix;                // 0, 1 .. R, -1 .. -R: the centre first
     int cx = bx + dx, mx = 0;
     if (d.pbc[0]) { mx = floordiv(cx, nbx); cx -= mx * nbx; } else if (cx < 0 || cx >= nbx) continue;
-    for (int dy = -R; dy <= R; dy++) {
+    for (int iy = 0; iy <= 2 * R; iy++) {
+      const int dy = iy <= R ? iy : R - iy;
       int cy = by + dy, my = 0;
       if (d.pbc[1]) { my = floordiv(cy, nby); cy -= my * nby; } else if (cy < 0 || cy >= nby) continue;
       int z0 = bz - R, z1 = bz + R;
