@@ -377,6 +377,10 @@ struct SmemKnnRows {
 // 6 blocks of 128 threads per SM: the shared-memory rows (280 B per thread) and
 // at most 85 registers per thread fit
 #define PTM_KNN_BLOCKS_PER_SM 6
+// The batch form (frame lookup per slot, descriptors in global memory) spills
+// at 85 registers; at 5 blocks per SM it keeps 96 (batch of 256 frames: 30.4 ->
+// 28.5 ms, while the single-frame kernel is faster at 6: 0.824 against 0.864 ms)
+#define PTM_KNN_BATCH_BLOCKS_PER_SM 5
 typedef SmemKnnRows<PTM_KNN, PTM_KNN_BLOCK> KnnRows;
 constexpr size_t knn_smem_bytes() { return (size_t)PTM_KNN_BLOCK * KnnRows::kRows * 4; }
 
@@ -1543,7 +1547,7 @@ __global__ void __launch_bounds__(PTM_KNN_BLOCK, PTM_KNN_BLOCKS_PER_SM) k_knn(co
 // The same over a batch: each slot finds its frame; frames in the topological
 // order are left to k_topo_batch.
 template <bool F64>
-__global__ void __launch_bounds__(PTM_KNN_BLOCK, PTM_KNN_BLOCKS_PER_SM)
+__global__ void __launch_bounds__(PTM_KNN_BLOCK, PTM_KNN_BATCH_BLOCKS_PER_SM)
     k_knn_batch(const FrameDesc *__restrict__ descs, const int64_t *__restrict__ atom_off, int nframes,
                 int64_t ntotal) {
   extern __shared__ __align__(16) int knn_smem[];
